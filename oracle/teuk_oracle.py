@@ -1,0 +1,226 @@
+"""ctypes wrapper of the plain FP64 C oracle (``teuk_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: imported by the tests, the smoke check and the
+CPU-baseline leg of the benchmark, never by the product path.  It shares no
+code with the CUDA library.
+
+Arrays:
+  state  u      float64 [4][n_theta][n_rstar]  = {Phi_R, Phi_I, Pi_R, Pi_I}  (Eq. 9)
+  wave          float64 [records][n_theta][2]   Phi at r*_ext, (re, im)
+  profiles      complex128 [n_theta][n_rstar] (integer nodes), [n_theta][n_rstar-1] (half nodes)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "teuk_oracle.c")
+_LIB = os.path.join(_HERE, "libteuk_oracle.so")
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (-O2, no contraction, no fast-math)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math",
+                               "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class Params(ctypes.Structure):
+    """Problem statement (Eq. 1 parameters, grid, Courant rule, orbit, extraction)."""
+
+    _fields_ = [
+        ("s", ctypes.c_int), ("m", ctypes.c_int),
+        ("M", ctypes.c_double), ("a", ctypes.c_double),
+        ("rstar_min", ctypes.c_double), ("rstar_max", ctypes.c_double),
+        ("n_rstar", ctypes.c_int), ("n_theta", ctypes.c_int),
+        ("courant", ctypes.c_double), ("dt_rule", ctypes.c_int), ("dt", ctypes.c_double),
+        ("rstar_ext", ctypes.c_double), ("r0", ctypes.c_double),
+        ("sigma_r_cells", ctypes.c_double), ("sigma_th_cells", ctypes.c_double),
+        ("sigma_r_abs", ctypes.c_double), ("sigma_th_abs", ctypes.c_double),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        D, I, P = ctypes.c_double, ctypes.c_int, ctypes.c_void_p
+        L = ctypes.c_int64
+        pp = ctypes.POINTER(Params)
+        _lib.orc_rstar_of_x.restype = D
+        _lib.orc_rstar_of_x.argtypes = [D, D, D]
+        _lib.orc_x_of_rstar.restype = D
+        _lib.orc_x_of_rstar.argtypes = [D, D, D]
+        _lib.orc_coeffs.restype = None
+        _lib.orc_coeffs.argtypes = [pp, D, D, P]
+        _lib.orc_grid.restype = I
+        _lib.orc_grid.argtypes = [pp, P]
+        _lib.orc_orbit.restype = I
+        _lib.orc_orbit.argtypes = [pp, P]
+        _lib.orc_orbit_profile.restype = I
+        _lib.orc_orbit_profile.argtypes = [pp, P, P, P, P]
+        _lib.orc_run.restype = I
+        _lib.orc_run.argtypes = [pp, D, D, P, P, P, L, L, L, P, P]
+        _lib.orc_apply_K.restype = I
+        _lib.orc_apply_K.argtypes = [pp, P, P]
+        _lib.orc_apply_KT.restype = I
+        _lib.orc_apply_KT.argtypes = [pp, P, P]
+        _lib.orc_theta_apply.restype = I
+        _lib.orc_theta_apply.argtypes = [pp, P, P]
+        _lib.orc_adjoint.restype = I
+        _lib.orc_adjoint.argtypes = [pp, D, D, P, P, P, P, D, D, P, L, L, L, P, P, P, P]
+    return _lib
+
+
+DEFAULTS = dict(s=-2, m=2, M=1.0, a=0.9, rstar_min=-50.0, rstar_max=150.0, n_rstar=800,
+                n_theta=64, courant=0.5, dt_rule=1, dt=0.0, rstar_ext=140.0, r0=10.0,
+                sigma_r_cells=4.0, sigma_th_cells=4.0, sigma_r_abs=0.0, sigma_th_abs=0.0)
+
+
+def params(**kw) -> Params:
+    d = dict(DEFAULTS)
+    for k, v in kw.items():
+        if k not in d:
+            raise KeyError(k)
+        d[k] = v
+    return Params(**d)
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _check(st):
+    if st != 0:
+        raise ValueError("oracle returned status %d" % st)
+
+
+def rstar_of_r(M, a, r):
+    rp = M + np.sqrt(M * M - a * a)
+    return lib().orc_rstar_of_x(M, a, r - rp)
+
+
+def x_of_rstar(M, a, rstar):
+    return lib().orc_x_of_rstar(M, a, rstar)
+
+
+def coeffs(p: Params, x: float, theta: float) -> dict:
+    out = np.zeros(12)
+    lib().orc_coeffs(ctypes.byref(p), x, theta, _ptr(out))
+    names = ["b", "w", "bbr", "ct_re", "ct_im", "pst_re", "pst_im", "Pst_re", "Pst_im",
+             "q_re", "q_im", "V"]
+    return dict(zip(names, out))
+
+
+def grid(p: Params) -> dict:
+    out = np.zeros(7)
+    _check(lib().orc_grid(ctypes.byref(p), _ptr(out)))
+    return dict(drs=out[0], dth=out[1], dt=out[2], rp=out[3], rm=out[4], i_e=int(out[5]),
+                f_e=out[6])
+
+
+def orbit(p: Params) -> dict:
+    out = np.zeros(10)
+    _check(lib().orc_orbit(ctypes.byref(p), _ptr(out)))
+    keys = ["Omega", "phi0", "rstar0", "r_ext", "dOmega_dr0", "dphi0_dr0", "drstar0_dr0",
+            "sigma_r", "sigma_th", "x0"]
+    return dict(zip(keys, out))
+
+
+class Source:
+    """tau = A_n exp(-i (omega t + phase0)) P with P at integer / half nodes."""
+
+    def __init__(self, omega, phase0, P_int, P_half, dP_int=None, dP_half=None,
+                 domega=0.0, dphase0=0.0):
+        self.omega, self.phase0 = float(omega), float(phase0)
+        self.P_int = np.ascontiguousarray(P_int, dtype=np.complex128)
+        self.P_half = np.ascontiguousarray(P_half, dtype=np.complex128)
+        nth, nr = self.P_int.shape
+        self.dP_int = (np.zeros_like(self.P_int) if dP_int is None
+                       else np.ascontiguousarray(dP_int, dtype=np.complex128))
+        self.dP_half = (np.zeros_like(self.P_half) if dP_half is None
+                        else np.ascontiguousarray(dP_half, dtype=np.complex128))
+        self.domega, self.dphase0 = float(domega), float(dphase0)
+
+
+def orbit_source(p: Params) -> Source:
+    """The synthetic circular-orbit source of the problem statement."""
+    nth, nr = p.n_theta, p.n_rstar
+    P_int = np.zeros((nth, nr), np.complex128)
+    P_half = np.zeros((nth, nr - 1), np.complex128)
+    dP_int = np.zeros_like(P_int)
+    dP_half = np.zeros_like(P_half)
+    _check(lib().orc_orbit_profile(ctypes.byref(p), _ptr(P_int), _ptr(P_half), _ptr(dP_int),
+                                   _ptr(dP_half)))
+    ob = orbit(p)
+    m = p.m
+    return Source(m * ob["Omega"], m * ob["phi0"], P_int, P_half, dP_int, dP_half,
+                  m * ob["dOmega_dr0"], m * ob["dphi0_dr0"])
+
+
+def run(p: Params, u0=None, nsteps=1, source: Source | None = None, amps=None, step0=0,
+        wave=True):
+    """Evolve ``nsteps`` steps; returns (u, wave) with wave [nsteps+1][n_theta][2]."""
+    nth, nr = p.n_theta, p.n_rstar
+    u = np.zeros((4, nth, nr)) if u0 is None else np.array(u0, dtype=np.float64, copy=True)
+    assert u.shape == (4, nth, nr)
+    w = np.zeros((nsteps + 1, nth, 2)) if wave else None
+    a = None if amps is None else np.ascontiguousarray(amps, dtype=np.float64)
+    na = 0 if a is None else a.size
+    if source is None:
+        _check(lib().orc_run(ctypes.byref(p), 0.0, 0.0, None, None, _ptr(a), na, step0, nsteps,
+                             _ptr(u), _ptr(w)))
+    else:
+        _check(lib().orc_run(ctypes.byref(p), source.omega, source.phase0, _ptr(source.P_int),
+                             _ptr(source.P_half), _ptr(a), na, step0, nsteps, _ptr(u), _ptr(w)))
+    return u, w
+
+
+def apply_K(p: Params, x):
+    y = np.zeros_like(x)
+    _check(lib().orc_apply_K(ctypes.byref(p), _ptr(np.ascontiguousarray(x)), _ptr(y)))
+    return y
+
+
+def apply_KT(p: Params, y):
+    x = np.zeros_like(y)
+    _check(lib().orc_apply_KT(ctypes.byref(p), _ptr(np.ascontiguousarray(y)), _ptr(x)))
+    return x
+
+
+def adjoint(p: Params, source: Source, gwave, amps=None, step0=0):
+    """Reverse sweep: returns (grad_amps [nsteps], grad_r0, lambda0 [4][nth][nr])."""
+    gwave = np.ascontiguousarray(gwave, dtype=np.float64)
+    nsteps = gwave.shape[0]
+    ga = np.zeros(nsteps)
+    gr = ctypes.c_double(0.0)
+    lam0 = np.zeros((4, p.n_theta, p.n_rstar))
+    a = None if amps is None else np.ascontiguousarray(amps, dtype=np.float64)
+    na = 0 if a is None else a.size
+    _check(lib().orc_adjoint(ctypes.byref(p), source.omega, source.phase0, _ptr(source.P_int),
+                             _ptr(source.P_half), _ptr(source.dP_int), _ptr(source.dP_half),
+                             source.domega, source.dphase0, _ptr(a), na, step0, nsteps,
+                             _ptr(gwave), _ptr(ga), ctypes.byref(gr), _ptr(lam0)))
+    return ga, gr.value, lam0
+
+
+def theta_apply(p: Params, F):
+    """Theta_h applied to one complex column F[n_theta] (with the angular ghosts)."""
+    F = np.ascontiguousarray(F, dtype=np.complex128)
+    out = np.zeros_like(F)
+    _check(lib().orc_theta_apply(ctypes.byref(p), _ptr(F), _ptr(out)))
+    return out
+
+
+def r_ext(p: Params) -> float:
+    return orbit(p)["r_ext"]
