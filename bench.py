@@ -1,0 +1,363 @@
+#!/usr/bin/env python
+"""Benchmark: grid-point updates/s of the Lax-Wendroff Teukolsky step on GB300.
+
+Workload: the paper-scale single mode (s=-2, m=2, a=0.9; N_r*=16384 over r* in
+[-200, 800], N_theta=256; circular-orbit source at r0=8M; extraction at r*=700).
+One bench step = --chunk-steps full time steps (predictor + corrector + source +
+extraction) of that grid.  The headline value is the FP32-Kahan path; the FP64
+path is timed beside it, and the oracle (single-threaded FP64 C) is timed on the
+host cores on a bounded sample.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun each rank advances its own replica of the grid (weak scaling);
+times are the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "paper-scale single mode 16384x256 (s=-2, m=2, a=0.9, r*=[-200,800], r0=8M, r*_ext=700)"
+KAHAN_BYTES_PER_UPDATE = 64   # read + write of (hi, c) for Phi and Pi, FP32
+FP64_BYTES_PER_UPDATE = 64    # read + write of Phi and Pi, FP64
+FP64_FLOPS_PER_UPDATE = 156   # FP64 flops of one point update in the kernel's formulation (FMA = 2)
+FP64_PEAK_TFLOPS = 1.25       # GB300 FP64 (non-tensor) nominal: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in ("teuk_step.cu", "teuk_step_common.cuh", "teuk_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_1001_3631_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(prec):
+    """DRAM bytes per launch of the step kernel from the committed ncu summary, if the
+    kernel source is unchanged since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        ent = d.get(prec)
+        if ent and ent.get("kernel_hash") == kernel_hash():
+            return float(ent["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for k, nm in enumerate(names):
+                    if r[5 + k].strip().lower() == "active":
+                        reasons.add(nm)
+            except Exception:
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def aggregate(times_ms, units_per_rank):
+    """Whole-job rate: the units all ranks processed over the slowest rank's time."""
+    t = max(times_ms)
+    return sum(units_per_rank) / (t * 1e-3), t
+
+
+def reduce_max(x, world):
+    if world == 1:
+        return [x]
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    out = [torch.zeros_like(t) for _ in range(world)]
+    dist.all_gather(out, t)
+    return [float(o.item()) for o in out]
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def time_path(prec, cfg, S, K, W, world, dev_index):
+    import torch
+
+    from paper_1001_3631_gb300 import TeukSolver
+    p = cfg["params"]
+    s = TeukSolver(dict(p, prec=prec))
+    s.set_source(cfg["r0"])
+    for _ in range(W):
+        s.step(S)
+    torch.cuda.synchronize()
+    barrier(world)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = s.kernel_launches()
+    clk = Clocks(dev_index)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(K):
+        s.step(S)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    barrier(world)
+    ms = e0.elapsed_time(e1)
+    launches = s.kernel_launches() - l0
+    npts = p["n_rstar"] * p["n_theta"]
+    s.sync()
+    return s, ms, launches, npts, clocks
+
+
+def e2e_path(prec, cfg, S, K, W):
+    """Same metric through the C ABI with host buffers: each step uploads the initial
+    state from pinned host memory, advances S steps and reads the waveform back."""
+    import numpy as np
+    import torch
+
+    from paper_1001_3631_gb300 import TeukSolver, inputs
+    p = cfg["params"]
+    s = TeukSolver(dict(p, prec=prec, wave_capacity=S + 1))
+    s.set_source(cfg["r0"])
+    host_u = torch.empty((4, p["n_theta"], p["n_rstar"]), dtype=torch.float64,
+                         pin_memory=True).numpy()
+    host_u[...] = inputs.smooth_state(p["n_theta"], p["n_rstar"], seed=5)
+    host_w = torch.empty((S + 1, p["n_theta"], 2), dtype=torch.float64, pin_memory=True).numpy()
+    import ctypes
+
+    from paper_1001_3631_gb300 import _lib
+    lib = _lib.load()
+    nw, first = ctypes.c_int64(0), ctypes.c_int64(0)
+
+    def one():
+        _lib.check(lib.teuk_set_state(s.ctx, 0, _lib.ptr(host_u), 0), s.ctx)
+        _lib.check(lib.teuk_step_n(s.ctx, S), s.ctx)
+        _lib.check(lib.teuk_extract(s.ctx, 0, _lib.ptr(host_w), None, S + 1, ctypes.byref(nw),
+                                    ctypes.byref(first)), s.ctx)
+
+    for _ in range(W):
+        one()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(K):
+        one()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    npts = p["n_rstar"] * p["n_theta"]
+    s.close()
+    return {"value": K * S * npts / dt, "unit": "updates/s",
+            "h2d_bytes_per_step": int(host_u.nbytes), "d2h_bytes_per_step": int(host_w.nbytes)}
+
+
+def accuracy(cfg, n_steps=4000, probe=12.0):
+    """FP32 paths against the FP64 path (which equals the oracle to 1e-12) on the
+    same grid.  The extraction radius of the workload (r* = 700) is not reached in
+    a few thousand steps of dt ~ 1e-3, so the waveform is taken at a near-zone
+    probe r* = 12, next to the particle (r*(r0) = 10.2)."""
+    import numpy as np
+
+    from paper_1001_3631_gb300 import TeukSolver
+    p = dict(cfg["params"], rstar_ext=probe)
+    res, ref = {}, None
+    for prec in ("fp64", "fp32_kahan", "fp32"):
+        with TeukSolver(dict(p, prec=prec, wave_capacity=n_steps + 1)) as s:
+            s.set_source(cfg["r0"])
+            s.step(n_steps)
+            u = s.get_state()
+            w, _ = s.extract()
+        if ref is None:
+            ref = (u, w)
+        else:
+            res[prec] = {"state_rel_l2": float(np.linalg.norm(u - ref[0]) / np.linalg.norm(ref[0])),
+                         "waveform_rel_l2": float(np.linalg.norm(w - ref[1]) / np.linalg.norm(ref[1]))}
+    res["steps"] = n_steps
+    res["probe_rstar"] = probe
+    return res
+
+
+def cpu_baseline(cfg, budget_s=12.0):
+    """The oracle (single-threaded FP64 C) on the same grid, per-step time from the
+    difference of two run lengths (so its setup is excluded)."""
+    from oracle import teuk_oracle as orc
+    p = orc.params(**cfg["params"], r0=cfg["r0"])
+    src = orc.orbit_source(p)
+    t0 = time.perf_counter()
+    orc.run(p, None, 1, src, wave=False)
+    t1 = time.perf_counter()
+    orc.run(p, None, 3, src, wave=False)
+    t2 = time.perf_counter()
+    per_step = max((t2 - t1) - (t1 - t0), 1e-9) / 2.0
+    n = max(2, int(budget_s / per_step))
+    t3 = time.perf_counter()
+    orc.run(p, None, n + 1, src, wave=False)
+    t4 = time.perf_counter()
+    per_step = ((t4 - t3) - (t1 - t0)) / n
+    npts = p.n_rstar * p.n_theta
+    return {"value": npts / per_step, "unit": "updates/s", "cores": 1, "kind": "oracle",
+            "sample": "%d full steps of the %dx%d grid (setup excluded by differencing)"
+                      % (n, p.n_rstar, p.n_theta)}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    from paper_1001_3631_gb300 import inputs
+    cfg = inputs.PAPER_SCALE_16384x256
+    cb = cpu_baseline(cfg, budget_s=8.0)
+    line = {"impl": "reference", "metric": "grid-point updates/s", "value": cb["value"],
+            "unit": "updates/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "impl": "oracle on host cores"},
+            "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": "updates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--chunk-steps", type=int, default=500)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+    args.warmup = max(args.warmup, 3)
+
+    import torch
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_1001_3631_gb300 import build as b
+    from paper_1001_3631_gb300 import inputs
+    b.build()
+    cfg = inputs.PAPER_SCALE_16384x256
+    S, K, W = args.chunk_steps, args.steps, args.warmup
+
+    s_k, ms_k, launches_k, npts, clocks = time_path("fp32_kahan", cfg, S, K, W, world, local)
+    s_k.close()
+    s_d, ms_d, launches_d, _, clocks_d = time_path("fp64", cfg, S, K, W, world, local)
+    s_d.close()
+    ms_k_all = reduce_max(ms_k, world)
+    ms_d_all = reduce_max(ms_d, world)
+    units = K * S * npts
+    val_k, tk = aggregate(ms_k_all, [units] * world)
+    val_d, td = aggregate(ms_d_all, [units] * world)
+
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return 0
+
+    peak, peak_kind = measured_peaks()
+    step_launches = K * S
+    avg_k = tk / step_launches          # ms per step-kernel launch (extract kernel included)
+    avg_d = td / step_launches
+    ach_k = KAHAN_BYTES_PER_UPDATE * npts / (avg_k * 1e-3) / 1e9
+    traffic = ncu_traffic("fp32_kahan")
+    fp64_tflops = FP64_FLOPS_PER_UPDATE * npts / (avg_d * 1e-3) / 1e12
+    line = {
+        "metric": "grid-point updates/s", "value": val_k, "unit": "updates/s",
+        "n_gpus": world, "steps": K, "warmup": W, "ms_per_step": tk / K,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32-kahan", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "time_steps_per_bench_step": S,
+                   "precision": "FP32 stencil, Kahan-compensated state; FP64 tables/source/extraction",
+                   "l2": "inputs larger than L2 (state 268 MB + coefficient tables 302 MB)",
+                   "parallelism": "replica per GPU" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "achieved": ach_k, "peak": peak, "unit": "GB/s",
+                     "frac": ach_k / peak, "traffic": traffic,
+                     "peak_source": peak_kind, "bytes_per_update": KAHAN_BYTES_PER_UPDATE,
+                     "kernel": "step_kernel<PK>"},
+        "fp64": {"value": val_d, "unit": "updates/s", "ms_per_step": td / K,
+                 "roofline": {"bound": "alu", "achieved": fp64_tflops, "peak": FP64_PEAK_TFLOPS,
+                              "unit": "TFLOP/s", "frac": fp64_tflops / FP64_PEAK_TFLOPS,
+                              "flops_per_update": FP64_FLOPS_PER_UPDATE,
+                              "hbm_frac": FP64_BYTES_PER_UPDATE * npts / (avg_d * 1e-3) / 1e9 / peak,
+                              "kernel": "step_kernel<P64>"},
+                 "clocks": clocks_d},
+        "fp32_kahan_over_fp64": val_k / val_d,
+        "gpu_launches": int(launches_k),
+        "clocks": clocks,
+    }
+    line["accuracy"] = accuracy(cfg)
+    line["e2e"] = e2e_path("fp32_kahan", cfg, S, max(2, K // 2), 1)
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(cfg)
+    print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

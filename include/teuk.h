@@ -1,0 +1,181 @@
+/*
+ * teuk.h -- C ABI of the GB300 (sm_103a) Teukolsky time-domain solver.
+ *
+ * The library advances the (2+1)D Teukolsky equation for one azimuthal mode m
+ * (Khanna & McKennon, arXiv 1001.3631, Sec. 2) with the two-step Lax-Wendroff
+ * scheme of Eqs. (13)-(14), on the (r*, theta) grid of Eqs. (2)-(4), with the
+ * boundary conditions stated after Eq. (14), plus a smeared point-particle
+ * source.  Every step of the time loop runs in the library's CUDA kernels on
+ * the device; host code only validates arguments, launches and copies.
+ *
+ * Conventions shared by every entry point:
+ *   - Grid: r*_i = rstar_min + i dr*, i = 0 .. n_rstar-1, dr* = (rstar_max -
+ *     rstar_min)/(n_rstar - 1); theta_j = (j + 1/2) pi / n_theta.
+ *   - State layout on the host side, "u-layout": double [4][n_theta][n_rstar]
+ *     holding {Phi_R, Phi_I, Pi_R, Pi_I} (the solution vector u of Eq. 9),
+ *     Pi = d_t Phi + b d_r* Phi (Eq. 5).
+ *   - Waveform record n: W_n[j] = Phi^n(r*_ext, theta_j), linear in r* between
+ *     the two bracketing nodes, as FP64 (re, im) pairs [n_theta][2].
+ *   - All host pointers are caller-owned; the library copies what it needs and
+ *     keeps no host pointer past the call.  Device memory is owned by the
+ *     context and released by teuk_destroy.
+ *   - Work is queued on the caller's CUDA stream (never the legacy default
+ *     stream).  Calls that return host data synchronize that stream.
+ *   - Every call returns a teuk_status; teuk_last_error() gives the message of
+ *     the last failing call on that context.  Nothing aborts the process and
+ *     no kernel traps: device-side failures are reported through a status
+ *     word read at the next synchronizing call.  There is no CPU fallback: a
+ *     missing or unusable GPU is TEUK_ECUDA.
+ */
+#ifndef TEUK_H
+#define TEUK_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TEUK_OK = 0,
+    TEUK_EINVAL = 1,    /* invalid argument; nothing was changed or allocated */
+    TEUK_ENOMEM = 2,    /* device allocation failed */
+    TEUK_ECUDA = 3,     /* CUDA runtime error (no device, launch failure, ...) */
+    TEUK_EUNSTABLE = 4, /* non-finite values found in the state or waveform */
+    TEUK_ETIMEOUT = 5,  /* a bounded device-side wait gave up */
+    TEUK_ESTATE = 6     /* call not valid in the context's current state */
+} teuk_status;
+
+typedef enum {
+    TEUK_FP64 = 0,        /* state, coefficients and arithmetic in FP64 */
+    TEUK_FP32 = 1,        /* state and arithmetic in FP32 (coefficients rounded from FP64) */
+    TEUK_FP32_KAHAN = 2   /* FP32 arithmetic, state as compensated (hi, c) FP32 pairs */
+} teuk_precision;
+
+/*
+ * Problem statement of one instance (one mode, one orbit, one grid).
+ * s, m, M, a: spin weight, azimuthal mode, Kerr mass and spin of Eq. (1); |a| < M.
+ * rstar_min, rstar_max, n_rstar: radial grid (Eq. 2); n_rstar >= 8.
+ * n_theta: angular cells; 4 <= n_theta <= 1024.
+ * courant, dt_rule, dt: the time step.  dt > 0 is used as given; otherwise
+ *   dt_rule 0: dt = courant * dr*  (the Courant factor read literally), or
+ *   dt_rule 1: dt = courant * min(dr*, dtheta / (|m| + |s| + 2)), which keeps the
+ *              explicitly integrated angular terms of Eq. (13)-(14) bounded.
+ * rstar_ext: extraction radius, inside [rstar_min, rstar_max].
+ * prec: arithmetic of this instance (all instances of a context must agree).
+ * wave_capacity: number of waveform records kept on the device (a ring); 0 means
+ *   4096.
+ */
+typedef struct {
+    int s, m;
+    double M, a;
+    double rstar_min, rstar_max;
+    int n_rstar, n_theta;
+    double courant;
+    int dt_rule;
+    double dt;
+    double rstar_ext;
+    int prec;
+    int64_t wave_capacity;
+} teuk_params;
+
+/*
+ * Synthetic particle source (the paper's source T is a Maple expression that is
+ * not printed, Sec. 2.1 and Sec. 3): a particle on a prograde circular
+ * equatorial orbit of radius r0, smeared by a 2D Gaussian in (r*, theta)
+ * centred on (r*(r0), pi/2), truncated at 8 sigma:
+ *   T_m = A_n exp(-i m (Omega t + phi0)) G,  Omega = M^(1/2)/(r0^(3/2) + a M^(1/2)),
+ *   phi0 = a/(r_+ - r_-) ln((r0 - r_+)/(r0 - r_-)),
+ * entering S_Pi as tau = 4 pi Delta (r^2 + a^2 cos^2) T_m / (Sigma^2 r^3).
+ * Widths: sigma_*_abs > 0 in absolute units, else sigma_*_cells grid cells
+ * (0 means 4 cells).
+ */
+typedef struct {
+    double r0;
+    double sigma_rstar_cells, sigma_theta_cells;
+    double sigma_rstar_abs, sigma_theta_abs;
+} teuk_orbit;
+
+typedef struct teuk_ctx teuk_ctx;
+
+/* Create a context of n_instances independent instances p[0 .. n_instances-1]
+ * (uneven grids allowed), on the caller's stream (cudaStream_t passed as void*).
+ * Builds the grids, inverts Eq. (2) for r at every node, forms the coefficient
+ * tables, and zeroes the state; no source is set (tau = 0) until
+ * teuk_set_source.  *out is NULL on failure.  Validation failures are
+ * TEUK_EINVAL with nothing allocated. */
+teuk_status teuk_create(const teuk_params* p, int n_instances, void* cuda_stream,
+                        teuk_ctx** out);
+
+/* Set the particle source of one instance.  amps: A_n for global step n < n_amps
+ * (host, copied); steps n >= n_amps (or amps == NULL) use A_n = 1.
+ * TEUK_EINVAL if r0 is not outside the horizon or the orbit is off the grid. */
+teuk_status teuk_set_source(teuk_ctx* ctx, int instance, const teuk_orbit* orbit,
+                            const double* amps, int64_t n_amps);
+
+/* Replace the state of one instance from host memory in u-layout (copied) and
+ * set its time level to step0 (t = step0 dt).  Clears that instance's
+ * waveform records. */
+teuk_status teuk_set_state(teuk_ctx* ctx, int instance, const double* host_u, int64_t step0);
+
+/* Copy the state of one instance to host memory in u-layout.  Synchronizes. */
+teuk_status teuk_get_state(teuk_ctx* ctx, int instance, double* host_u);
+
+/* Advance every instance by n full Lax-Wendroff steps (Eqs. 13-14), recording the
+ * waveform at every time level.  Asynchronous on the context's stream. */
+teuk_status teuk_step_n(teuk_ctx* ctx, int64_t n);
+
+/* Copy the waveform records of one instance to host memory: out [k][n_theta][2]
+ * and, if out_scalar != NULL, w_n = sum_j W_n[j] sin(theta_j) dtheta as [k][2]
+ * (FP64, j ascending).  Records are the time levels first_step .. first_step+k-1
+ * where k = min(cap_steps, records held) and the records are the most recent
+ * ones held (the ring keeps wave_capacity).  *n_written = k, *first_step is the
+ * time level of the first record.  Synchronizes. */
+teuk_status teuk_extract(teuk_ctx* ctx, int instance, double* out, double* out_scalar,
+                         int64_t cap_steps, int64_t* n_written, int64_t* first_step);
+
+/* Reverse-mode derivative of a waveform loss over the steps step0 .. step0+n-1 of
+ * one instance (the transposed stencil of Eqs. 13-14, applied in kernels).
+ *   grad_wave != NULL: host [n][n_theta][2] holding dL/dW for records step0+1 ..
+ *     step0+n (real and imaginary parts); no forward state is needed because the
+ *     step is linear; the context's state is not touched; *loss is not written.
+ *   grad_wave == NULL: the built-in loss L = sum_{k=1..n} sum_j |r_ext^3 W_{step0+k}[j]|^2
+ *     (psi = r^3 Phi, Eq. 4).  The instance's time level must be step0
+ *     (else TEUK_ESTATE).  The forward sweep runs from the current state with a
+ *     checkpoint every ckpt_every steps (ckpt_every <= 0: no checkpoints, the
+ *     forward waveform is kept instead); the reverse sweep recomputes each
+ *     segment's waveform from its checkpoint.  The state ends at step0 + n.
+ * Out (host): grad_amps[k] = dL/dA_{step0+k} (n values, may be NULL),
+ *   *grad_r0 = dL/dr0 (may be NULL), *loss (built-in loss only, may be NULL).
+ * Synchronizes. */
+teuk_status teuk_adjoint_n(teuk_ctx* ctx, int instance, int64_t step0, int64_t n,
+                           int64_t ckpt_every, const double* grad_wave, double* grad_amps,
+                           double* grad_r0, double* loss);
+
+/* Wait for queued work, read the device status word and check the state of
+ * every instance for non-finite values (TEUK_EUNSTABLE). */
+teuk_status teuk_sync(teuk_ctx* ctx);
+
+/* Time level (global step index) of one instance, and its time step dt. */
+teuk_status teuk_get_time(const teuk_ctx* ctx, int instance, int64_t* step, double* dt);
+
+/* Launch configuration of the step kernels: rows per theta-chunk (0 = automatic).
+ * Results do not depend on it (the per-point arithmetic is fixed).  The batched
+ * path also takes the work-item size from here. */
+teuk_status teuk_set_tiling(teuk_ctx* ctx, int theta_chunk, int steps_per_launch);
+
+/* Number of kernels the library launched on this context since creation. */
+int64_t teuk_kernel_launches(const teuk_ctx* ctx);
+
+/* Free all device memory of the context (synchronizes its stream).  NULL is a no-op. */
+void teuk_destroy(teuk_ctx* ctx);
+
+/* Message of the last failing call on ctx (or of the last failed teuk_create when
+ * ctx == NULL).  Never NULL. */
+const char* teuk_last_error(const teuk_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TEUK_H */

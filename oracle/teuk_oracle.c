@@ -292,20 +292,27 @@ int orc_orbit_profile(const orc_params* p, double* P_int, double* P_half, double
     st = orc_orbit(p, orb);
     if (st) return st;
     cplx *Pi_ = (cplx*)P_int, *Ph = (cplx*)P_half, *dPi = (cplx*)dP_int, *dPh = (cplx*)dP_half;
+    /* r at each column, once (the inversion does not depend on theta) */
+    double* xi = malloc(sizeof(double) * g.nr);
+    double* xh = malloc(sizeof(double) * g.nr);
+    if (!xi || !xh) { free(xi); free(xh); return ORC_ENOMEM; }
+    for (int i = 0; i < g.nr; ++i) xi[i] = orc_x_of_rstar(p->M, p->a, p->rstar_min + i * g.drs);
+    for (int i = 0; i < g.nr - 1; ++i)
+        xh[i] = orc_x_of_rstar(p->M, p->a, p->rstar_min + (i + 0.5) * g.drs);
     for (int j = 0; j < g.nth; ++j) {
         double th = (j + 0.5) * g.dth;
         for (int i = 0; i < g.nr; ++i) {
             double rs = p->rstar_min + i * g.drs;
-            double x = orc_x_of_rstar(p->M, p->a, rs);
-            profile_at(p, orb, x, rs, th, &Pi_[(size_t)j * g.nr + i], &dPi[(size_t)j * g.nr + i]);
+            profile_at(p, orb, xi[i], rs, th, &Pi_[(size_t)j * g.nr + i], &dPi[(size_t)j * g.nr + i]);
         }
         for (int i = 0; i < g.nr - 1; ++i) {
             double rs = p->rstar_min + (i + 0.5) * g.drs;
-            double x = orc_x_of_rstar(p->M, p->a, rs);
-            profile_at(p, orb, x, rs, th, &Ph[(size_t)j * (g.nr - 1) + i],
+            profile_at(p, orb, xh[i], rs, th, &Ph[(size_t)j * (g.nr - 1) + i],
                        &dPh[(size_t)j * (g.nr - 1) + i]);
         }
     }
+    free(xi);
+    free(xh);
     return ORC_OK;
 }
 

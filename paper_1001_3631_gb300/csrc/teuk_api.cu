@@ -1,0 +1,493 @@
+// teuk_api.cu -- the C ABI of include/teuk.h: argument validation, device memory
+// (stream-ordered allocation on the caller's stream), kernel launches and copies.
+// No arithmetic of the time step happens on the host.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "teuk.h"
+#include "teuk_internal.cuh"
+#include "teuk_step_common.cuh"
+
+using namespace teuk;
+
+namespace {
+
+constexpr double kPi = 3.141592653589793238462643;
+
+struct Instance {
+    teuk_params p{};
+    double drs = 0, dth = 0, dt = 0, rp = 0, rm = 0;
+    int pitch = 0;
+    int64_t step = 0;   // time level of the state
+    int cur = 0;        // buffer holding the state
+    void* state[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    size_t plane_bytes = 0;
+    void* coef_h = nullptr;
+    void* coef_i = nullptr;
+    double* x_int = nullptr;
+    double* x_half = nullptr;
+    // source
+    bool src_on = false;
+    teuk_orbit orbit{};
+    double rs0 = 0, sig_r = 0, sig_t = 0, drs0_dr0 = 0;
+    double2* P_win = nullptr;   // P_int | P_half | dP_int | dP_half
+    double* amps = nullptr;
+    SourceDev sd{};
+    // waveform ring: time levels [wave_lo, wave_hi) are held
+    double2* wave = nullptr;
+    int64_t wave_cap = 0, wave_lo = 0, wave_hi = 0;
+    int i_e = 0;
+    double f_e = 0, r_ext = 0;
+};
+
+}  // namespace
+
+struct teuk_ctx {
+    cudaStream_t stream = nullptr;
+    int prec = 0;
+    std::vector<Instance> inst;
+    unsigned* status = nullptr;
+    std::string err;
+    int chunk = 0;           // theta rows per warp task (0 = automatic)
+    int steps_per_launch = 1;
+    int64_t launches = 0;
+};
+
+static std::string g_create_err = "no error";
+
+#define TK_FAIL(ctx, code, ...)                                              \
+    do {                                                                     \
+        char _b[512];                                                        \
+        snprintf(_b, sizeof(_b), __VA_ARGS__);                               \
+        (ctx)->err = _b;                                                     \
+        return code;                                                         \
+    } while (0)
+
+#define TK_CUDA(ctx, call)                                                   \
+    do {                                                                     \
+        cudaError_t _e = (call);                                             \
+        if (_e != cudaSuccess) {                                             \
+            (ctx)->err = std::string(#call) + ": " + cudaGetErrorString(_e); \
+            return _e == cudaErrorMemoryAllocation ? TEUK_ENOMEM : TEUK_ECUDA; \
+        }                                                                    \
+    } while (0)
+
+namespace {
+
+double rstar_of_r(double M, double a, double r) {
+    double d = std::sqrt(M * M - a * a), rp = M + d, rm = M - d;
+    double k = 2.0 * M / (rp - rm);
+    return r + k * rp * std::log((r - rp) / (2.0 * M)) - k * rm * std::log((r - rm) / (2.0 * M));
+}
+
+// Validate one instance and fill its derived geometry.  Returns an error text or "".
+std::string derive(const teuk_params& p, Instance& I) {
+    if (!(p.M > 0) || !(std::fabs(p.a) < p.M)) return "need M > 0 and |a| < M";
+    if (p.n_rstar < 8) return "n_rstar must be >= 8";
+    if (p.n_theta < 4 || p.n_theta > 1024) return "n_theta must be in [4, 1024]";
+    if ((int64_t)p.n_rstar * p.n_theta > (int64_t)1 << 30) return "grid too large";
+    if (!(p.rstar_max > p.rstar_min)) return "need rstar_max > rstar_min";
+    if (p.prec < 0 || p.prec > 2) return "prec must be TEUK_FP64, TEUK_FP32 or TEUK_FP32_KAHAN";
+    if (p.wave_capacity < 0) return "wave_capacity must be >= 0";
+    I.p = p;
+    I.drs = (p.rstar_max - p.rstar_min) / (double)(p.n_rstar - 1);
+    I.dth = kPi / (double)p.n_theta;
+    double d = std::sqrt(p.M * p.M - p.a * p.a);
+    I.rp = p.M + d;
+    I.rm = p.M - d;
+    if (p.dt > 0) {
+        I.dt = p.dt;
+    } else if (p.dt_rule == 0) {
+        I.dt = p.courant * I.drs;
+    } else if (p.dt_rule == 1) {
+        double lim = I.dth / (double)(std::abs(p.m) + std::abs(p.s) + 2);
+        I.dt = p.courant * std::fmin(I.drs, lim);
+    } else {
+        return "dt_rule must be 0 or 1";
+    }
+    if (!(I.dt > 0) || !std::isfinite(I.dt)) return "time step must be positive";
+    double pos = (p.rstar_ext - p.rstar_min) / I.drs;
+    if (!(pos >= 0.0) || !(pos <= (double)(p.n_rstar - 1))) return "rstar_ext outside the grid";
+    int ie = (int)std::floor(pos);
+    if (ie > p.n_rstar - 2) ie = p.n_rstar - 2;
+    I.i_e = ie;
+    I.f_e = (p.rstar_ext - (p.rstar_min + ie * I.drs)) / I.drs;
+    I.pitch = (p.n_rstar + kPitchAlign - 1) / kPitchAlign * kPitchAlign;
+    I.wave_cap = p.wave_capacity > 0 ? p.wave_capacity : 4096;
+    return "";
+}
+
+InstDev dev_of(const teuk_ctx* c, const Instance& I) {
+    InstDev d{};
+    d.nr = I.p.n_rstar;
+    d.nth = I.p.n_theta;
+    d.pitch = I.pitch;
+    d.prec = I.p.prec;
+    d.drs = I.drs;
+    d.dth = I.dth;
+    d.dt = I.dt;
+    d.ghost = (std::abs(I.p.m) % 2 == 0) ? 1.0 : -1.0;
+    d.ghost_f = (float)d.ghost;
+    for (int b = 0; b < 2; ++b)
+        for (int k = 0; k < 2; ++k) d.buf[b][k] = I.state[b][k];
+    d.coef_h = I.coef_h;
+    d.coef_i = I.coef_i;
+    d.src = I.sd;
+    d.src.on = I.src_on ? 1 : 0;
+    d.i_e = I.i_e;
+    d.f_e = I.f_e;
+    d.wave = I.wave;
+    d.wave_cap = I.wave_cap;
+    d.status = c->status;
+    return d;
+}
+
+int auto_chunk(const Instance& I) {
+    // at least 16 warp tasks per SM (152 SMs), chunks of at least 16 rows
+    int nstrip = (I.p.n_rstar - 2 + 29) / 30;
+    int chunk = I.p.n_theta;
+    while (chunk > 16 && (int64_t)nstrip * ((I.p.n_theta + chunk - 1) / chunk) < 152 * 16)
+        chunk /= 2;
+    return chunk;
+}
+
+void do_step(teuk_ctx* c, Instance& I, int chunk) {
+    launch_step(c->stream, dev_of(c, I), I.step, I.cur, chunk);
+    c->launches++;
+    I.cur = 1 - I.cur;
+    I.step++;
+}
+
+void do_extract(teuk_ctx* c, Instance& I) {
+    launch_extract(c->stream, dev_of(c, I), I.step, I.cur);
+    c->launches++;
+}
+
+void free_instance(cudaStream_t s, Instance& I) {
+    for (int b = 0; b < 2; ++b)
+        for (int k = 0; k < 2; ++k)
+            if (I.state[b][k]) cudaFreeAsync(I.state[b][k], s);
+    void* ptrs[] = {I.coef_h, I.coef_i, I.x_int, I.x_half, I.P_win, I.amps, I.wave};
+    for (void* q : ptrs)
+        if (q) cudaFreeAsync(q, s);
+    I = Instance();
+}
+
+teuk_status check_instance(teuk_ctx* c, int instance) {
+    if (!c) return TEUK_EINVAL;
+    if (instance < 0 || instance >= (int)c->inst.size())
+        TK_FAIL(c, TEUK_EINVAL, "instance %d out of range [0, %d)", instance, (int)c->inst.size());
+    return TEUK_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ create
+
+extern "C" teuk_status teuk_create(const teuk_params* p, int n_instances, void* cuda_stream,
+                                   teuk_ctx** out) {
+    if (out) *out = nullptr;
+    if (!p || !out || n_instances < 1) {
+        g_create_err = "teuk_create: null argument or n_instances < 1";
+        return TEUK_EINVAL;
+    }
+    std::vector<Instance> inst(n_instances);
+    for (int k = 0; k < n_instances; ++k) {
+        std::string e = derive(p[k], inst[k]);
+        if (!e.empty()) {
+            g_create_err = "instance " + std::to_string(k) + ": " + e;
+            return TEUK_EINVAL;
+        }
+        if (p[k].prec != p[0].prec) {
+            g_create_err = "all instances of a context must use the same precision";
+            return TEUK_EINVAL;
+        }
+    }
+    int dev = -1;
+    cudaError_t ce = cudaGetDevice(&dev);
+    if (ce != cudaSuccess) {
+        g_create_err = std::string("no usable CUDA device: ") + cudaGetErrorString(ce);
+        return TEUK_ECUDA;
+    }
+    teuk_ctx* c = new teuk_ctx();
+    c->stream = (cudaStream_t)cuda_stream;
+    c->prec = p[0].prec;
+    c->inst = std::move(inst);
+    auto fail = [&](teuk_status st) {
+        g_create_err = c->err;
+        teuk_destroy(c);
+        return st;
+    };
+#define TK_CCUDA(call)                                                            \
+    do {                                                                          \
+        cudaError_t _e = (call);                                                  \
+        if (_e != cudaSuccess) {                                                  \
+            c->err = std::string(#call) + ": " + cudaGetErrorString(_e);          \
+            return fail(_e == cudaErrorMemoryAllocation ? TEUK_ENOMEM : TEUK_ECUDA); \
+        }                                                                         \
+    } while (0)
+    TK_CCUDA(cudaMallocAsync((void**)&c->status, sizeof(unsigned), c->stream));
+    TK_CCUDA(cudaMemsetAsync(c->status, 0, sizeof(unsigned), c->stream));
+    for (Instance& I : c->inst) {
+        const teuk_params& q = I.p;
+        size_t es = q.prec == TEUK_FP64 ? sizeof(double2) : sizeof(float4);
+        int nplanes = q.prec == TEUK_FP32 ? 1 : 2;
+        I.plane_bytes = (size_t)q.n_theta * I.pitch * es;
+        for (int b = 0; b < 2; ++b)
+            for (int k = 0; k < nplanes; ++k) {
+                TK_CCUDA(cudaMallocAsync(&I.state[b][k], I.plane_bytes, c->stream));
+                TK_CCUDA(cudaMemsetAsync(I.state[b][k], 0, I.plane_bytes, c->stream));
+            }
+        size_t cs = q.prec == TEUK_FP64 ? sizeof(double) : sizeof(float);
+        size_t cbytes = (size_t)kNCoef * q.n_theta * I.pitch * cs;
+        TK_CCUDA(cudaMallocAsync(&I.coef_h, cbytes, c->stream));
+        TK_CCUDA(cudaMallocAsync(&I.coef_i, cbytes, c->stream));
+        TK_CCUDA(cudaMallocAsync((void**)&I.x_int, sizeof(double) * q.n_rstar, c->stream));
+        TK_CCUDA(cudaMallocAsync((void**)&I.x_half, sizeof(double) * q.n_rstar, c->stream));
+        TK_CCUDA(cudaMallocAsync((void**)&I.wave, sizeof(double2) * I.wave_cap * q.n_theta,
+                                 c->stream));
+        launch_invert_tortoise(c->stream, q.M, q.a, q.rstar_min, I.drs, q.n_rstar, I.x_int,
+                               I.x_half);
+        launch_coefficients(c->stream, q.prec, q.M, q.a, q.s, q.m, q.rstar_min, I.drs, I.dth,
+                            I.dt, q.n_rstar, q.n_theta, I.pitch, I.x_int, I.x_half, I.coef_h,
+                            I.coef_i);
+        c->launches += 2;
+        TK_CCUDA(cudaGetLastError());
+        I.r_ext = 0;  // filled lazily from x at r*_ext when needed (adjoint loss)
+    }
+#undef TK_CCUDA
+    *out = c;
+    return TEUK_OK;
+}
+
+// ------------------------------------------------------------------ source
+
+extern "C" teuk_status teuk_set_source(teuk_ctx* c, int instance, const teuk_orbit* orbit,
+                                       const double* amps, int64_t n_amps) {
+    teuk_status st = check_instance(c, instance);
+    if (st) return st;
+    Instance& I = c->inst[instance];
+    if (!orbit) TK_FAIL(c, TEUK_EINVAL, "orbit is NULL");
+    if (n_amps < 0 || (n_amps > 0 && !amps)) TK_FAIL(c, TEUK_EINVAL, "bad amplitude array");
+    const teuk_params& q = I.p;
+    double r0 = orbit->r0;
+    if (!(r0 > I.rp)) TK_FAIL(c, TEUK_EINVAL, "orbit radius r0=%g inside the horizon", r0);
+    double rs0 = rstar_of_r(q.M, q.a, r0);
+    if (!(rs0 > q.rstar_min && rs0 < q.rstar_max))
+        TK_FAIL(c, TEUK_EINVAL, "orbit r*(r0)=%g outside the radial grid", rs0);
+    double sr = orbit->sigma_rstar_abs > 0 ? orbit->sigma_rstar_abs
+                : (orbit->sigma_rstar_cells > 0 ? orbit->sigma_rstar_cells : 4.0) * I.drs;
+    double stt = orbit->sigma_theta_abs > 0 ? orbit->sigma_theta_abs
+                 : (orbit->sigma_theta_cells > 0 ? orbit->sigma_theta_cells : 4.0) * I.dth;
+    // window of nodes that can be within 8 sigma (the kernel applies the exact cut)
+    SourceDev sd{};
+    int nr = q.n_rstar, nth = q.n_theta;
+    auto clampi = [](double v, int lo, int hi) {
+        return v < lo ? lo : (v > hi ? hi : (int)v);
+    };
+    int ilo = clampi(std::floor((rs0 - 8 * sr - q.rstar_min) / I.drs) - 1, 0, nr - 1);
+    int ihi = clampi(std::ceil((rs0 + 8 * sr - q.rstar_min) / I.drs) + 1, 0, nr - 1);
+    int hlo = clampi(std::floor((rs0 - 8 * sr - q.rstar_min) / I.drs - 0.5) - 1, 0, nr - 2);
+    int hhi = clampi(std::ceil((rs0 + 8 * sr - q.rstar_min) / I.drs - 0.5) + 1, 0, nr - 2);
+    int jlo = clampi(std::floor((0.5 * kPi - 8 * stt) / I.dth - 0.5) - 1, 0, nth - 1);
+    int jhi = clampi(std::ceil((0.5 * kPi + 8 * stt) / I.dth - 0.5) + 1, 0, nth - 1);
+    sd.i_lo = ilo; sd.ni = ihi - ilo + 1;
+    sd.h_lo = hlo; sd.nh = hhi - hlo + 1;
+    sd.j_lo = jlo; sd.nj = jhi - jlo + 1;
+    double Omega = std::sqrt(q.M) / (std::pow(r0, 1.5) + q.a * std::sqrt(q.M));
+    double phi0 = q.a / (I.rp - I.rm) * std::log((r0 - I.rp) / (r0 - I.rm));
+    double Delta0 = r0 * r0 - 2 * q.M * r0 + q.a * q.a;
+    double dOmega = -std::sqrt(q.M) * 1.5 * std::sqrt(r0) /
+                    ((std::pow(r0, 1.5) + q.a * std::sqrt(q.M)) * (std::pow(r0, 1.5) + q.a * std::sqrt(q.M)));
+    sd.omega = q.m * Omega;
+    sd.phase0 = q.m * phi0;
+    sd.domega = q.m * dOmega;
+    sd.dphase0 = q.m * q.a / Delta0;
+    // (re)allocate window and amplitudes
+    if (I.P_win) { cudaFreeAsync(I.P_win, c->stream); I.P_win = nullptr; }
+    if (I.amps) { cudaFreeAsync(I.amps, c->stream); I.amps = nullptr; }
+    size_t nwi = (size_t)sd.nj * sd.ni, nwh = (size_t)sd.nj * sd.nh;
+    TK_CUDA(c, cudaMallocAsync((void**)&I.P_win, sizeof(double2) * 2 * (nwi + nwh), c->stream));
+    sd.P_int = I.P_win;
+    sd.P_half = I.P_win + nwi;
+    sd.dP_int = I.P_win + nwi + nwh;
+    sd.dP_half = I.P_win + 2 * nwi + nwh;
+    if (n_amps > 0) {
+        TK_CUDA(c, cudaMallocAsync((void**)&I.amps, sizeof(double) * n_amps, c->stream));
+        TK_CUDA(c, cudaMemcpyAsync(I.amps, amps, sizeof(double) * n_amps, cudaMemcpyHostToDevice,
+                                   c->stream));
+    }
+    sd.amps = I.amps;
+    sd.n_amps = n_amps;
+    I.rs0 = rs0;
+    I.sig_r = sr;
+    I.sig_t = stt;
+    I.drs0_dr0 = (r0 * r0 + q.a * q.a) / Delta0;
+    launch_profile(c->stream, q.M, q.a, q.rstar_min, I.drs, I.dth, rs0, sr, stt, I.drs0_dr0,
+                   I.x_int, I.x_half, sd);
+    c->launches++;
+    TK_CUDA(c, cudaGetLastError());
+    I.sd = sd;
+    I.orbit = *orbit;
+    I.src_on = true;
+    if (n_amps > 0) TK_CUDA(c, cudaStreamSynchronize(c->stream));  // host amps may be freed
+    return TEUK_OK;
+}
+
+// ------------------------------------------------------------------ state
+
+extern "C" teuk_status teuk_set_state(teuk_ctx* c, int instance, const double* host_u,
+                                      int64_t step0) {
+    teuk_status st = check_instance(c, instance);
+    if (st) return st;
+    if (!host_u || step0 < 0) TK_FAIL(c, TEUK_EINVAL, "host_u is NULL or step0 < 0");
+    Instance& I = c->inst[instance];
+    size_t bytes = sizeof(double) * 4 * (size_t)I.p.n_rstar * I.p.n_theta;
+    double* du = nullptr;
+    TK_CUDA(c, cudaMallocAsync((void**)&du, bytes, c->stream));
+    TK_CUDA(c, cudaMemcpyAsync(du, host_u, bytes, cudaMemcpyHostToDevice, c->stream));
+    launch_import_state(c->stream, dev_of(c, I), I.cur, du);
+    c->launches++;
+    TK_CUDA(c, cudaGetLastError());
+    TK_CUDA(c, cudaFreeAsync(du, c->stream));
+    TK_CUDA(c, cudaStreamSynchronize(c->stream));  // the host buffer may go away after return
+    I.step = step0;
+    I.wave_lo = I.wave_hi = step0;
+    return TEUK_OK;
+}
+
+extern "C" teuk_status teuk_get_state(teuk_ctx* c, int instance, double* host_u) {
+    teuk_status st = check_instance(c, instance);
+    if (st) return st;
+    if (!host_u) TK_FAIL(c, TEUK_EINVAL, "host_u is NULL");
+    Instance& I = c->inst[instance];
+    size_t bytes = sizeof(double) * 4 * (size_t)I.p.n_rstar * I.p.n_theta;
+    double* du = nullptr;
+    TK_CUDA(c, cudaMallocAsync((void**)&du, bytes, c->stream));
+    launch_export_state(c->stream, dev_of(c, I), I.cur, du);
+    c->launches++;
+    TK_CUDA(c, cudaGetLastError());
+    TK_CUDA(c, cudaMemcpyAsync(host_u, du, bytes, cudaMemcpyDeviceToHost, c->stream));
+    TK_CUDA(c, cudaFreeAsync(du, c->stream));
+    TK_CUDA(c, cudaStreamSynchronize(c->stream));
+    return TEUK_OK;
+}
+
+// ------------------------------------------------------------------ step
+
+extern "C" teuk_status teuk_step_n(teuk_ctx* c, int64_t n) {
+    if (!c) return TEUK_EINVAL;
+    if (n < 0) TK_FAIL(c, TEUK_EINVAL, "n < 0");
+    if (n == 0) return TEUK_OK;
+    for (Instance& I : c->inst) {
+        int chunk = c->chunk > 0 ? std::min(c->chunk, I.p.n_theta) : auto_chunk(I);
+        int64_t s0 = I.step;
+        for (int64_t k = 0; k < n; ++k) do_step(c, I, chunk);
+        do_extract(c, I);
+        if (I.wave_hi != s0 + 1 || I.wave_lo == I.wave_hi) I.wave_lo = s0;
+        I.wave_hi = I.step + 1;
+        if (I.wave_hi - I.wave_lo > I.wave_cap) I.wave_lo = I.wave_hi - I.wave_cap;
+    }
+    TK_CUDA(c, cudaGetLastError());
+    return TEUK_OK;
+}
+
+extern "C" teuk_status teuk_extract(teuk_ctx* c, int instance, double* out, double* out_scalar,
+                                    int64_t cap_steps, int64_t* n_written, int64_t* first_step) {
+    teuk_status st = check_instance(c, instance);
+    if (st) return st;
+    if (cap_steps < 0 || (cap_steps > 0 && !out)) TK_FAIL(c, TEUK_EINVAL, "bad output buffer");
+    Instance& I = c->inst[instance];
+    int64_t held = I.wave_hi - I.wave_lo;
+    int64_t k = std::min(cap_steps, held);
+    int64_t lvl0 = I.wave_hi - k;
+    int nth = I.p.n_theta;
+    size_t rec = sizeof(double2) * nth;
+    // copy in at most two segments of the ring
+    int64_t done = 0;
+    while (done < k) {
+        int64_t slot = (lvl0 + done) % I.wave_cap;
+        int64_t run = std::min(k - done, I.wave_cap - slot);
+        TK_CUDA(c, cudaMemcpyAsync(out + done * 2 * nth, I.wave + slot * nth, rec * run,
+                                   cudaMemcpyDeviceToHost, c->stream));
+        done += run;
+    }
+    if (out_scalar && k > 0) {
+        double2* tmp = nullptr;
+        TK_CUDA(c, cudaMallocAsync((void**)&tmp, sizeof(double2) * k, c->stream));
+        launch_wave_sum(c->stream, I.wave, I.wave_cap, nth, I.dth, lvl0, k, tmp);
+        c->launches++;
+        TK_CUDA(c, cudaGetLastError());
+        TK_CUDA(c, cudaMemcpyAsync(out_scalar, tmp, sizeof(double2) * k, cudaMemcpyDeviceToHost,
+                                   c->stream));
+        TK_CUDA(c, cudaFreeAsync(tmp, c->stream));
+    }
+    TK_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (n_written) *n_written = k;
+    if (first_step) *first_step = lvl0;
+    return TEUK_OK;
+}
+
+extern "C" teuk_status teuk_sync(teuk_ctx* c) {
+    if (!c) return TEUK_EINVAL;
+    for (Instance& I : c->inst) {
+        launch_scan_finite(c->stream, dev_of(c, I), I.cur);
+        c->launches++;
+    }
+    TK_CUDA(c, cudaGetLastError());
+    unsigned h = 0;
+    TK_CUDA(c, cudaMemcpyAsync(&h, c->status, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+    TK_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (h & ST_TIMEOUT) TK_FAIL(c, TEUK_ETIMEOUT, "a bounded device wait gave up");
+    if (h & ST_NONFINITE) TK_FAIL(c, TEUK_EUNSTABLE, "non-finite values in the state or waveform");
+    if (h & ST_BOUNDS) TK_FAIL(c, TEUK_ECUDA, "device-side bounds check failed");
+    return TEUK_OK;
+}
+
+extern "C" teuk_status teuk_get_time(const teuk_ctx* c, int instance, int64_t* step, double* dt) {
+    if (!c || instance < 0 || instance >= (int)c->inst.size()) return TEUK_EINVAL;
+    if (step) *step = c->inst[instance].step;
+    if (dt) *dt = c->inst[instance].dt;
+    return TEUK_OK;
+}
+
+extern "C" teuk_status teuk_set_tiling(teuk_ctx* c, int theta_chunk, int steps_per_launch) {
+    if (!c) return TEUK_EINVAL;
+    if (theta_chunk < 0 || steps_per_launch < 0)
+        TK_FAIL(c, TEUK_EINVAL, "tiling parameters must be >= 0");
+    c->chunk = theta_chunk;
+    c->steps_per_launch = steps_per_launch > 0 ? steps_per_launch : 1;
+    return TEUK_OK;
+}
+
+extern "C" int64_t teuk_kernel_launches(const teuk_ctx* c) { return c ? c->launches : 0; }
+
+extern "C" teuk_status teuk_adjoint_n(teuk_ctx* c, int instance, int64_t step0, int64_t n,
+                                      int64_t ckpt_every, const double* grad_wave,
+                                      double* grad_amps, double* grad_r0, double* loss);
+
+extern "C" void teuk_destroy(teuk_ctx* c) {
+    if (!c) return;
+    for (Instance& I : c->inst) free_instance(c->stream, I);
+    if (c->status) cudaFreeAsync(c->status, c->stream);
+    cudaStreamSynchronize(c->stream);
+    delete c;
+}
+
+extern "C" const char* teuk_last_error(const teuk_ctx* c) {
+    return c ? c->err.c_str() : g_create_err.c_str();
+}
+
+// ------------------------------------------------------------------ adjoint (placeholder)
+extern "C" teuk_status teuk_adjoint_n(teuk_ctx* c, int instance, int64_t step0, int64_t n,
+                                      int64_t ckpt_every, const double* grad_wave,
+                                      double* grad_amps, double* grad_r0, double* loss) {
+    (void)step0; (void)n; (void)ckpt_every; (void)grad_wave; (void)grad_amps; (void)grad_r0;
+    (void)loss;
+    teuk_status st = check_instance(c, instance);
+    if (st) return st;
+    TK_FAIL(c, TEUK_ESTATE, "adjoint not available in this build");
+}

@@ -1,0 +1,91 @@
+// teuk_internal.cuh -- device-side data structures shared by the library's kernels.
+//
+// HBM layout of one instance (r* is the fastest index; rows are padded to a pitch
+// that is a multiple of 32 elements so every row starts 512-byte aligned):
+//   state   two ping-pong buffers, each made of "planes" [n_theta][pitch]:
+//             FP64        plane 0 = Phi (double2), plane 1 = Pi (double2)
+//             FP32        plane 0 = {Phi_R, Phi_I, Pi_R, Pi_I} (float4)
+//             FP32_KAHAN  plane 0 = hi {Phi, Pi} (float4), plane 1 = c {Phi, Pi} (float4),
+//                         the represented value being hi - c
+//   coef_h  [9][n_theta][pitch] coefficients of the predictor at half nodes (i+1/2, j)
+//   coef_i  [9][n_theta][pitch] coefficients of the corrector at integer nodes (i, j)
+//   source  FP64 complex profile on a window of nodes around the particle
+//   wave    FP64 ring of waveform records [capacity][n_theta] (double2)
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace teuk {
+
+constexpr int kNCoef = 9;        // coefficients per node and sub-step
+constexpr int kPitchAlign = 32;  // elements
+
+// Coefficient planes (same order at half and integer nodes; "s" is 1/2 for the
+// predictor and 1 for the corrector, i.e. the fraction of dt of the sub-step):
+//   0: g    = s dt b / dr*                       (D term of Eqs. 13-14)
+//   1,2: E1 = -s dt c_t                          (Pi coefficient of S_Pi)
+//   3,4: E2 = s dt P* / dr*,  P* = c_t b + p* - b b_{,r*}
+//   5:   ep = s dt w (1/dth^2 + cot/(2 dth))     (forward theta difference)
+//   6:   em = s dt w (1/dth^2 - cot/(2 dth))     (backward theta difference)
+//   7,8: E3 = s dt (q - w V)                     (zero-order term)
+enum CoefIdx { C_G = 0, C_E1R, C_E1I, C_E2R, C_E2I, C_EP, C_EM, C_E3R, C_E3I };
+
+struct SourceDev {
+    int on;
+    // integer nodes i in [i_lo, i_lo + ni), half nodes i+1/2 in [h_lo, h_lo + nh),
+    // rows j in [j_lo, j_lo + nj)
+    int i_lo, ni, h_lo, nh, j_lo, nj;
+    const double2* P_int;    // [nj][ni]   profile P (no phase)
+    const double2* P_half;   // [nj][nh]
+    const double2* dP_int;   // [nj][ni]   dP/dr0
+    const double2* dP_half;  // [nj][nh]
+    double omega, phase0;    // tau = A_n exp(-i (omega t + phase0)) P
+    double domega, dphase0;  // d omega/d r0, d phase0/d r0
+    const double* amps;      // A_n for n < n_amps, else 1
+    int64_t n_amps;
+};
+
+struct InstDev {
+    int nr, nth, pitch, prec;
+    double drs, dth, dt;
+    float ghost_f;            // +1 even |m|, -1 odd |m|
+    double ghost;
+    void* buf[2][2];          // [ping-pong buffer][plane]
+    const void* coef_h;       // [9][nth][pitch] (double or float)
+    const void* coef_i;
+    SourceDev src;
+    int i_e;                  // extraction between i_e and i_e + 1
+    double f_e;
+    double2* wave;            // [wave_cap][nth]
+    int64_t wave_cap;
+    unsigned int* status;     // device status word (bit flags)
+};
+
+enum StatusBits : unsigned int { ST_NONFINITE = 1u, ST_TIMEOUT = 2u, ST_BOUNDS = 4u };
+
+__host__ __device__ inline size_t plane_elems(const InstDev& d) {
+    return (size_t)d.nth * (size_t)d.pitch;
+}
+
+// ---- host launchers (each defined next to its kernels) ----
+// teuk_setup.cu
+void launch_invert_tortoise(cudaStream_t st, double M, double a, double rstar_min, double drs,
+                            int nr, double* x_int, double* x_half);
+void launch_coefficients(cudaStream_t st, int prec, double M, double a, int s, int m,
+                         double rstar_min, double drs, double dth, double dt, int nr, int nth,
+                         int pitch, const double* x_int, const double* x_half, void* coef_h,
+                         void* coef_i);
+void launch_profile(cudaStream_t st, double M, double a, double rstar_min, double drs, double dth,
+                    double rs0, double sig_r, double sig_t, double drs0_dr0, const double* x_int,
+                    const double* x_half, const SourceDev& src);
+// teuk_step.cu
+void launch_step(cudaStream_t st, const InstDev& d, int64_t step, int bin, int chunk);
+void launch_extract(cudaStream_t st, const InstDev& d, int64_t step, int bin);
+// teuk_aux.cu
+void launch_import_state(cudaStream_t st, const InstDev& d, int bin, const double* u);
+void launch_export_state(cudaStream_t st, const InstDev& d, int bin, double* u);
+void launch_scan_finite(cudaStream_t st, const InstDev& d, int bin);
+void launch_wave_sum(cudaStream_t st, const double2* wave, int64_t cap, int nth, double dth,
+                     int64_t level0, int64_t k_count, double2* out);
+
+}  // namespace teuk

@@ -1,0 +1,206 @@
+// teuk_setup.cu -- one-time setup kernels (FP64): tortoise inversion, coefficient
+// tables and the source profile.
+//
+// Coefficients of the first-order system d_t u + D d_r* u = S (Eqs. 8-12), obtained
+// from Eq. (1) by the substitutions of Eqs. (2)-(7):
+//   S_Phi = Pi
+//   S_Pi  = -c_t Pi + P* Phi_* + w Theta[Phi] + q Phi + tau
+// with R = r^2 + a^2, Sigma^2 = R^2 - a^2 Delta sin^2 (Eq. 7), b = R/Sigma (Eq. 6),
+//   w   = Delta / Sigma^2
+//   c_t = [4 i M a m r + 2 s (r Delta - M (r^2 - a^2)) + 2 i s a Delta cos] / Sigma^2
+//   p*  = w (6 R / r + 2 r) + 2 R (s (r - M) + i m a) / Sigma^2
+//   q   = [6 Delta^2/r^2 + 6 Delta ((s+1)(r-M) + i m a)/r + 4 i s m a (r - M)] / Sigma^2
+//   b b_{,r*} = a^2 Delta sin^2 (2 R (r - M) - 4 r Delta) / (2 Sigma^4)
+//   P*  = c_t b + p* - b b_{,r*}
+//   Theta[F] = F_thth + cot F_th - V F,  V = (m + s cos)^2 / sin^2 - s
+// evaluated at r = r_+ + x with x from the inversion of Eq. (2), so that
+// Delta = x (x + r_+ - r_-) keeps full relative precision next to the horizon.
+#include "teuk_internal.cuh"
+
+namespace teuk {
+
+__device__ __forceinline__ double rstar_of_x(double M, double rp, double rm, double x) {
+    double k = 2.0 * M / (rp - rm);
+    double r = rp + x;
+    return r + k * rp * log(x / (2.0 * M)) - k * rm * log((r - rm) / (2.0 * M));
+}
+
+// Solve r*(r_+ + x) = target for x > 0: safeguarded Newton in y = ln x.
+// dr*/dy = x dr*/dr = x R / Delta = R / (x + r_+ - r_-).
+__device__ double x_of_rstar(double M, double a, double target) {
+    double d = sqrt(M * M - a * a);
+    double rp = M + d, rm = M - d;
+    double lo = -700.0, hi = 30.0;
+    double k = 2.0 * M * rp / (rp - rm);
+    // initial guess from the two asymptotes (far: r* ~ r, near horizon: r* ~ k ln x)
+    double y = target > rp + 4.0 ? log(target) : (target - rp) / k;
+    y = fmin(fmax(y, lo + 1.0), hi - 1.0);
+    for (int it = 0; it < 200; ++it) {
+        double x = exp(y);
+        double f = rstar_of_x(M, rp, rm, x) - target;
+        if (f > 0.0) hi = y; else lo = y;
+        double r = rp + x;
+        double fp = (r * r + a * a) / (x + rp - rm);
+        double yn = y - f / fp;
+        if (!(yn > lo && yn < hi)) yn = 0.5 * (lo + hi);  // keep the bracket
+        if (fabs(yn - y) <= 1e-15 * fmax(1.0, fabs(y))) { y = yn; break; }
+        y = yn;
+    }
+    return exp(y);
+}
+
+__global__ void invert_tortoise_kernel(double M, double a, double rstar_min, double drs, int nr,
+                                       double* x_int, double* x_half) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < nr) x_int[k] = x_of_rstar(M, a, rstar_min + k * drs);
+    if (k < nr - 1) x_half[k] = x_of_rstar(M, a, rstar_min + (k + 0.5) * drs);
+}
+
+struct Cplx { double re, im; };
+
+// The nine scaled coefficients (order of CoefIdx) of a sub-step that spans the
+// fraction sfrac of dt, at (r = r_+ + x, theta).
+__device__ void node_coefficients(double M, double a, int s_, int m_, double x, double th,
+                                  double dth, double dt, double drs, double sfrac, double* out) {
+    double d = sqrt(M * M - a * a);
+    double rp = M + d, rm = M - d;
+    double s = (double)s_, m = (double)m_;
+    double r = rp + x;
+    double Delta = x * (x + rp - rm);
+    double R = r * r + a * a;
+    double sn, cs;
+    sincos(th, &sn, &cs);
+    double sn2 = sn * sn;
+    double Sig2 = R * R - a * a * Delta * sn2;
+    double iS2 = 1.0 / Sig2;
+    double b = R / sqrt(Sig2);
+    double w = Delta * iS2;
+    Cplx ct = {2.0 * s * (r * Delta - M * (r * r - a * a)) * iS2,
+               (4.0 * M * a * m * r + 2.0 * s * a * Delta * cs) * iS2};
+    Cplx pst = {w * (6.0 * R / r + 2.0 * r) + 2.0 * R * s * (r - M) * iS2,
+                2.0 * R * m * a * iS2};
+    Cplx q = {(6.0 * Delta * Delta / (r * r) + 6.0 * Delta * (s + 1.0) * (r - M) / r) * iS2,
+              (6.0 * Delta * m * a / r + 4.0 * s * m * a * (r - M)) * iS2};
+    double bbr = a * a * Delta * sn2 * (2.0 * R * (r - M) - 4.0 * r * Delta) * 0.5 * iS2 * iS2;
+    Cplx Pst = {ct.re * b + pst.re - bbr, ct.im * b + pst.im};
+    double V = (m + s * cs) * (m + s * cs) / sn2 - s;
+    double cot = cs / sn;
+    double sdt = sfrac * dt;
+    double i2 = 1.0 / (dth * dth), i1 = cot / (2.0 * dth);
+    out[C_G] = sdt * b / drs;
+    out[C_E1R] = -sdt * ct.re;
+    out[C_E1I] = -sdt * ct.im;
+    out[C_E2R] = sdt * Pst.re / drs;
+    out[C_E2I] = sdt * Pst.im / drs;
+    out[C_EP] = sdt * w * (i2 + i1);
+    out[C_EM] = sdt * w * (i2 - i1);
+    out[C_E3R] = sdt * (q.re - w * V);
+    out[C_E3I] = sdt * q.im;
+}
+
+template <typename T>
+__global__ void coef_kernel(double M, double a, int s, int m, double rstar_min, double drs,
+                            double dth, double dt, int nr, int nth, int pitch,
+                            const double* x_int, const double* x_half, T* coef_h, T* coef_i) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int j = blockIdx.y;
+    if (i >= pitch || j >= nth) return;
+    size_t pl = (size_t)nth * pitch;
+    size_t o = (size_t)j * pitch + i;
+    double th = (j + 0.5) * dth;
+    double c[kNCoef];
+    if (i < nr - 1) {
+        node_coefficients(M, a, s, m, x_half[i], th, dth, dt, drs, 0.5, c);
+        for (int k = 0; k < kNCoef; ++k) coef_h[k * pl + o] = (T)c[k];
+    } else {
+        for (int k = 0; k < kNCoef; ++k) coef_h[k * pl + o] = (T)0;
+    }
+    if (i < nr) {
+        node_coefficients(M, a, s, m, x_int[i], th, dth, dt, drs, 1.0, c);
+        for (int k = 0; k < kNCoef; ++k) coef_i[k * pl + o] = (T)c[k];
+    } else {
+        for (int k = 0; k < kNCoef; ++k) coef_i[k * pl + o] = (T)0;
+    }
+}
+
+
+// Source profile on the window: P = 4 pi (r^2 + a^2 cos^2) Delta / (Sigma^2 r^3) * G,
+// G = exp(-(dr^2/sig_r^2 + dth^2/sig_t^2)/2) / (2 pi sig_r sig_t), zero beyond 8 sigma;
+// dP/dr0 = P (r* - r*0)/sig_r^2 * dr*0/dr0 (widths fixed in cells or absolute units).
+__device__ void profile_point(double M, double a, double x, double rs, double th, double rs0,
+                              double sig_r, double sig_t, double drs0_dr0, double2* P,
+                              double2* dP) {
+    double dr = rs - rs0, dtt = th - 0.5 * 3.141592653589793238462643;
+    if (fabs(dr) > 8.0 * sig_r || fabs(dtt) > 8.0 * sig_t) {
+        *P = make_double2(0.0, 0.0);
+        *dP = make_double2(0.0, 0.0);
+        return;
+    }
+    double d = sqrt(M * M - a * a);
+    double rp = M + d, rm = M - d;
+    double r = rp + x;
+    double Delta = x * (x + rp - rm);
+    double R = r * r + a * a;
+    double sn, cs;
+    sincos(th, &sn, &cs);
+    double Sig2 = R * R - a * a * Delta * sn * sn;
+    double G = exp(-0.5 * (dr * dr / (sig_r * sig_r) + dtt * dtt / (sig_t * sig_t))) /
+               (2.0 * 3.141592653589793238462643 * sig_r * sig_t);
+    double pref = 4.0 * 3.141592653589793238462643 * (r * r + a * a * cs * cs) * Delta /
+                  (Sig2 * r * r * r);
+    *P = make_double2(pref * G, 0.0);
+    *dP = make_double2(pref * G * dr / (sig_r * sig_r) * drs0_dr0, 0.0);
+}
+
+__global__ void profile_kernel(double M, double a, double rstar_min, double drs, double dth,
+                               double rs0, double sig_r, double sig_t, double drs0_dr0,
+                               const double* x_int, const double* x_half, SourceDev src,
+                               double2* P_int, double2* P_half, double2* dP_int,
+                               double2* dP_half) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    int jj = blockIdx.y;
+    if (jj >= src.nj) return;
+    double th = (src.j_lo + jj + 0.5) * dth;
+    if (k < src.ni) {
+        int i = src.i_lo + k;
+        profile_point(M, a, x_int[i], rstar_min + i * drs, th, rs0, sig_r, sig_t, drs0_dr0,
+                      &P_int[(size_t)jj * src.ni + k], &dP_int[(size_t)jj * src.ni + k]);
+    }
+    if (k < src.nh) {
+        int i = src.h_lo + k;
+        profile_point(M, a, x_half[i], rstar_min + (i + 0.5) * drs, th, rs0, sig_r, sig_t,
+                      drs0_dr0, &P_half[(size_t)jj * src.nh + k],
+                      &dP_half[(size_t)jj * src.nh + k]);
+    }
+}
+
+void launch_invert_tortoise(cudaStream_t st, double M, double a, double rstar_min, double drs,
+                            int nr, double* x_int, double* x_half) {
+    invert_tortoise_kernel<<<(nr + 127) / 128, 128, 0, st>>>(M, a, rstar_min, drs, nr, x_int,
+                                                              x_half);
+}
+
+void launch_coefficients(cudaStream_t st, int prec, double M, double a, int s, int m,
+                         double rstar_min, double drs, double dth, double dt, int nr, int nth,
+                         int pitch, const double* x_int, const double* x_half, void* coef_h,
+                         void* coef_i) {
+    dim3 g((pitch + 127) / 128, nth);
+    if (prec == 0)
+        coef_kernel<double><<<g, 128, 0, st>>>(M, a, s, m, rstar_min, drs, dth, dt, nr, nth, pitch,
+                                               x_int, x_half, (double*)coef_h, (double*)coef_i);
+    else
+        coef_kernel<float><<<g, 128, 0, st>>>(M, a, s, m, rstar_min, drs, dth, dt, nr, nth, pitch,
+                                              x_int, x_half, (float*)coef_h, (float*)coef_i);
+}
+
+void launch_profile(cudaStream_t st, double M, double a, double rstar_min, double drs, double dth,
+                    double rs0, double sig_r, double sig_t, double drs0_dr0, const double* x_int,
+                    const double* x_half, const SourceDev& src) {
+    dim3 g(((src.ni > src.nh ? src.ni : src.nh) + 127) / 128, src.nj);
+    profile_kernel<<<g, 128, 0, st>>>(M, a, rstar_min, drs, dth, rs0, sig_r, sig_t, drs0_dr0,
+                                      x_int, x_half, src, (double2*)src.P_int,
+                                      (double2*)src.P_half, (double2*)src.dP_int,
+                                      (double2*)src.dP_half);
+}
+
+}  // namespace teuk

@@ -1,0 +1,140 @@
+"""TeukSolver: a thin Python handle over the C ABI (include/teuk.h).
+
+It marshals numpy arrays and torch streams into the C calls; the time loop, the
+source and the extraction all run in the library's CUDA kernels."""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import TEUK_FP32, TEUK_FP32_KAHAN, TEUK_FP64, check, ptr
+
+PREC = {"fp64": TEUK_FP64, "fp32": TEUK_FP32, "fp32_kahan": TEUK_FP32_KAHAN,
+        TEUK_FP64: TEUK_FP64, TEUK_FP32: TEUK_FP32, TEUK_FP32_KAHAN: TEUK_FP32_KAHAN}
+
+PARAM_DEFAULTS = dict(s=-2, m=2, M=1.0, a=0.9, rstar_min=-50.0, rstar_max=150.0, n_rstar=800,
+                      n_theta=64, courant=0.5, dt_rule=1, dt=0.0, rstar_ext=140.0,
+                      prec="fp64", wave_capacity=0)
+
+
+def make_params(**kw) -> _lib.teuk_params:
+    d = dict(PARAM_DEFAULTS)
+    for k, v in kw.items():
+        if k not in d:
+            raise KeyError("unknown parameter %r" % k)
+        d[k] = v
+    d["prec"] = PREC[d["prec"]]
+    return _lib.teuk_params(**d)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class TeukSolver:
+    """One context of one or more instances (see teuk_create)."""
+
+    def __init__(self, params, stream=None):
+        if isinstance(params, dict):
+            params = [params]
+        plist = [p if isinstance(p, _lib.teuk_params) else make_params(**p) for p in params]
+        self.n = len(plist)
+        arr = (_lib.teuk_params * self.n)(*plist)
+        self.params = plist
+        self._stream = stream
+        h = ctypes.c_void_p()
+        lib = _lib.load()
+        st = lib.teuk_create(arr, self.n, ctypes.c_void_p(_stream_handle(stream)), ctypes.byref(h))
+        check(st, None)
+        self.ctx = h
+
+    # -- lifetime
+    def close(self):
+        if getattr(self, "ctx", None):
+            _lib.load().teuk_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- calls
+    def set_source(self, r0, amps=None, instance=0, sigma_rstar_cells=4.0, sigma_theta_cells=4.0,
+                   sigma_rstar_abs=0.0, sigma_theta_abs=0.0):
+        orb = _lib.teuk_orbit(r0, sigma_rstar_cells, sigma_theta_cells, sigma_rstar_abs,
+                              sigma_theta_abs)
+        a = None if amps is None else np.ascontiguousarray(amps, dtype=np.float64)
+        check(_lib.load().teuk_set_source(self.ctx, instance, ctypes.byref(orb), ptr(a),
+                                          0 if a is None else a.size), self.ctx)
+
+    def shape(self, instance=0):
+        p = self.params[instance]
+        return (4, p.n_theta, p.n_rstar)
+
+    def set_state(self, u, step0=0, instance=0):
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        assert u.shape == self.shape(instance)
+        check(_lib.load().teuk_set_state(self.ctx, instance, ptr(u), step0), self.ctx)
+
+    def get_state(self, instance=0):
+        u = np.empty(self.shape(instance))
+        check(_lib.load().teuk_get_state(self.ctx, instance, ptr(u)), self.ctx)
+        return u
+
+    def step(self, n):
+        check(_lib.load().teuk_step_n(self.ctx, int(n)), self.ctx)
+
+    def extract(self, cap=None, instance=0, scalar=False):
+        """Returns (records [k][n_theta][2], first_step[, scalar [k][2]])."""
+        p = self.params[instance]
+        step, _ = self.time(instance)
+        if cap is None:
+            cap = step + 1
+        out = np.empty((cap, p.n_theta, 2))
+        sc = np.empty((cap, 2)) if scalar else None
+        nw, first = ctypes.c_int64(0), ctypes.c_int64(0)
+        check(_lib.load().teuk_extract(self.ctx, instance, ptr(out), ptr(sc), cap,
+                                       ctypes.byref(nw), ctypes.byref(first)), self.ctx)
+        k = nw.value
+        if scalar:
+            return out[:k], first.value, sc[:k]
+        return out[:k], first.value
+
+    def adjoint(self, n, step0=0, grad_wave=None, ckpt_every=100, instance=0):
+        """Returns (grad_amps [n], grad_r0, loss)."""
+        gw = None if grad_wave is None else np.ascontiguousarray(grad_wave, dtype=np.float64)
+        ga = np.zeros(n)
+        gr, loss = ctypes.c_double(0.0), ctypes.c_double(0.0)
+        check(_lib.load().teuk_adjoint_n(self.ctx, instance, step0, n, ckpt_every, ptr(gw),
+                                         ptr(ga), ctypes.byref(gr), ctypes.byref(loss)), self.ctx)
+        return ga, gr.value, loss.value
+
+    def sync(self):
+        check(_lib.load().teuk_sync(self.ctx), self.ctx)
+
+    def time(self, instance=0):
+        s, dt = ctypes.c_int64(0), ctypes.c_double(0.0)
+        check(_lib.load().teuk_get_time(self.ctx, instance, ctypes.byref(s), ctypes.byref(dt)),
+              self.ctx)
+        return s.value, dt.value
+
+    def set_tiling(self, theta_chunk=0, steps_per_launch=0):
+        check(_lib.load().teuk_set_tiling(self.ctx, theta_chunk, steps_per_launch), self.ctx)
+
+    def kernel_launches(self):
+        return _lib.load().teuk_kernel_launches(self.ctx)

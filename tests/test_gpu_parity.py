@@ -1,0 +1,194 @@
+"""GPU path (through the C ABI) against the FP64 oracle, element by element.
+
+FP64: relative L2 <= 1e-12 on the state and the waveform (the tolerance the
+problem statement fixes).  FP32 / FP32-Kahan: the bounds derived in the design doc
+from the FP32 rounding unit.  Results must not depend on the launch tiling."""
+import numpy as np
+import pytest
+
+from paper_1001_3631_gb300 import TeukSolver, inputs
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+
+
+def rel(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def gpu_run(params, r0, nsteps, u0=None, amps=None, prec="fp64", chunk=0, step0=0,
+            sigma_abs=None):
+    with TeukSolver(dict(params, prec=prec)) as s:
+        s.set_tiling(chunk)
+        if r0 is not None:
+            if sigma_abs:
+                s.set_source(r0, amps, sigma_rstar_abs=sigma_abs[0], sigma_theta_abs=sigma_abs[1])
+            else:
+                s.set_source(r0, amps)
+        if u0 is not None or step0:
+            s.set_state(np.zeros(s.shape()) if u0 is None else u0, step0)
+        s.step(nsteps)
+        u = s.get_state()
+        w, first = s.extract()
+        s.sync()
+    return u, w, first
+
+
+def oracle_run(orc, params, r0, nsteps, u0=None, amps=None, step0=0, sigma_abs=None):
+    kw = {k: v for k, v in params.items() if k not in ("prec", "wave_capacity")}
+    if sigma_abs:
+        kw.update(sigma_r_abs=sigma_abs[0], sigma_th_abs=sigma_abs[1])
+    p = orc.params(**kw, r0=r0 if r0 is not None else 10.0)
+    src = orc.orbit_source(p) if r0 is not None else None
+    return orc.run(p, u0, nsteps, src, amps=amps, step0=step0)
+
+
+SMALL = [
+    # (n_rstar, n_theta, m, a, rstar range, r0, ext)  ragged sizes on purpose
+    (97, 12, 2, 0.9, (-10.0, 30.0), 6.0, 20.0),
+    (151, 33, 3, 0.7, (-20.0, 40.0), 8.0, 35.0),
+    (64, 8, 1, 0.0, (-10.0, 30.0), 7.0, 29.9),
+    (8, 4, 2, 0.5, (-2.0, 12.0), 6.0, 10.0),
+]
+
+
+@pytest.mark.parametrize("case", SMALL)
+def test_fp64_small_grids_random_state_and_source(orc, case):
+    nr, nth, m, a, (lo, hi), r0, ext = case
+    params = dict(s=-2, m=m, a=a, rstar_min=lo, rstar_max=hi, n_rstar=nr, n_theta=nth,
+                  rstar_ext=ext, dt_rule=1, courant=0.5)
+    u0 = inputs.random_state(nth, nr, seed=nr + nth)
+    amps = inputs.amplitudes(40, seed=nr)
+    uo, wo = oracle_run(orc, params, r0, 37, u0, amps)
+    ref = None
+    for chunk in (0, 5, nth):
+        ug, wg, first = gpu_run(params, r0, 37, u0, amps, chunk=chunk)
+        assert first == 0 and wg.shape == wo.shape
+        assert rel(ug, uo) <= FP64_TOL, (chunk, rel(ug, uo))
+        assert rel(wg, wo) <= FP64_TOL, (chunk, rel(wg, wo))
+        if ref is None:
+            ref = (ug, wg)
+        else:  # the per-point arithmetic does not depend on the tiling
+            assert np.array_equal(ug, ref[0]) and np.array_equal(wg, ref[1])
+
+
+def test_fp64_single_mode_800x64_full_run(orc):
+    cfg = inputs.SINGLE_MODE_800x64
+    uo, wo = oracle_run(orc, cfg["params"], cfg["r0"], cfg["steps"])
+    ug, wg, _ = gpu_run(cfg["params"], cfg["r0"], cfg["steps"])
+    print("FP64 800x64x2000: state rel L2 %.3e  waveform rel L2 %.3e" % (rel(ug, uo), rel(wg, wo)))
+    assert rel(ug, uo) <= FP64_TOL
+    assert rel(wg, wo) <= FP64_TOL
+
+
+def test_fp64_paper_scale_grid_few_steps(orc):
+    # full 16384 x 256 grid in the benchmark's launch configuration, from smooth data
+    cfg = inputs.PAPER_SCALE_16384x256
+    p = cfg["params"]
+    u0 = inputs.smooth_state(p["n_theta"], p["n_rstar"], seed=2)
+    uo, wo = oracle_run(orc, p, cfg["r0"], 3, u0)
+    ug, wg, _ = gpu_run(p, cfg["r0"], 3, u0)
+    assert rel(ug, uo) <= FP64_TOL
+    assert rel(wg, wo) <= FP64_TOL
+
+
+@pytest.mark.parametrize("prec,tol_state,tol_wave", [("fp32_kahan", 2e-6, 2e-6),
+                                                     ("fp32", 1e-4, 1e-4)])
+def test_fp32_paths_single_mode(orc, prec, tol_state, tol_wave):
+    cfg = inputs.SINGLE_MODE_800x64
+    uo, wo = oracle_run(orc, cfg["params"], cfg["r0"], cfg["steps"])
+    ug, wg, _ = gpu_run(cfg["params"], cfg["r0"], cfg["steps"], prec=prec)
+    es, ew = rel(ug, uo), rel(wg, wo)
+    print("%s 800x64x2000: state rel L2 %.3e  waveform rel L2 %.3e" % (prec, es, ew))
+    assert es <= tol_state and ew <= tol_wave
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp32_kahan"])
+def test_fp32_paths_small_grids(orc, prec):
+    nr, nth, m, a, (lo, hi), r0, ext = SMALL[1]
+    params = dict(s=-2, m=m, a=a, rstar_min=lo, rstar_max=hi, n_rstar=nr, n_theta=nth,
+                  rstar_ext=ext, dt_rule=1, courant=0.5)
+    u0 = inputs.smooth_state(nth, nr, seed=3)
+    uo, wo = oracle_run(orc, params, r0, 50, u0)
+    ug, wg, _ = gpu_run(params, r0, 50, u0, prec=prec)
+    assert rel(ug, uo) <= (1e-6 if prec == "fp32_kahan" else 1e-5)
+
+
+def test_edge_cases_extraction_at_nodes_and_ends(orc):
+    base = dict(s=-2, m=2, a=0.6, rstar_min=-10.0, rstar_max=30.0, n_rstar=81, n_theta=16,
+                dt_rule=1, courant=0.5)
+    u0 = inputs.smooth_state(16, 81, seed=4)
+    for ext in (-10.0, 0.0, 30.0):  # first node, an interior node (weight 0), last node
+        params = dict(base, rstar_ext=ext)
+        uo, wo = oracle_run(orc, params, 6.0, 5, u0)
+        ug, wg, _ = gpu_run(params, 6.0, 5, u0)
+        assert rel(wg, wo) <= FP64_TOL and rel(ug, uo) <= FP64_TOL
+
+
+def test_source_window_clipped_at_grid_edge(orc):
+    # orbit close to the inner edge: the 8-sigma window is cut by the grid
+    params = dict(s=-2, m=2, a=0.3, rstar_min=0.0, rstar_max=40.0, n_rstar=121, n_theta=16,
+                  rstar_ext=30.0, dt_rule=1, courant=0.5)
+    r0 = 3.2  # r*(r0) just above r*_min
+    uo, wo = oracle_run(orc, params, r0, 20)
+    ug, wg, _ = gpu_run(params, r0, 20)
+    assert np.abs(uo).max() > 0
+    assert rel(ug, uo) <= FP64_TOL
+
+
+def test_restart_at_step0_and_zero_steps(orc):
+    params = dict(inputs.SINGLE_MODE_800x64["params"], n_rstar=200, rstar_min=-50.0,
+                  rstar_max=50.0, rstar_ext=-5.0)
+    u0 = inputs.smooth_state(64, 200, seed=9)
+    amps = inputs.amplitudes(60)
+    uo, wo = oracle_run(orc, params, 8.0, 11, u0, amps, step0=40)
+    ug, wg, first = gpu_run(params, 8.0, 11, u0, amps, step0=40)
+    assert first == 40
+    assert rel(ug, uo) <= FP64_TOL and rel(wg, wo) <= FP64_TOL
+    with TeukSolver(dict(params, prec="fp64")) as s:
+        s.set_state(u0)
+        s.step(0)
+        assert np.array_equal(s.get_state(), u0)
+        assert s.extract()[0].shape[0] == 0
+
+
+def test_state_roundtrip_and_scalar_waveform(orc):
+    params = dict(inputs.SINGLE_MODE_800x64["params"])
+    with TeukSolver(dict(params, prec="fp64")) as s:
+        u0 = inputs.random_state(64, 800, seed=1)
+        s.set_state(u0)
+        assert np.array_equal(s.get_state(), u0)
+        s.set_source(10.0)
+        s.step(7)
+        w, first, sc = s.extract(scalar=True)
+        th = (np.arange(64) + 0.5) * np.pi / 64
+        wt = np.sin(th) * (np.pi / 64)
+        ref = np.stack([(w[:, :, 0] * wt).sum(1), (w[:, :, 1] * wt).sum(1)], axis=1)
+        assert np.allclose(sc, ref, rtol=1e-13, atol=1e-300)
+
+
+def test_nonfinite_state_reported():
+    params = dict(inputs.SINGLE_MODE_800x64["params"])
+    with TeukSolver(dict(params, prec="fp64")) as s:
+        u0 = np.zeros(s.shape())
+        u0[0, 10, 100] = np.inf
+        s.set_state(u0)
+        s.step(2)
+        from paper_1001_3631_gb300 import TeukError
+        with pytest.raises(TeukError) as e:
+            s.sync()
+        assert e.value.status == 4
+
+
+def test_waveform_ring_keeps_most_recent_records(orc):
+    params = dict(inputs.SINGLE_MODE_800x64["params"], wave_capacity=16)
+    uo, wo = oracle_run(orc, params, 10.0, 40)
+    with TeukSolver(dict(params, prec="fp64")) as s:
+        s.set_source(10.0)
+        s.step(25)
+        s.step(15)
+        w, first = s.extract()
+    assert first == 41 - 16 and w.shape[0] == 16
+    assert rel(w, wo[first:]) <= FP64_TOL
