@@ -170,9 +170,40 @@ int64_t teuk_kernel_launches(const teuk_ctx* ctx);
 /* Free all device memory of the context (synchronizes its stream).  NULL is a no-op. */
 void teuk_destroy(teuk_ctx* ctx);
 
-/* Message of the last failing call on ctx (or of the last failed teuk_create when
- * ctx == NULL).  Never NULL. */
+/* Message of the last failing call on ctx (or, when ctx == NULL, of the last failed
+ * teuk_create or teuk_waveform_sum_noalloc).  Never NULL. */
 const char* teuk_last_error(const teuk_ctx* ctx);
+
+/* Largest n_records accepted by teuk_waveform_sum_noalloc. */
+#define TEUK_NOALLOC_MAX_RECORDS 65536
+
+/*
+ * Allocation-free reduction of waveform records, for callers that must not allocate
+ * device memory: for example an application that has given all device memory to
+ * its own pool (so a cudaMalloc here would fail or fragment it), or a
+ * latency-critical loop where a driver allocation, which may synchronize the
+ * device, is not acceptable.  The paper has no counterpart; this is a service of
+ * the library.
+ *
+ * Computes out_host[k] = sum_j W_k[j] sin(theta_j) dtheta (j ascending, FP64, with
+ * theta_j = (j + 1/2) pi / n_theta), the same value teuk_extract returns in
+ * out_scalar, for k = 0 .. n_records-1.
+ *   wave_dev  device memory, [n_records][n_theta][2] doubles (re, im), caller-owned
+ *   out_host  host memory, [n_records][2] doubles, caller-owned
+ *   cuda_stream  the caller's stream (NULL: the legacy default stream); the call
+ *             synchronizes it before returning
+ * No device memory is allocated or freed: the intermediate results live in one
+ * fixed device array of TEUK_NOALLOC_MAX_RECORDS (re, im) pairs (1 MiB) that every
+ * GPU loading the library holds until the process exits.  n_records above that
+ * size, n_theta outside [1, 1024] or NULL pointers are TEUK_EINVAL (message in
+ * teuk_last_error(NULL)); CUDA failures are TEUK_ECUDA.
+ * The first call on each device looks up the array's device address (once, with
+ * that device current); make that first call before any stream capture.
+ * All calls share the one array: calls whose GPU work overlaps (different streams
+ * or threads at the same time) race on it and must be serialized by the caller.
+ */
+teuk_status teuk_waveform_sum_noalloc(const double* wave_dev, int64_t n_records, int n_theta,
+                                      double* out_host, void* cuda_stream);
 
 #ifdef __cplusplus
 }

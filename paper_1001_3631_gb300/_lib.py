@@ -57,7 +57,9 @@ _PROTOS = {
     "teuk_kernel_launches": (_L, [_P]),
     "teuk_destroy": (None, [_P]),
     "teuk_last_error": (ctypes.c_char_p, [_P]),
+    "teuk_waveform_sum_noalloc": (_I, [_P, _L, _I, _P, _P]),
 }
+TEUK_NOALLOC_MAX_RECORDS = 65536
 
 
 def header_functions():

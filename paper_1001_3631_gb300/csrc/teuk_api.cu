@@ -58,6 +58,11 @@ struct teuk_ctx {
 
 static std::string g_create_err = "no error";
 
+namespace teuk {
+// Error text for calls that have no context (returned by teuk_last_error(NULL)).
+void set_global_error(const std::string& msg) { g_create_err = msg; }
+}  // namespace teuk
+
 #define TK_FAIL(ctx, code, ...)                                              \
     do {                                                                     \
         char _b[512];                                                        \
