@@ -284,6 +284,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--chunk-steps", type=int, default=500)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the accuracy, end-to-end and CPU-baseline legs")
+    ap.add_argument("--only", choices=["fp32_kahan", "fp64"], default=None,
+                    help="time one path only (for profiler captures)")
+    ap.add_argument("--accuracy-steps", type=int, default=4000)
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
@@ -301,6 +306,12 @@ def main():
     cfg = inputs.PAPER_SCALE_16384x256
     S, K, W = args.chunk_steps, args.steps, args.warmup
 
+    if args.only:
+        s_o, ms_o, _, _, _ = time_path(args.only, cfg, S, K, W, world, local)
+        s_o.close()
+        if rank == 0:
+            print(json.dumps({"only": args.only, "ms": ms_o, "time_steps": K * S}))
+        return 0
     s_k, ms_k, launches_k, npts, clocks = time_path("fp32_kahan", cfg, S, K, W, world, local)
     s_k.close()
     s_d, ms_d, launches_d, _, clocks_d = time_path("fp64", cfg, S, K, W, world, local)
@@ -348,10 +359,11 @@ def main():
         "gpu_launches": int(launches_k),
         "clocks": clocks,
     }
-    line["accuracy"] = accuracy(cfg)
-    line["e2e"] = e2e_path("fp32_kahan", cfg, S, max(2, K // 2), 1)
-    if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(cfg)
+    if not args.no_extras:
+        line["accuracy"] = accuracy(cfg, n_steps=args.accuracy_steps)
+        line["e2e"] = e2e_path("fp32_kahan", cfg, S, max(2, K // 2), 1)
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(cfg)
     print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist
