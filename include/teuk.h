@@ -19,8 +19,10 @@
  *   - All host pointers are caller-owned; the library copies what it needs and
  *     keeps no host pointer past the call.  Device memory is owned by the
  *     context and released by teuk_destroy.
- *   - Work is queued on the caller's CUDA stream (never the legacy default
- *     stream).  Calls that return host data synchronize that stream.
+ *   - Work is queued on the caller's CUDA stream (the cuda_stream of
+ *     teuk_create; NULL is the legacy default stream, on which the batched launch
+ *     cannot be captured in a CUDA graph and is issued directly).  Calls that return
+ *     host data synchronize that stream.
  *   - Every call returns a teuk_status; teuk_last_error() gives the message of
  *     the last failing call on that context.  Nothing aborts the process and
  *     no kernel traps: device-side failures are reported through a status
@@ -153,16 +155,43 @@ teuk_status teuk_adjoint_n(teuk_ctx* ctx, int instance, int64_t step0, int64_t n
                            double* grad_r0, double* loss);
 
 /* Wait for queued work, read the device status word and check the state of
- * every instance for non-finite values (TEUK_EUNSTABLE). */
+ * every instance for non-finite values (TEUK_EUNSTABLE); a bounded device wait
+ * that gave up is TEUK_ETIMEOUT.  The status word is cleared once reported. */
 teuk_status teuk_sync(teuk_ctx* ctx);
 
 /* Time level (global step index) of one instance, and its time step dt. */
 teuk_status teuk_get_time(const teuk_ctx* ctx, int instance, int64_t* step, double* dt);
 
-/* Launch configuration of the step kernels: rows per theta-chunk (0 = automatic).
- * Results do not depend on it (the per-point arithmetic is fixed).  The batched
- * path also takes the work-item size from here. */
+/* Derived geometry of one instance: out[0..7] = {dr*, dtheta, dt, r_+, r_-, r_ext,
+ * i_e, f_e} with r_ext = r(rstar_ext) (Eq. 2 inverted) and the extraction weights
+ * W = (1 - f_e) Phi_{i_e} + f_e Phi_{i_e + 1}. */
+teuk_status teuk_get_geometry(const teuk_ctx* ctx, int instance, double* out);
+
+/* Launch configuration: theta rows per work item for every instance (0 = automatic;
+ * a per-instance choice from teuk_set_instance_tiling / teuk_autotune wins), and the
+ * launch mode: steps_per_launch >= 1 launches one fused kernel per step (single-instance
+ * contexts); 0 sends a single-instance context through the persistent batched kernel
+ * that multi-instance contexts always use.  Results do not depend on either choice
+ * (the per-point arithmetic is fixed). */
 teuk_status teuk_set_tiling(teuk_ctx* ctx, int theta_chunk, int steps_per_launch);
+
+/* Theta rows per work item of one instance (0 = back to the context default). */
+teuk_status teuk_set_instance_tiling(teuk_ctx* ctx, int instance, int theta_chunk);
+
+/* Autotuner: for every distinct (n_theta, precision, n_rstar rounded up to a power of
+ * two) class of the context, time trial_steps steps of each candidate theta chunk
+ * (4 .. n_theta, powers of two) on a scratch copy of one instance of the class and keep
+ * the fastest for all its instances.  chosen (may be NULL) receives the chunk of each
+ * instance.  The state and the waveform records are not changed.  Synchronizes. */
+teuk_status teuk_autotune(teuk_ctx* ctx, int trial_steps, int* chosen);
+
+/* Testing aid for the bounded device waits of the batched kernel: work item
+ * skip_release_item (numbered within a step, -1 = none) of the first step of each
+ * call never publishes its completion, so the items that depend on it give up after
+ * spin_limit polls (0 = the default of about one second) and the next teuk_sync
+ * reports TEUK_ETIMEOUT; the state is then undefined until teuk_set_state. */
+teuk_status teuk_set_fault_injection(teuk_ctx* ctx, int64_t skip_release_item,
+                                     long long spin_limit);
 
 /* Number of kernels the library launched on this context since creation. */
 int64_t teuk_kernel_launches(const teuk_ctx* ctx);

@@ -54,6 +54,10 @@ _PROTOS = {
     "teuk_sync": (_I, [_P]),
     "teuk_get_time": (_I, [_P, _I, ctypes.POINTER(_L), ctypes.POINTER(_D)]),
     "teuk_set_tiling": (_I, [_P, _I, _I]),
+    "teuk_get_geometry": (_I, [_P, _I, _P]),
+    "teuk_set_instance_tiling": (_I, [_P, _I, _I]),
+    "teuk_autotune": (_I, [_P, _I, _P]),
+    "teuk_set_fault_injection": (_I, [_P, _L, ctypes.c_longlong]),
     "teuk_kernel_launches": (_L, [_P]),
     "teuk_destroy": (None, [_P]),
     "teuk_last_error": (ctypes.c_char_p, [_P]),

@@ -41,6 +41,25 @@ struct Instance {
     int64_t wave_cap = 0, wave_lo = 0, wave_hi = 0;
     int i_e = 0;
     double f_e = 0, r_ext = 0;
+    int chunk = 0;      // theta rows per work item chosen for this instance (0 = context default)
+};
+
+// Device side of the batched persistent launch of one context.
+struct Batch {
+    bool alloc = false;
+    char* d_blob = nullptr;       // descriptors of the current call
+    size_t blob_bytes = 0;
+    unsigned long long* d_counter = nullptr;
+    int* d_flags = nullptr;
+    int64_t flags_cap = 0;
+    int* d_abort = nullptr;
+    int64_t items_per_step = -1;
+    int grid = 0;
+    int max_nth = 0;
+    BatchDev bd{};
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    bool graph_failed = false;
 };
 
 }  // namespace
@@ -54,6 +73,9 @@ struct teuk_ctx {
     int chunk = 0;           // theta rows per warp task (0 = automatic)
     int steps_per_launch = 1;
     int64_t launches = 0;
+    Batch batch;
+    int64_t inject_skip_item = -1;   // testing aid: a work item that never releases its flag
+    long long spin_limit = 20000000LL;
 };
 
 static std::string g_create_err = "no error";
@@ -157,6 +179,11 @@ int auto_chunk(const Instance& I) {
     while (chunk > 16 && (int64_t)nstrip * ((I.p.n_theta + chunk - 1) / chunk) < 152 * 16)
         chunk /= 2;
     return chunk;
+}
+
+int eff_chunk(const teuk_ctx* c, const Instance& I) {
+    int ch = I.chunk > 0 ? I.chunk : (c->chunk > 0 ? c->chunk : auto_chunk(I));
+    return std::max(1, std::min(ch, I.p.n_theta));
 }
 
 void do_step(teuk_ctx* c, Instance& I, int chunk) {
@@ -383,12 +410,141 @@ extern "C" teuk_status teuk_get_state(teuk_ctx* c, int instance, double* host_u)
 
 // ------------------------------------------------------------------ step
 
+namespace {
+
+void invalidate_graph(teuk_ctx* c) {
+    Batch& B = c->batch;
+    if (B.exec) cudaGraphExecDestroy(B.exec);
+    if (B.graph) cudaGraphDestroy(B.graph);
+    B.exec = nullptr;
+    B.graph = nullptr;
+}
+
+void enqueue_batched(teuk_ctx* c) {
+    Batch& B = c->batch;
+    cudaMemsetAsync(B.d_counter, 0, sizeof(unsigned long long), c->stream);
+    cudaMemsetAsync(B.d_flags, 0, sizeof(int) * B.items_per_step, c->stream);
+    cudaMemsetAsync(B.d_abort, 0, sizeof(int), c->stream);
+    launch_batched_step(c->stream, c->prec, B.bd, B.grid);
+    launch_batched_extract(c->stream, c->prec, B.bd, B.max_nth);
+}
+
+// All instances advance n steps in one persistent launch (captured once in a CUDA
+// graph and replayed; the per-call descriptors are uploaded before each replay).
+teuk_status batched_step(teuk_ctx* c, int64_t n) {
+    Batch& B = c->batch;
+    const int ni = (int)c->inst.size();
+    std::vector<int64_t> item_base(ni + 1, 0), base_step(ni);
+    std::vector<int> chunk(ni), nstrip(ni), base_bin(ni);
+    std::vector<InstDev> idev(ni);
+    int max_nth = 0;
+    for (int k = 0; k < ni; ++k) {
+        Instance& I = c->inst[k];
+        chunk[k] = std::max(2, eff_chunk(c, I));  // an item's 2-row halo must lie in the next chunk
+        nstrip[k] = (I.p.n_rstar - 2 + 29) / 30;
+        int nck = (I.p.n_theta + chunk[k] - 1) / chunk[k];
+        item_base[k + 1] = item_base[k] + (int64_t)nstrip[k] * nck;
+        base_step[k] = I.step;
+        base_bin[k] = I.cur;
+        idev[k] = dev_of(c, I);
+        max_nth = std::max(max_nth, I.p.n_theta);
+    }
+    const int64_t items = item_base[ni];
+    // blob layout: InstDev[ni] | item_base[ni+1] | base_step[ni] | n_steps | chunk[ni] | nstrip[ni] | base_bin[ni]
+    size_t off_inst = 0, off_ib = off_inst + sizeof(InstDev) * ni;
+    size_t off_bs = off_ib + sizeof(int64_t) * (ni + 1), off_n = off_bs + sizeof(int64_t) * ni;
+    size_t off_ch = off_n + sizeof(int64_t), off_ns = off_ch + sizeof(int) * ni;
+    size_t off_bb = off_ns + sizeof(int) * ni, bytes = off_bb + sizeof(int) * ni;
+    if (!B.alloc) {
+        TK_CUDA(c, cudaMallocAsync((void**)&B.d_blob, bytes, c->stream));
+        TK_CUDA(c, cudaMallocAsync((void**)&B.d_counter, sizeof(unsigned long long), c->stream));
+        TK_CUDA(c, cudaMallocAsync((void**)&B.d_abort, sizeof(int), c->stream));
+        B.blob_bytes = bytes;
+        B.grid = batched_grid(c->prec);
+        B.alloc = true;
+    }
+    if (items > B.flags_cap) {
+        if (B.d_flags) cudaFreeAsync(B.d_flags, c->stream);
+        TK_CUDA(c, cudaMallocAsync((void**)&B.d_flags, sizeof(int) * items, c->stream));
+        B.flags_cap = items;
+        invalidate_graph(c);
+    }
+    if (items != B.items_per_step || max_nth != B.max_nth || c->spin_limit != B.bd.spin_limit ||
+        c->inject_skip_item != B.bd.skip_release_item)
+        invalidate_graph(c);
+    std::vector<char> blob(bytes);
+    std::memcpy(blob.data() + off_inst, idev.data(), sizeof(InstDev) * ni);
+    std::memcpy(blob.data() + off_ib, item_base.data(), sizeof(int64_t) * (ni + 1));
+    std::memcpy(blob.data() + off_bs, base_step.data(), sizeof(int64_t) * ni);
+    std::memcpy(blob.data() + off_n, &n, sizeof(int64_t));
+    std::memcpy(blob.data() + off_ch, chunk.data(), sizeof(int) * ni);
+    std::memcpy(blob.data() + off_ns, nstrip.data(), sizeof(int) * ni);
+    std::memcpy(blob.data() + off_bb, base_bin.data(), sizeof(int) * ni);
+    // pageable source: the call returns once the host bytes are staged
+    TK_CUDA(c, cudaMemcpyAsync(B.d_blob, blob.data(), bytes, cudaMemcpyHostToDevice, c->stream));
+    BatchDev bd{};
+    bd.inst = (const InstDev*)(B.d_blob + off_inst);
+    bd.item_base = (const int64_t*)(B.d_blob + off_ib);
+    bd.base_step = (const int64_t*)(B.d_blob + off_bs);
+    bd.n_steps = (const int64_t*)(B.d_blob + off_n);
+    bd.chunk = (const int*)(B.d_blob + off_ch);
+    bd.nstrip = (const int*)(B.d_blob + off_ns);
+    bd.base_bin = (const int*)(B.d_blob + off_bb);
+    bd.n_inst = ni;
+    bd.items_per_step = items;
+    bd.counter = B.d_counter;
+    bd.flags = B.d_flags;
+    bd.abort = B.d_abort;
+    bd.status = c->status;
+    bd.spin_limit = c->spin_limit;   // default ~1.3 s of 64 ns sleeps per wait
+    bd.skip_release_item = c->inject_skip_item;
+    B.bd = bd;
+    B.items_per_step = items;
+    B.max_nth = max_nth;
+    if (!B.exec && !B.graph_failed) {
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+            enqueue_batched(c);
+            if (cudaStreamEndCapture(c->stream, &g) == cudaSuccess && g &&
+                cudaGraphInstantiate(&B.exec, g, 0) == cudaSuccess) {
+                B.graph = g;
+            } else {
+                if (g) cudaGraphDestroy(g);
+                B.exec = nullptr;
+                B.graph_failed = true;
+            }
+        } else {
+            B.graph_failed = true;
+        }
+        cudaGetLastError();  // a refused capture (legacy stream) is not an error here
+    }
+    if (B.exec) {
+        TK_CUDA(c, cudaGraphLaunch(B.exec, c->stream));
+    } else {
+        enqueue_batched(c);
+    }
+    c->launches += 2;
+    for (Instance& I : c->inst) {
+        int64_t s0 = I.step;
+        I.step += n;
+        I.cur = (int)((I.cur + n) & 1);
+        if (I.wave_hi != s0 + 1 || I.wave_lo == I.wave_hi) I.wave_lo = s0;
+        I.wave_hi = I.step + 1;
+        if (I.wave_hi - I.wave_lo > I.wave_cap) I.wave_lo = I.wave_hi - I.wave_cap;
+    }
+    TK_CUDA(c, cudaGetLastError());
+    return TEUK_OK;
+}
+
+}  // namespace
+
 extern "C" teuk_status teuk_step_n(teuk_ctx* c, int64_t n) {
     if (!c) return TEUK_EINVAL;
     if (n < 0) TK_FAIL(c, TEUK_EINVAL, "n < 0");
     if (n == 0) return TEUK_OK;
+    if (c->inst.size() > 1 || c->steps_per_launch == 0) return batched_step(c, n);
     for (Instance& I : c->inst) {
-        int chunk = c->chunk > 0 ? std::min(c->chunk, I.p.n_theta) : auto_chunk(I);
+        int chunk = eff_chunk(c, I);
         int64_t s0 = I.step;
         for (int64_t k = 0; k < n; ++k) do_step(c, I, chunk);
         do_extract(c, I);
@@ -445,6 +601,7 @@ extern "C" teuk_status teuk_sync(teuk_ctx* c) {
     TK_CUDA(c, cudaGetLastError());
     unsigned h = 0;
     TK_CUDA(c, cudaMemcpyAsync(&h, c->status, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+    TK_CUDA(c, cudaMemsetAsync(c->status, 0, sizeof(unsigned), c->stream));  // reported once
     TK_CUDA(c, cudaStreamSynchronize(c->stream));
     if (h & ST_TIMEOUT) TK_FAIL(c, TEUK_ETIMEOUT, "a bounded device wait gave up");
     if (h & ST_NONFINITE) TK_FAIL(c, TEUK_EUNSTABLE, "non-finite values in the state or waveform");
@@ -459,23 +616,126 @@ extern "C" teuk_status teuk_get_time(const teuk_ctx* c, int instance, int64_t* s
     return TEUK_OK;
 }
 
+extern "C" teuk_status teuk_get_geometry(const teuk_ctx* c, int instance, double* out);
+
 extern "C" teuk_status teuk_set_tiling(teuk_ctx* c, int theta_chunk, int steps_per_launch) {
     if (!c) return TEUK_EINVAL;
     if (theta_chunk < 0 || steps_per_launch < 0)
         TK_FAIL(c, TEUK_EINVAL, "tiling parameters must be >= 0");
     c->chunk = theta_chunk;
-    c->steps_per_launch = steps_per_launch > 0 ? steps_per_launch : 1;
+    c->steps_per_launch = steps_per_launch;
+    invalidate_graph(c);
+    return TEUK_OK;
+}
+
+extern "C" teuk_status teuk_set_fault_injection(teuk_ctx* c, int64_t skip_release_item,
+                                                long long spin_limit) {
+    if (!c) return TEUK_EINVAL;
+    if (spin_limit < 0) TK_FAIL(c, TEUK_EINVAL, "spin_limit must be >= 0");
+    c->inject_skip_item = skip_release_item;
+    c->spin_limit = spin_limit > 0 ? spin_limit : 20000000LL;
+    invalidate_graph(c);
+    return TEUK_OK;
+}
+
+extern "C" teuk_status teuk_set_instance_tiling(teuk_ctx* c, int instance, int theta_chunk) {
+    teuk_status st = check_instance(c, instance);
+    if (st) return st;
+    if (theta_chunk < 0) TK_FAIL(c, TEUK_EINVAL, "theta_chunk must be >= 0");
+    c->inst[instance].chunk = theta_chunk;
+    invalidate_graph(c);
+    return TEUK_OK;
+}
+
+// Time each candidate theta chunk on a scratch copy of one instance of every
+// distinct (n_theta, precision, n_rstar bucket) class and keep the fastest.
+extern "C" teuk_status teuk_autotune(teuk_ctx* c, int trial_steps, int* chosen) {
+    if (!c) return TEUK_EINVAL;
+    if (trial_steps < 1) TK_FAIL(c, TEUK_EINVAL, "trial_steps must be >= 1");
+    const int ni = (int)c->inst.size();
+    std::vector<int> best(ni, 0);
+    cudaEvent_t e0, e1;
+    TK_CUDA(c, cudaEventCreate(&e0));
+    TK_CUDA(c, cudaEventCreate(&e1));
+    for (int k = 0; k < ni; ++k) {
+        if (best[k]) continue;
+        Instance& I = c->inst[k];
+        auto bucket = [](int nr) { int b = 0; while ((1 << b) < nr) ++b; return b; };
+        const int nplanes = I.p.prec == TEUK_FP32 ? 1 : 2;
+        void* scr[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+        double2* scr_wave = nullptr;
+        teuk_status err = TEUK_OK;
+        for (int b = 0; b < 2 && !err; ++b)
+            for (int q = 0; q < nplanes && !err; ++q)
+                if (cudaMallocAsync(&scr[b][q], I.plane_bytes, c->stream) != cudaSuccess) err = TEUK_ENOMEM;
+        if (!err && cudaMallocAsync((void**)&scr_wave, sizeof(double2) * I.p.n_theta * (trial_steps + 2),
+                                    c->stream) != cudaSuccess)
+            err = TEUK_ENOMEM;
+        float best_ms = 1e30f;
+        int best_chunk = auto_chunk(I);
+        if (!err) {
+            InstDev d = dev_of(c, I);
+            d.wave = scr_wave;           // trial records must not touch the live ring
+            d.wave_cap = trial_steps + 2;
+            for (int q = 0; q < nplanes; ++q) {
+                cudaMemcpyAsync(scr[0][q], I.state[I.cur][q], I.plane_bytes, cudaMemcpyDeviceToDevice,
+                                c->stream);
+                d.buf[0][q] = scr[0][q];
+                d.buf[1][q] = scr[1][q];
+            }
+            const int cand[] = {4, 8, 16, 32, 64, 128, 256, 512, 1024};
+            for (int ch : cand) {
+                if (ch > I.p.n_theta) break;
+                for (int w = 0; w < 2; ++w) launch_step(c->stream, d, I.step + w, w & 1, ch);
+                cudaEventRecord(e0, c->stream);
+                for (int t = 0; t < trial_steps; ++t) launch_step(c->stream, d, I.step + t, t & 1, ch);
+                cudaEventRecord(e1, c->stream);
+                cudaEventSynchronize(e1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                c->launches += trial_steps + 2;
+                if (ms < best_ms) { best_ms = ms; best_chunk = ch; }
+            }
+        }
+        for (int b = 0; b < 2; ++b)
+            for (int q = 0; q < 2; ++q)
+                if (scr[b][q]) cudaFreeAsync(scr[b][q], c->stream);
+        if (scr_wave) cudaFreeAsync(scr_wave, c->stream);
+        if (err) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            TK_FAIL(c, err, "autotune: scratch allocation failed");
+        }
+        for (int k2 = k; k2 < ni; ++k2) {
+            Instance& J = c->inst[k2];
+            if (J.p.n_theta == I.p.n_theta && J.p.prec == I.p.prec &&
+                bucket(J.p.n_rstar) == bucket(I.p.n_rstar) && !best[k2])
+                best[k2] = best_chunk;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    for (int k = 0; k < ni; ++k) {
+        c->inst[k].chunk = best[k];
+        if (chosen) chosen[k] = best[k];
+    }
+    invalidate_graph(c);
+    TK_CUDA(c, cudaGetLastError());
     return TEUK_OK;
 }
 
 extern "C" int64_t teuk_kernel_launches(const teuk_ctx* c) { return c ? c->launches : 0; }
 
-extern "C" teuk_status teuk_adjoint_n(teuk_ctx* c, int instance, int64_t step0, int64_t n,
-                                      int64_t ckpt_every, const double* grad_wave,
-                                      double* grad_amps, double* grad_r0, double* loss);
-
 extern "C" void teuk_destroy(teuk_ctx* c) {
     if (!c) return;
+    {
+        Batch& B = c->batch;
+        if (B.exec) cudaGraphExecDestroy(B.exec);
+        if (B.graph) cudaGraphDestroy(B.graph);
+        void* ptrs[] = {B.d_blob, B.d_counter, B.d_flags, B.d_abort};
+        for (void* q : ptrs)
+            if (q) cudaFreeAsync(q, c->stream);
+    }
     for (Instance& I : c->inst) free_instance(c->stream, I);
     if (c->status) cudaFreeAsync(c->status, c->stream);
     cudaStreamSynchronize(c->stream);
@@ -486,13 +746,207 @@ extern "C" const char* teuk_last_error(const teuk_ctx* c) {
     return c ? c->err.c_str() : g_create_err.c_str();
 }
 
-// ------------------------------------------------------------------ adjoint (placeholder)
+// ------------------------------------------------------------------ adjoint
+
+namespace {
+
+// r(r*) on the host (the extraction radius of the built-in loss): safeguarded Newton
+// in y = ln(r - r_+), the same inversion of Eq. (2) the setup kernel performs.
+double r_of_rstar_host(double M, double a, double target) {
+    double d = std::sqrt(M * M - a * a), rp = M + d, rm = M - d;
+    double k = 2.0 * M / (rp - rm);
+    auto rs = [&](double x) {
+        double r = rp + x;
+        return r + k * rp * std::log(x / (2.0 * M)) - k * rm * std::log((r - rm) / (2.0 * M));
+    };
+    double lo = -700.0, hi = 30.0;
+    double y = target > rp + 4.0 ? std::log(target) : (target - rp) / (k * rp);
+    y = std::fmin(std::fmax(y, lo + 1.0), hi - 1.0);
+    for (int it = 0; it < 200; ++it) {
+        double x = std::exp(y), f = rs(x) - target;
+        if (f > 0.0) hi = y; else lo = y;
+        double r = rp + x;
+        double yn = y - f / ((r * r + a * a) / (x + rp - rm));
+        if (!(yn > lo && yn < hi)) yn = 0.5 * (lo + hi);
+        if (std::fabs(yn - y) <= 1e-15 * std::fmax(1.0, std::fabs(y))) { y = yn; break; }
+        y = yn;
+    }
+    return rp + std::exp(y);
+}
+
+// Device buffers of one adjoint call, released in reverse order of allocation.
+struct AdjBuffers {
+    cudaStream_t st;
+    std::vector<void*> ptrs;
+    explicit AdjBuffers(cudaStream_t s) : st(s) {}
+    cudaError_t get(void** p, size_t bytes) {
+        cudaError_t e = cudaMallocAsync(p, bytes, st);
+        if (e == cudaSuccess) ptrs.push_back(*p);
+        return e;
+    }
+    ~AdjBuffers() {
+        for (void* q : ptrs) cudaFreeAsync(q, st);
+    }
+};
+
+}  // namespace
+
+extern "C" teuk_status teuk_get_geometry(const teuk_ctx* c, int instance, double* out) {
+    if (!c || !out || instance < 0 || instance >= (int)c->inst.size()) return TEUK_EINVAL;
+    const Instance& I = c->inst[instance];
+    out[0] = I.drs; out[1] = I.dth; out[2] = I.dt; out[3] = I.rp; out[4] = I.rm;
+    out[5] = r_of_rstar_host(I.p.M, I.p.a, I.p.rstar_ext);
+    out[6] = (double)I.i_e; out[7] = I.f_e;
+    return TEUK_OK;
+}
+
 extern "C" teuk_status teuk_adjoint_n(teuk_ctx* c, int instance, int64_t step0, int64_t n,
                                       int64_t ckpt_every, const double* grad_wave,
                                       double* grad_amps, double* grad_r0, double* loss) {
-    (void)step0; (void)n; (void)ckpt_every; (void)grad_wave; (void)grad_amps; (void)grad_r0;
-    (void)loss;
     teuk_status st = check_instance(c, instance);
     if (st) return st;
-    TK_FAIL(c, TEUK_ESTATE, "adjoint not available in this build");
+    Instance& I = c->inst[instance];
+    if (n < 1 || step0 < 0) TK_FAIL(c, TEUK_EINVAL, "need n >= 1 and step0 >= 0");
+    const bool builtin = grad_wave == nullptr;
+    if (builtin && I.step != step0)
+        TK_FAIL(c, TEUK_ESTATE, "built-in loss: the state is at step %lld, not step0 = %lld",
+                (long long)I.step, (long long)step0);
+    cudaStream_t s = c->stream;
+    const int nth = I.p.n_theta;
+    const size_t plane = (size_t)nth * I.pitch * sizeof(double2);
+    AdjBuffers B(s);
+    double2 *lam[2][2], *mu[2];
+    for (int b = 0; b < 2; ++b)
+        for (int k = 0; k < 2; ++k) TK_CUDA(c, B.get((void**)&lam[b][k], plane));
+    for (int k = 0; k < 2; ++k) TK_CUDA(c, B.get((void**)&mu[k], plane));
+    double *gA = nullptr, *gR = nullptr, *lossrec = nullptr, *scal = nullptr;
+    double2* gbar = nullptr;
+    TK_CUDA(c, B.get((void**)&gA, sizeof(double) * n));
+    TK_CUDA(c, B.get((void**)&gR, sizeof(double) * n));
+    TK_CUDA(c, B.get((void**)&scal, sizeof(double) * 3));
+    TK_CUDA(c, B.get((void**)&gbar, sizeof(double2) * nth * (size_t)n));
+    TK_CUDA(c, cudaMemsetAsync(gA, 0, sizeof(double) * n, s));
+    TK_CUDA(c, cudaMemsetAsync(gR, 0, sizeof(double) * n, s));
+    TK_CUDA(c, cudaMemsetAsync(scal, 0, sizeof(double) * 3, s));
+    InstDev d = dev_of(c, I);
+    double r6 = 0.0;
+    // forward-sweep helpers ------------------------------------------------
+    // run `count` steps on the buffers of dv (which start in buffer cur), recording
+    // levels into the ring of dv; returns the buffer holding the result.
+    auto forward = [&](InstDev dv, int cur, int64_t level, int64_t count, int chunk) {
+        for (int64_t k = 0; k < count; ++k) {
+            launch_step(s, dv, level + k, cur, chunk);
+            c->launches++;
+            cur = 1 - cur;
+        }
+        launch_extract(s, dv, level + count, cur);
+        c->launches++;
+        return cur;
+    };
+    const int chunk = eff_chunk(c, I);
+    // the segment plan: segments [a_k, a_k + len_k) of the steps step0 .. step0+n-1
+    int64_t K = (builtin && ckpt_every > 0) ? ckpt_every : n;
+    int64_t nseg = (n + K - 1) / K;
+    void* ckpt = nullptr;
+    void* scratch_state[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    double2* segrec = nullptr;
+    const int nplanes = I.p.prec == TEUK_FP32 ? 1 : 2;
+    if (builtin) {
+        r6 = std::pow(r_of_rstar_host(I.p.M, I.p.a, I.p.rstar_ext), 6);
+        TK_CUDA(c, B.get((void**)&lossrec, sizeof(double) * n));
+        TK_CUDA(c, B.get((void**)&segrec, sizeof(double2) * nth * (size_t)(K + 1)));
+        if (ckpt_every > 0) {
+            TK_CUDA(c, B.get(&ckpt, I.plane_bytes * nplanes * (size_t)nseg));
+            for (int b = 0; b < 2; ++b)
+                for (int k = 0; k < nplanes; ++k)
+                    TK_CUDA(c, B.get(&scratch_state[b][k], I.plane_bytes));
+        }
+        // forward sweep on the context's own state, checkpointing each segment start
+        InstDev fw = d;
+        fw.wave = segrec;
+        fw.wave_cap = K + 1;
+        for (int64_t sg = 0; sg < nseg; ++sg) {
+            int64_t a = step0 + sg * K, len = std::min(K, n - sg * K);
+            if (ckpt)
+                for (int k = 0; k < nplanes; ++k)
+                    TK_CUDA(c, cudaMemcpyAsync((char*)ckpt + ((size_t)sg * nplanes + k) * I.plane_bytes,
+                                               I.state[I.cur][k], I.plane_bytes,
+                                               cudaMemcpyDeviceToDevice, s));
+            fw = dev_of(c, I);
+            fw.wave = segrec;
+            fw.wave_cap = K + 1;
+            I.cur = forward(fw, I.cur, a, len, chunk);
+            I.step = a + len;
+            if (!ckpt) {  // one segment holds everything: take the loss now
+                launch_loss_records(s, segrec, K + 1, nth, a + 1, len, r6, lossrec + (a - step0),
+                                    gbar + (size_t)(a - step0) * nth);
+                c->launches++;
+            }
+        }
+        I.wave_lo = I.wave_hi = I.step;  // the forward records went to the adjoint's own buffer
+    } else {
+        TK_CUDA(c, cudaMemcpyAsync(gbar, grad_wave, sizeof(double2) * nth * (size_t)n,
+                                   cudaMemcpyHostToDevice, s));
+    }
+    // reverse sweep ----------------------------------------------------------
+    int cur = 0;
+    bool started = false;
+    for (int64_t sg = nseg - 1; sg >= 0; --sg) {
+        int64_t a = step0 + sg * K, len = std::min(K, n - sg * K);
+        if (builtin && ckpt) {
+            // recompute this segment's waveform from its checkpoint
+            InstDev rv = d;
+            for (int k = 0; k < nplanes; ++k) {
+                rv.buf[0][k] = scratch_state[0][k];
+                rv.buf[1][k] = scratch_state[1][k];
+                TK_CUDA(c, cudaMemcpyAsync(scratch_state[0][k],
+                                           (char*)ckpt + ((size_t)sg * nplanes + k) * I.plane_bytes,
+                                           I.plane_bytes, cudaMemcpyDeviceToDevice, s));
+            }
+            rv.wave = segrec;
+            rv.wave_cap = K + 1;
+            forward(rv, 0, a, len, chunk);
+            // records a+1 .. a+len, and also record a (the last record of the previous
+            // segment), which this segment's first reverse step needs before the
+            // previous segment is recomputed; writing it twice stores the same value
+            int64_t lo = a > step0 ? a : a + 1;
+            launch_loss_records(s, segrec, K + 1, nth, lo, a + len - lo + 1, r6,
+                                lossrec + (lo - step0 - 1), gbar + (size_t)(lo - step0 - 1) * nth);
+            c->launches++;
+        }
+        for (int64_t m = a + len - 1; m >= a; --m) {
+            const int64_t k = m - step0;  // step index within the call
+            if (!started) {
+                launch_adj_init(s, d, gbar + (size_t)(n - 1) * nth, lam[cur][0], lam[cur][1]);
+                c->launches++;
+                started = true;
+            }
+            launch_adj_corrector(s, d, lam[cur][0], lam[cur][1], mu[0], mu[1]);
+            c->launches++;
+            if (I.src_on) {
+                launch_adj_source(s, d, m, lam[cur][1], mu[1], gA + k, gR + k);
+                c->launches++;
+            }
+            const double2* gb = k >= 1 ? gbar + (size_t)(k - 1) * nth : nullptr;
+            launch_adj_predictor(s, d, lam[cur][0], lam[cur][1], mu[0], mu[1], gb,
+                                 lam[1 - cur][0], lam[1 - cur][1]);
+            c->launches++;
+            cur = 1 - cur;
+        }
+    }
+    launch_ordered_sum(s, gR, n, scal + 0);
+    c->launches++;
+    if (builtin) {
+        launch_ordered_sum(s, lossrec, n, scal + 1);
+        c->launches++;
+    }
+    TK_CUDA(c, cudaGetLastError());
+    double h[3] = {0, 0, 0};
+    TK_CUDA(c, cudaMemcpyAsync(h, scal, sizeof(double) * 3, cudaMemcpyDeviceToHost, s));
+    if (grad_amps)
+        TK_CUDA(c, cudaMemcpyAsync(grad_amps, gA, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+    TK_CUDA(c, cudaStreamSynchronize(s));
+    if (grad_r0) *grad_r0 = h[0];
+    if (loss && builtin) *loss = h[1];
+    return TEUK_OK;
 }

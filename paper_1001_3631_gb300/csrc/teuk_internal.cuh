@@ -63,6 +63,28 @@ struct InstDev {
 
 enum StatusBits : unsigned int { ST_NONFINITE = 1u, ST_TIMEOUT = 2u, ST_BOUNDS = 4u };
 
+// Batched persistent launch over many instances (teuk_step.cu).  Work items are
+// (relative step s, instance k, theta chunk ck, strip) in that order of priority;
+// items of one step are numbered instance by instance from item_base[k].
+struct BatchDev {
+    const InstDev* inst;        // [n_inst] descriptors of this call
+    const int64_t* item_base;   // [n_inst + 1] first item of each instance within a step
+    const int* chunk;           // [n_inst] theta rows per item
+    const int* nstrip;          // [n_inst] strips per chunk row
+    const int64_t* base_step;   // [n_inst] time level at the start of the call
+    const int* base_bin;        // [n_inst] buffer holding that level
+    const int64_t* n_steps;     // steps of this call (device scalar)
+    int n_inst;
+    int64_t items_per_step;
+    unsigned long long* counter;  // next work item
+    int* flags;                 // [items_per_step] relative steps completed by each item
+    int* abort;                 // set when a wait gives up: everyone stops
+    unsigned int* status;
+    long long spin_limit;       // polls before a wait gives up
+    int64_t skip_release_item;  // testing aid (-1: none): this item of relative step 0 never
+                                // releases its flag, so its neighbours' waits run out
+};
+
 __host__ __device__ inline size_t plane_elems(const InstDev& d) {
     return (size_t)d.nth * (size_t)d.pitch;
 }
@@ -81,11 +103,28 @@ void launch_profile(cudaStream_t st, double M, double a, double rstar_min, doubl
 // teuk_step.cu
 void launch_step(cudaStream_t st, const InstDev& d, int64_t step, int bin, int chunk);
 void launch_extract(cudaStream_t st, const InstDev& d, int64_t step, int bin);
+void launch_batched_step(cudaStream_t st, int prec, const BatchDev& b, int grid);
+int batched_grid(int prec);
+void launch_batched_extract(cudaStream_t st, int prec, const BatchDev& b, int max_nth);
 // teuk_aux.cu
 void launch_import_state(cudaStream_t st, const InstDev& d, int bin, const double* u);
 void launch_export_state(cudaStream_t st, const InstDev& d, int bin, double* u);
 void launch_scan_finite(cudaStream_t st, const InstDev& d, int bin);
 void launch_wave_sum(cudaStream_t st, const double2* wave, int64_t cap, int nth, double dth,
                      int64_t level0, int64_t k_count, double2* out);
+// teuk_adjoint.cu
+void launch_adj_corrector(cudaStream_t st, const InstDev& d, const double2* lF, const double2* lP,
+                          double2* mF, double2* mP);
+void launch_adj_predictor(cudaStream_t st, const InstDev& d, const double2* lF, const double2* lP,
+                          const double2* mF, const double2* mP, const double2* gbar, double2* oF,
+                          double2* oP);
+void launch_adj_init(cudaStream_t st, const InstDev& d, const double2* gbar, double2* oF,
+                     double2* oP);
+void launch_adj_source(cudaStream_t st, const InstDev& d, int64_t n, const double2* lP,
+                       const double2* mP, double* gA, double* gR);
+void launch_loss_records(cudaStream_t st, const double2* wave, int64_t cap, int nth,
+                         int64_t level0, int64_t count, double r6, double* lossrec,
+                         double2* gbar);
+void launch_ordered_sum(cudaStream_t st, const double* v, int64_t n, double* out);
 
 }  // namespace teuk

@@ -33,16 +33,14 @@
 
 namespace teuk {
 
+// One work item: the strip `strip` (columns 30*strip .. 30*strip+31) and the theta
+// chunk `ck` (rows ck*chunk .. ) of one step, executed by one whole warp.
 template <class P>
-__global__ void __launch_bounds__(128) step_kernel(InstDev d, int64_t step, int bin, int chunk) {
+__device__ __forceinline__ void step_item(const InstDev& d, int64_t step, int bin, int chunk,
+                                          int strip, int ck) {
     using T = typename P::T;
     using C = Cx<T>;
     const int lane = threadIdx.x & 31;
-    const int gw = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
-    const int nstrip = (d.nr - 2 + 29) / 30;
-    const int nck = (d.nth + chunk - 1) / chunk;
-    if (gw >= nstrip * nck) return;  // whole warps only
-    const int strip = gw % nstrip, ck = gw / nstrip;
     const int i = 30 * strip + lane;
     const bool col_ok = i < d.nr;
     const bool half_ok = lane < 31 && i + 1 < d.nr;
@@ -128,6 +126,15 @@ __global__ void __launch_bounds__(128) step_kernel(InstDev d, int64_t step, int 
     }
 }
 
+template <class P>
+__global__ void __launch_bounds__(128) step_kernel(InstDev d, int64_t step, int bin, int chunk) {
+    const int gw = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
+    const int nstrip = (d.nr - 2 + 29) / 30;
+    const int nck = (d.nth + chunk - 1) / chunk;
+    if (gw >= nstrip * nck) return;  // whole warps only
+    step_item<P>(d, step, bin, chunk, gw % nstrip, gw / nstrip);
+}
+
 // Waveform record of the state in buffer bin (time level `step`): one thread per row.
 template <class P>
 __global__ void extract_kernel(InstDev d, int64_t step, int bin) {
@@ -140,6 +147,121 @@ __global__ void extract_kernel(InstDev d, int64_t step, int bin) {
     double2 w = make_double2((1.0 - f) * a.x + f * b.x, (1.0 - f) * a.y + f * b.y);
     d.wave[(size_t)(step % d.wave_cap) * d.nth + j] = w;
     if (!isfinite(w.x) || !isfinite(w.y)) atomicOr(d.status, (unsigned)ST_NONFINITE);
+}
+
+// ---------------------------------------------------------------- batched path
+__device__ __forceinline__ int ld_acquire(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(int* p, int v) {
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Wait until the items of the 3x3 neighbourhood (strips strip-1..strip+1, chunks
+// ck-1..ck+1) have completed relative step s-1.  That covers what this item reads
+// (halo of one column and two rows) and what it overwrites (the buffer the
+// neighbours of step s-1 read).  Lanes 0..8 each poll one neighbour with acquire
+// loads; the wait gives up after spin_limit polls.  Returns false on give-up or abort.
+__device__ bool wait_neighbours(const BatchDev& b, const int* fl, int nstrip, int nck, int strip,
+                                int ck, int64_t s) {
+    const int lane = threadIdx.x & 31;
+    bool ok = true;
+    if (lane < 9) {
+        int st = strip + lane % 3 - 1, c = ck + lane / 3 - 1;
+        if (st >= 0 && st < nstrip && c >= 0 && c < nck) {
+            const int* f = fl + (size_t)c * nstrip + st;
+            long long it = 0;
+            while (ld_acquire(f) < (int)s) {
+                if (++it > b.spin_limit || *(volatile int*)b.abort) { ok = false; break; }
+                __nanosleep(64);
+            }
+        }
+    }
+    ok = __all_sync(kFull, ok);
+    __threadfence();
+    return ok;
+}
+
+template <class P>
+__global__ void __launch_bounds__(128) batched_step_kernel(BatchDev b) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nsteps = *b.n_steps;
+    const int64_t total = b.items_per_step * nsteps;
+    for (;;) {
+        unsigned long long g = 0;
+        if (lane == 0) g = atomicAdd(b.counter, 1ull);
+        g = __shfl_sync(kFull, g, 0);
+        if ((int64_t)g >= total) return;
+        if (*(volatile int*)b.abort) return;
+        const int64_t s = (int64_t)g / b.items_per_step, r = (int64_t)g % b.items_per_step;
+        int lo = 0, hi = b.n_inst - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (b.item_base[mid] <= r) lo = mid; else hi = mid - 1;
+        }
+        const int k = lo;
+        const int64_t local = r - b.item_base[k];
+        const InstDev d = b.inst[k];
+        const int nstrip = b.nstrip[k], chunk = b.chunk[k];
+        const int nck = (d.nth + chunk - 1) / chunk;
+        const int ck = (int)(local / nstrip), strip = (int)(local % nstrip);
+        int* fl = b.flags + b.item_base[k];
+        if (s > 0 && !wait_neighbours(b, fl, nstrip, nck, strip, ck, s)) {
+            if (lane == 0) {
+                atomicOr(b.status, (unsigned)ST_TIMEOUT);
+                atomicExch(b.abort, 1);
+            }
+            return;
+        }
+        step_item<P>(d, b.base_step[k] + s, (int)((b.base_bin[k] + s) & 1), chunk, strip, ck);
+        __threadfence();
+        __syncwarp();
+        if (lane == 0 && !(s == 0 && r == b.skip_release_item)) st_release(fl + local, (int)(s + 1));
+    }
+}
+
+// Waveform record of the final level of every instance (block row y = instance).
+template <class P>
+__global__ void batched_extract_kernel(BatchDev b) {
+    const int k = blockIdx.y;
+    const InstDev& d = b.inst[k];
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= d.nth) return;
+    const int64_t n = *b.n_steps;
+    const int bin = (int)((b.base_bin[k] + n) & 1);
+    const int64_t step = b.base_step[k] + n;
+    const Planes<P> in = Planes<P>::of(d, bin);
+    size_t o = (size_t)j * d.pitch + d.i_e;
+    double2 a = in.load(o).phi64(), c = in.load(o + 1).phi64();
+    double f = d.f_e;
+    double2 w = make_double2((1.0 - f) * a.x + f * c.x, (1.0 - f) * a.y + f * c.y);
+    d.wave[(size_t)(step % d.wave_cap) * d.nth + j] = w;
+    if (!isfinite(w.x) || !isfinite(w.y)) atomicOr(d.status, (unsigned)ST_NONFINITE);
+}
+
+int batched_grid(int prec) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (prec == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batched_step_kernel<P64>, 128, 0);
+    else if (prec == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batched_step_kernel<P32>, 128, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batched_step_kernel<PK>, 128, 0);
+    return (per > 0 ? per : 1) * (sms > 0 ? sms : 1);
+}
+
+void launch_batched_step(cudaStream_t st, int prec, const BatchDev& b, int grid) {
+    if (prec == 0) batched_step_kernel<P64><<<grid, 128, 0, st>>>(b);
+    else if (prec == 1) batched_step_kernel<P32><<<grid, 128, 0, st>>>(b);
+    else batched_step_kernel<PK><<<grid, 128, 0, st>>>(b);
+}
+
+void launch_batched_extract(cudaStream_t st, int prec, const BatchDev& b, int max_nth) {
+    dim3 g((max_nth + 127) / 128, b.n_inst);
+    if (prec == 0) batched_extract_kernel<P64><<<g, 128, 0, st>>>(b);
+    else if (prec == 1) batched_extract_kernel<P32><<<g, 128, 0, st>>>(b);
+    else batched_extract_kernel<PK><<<g, 128, 0, st>>>(b);
 }
 
 void launch_step(cudaStream_t st, const InstDev& d, int64_t step, int bin, int chunk) {

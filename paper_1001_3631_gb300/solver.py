@@ -5,6 +5,8 @@ source and the extraction all run in the library's CUDA kernels."""
 from __future__ import annotations
 
 import ctypes
+import json
+import os
 
 import numpy as np
 
@@ -133,8 +135,57 @@ class TeukSolver:
               self.ctx)
         return s.value, dt.value
 
+    def geometry(self, instance=0):
+        """dict(drs, dth, dt, rp, rm, r_ext, i_e, f_e) of one instance."""
+        out = np.zeros(8)
+        check(_lib.load().teuk_get_geometry(self.ctx, instance, ptr(out)), self.ctx)
+        return dict(drs=out[0], dth=out[1], dt=out[2], rp=out[3], rm=out[4], r_ext=out[5],
+                    i_e=int(out[6]), f_e=out[7])
+
     def set_tiling(self, theta_chunk=0, steps_per_launch=0):
         check(_lib.load().teuk_set_tiling(self.ctx, theta_chunk, steps_per_launch), self.ctx)
 
     def kernel_launches(self):
         return _lib.load().teuk_kernel_launches(self.ctx)
+
+    def set_instance_tiling(self, instance, theta_chunk):
+        check(_lib.load().teuk_set_instance_tiling(self.ctx, instance, theta_chunk), self.ctx)
+
+    def set_fault_injection(self, skip_release_item=-1, spin_limit=0):
+        check(_lib.load().teuk_set_fault_injection(self.ctx, skip_release_item, spin_limit),
+              self.ctx)
+
+    def autotune(self, trial_steps=10, cache_path=None):
+        """Theta chunk per instance from a cached table keyed by (GPU, n_theta, precision,
+        n_rstar bucket); classes missing from the table are timed by teuk_autotune."""
+        import torch
+        path = cache_path or os.environ.get("TEUK_TUNE_CACHE") or os.path.join(
+            os.path.expanduser("~"), ".cache", "teuk_gb300", "tune.json")
+        gpu = torch.cuda.get_device_name()
+        keys = ["%s|%d|%d|%d" % (gpu, p.n_theta, p.prec, int(np.ceil(np.log2(p.n_rstar))))
+                for p in self.params]
+        table = {}
+        if os.path.exists(path):
+            try:
+                with open(path) as f:
+                    table = json.load(f)
+            except (OSError, ValueError):
+                table = {}
+        if all(k in table for k in keys):
+            for i, k in enumerate(keys):
+                self.set_instance_tiling(i, int(table[k]))
+            return [int(table[k]) for k in keys]
+        chosen = np.zeros(self.n, dtype=np.int32)
+        check(_lib.load().teuk_autotune(self.ctx, trial_steps, chosen.ctypes.data_as(ctypes.c_void_p)),
+              self.ctx)
+        for k, c in zip(keys, chosen):
+            table[k] = int(c)
+        try:
+            os.makedirs(os.path.dirname(path), exist_ok=True)
+            tmp = path + ".tmp%d" % os.getpid()
+            with open(tmp, "w") as f:
+                json.dump(table, f, indent=1, sort_keys=True)
+            os.replace(tmp, path)
+        except OSError:
+            pass
+        return [int(c) for c in chosen]
