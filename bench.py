@@ -236,6 +236,70 @@ def accuracy(cfg, n_steps=4000, probe=12.0):
     return res
 
 
+def batched_leg(n_calls=4, steps_per_call=25, warm_calls=2):
+    """The 128-instance uneven workload (8 modes x 16 orbits) in FP32-Kahan: one
+    persistent launch per call, replayed from a CUDA graph on a side stream, tiles from
+    the autotuner's cached table."""
+    import torch
+
+    from paper_1001_3631_gb300 import TeukSolver, inputs
+    insts = inputs.batched_uneven()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        s = TeukSolver([dict(i["params"], prec="fp32_kahan") for i in insts], stream=stream)
+        for k, inst in enumerate(insts):
+            s.set_source(inst["r0"], instance=k)
+        chunks = s.autotune(trial_steps=5)
+        for _ in range(warm_calls):
+            s.step(steps_per_call)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        stream.synchronize()
+        e0.record(stream)
+        for _ in range(n_calls):
+            s.step(steps_per_call)
+        e1.record(stream)
+        stream.synchronize()
+        ms = e0.elapsed_time(e1)
+        s.sync()
+        npts = sum(i["params"]["n_rstar"] * i["params"]["n_theta"] for i in insts)
+        s.close()
+    return {"workload": "128 instances: m=1..8 x 16 orbits, N_r* in {2048..16384}, "
+                        "N_theta in {64,128,256} (seed 3003), FP32-Kahan",
+            "value": npts * n_calls * steps_per_call / (ms * 1e-3), "unit": "updates/s",
+            "points": npts, "steps_timed": n_calls * steps_per_call,
+            "ms_per_call": ms / n_calls, "launches_per_call": 2,
+            "distinct_chunks": sorted(set(chunks))}
+
+
+def single_mode_leg(steps=2000):
+    """The 800 x 64 single mode (51,200 points, L2-resident): one kernel per step on the
+    default stream versus the whole run in one persistent launch from a CUDA graph."""
+    import torch
+
+    from paper_1001_3631_gb300 import TeukSolver, inputs
+    cfg = inputs.SINGLE_MODE_800x64
+    out = {"workload": "single mode 800x64 (s=-2, m=2, a=0.9), %d steps" % steps}
+    for prec in ("fp64", "fp32_kahan"):
+        for mode in ("per_step", "persistent"):
+            stream = torch.cuda.Stream()
+            with torch.cuda.stream(stream):
+                s = TeukSolver(dict(cfg["params"], prec=prec), stream=stream)
+                s.set_tiling(0, 1 if mode == "per_step" else 0)
+                s.set_source(cfg["r0"])
+                s.step(steps)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                stream.synchronize()
+                e0.record(stream)
+                s.step(steps)
+                e1.record(stream)
+                stream.synchronize()
+                ms = e0.elapsed_time(e1)
+                s.close()
+            out["%s_%s" % (prec, mode)] = 51200 * steps / (ms * 1e-3)
+    out["unit"] = "updates/s"
+    return out
+
+
 def cpu_baseline(cfg, budget_s=12.0):
     """The oracle (single-threaded FP64 C) on the same grid, per-step time from the
     difference of two run lengths (so its setup is excluded)."""
@@ -360,6 +424,8 @@ def main():
         "clocks": clocks,
     }
     if not args.no_extras:
+        line["batched"] = batched_leg()
+        line["single_mode_800x64"] = single_mode_leg()
         line["accuracy"] = accuracy(cfg, n_steps=args.accuracy_steps)
         line["e2e"] = e2e_path("fp32_kahan", cfg, S, max(2, K // 2), 1)
         if not args.no_cpu_baseline:

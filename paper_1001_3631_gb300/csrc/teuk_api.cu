@@ -29,6 +29,8 @@ struct Instance {
     void* coef_i = nullptr;
     double* x_int = nullptr;
     double* x_half = nullptr;
+    RTab* rtab = nullptr;       // [2][nr]: half nodes, then integer nodes (FP32 paths)
+    ThTab* thtab = nullptr;     // [nth]
     // source
     bool src_on = false;
     teuk_orbit orbit{};
@@ -162,6 +164,9 @@ InstDev dev_of(const teuk_ctx* c, const Instance& I) {
         for (int k = 0; k < 2; ++k) d.buf[b][k] = I.state[b][k];
     d.coef_h = I.coef_h;
     d.coef_i = I.coef_i;
+    d.rtab_h = I.rtab;
+    d.rtab_i = I.rtab ? I.rtab + I.p.n_rstar : nullptr;
+    d.thtab = I.thtab;
     d.src = I.sd;
     d.src.on = I.src_on ? 1 : 0;
     d.i_e = I.i_e;
@@ -202,7 +207,7 @@ void free_instance(cudaStream_t s, Instance& I) {
     for (int b = 0; b < 2; ++b)
         for (int k = 0; k < 2; ++k)
             if (I.state[b][k]) cudaFreeAsync(I.state[b][k], s);
-    void* ptrs[] = {I.coef_h, I.coef_i, I.x_int, I.x_half, I.P_win, I.amps, I.wave};
+    void* ptrs[] = {I.coef_h, I.coef_i, I.x_int, I.x_half, I.P_win, I.amps, I.wave, I.rtab, I.thtab};
     for (void* q : ptrs)
         if (q) cudaFreeAsync(q, s);
     I = Instance();
@@ -286,6 +291,13 @@ extern "C" teuk_status teuk_create(const teuk_params* p, int n_instances, void* 
         launch_coefficients(c->stream, q.prec, q.M, q.a, q.s, q.m, q.rstar_min, I.drs, I.dth,
                             I.dt, q.n_rstar, q.n_theta, I.pitch, I.x_int, I.x_half, I.coef_h,
                             I.coef_i);
+        if (q.prec != TEUK_FP64) {
+            TK_CCUDA(cudaMallocAsync((void**)&I.rtab, sizeof(RTab) * 2 * q.n_rstar, c->stream));
+            TK_CCUDA(cudaMallocAsync((void**)&I.thtab, sizeof(ThTab) * q.n_theta, c->stream));
+            launch_tables_1d(c->stream, q.M, q.a, q.s, q.m, I.drs, I.dth, I.dt, q.n_rstar,
+                             q.n_theta, I.x_int, I.x_half, I.rtab, I.rtab + q.n_rstar, I.thtab);
+            c->launches++;
+        }
         c->launches += 2;
         TK_CCUDA(cudaGetLastError());
         I.r_ext = 0;  // filled lazily from x at r*_ext when needed (adjoint loss)

@@ -45,6 +45,19 @@ struct SourceDev {
     int64_t n_amps;
 };
 
+// FP32 paths form their coefficients in registers from these 1D tables (rounded from
+// FP64 at setup), instead of reading 2D tables every step.  Per radial node and
+// sub-step fraction s (1/2 at half nodes, 1 at integer nodes), sdt = s dt:
+//   Sigma^2 = R2 - aD sin^2,  iS = 1/Sigma^2,  rs = Sigma^{-1}
+//   g  = Rd * rs                                     (Rd = sdt R / dr*)
+//   c_t = (ctr iS, (cti + ctc cos) iS),  E1 = -sdt c_t
+//   E2 = c_t g + ((pr - bb sin^2 iS) iS, pi iS)      (pr, pi, bb scaled by sdt/dr*)
+//   ep, em = Ds iS (1/dth^2 +- cot/(2 dth))          (Ds = sdt Delta)
+//   E3 = ((qr - Ds V) iS, qi iS)                      (qr, qi scaled by sdt)
+struct RTab { float R2, aD, Rd, ctr, cti, ctc, pr, pi, bb, Ds, qr, qi, sdt, pad0, pad1, pad2; };
+// Per theta row: sin^2, cos, V = (m + s cos)^2/sin^2 - s, th_p, th_m = 1/dth^2 +- cot/(2 dth)
+struct ThTab { float sin2, cs, V, thp, thm, pad0, pad1, pad2; };
+
 struct InstDev {
     int nr, nth, pitch, prec;
     double drs, dth, dt;
@@ -53,6 +66,9 @@ struct InstDev {
     void* buf[2][2];          // [ping-pong buffer][plane]
     const void* coef_h;       // [9][nth][pitch] (double or float)
     const void* coef_i;
+    const RTab* rtab_h;       // [nr] FP32 paths: radial tables at half nodes i+1/2
+    const RTab* rtab_i;       // [nr] at integer nodes
+    const ThTab* thtab;       // [nth]
     SourceDev src;
     int i_e;                  // extraction between i_e and i_e + 1
     double f_e;
@@ -97,6 +113,9 @@ void launch_coefficients(cudaStream_t st, int prec, double M, double a, int s, i
                          double rstar_min, double drs, double dth, double dt, int nr, int nth,
                          int pitch, const double* x_int, const double* x_half, void* coef_h,
                          void* coef_i);
+void launch_tables_1d(cudaStream_t st, double M, double a, int s, int m, double drs, double dth,
+                      double dt, int nr, int nth, const double* x_int, const double* x_half,
+                      RTab* rtab_h, RTab* rtab_i, ThTab* thtab);
 void launch_profile(cudaStream_t st, double M, double a, double rstar_min, double drs, double dth,
                     double rs0, double sig_r, double sig_t, double drs0_dr0, const double* x_int,
                     const double* x_half, const SourceDev& src);

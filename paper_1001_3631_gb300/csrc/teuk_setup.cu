@@ -174,6 +174,62 @@ __global__ void profile_kernel(double M, double a, double rstar_min, double drs,
     }
 }
 
+// 1D tables of the FP32 paths (see RTab / ThTab), computed in FP64 and rounded once.
+__device__ RTab radial_table(double M, double a, int s_, int m_, double x, double drs, double sdt) {
+    double d = sqrt(M * M - a * a);
+    double rp = M + d, rm = M - d;
+    double s = (double)s_, m = (double)m_;
+    double r = rp + x;
+    double Delta = x * (x + rp - rm);
+    double R = r * r + a * a;
+    RTab t;
+    t.R2 = (float)(R * R);
+    t.aD = (float)(a * a * Delta);
+    t.Rd = (float)(sdt * R / drs);
+    t.ctr = (float)(2.0 * s * (r * Delta - M * (r * r - a * a)));
+    t.cti = (float)(4.0 * M * a * m * r);
+    t.ctc = (float)(2.0 * s * a * Delta);
+    t.pr = (float)(sdt / drs * (Delta * (6.0 * R / r + 2.0 * r) + 2.0 * R * s * (r - M)));
+    t.pi = (float)(sdt / drs * (2.0 * R * m * a));
+    t.bb = (float)(sdt / drs * (a * a * Delta * (2.0 * R * (r - M) - 4.0 * r * Delta) * 0.5));
+    t.Ds = (float)(sdt * Delta);
+    t.qr = (float)(sdt * (6.0 * Delta * Delta / (r * r) + 6.0 * Delta * (s + 1.0) * (r - M) / r));
+    t.qi = (float)(sdt * (6.0 * Delta * m * a / r + 4.0 * s * m * a * (r - M)));
+    t.sdt = (float)sdt;
+    t.pad0 = t.pad1 = t.pad2 = 0.f;
+    return t;
+}
+
+__global__ void tables_1d_kernel(double M, double a, int s, int m, double drs, double dth,
+                                 double dt, int nr, int nth, const double* x_int,
+                                 const double* x_half, RTab* rtab_h, RTab* rtab_i, ThTab* thtab) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < nr) rtab_i[k] = radial_table(M, a, s, m, x_int[k], drs, dt);
+    if (k < nr - 1) rtab_h[k] = radial_table(M, a, s, m, x_half[k], drs, 0.5 * dt);
+    if (k == nr - 1) rtab_h[k] = RTab{};
+    if (k < nth) {
+        double th = (k + 0.5) * dth, sn, cs;
+        sincos(th, &sn, &cs);
+        double sv = (double)s, mv = (double)m;
+        ThTab t;
+        t.sin2 = (float)(sn * sn);
+        t.cs = (float)cs;
+        t.V = (float)((mv + sv * cs) * (mv + sv * cs) / (sn * sn) - sv);
+        t.thp = (float)(1.0 / (dth * dth) + cs / sn / (2.0 * dth));
+        t.thm = (float)(1.0 / (dth * dth) - cs / sn / (2.0 * dth));
+        t.pad0 = t.pad1 = t.pad2 = 0.f;
+        thtab[k] = t;
+    }
+}
+
+void launch_tables_1d(cudaStream_t st, double M, double a, int s, int m, double drs, double dth,
+                      double dt, int nr, int nth, const double* x_int, const double* x_half,
+                      RTab* rtab_h, RTab* rtab_i, ThTab* thtab) {
+    int n = nr > nth ? nr : nth;
+    tables_1d_kernel<<<(n + 127) / 128, 128, 0, st>>>(M, a, s, m, drs, dth, dt, nr, nth, x_int,
+                                                      x_half, rtab_h, rtab_i, thtab);
+}
+
 void launch_invert_tortoise(cudaStream_t st, double M, double a, double rstar_min, double drs,
                             int nr, double* x_int, double* x_half) {
     invert_tortoise_kernel<<<(nr + 127) / 128, 128, 0, st>>>(M, a, rstar_min, drs, nr, x_int,

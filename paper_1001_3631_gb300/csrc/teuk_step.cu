@@ -48,9 +48,6 @@ __device__ __forceinline__ void step_item(const InstDev& d, int64_t step, int bi
     const bool bnd = (i == 0 || i == d.nr - 1) && (lane <= 30);
     const int j0 = ck * chunk, j1 = min(d.nth, j0 + chunk);
     const int nth = d.nth, pitch = d.pitch;
-    const size_t pl = plane_elems(d);
-    const T* ch = (const T*)d.coef_h;
-    const T* ci = (const T*)d.coef_i;
     const T g = (T)d.ghost;
     const T hdt = (T)(0.5 * d.dt), fdt = (T)d.dt;
     const int ex_strip = d.i_e >= 1 ? (d.i_e - 1) / 30 : 0;
@@ -58,10 +55,19 @@ __device__ __forceinline__ void step_item(const InstDev& d, int64_t step, int bi
 
     // source factors of this step: (dt/2) A_n e^{-i(omega t_n + phase0)} and
     // dt A_n e^{-i(omega (t_n + dt/2) + phase0)}, FP64
+    // only warps whose columns and rows meet the source window need them
+    const int c_lo = 30 * strip, c_hi = 30 * strip + 31, r_lo = j0 - 1, r_hi = j1;
+    const SourceDev& sw = d.src;
+    const bool src_warp = sw.on && r_lo < sw.j_lo + sw.nj && r_hi >= sw.j_lo &&
+                          ((c_lo < sw.i_lo + sw.ni && c_hi >= sw.i_lo) ||
+                           (c_lo < sw.h_lo + sw.nh && c_hi >= sw.h_lo));
     double2 sp_fac = make_double2(0.0, 0.0), sc_fac = make_double2(0.0, 0.0);
-    if (d.src.on) source_factors(d, step, sp_fac, sc_fac);
+    if (src_warp) source_factors(d, step, sp_fac, sc_fac);
 
     const Planes<P> in = Planes<P>::of(d, bin), out = Planes<P>::of(d, 1 - bin);
+    ColTab<P> colh, coli;  // radial coefficient tables of this lane's column (FP32 paths)
+    colh.load(d.rtab_h, i, half_ok);
+    coli.load(d.rtab_i, i, col_ok);
 
     NodeV<P> prev = NodeV<P>::zero();
     Half<T> pend;           // Fb, Pb, dF, dP of the previous loaded row
@@ -93,9 +99,9 @@ __device__ __forceinline__ void step_item(const InstDev& d, int64_t step, int bi
         const int jp = jl - 1;
         if (jl > jl_begin && jp >= jp_lo && jp <= jp_hi) {
             T cf[kNCoef];
-            load_coefs(ch, pl, (size_t)jp * pitch + i, half_ok, cf);
+            get_coefs<P>(d, colh, true, i, jp, half_ok, cf);
             C src = C::zero();
-            if (d.src.on) src = source_half<T>(d.src, sp_fac, i, jp);
+            if (src_warp) src = source_half<T>(d.src, sp_fac, i, jp);
             HalfRec<T> rec = predictor<T>(pend, dp_cur, dp_prev, cf, hdt, src);
             CRow<T> row = combine_lr<T>(rec);
             if (jp == 0) {  // ghost row -1 of the half-node results
@@ -109,16 +115,16 @@ __device__ __forceinline__ void step_item(const InstDev& d, int64_t step, int bi
             ++ring_n;
             ring_top = jp;
             if (ring_n >= 3 && ring_top - 1 >= j0 && ring_top - 1 < j1)
-                corrector<P>(d, in, out, ring, ring_top - 1, i, out_ok, bnd, ex_warp, ci, pl,
-                             fdt, sc_fac, step);
+                corrector<P>(d, in, out, ring, ring_top - 1, i, out_ok, bnd, ex_warp, src_warp,
+                             coli, fdt, sc_fac, step);
             if (jp == nth - 1) {  // ghost row nth
                 CRow<T> gr = row.mirror(g);
                 ring.push(gr);
                 ++ring_n;
                 ring_top = nth;
                 if (ring_n >= 3 && nth - 1 >= j0 && nth - 1 < j1)
-                    corrector<P>(d, in, out, ring, nth - 1, i, out_ok, bnd, ex_warp, ci, pl, fdt,
-                                 sc_fac, step);
+                    corrector<P>(d, in, out, ring, nth - 1, i, out_ok, bnd, ex_warp, src_warp,
+                                 coli, fdt, sc_fac, step);
             }
         }
         pend = cur;
@@ -203,7 +209,7 @@ __global__ void __launch_bounds__(128) batched_step_kernel(BatchDev b) {
         }
         const int k = lo;
         const int64_t local = r - b.item_base[k];
-        const InstDev d = b.inst[k];
+        const InstDev& d = b.inst[k];
         const int nstrip = b.nstrip[k], chunk = b.chunk[k];
         const int nck = (d.nth + chunk - 1) / chunk;
         const int ck = (int)(local / nstrip), strip = (int)(local % nstrip);

@@ -205,6 +205,65 @@ __device__ __forceinline__ void load_coefs(const T* tab, size_t pl, size_t o, bo
     for (int k = 0; k < kNCoef; ++k) cf[k] = ok ? __ldg(tab + k * pl + o) : T(0);
 }
 
+// FP32 coefficients of one node from its radial table and its theta row (see RTab).
+__device__ __forceinline__ void form_coefs(const RTab& t, const ThTab& h, float* cf) {
+    float sig2 = fmaf(-t.aD, h.sin2, t.R2);
+    float iS = __frcp_rn(sig2);
+    float rs = rsqrtf(sig2);
+    rs = rs * fmaf(-0.5f * sig2 * rs, rs, 1.5f);  // one Newton step on 1/sqrt
+    float g = t.Rd * rs;
+    float ctre = t.ctr * iS;
+    float ctim = fmaf(t.ctc, h.cs, t.cti) * iS;
+    cf[C_G] = g;
+    cf[C_E1R] = -t.sdt * ctre;
+    cf[C_E1I] = -t.sdt * ctim;
+    float bbt = t.bb * h.sin2 * iS;
+    cf[C_E2R] = fmaf(ctre, g, (t.pr - bbt) * iS);
+    cf[C_E2I] = fmaf(ctim, g, t.pi * iS);
+    float ws = t.Ds * iS;
+    cf[C_EP] = ws * h.thp;
+    cf[C_EM] = ws * h.thm;
+    cf[C_E3R] = fmaf(-t.Ds, h.V, t.qr) * iS;
+    cf[C_E3I] = t.qi * iS;
+}
+
+// The radial table of one column, held in registers for a whole work item (FP32 paths;
+// empty for FP64, which reads 2D tables).
+template <class P>
+struct ColTab {
+    RTab t;
+    __device__ __forceinline__ void load(const RTab* tab, int i, bool ok) {
+        if constexpr (sizeof(typename P::T) == 4) {
+            if (ok) {
+                const float4* q = (const float4*)(tab + i);
+                float4 a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + 2), e = __ldg(q + 3);
+                t = RTab{a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w, e.x, 0.f, 0.f, 0.f};
+            } else {
+                t = RTab{};
+            }
+        }
+    }
+};
+
+// Coefficients of the predictor (half = true, node i+1/2) or the corrector (node i) at
+// row j: read from the 2D FP64 tables, or formed in registers on the FP32 paths from
+// the column's radial table and the row's theta table.
+template <class P>
+__device__ __forceinline__ void get_coefs(const InstDev& d, const ColTab<P>& col, bool half, int i,
+                                          int j, bool ok, typename P::T* cf) {
+    if constexpr (sizeof(typename P::T) == 8) {
+        load_coefs((const double*)(half ? d.coef_h : d.coef_i), plane_elems(d),
+                   (size_t)j * d.pitch + i, ok, cf);
+    } else {
+        const ThTab h = d.thtab[j];
+        form_coefs(col.t, h, cf);
+        if (!ok) {
+#pragma unroll
+            for (int k = 0; k < kNCoef; ++k) cf[k] = 0.f;
+        }
+    }
+}
+
 // Eq. (13) at the own half node, as an increment on the averaged state.
 template <typename T>
 __device__ __forceinline__ HalfRec<T> predictor(const Half<T>& h, Cx<T> Dp, Cx<T> Dm, const T* cf,
@@ -279,8 +338,8 @@ template <class P>
 __device__ __forceinline__ void corrector(const InstDev& d, const Planes<P>& in,
                                           const Planes<P>& out, const CRing<typename P::T>& ring,
                                           int jc, int i, bool out_ok, bool bnd, bool ex_warp,
-                                          const typename P::T* ci, size_t pl, typename P::T fdt,
-                                          double2 sc_fac, int64_t step) {
+                                          bool src_warp, const ColTab<P>& coli,
+                                          typename P::T fdt, double2 sc_fac, int64_t step) {
     using T = typename P::T;
     using C = Cx<T>;
     const CRow<T>& a = ring.a;
@@ -291,9 +350,9 @@ __device__ __forceinline__ void corrector(const InstDev& d, const Planes<P>& in,
     C Dminus = a.DpS + (b.Hs - a.Hs);
     const size_t o = (size_t)jc * d.pitch + i;
     T cf[kNCoef];
-    load_coefs(ci, pl, o, col_ok, cf);
+    get_coefs<P>(d, coli, false, i, jc, col_ok, cf);
     C src = C::zero();
-    if (d.src.on) src = source_int<T>(d.src, sc_fac, i, jc);
+    if (src_warp) src = source_int<T>(d.src, sc_fac, i, jc);
     C dPhi = rmac(rmac(C::zero(), -cf[C_G], b.dFc), fdt, b.PC);
     C dPi = rmac(src, cf[C_G], b.dPc);
     dPi = cmac(dPi, cf[C_E1R], cf[C_E1I], b.PC);
