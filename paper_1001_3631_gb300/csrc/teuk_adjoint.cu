@@ -39,20 +39,21 @@ __device__ __forceinline__ double cget(const T* tab, size_t pl, int k, size_t o)
 // Cotangent of the averaged Phi~ at (col, j) produced by the angular term of the
 // sub-step whose coefficients are `tab` and whose Pi cotangents are L (col fixed).
 template <typename T>
-__device__ __forceinline__ Z theta_cotangent(const T* tab, size_t pl, const double2* LP, int pitch,
-                                             int nth, int col, int j, double g) {
-    size_t o = (size_t)j * pitch + col;
+__device__ __forceinline__ Z theta_cotangent(const T* tab, size_t pl, const double2* LP,
+                                             const InstDev& d, int col, int j, double g) {
+    const int nth = d.nth;
+    size_t o = node_index(d, col, j);
     Z l0 = zld(LP, o);
     double ep0 = cget(tab, pl, C_EP, o), em0 = cget(tab, pl, C_EM, o);
     Z r = zconjmul(cget(tab, pl, C_E3R, o) - ep0 - em0, cget(tab, pl, C_E3I, o), l0);
     if (j >= 1) {
-        size_t om = o - pitch;
+        size_t om = o - 1;   // row j-1
         r = zadd(r, zscale(cget(tab, pl, C_EP, om), zld(LP, om)));
     } else {
         r = zadd(r, zscale(g * em0, l0));   // ghost row -1 = g * row 0
     }
     if (j + 1 < nth) {
-        size_t op = o + pitch;
+        size_t op = o + 1;   // row j+1
         r = zadd(r, zscale(cget(tab, pl, C_EM, op), zld(LP, op)));
     } else {
         r = zadd(r, zscale(g * ep0, l0));   // ghost row nth = g * row nth-1
@@ -64,12 +65,11 @@ __device__ __forceinline__ Z theta_cotangent(const T* tab, size_t pl, const doub
 template <typename T>
 __global__ void adj_corrector_kernel(InstDev d, const double2* lF, const double2* lP, double2* mF,
                                      double2* mP) {
-    int h = blockIdx.x * blockDim.x + threadIdx.x;
-    int j = blockIdx.y;
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    int h = blockIdx.y;
     if (h > d.nr - 2 || j >= d.nth) return;
     const T* ci = (const T*)d.coef_i;
     const size_t pl = plane_elems(d);
-    const int pitch = d.pitch;
     Z muF = {0, 0}, muP = {0, 0};
     // integer node h (this half node is its right neighbour R, sign +1) and
     // integer node h+1 (this half node is its left neighbour L, sign -1)
@@ -77,10 +77,10 @@ __global__ void adj_corrector_kernel(InstDev d, const double2* lF, const double2
         int col = h + side;
         if (col < 1 || col > d.nr - 2) continue;   // P: boundary columns carry no cotangent
         double sR = side == 0 ? 1.0 : -1.0;
-        size_t o = (size_t)j * pitch + col;
+        size_t o = node_index(d, col, j);
         Z LF = zld(lF, o), LPi = zld(lP, o);
         double G = cget(ci, pl, C_G, o);
-        Z tc = theta_cotangent<T>(ci, pl, lP, pitch, d.nth, col, j, d.ghost);
+        Z tc = theta_cotangent<T>(ci, pl, lP, d, col, j, d.ghost);
         // Delta Phi = -G (hF_R - hF_L) + dt (hP_R + hP_L)/2
         // Delta Pi  =  G (hP_R - hP_L) + E1 (hP_R + hP_L)/2 + E2 (hF_R - hF_L) + angular(Phi~)
         muF = zadd(muF, zscale(-sR * G, LF));
@@ -90,7 +90,7 @@ __global__ void adj_corrector_kernel(InstDev d, const double2* lF, const double2
         muP = zadd(muP, zscale(sR * G, LPi));
         muP = zadd(muP, zscale(0.5, zconjmul(cget(ci, pl, C_E1R, o), cget(ci, pl, C_E1I, o), LPi)));
     }
-    size_t oh = (size_t)j * pitch + h;
+    size_t oh = node_index(d, h, j);
     mF[oh] = make_double2(muF.x, muF.y);
     mP[oh] = make_double2(muP.x, muP.y);
 }
@@ -100,13 +100,12 @@ template <typename T>
 __global__ void adj_predictor_kernel(InstDev d, const double2* lF, const double2* lP,
                                      const double2* mF, const double2* mP, const double2* gbar,
                                      double2* oF, double2* oP) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    int j = blockIdx.y;
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    int i = blockIdx.y;
     if (i >= d.nr || j >= d.nth) return;
     const T* ch = (const T*)d.coef_h;
     const size_t pl = plane_elems(d);
-    const int pitch = d.pitch;
-    const size_t o = (size_t)j * pitch + i;
+    const size_t o = node_index(d, i, j);
     const bool interior = i >= 1 && i <= d.nr - 2;
     Z aF = interior ? zld(lF, o) : Z{0, 0};
     Z aP = interior ? zld(lP, o) : Z{0, 0};
@@ -117,10 +116,10 @@ __global__ void adj_predictor_kernel(InstDev d, const double2* lF, const double2
         int h = i - 1 + side;
         if (h < 0 || h > d.nr - 2) continue;
         double sR = side == 0 ? 1.0 : -1.0;
-        size_t oh = (size_t)j * pitch + h;
+        size_t oh = node_index(d, h, j);
         Z MF = zld(mF, oh), MP = zld(mP, oh);
         double G = cget(ch, pl, C_G, oh);
-        Z tc = theta_cotangent<T>(ch, pl, mP, pitch, d.nth, h, j, d.ghost);
+        Z tc = theta_cotangent<T>(ch, pl, mP, d, h, j, d.ghost);
         // hF = (F_L + F_R)/2 - G (F_R - F_L) + hdt (P_L + P_R)/2
         // hP = (P_L + P_R)/2 + G (P_R - P_L) + E1 (P_L + P_R)/2 + E2 (F_R - F_L) + angular(Fbar)
         aF = zadd(aF, zscale(0.5 - sR * G, MF));
@@ -140,10 +139,10 @@ __global__ void adj_predictor_kernel(InstDev d, const double2* lF, const double2
 
 // lam = E^T gbar (the start of the reverse sweep).
 __global__ void adj_init_kernel(InstDev d, const double2* gbar, double2* oF, double2* oP) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    int j = blockIdx.y;
-    if (i >= d.pitch || j >= d.nth) return;
-    size_t o = (size_t)j * d.pitch + i;
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    int i = blockIdx.y;
+    if (j >= d.pitch || i >= d.nr) return;
+    size_t o = node_index(d, i, j);
     Z a = {0, 0};
     if (gbar && i == d.i_e) a = zscale(1.0 - d.f_e, zld(gbar, j));
     if (gbar && i == d.i_e + 1) a = zscale(d.f_e, zld(gbar, j));
@@ -174,7 +173,7 @@ __global__ void adj_source_kernel(InstDev d, int64_t n, const double2* lP, const
         double w;
         if (k < nh_tot) {
             int jj = k / s.nh, hh = k % s.nh;
-            size_t o = (size_t)(s.j_lo + jj) * d.pitch + (s.h_lo + hh);
+            size_t o = node_index(d, s.h_lo + hh, s.j_lo + jj);
             lam = zld(mP, o);
             P = {s.P_half[k].x, s.P_half[k].y};
             dP = {s.dP_half[k].x, s.dP_half[k].y};
@@ -184,7 +183,7 @@ __global__ void adj_source_kernel(InstDev d, int64_t n, const double2* lP, const
             int jj = kk / s.ni, ii = kk % s.ni;
             int col = s.i_lo + ii;
             if (col < 1 || col > d.nr - 2) continue;
-            size_t o = (size_t)(s.j_lo + jj) * d.pitch + col;
+            size_t o = node_index(d, col, s.j_lo + jj);
             lam = zld(lP, o);
             P = {s.P_int[kk].x, s.P_int[kk].y};
             dP = {s.dP_int[kk].x, s.dP_int[kk].y};
@@ -241,7 +240,7 @@ __global__ void ordered_sum_kernel(const double* v, int64_t n, double* out) {
 
 void launch_adj_corrector(cudaStream_t st, const InstDev& d, const double2* lF, const double2* lP,
                           double2* mF, double2* mP) {
-    dim3 g((d.nr - 1 + 127) / 128, d.nth);
+    dim3 g((d.nth + 127) / 128, d.nr - 1);
     if (d.prec == 0) adj_corrector_kernel<double><<<g, 128, 0, st>>>(d, lF, lP, mF, mP);
     else adj_corrector_kernel<float><<<g, 128, 0, st>>>(d, lF, lP, mF, mP);
 }
@@ -249,7 +248,7 @@ void launch_adj_corrector(cudaStream_t st, const InstDev& d, const double2* lF, 
 void launch_adj_predictor(cudaStream_t st, const InstDev& d, const double2* lF, const double2* lP,
                           const double2* mF, const double2* mP, const double2* gbar, double2* oF,
                           double2* oP) {
-    dim3 g((d.nr + 127) / 128, d.nth);
+    dim3 g((d.nth + 127) / 128, d.nr);
     if (d.prec == 0)
         adj_predictor_kernel<double><<<g, 128, 0, st>>>(d, lF, lP, mF, mP, gbar, oF, oP);
     else
@@ -258,7 +257,7 @@ void launch_adj_predictor(cudaStream_t st, const InstDev& d, const double2* lF, 
 
 void launch_adj_init(cudaStream_t st, const InstDev& d, const double2* gbar, double2* oF,
                      double2* oP) {
-    dim3 g((d.pitch + 127) / 128, d.nth);
+    dim3 g((d.pitch + 127) / 128, d.nr);
     adj_init_kernel<<<g, 128, 0, st>>>(d, gbar, oF, oP);
 }
 

@@ -43,22 +43,31 @@ struct Instance {
     int64_t wave_cap = 0, wave_lo = 0, wave_hi = 0;
     int i_e = 0;
     double f_e = 0, r_ext = 0;
-    int chunk = 0;      // theta rows per work item chosen for this instance (0 = context default)
+    int strip = 0;      // r* columns per work item chosen for this instance (0 = context default)
 };
 
-// Device side of the batched persistent launch of one context.
-struct Batch {
-    bool alloc = false;
-    char* d_blob = nullptr;       // descriptors of the current call
-    size_t blob_bytes = 0;
+// Device side of the batched persistent launch of one context: one persistent kernel
+// per block-size class (instances whose theta pitch is the same), run one after the
+// other (classes are independent).
+struct BatchClass {
+    int pitch = 0;                  // threads per block
+    std::vector<int> members;       // instance indices
+    size_t off = 0;                 // descriptor offset in the blob
     unsigned long long* d_counter = nullptr;
     int* d_flags = nullptr;
     int64_t flags_cap = 0;
-    int* d_abort = nullptr;
-    int64_t items_per_step = -1;
+    int64_t items = -1;
     int grid = 0;
     int max_nth = 0;
     BatchDev bd{};
+};
+
+struct Batch {
+    bool alloc = false;
+    char* d_blob = nullptr;         // descriptors of the current call, all classes
+    size_t blob_bytes = 0;
+    int* d_abort = nullptr;
+    std::vector<BatchClass> cls;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     bool graph_failed = false;
@@ -72,7 +81,7 @@ struct teuk_ctx {
     std::vector<Instance> inst;
     unsigned* status = nullptr;
     std::string err;
-    int chunk = 0;           // theta rows per warp task (0 = automatic)
+    int strip = 0;           // r* columns per thread block (0 = automatic)
     int steps_per_launch = 1;
     int64_t launches = 0;
     Batch batch;
@@ -144,7 +153,7 @@ std::string derive(const teuk_params& p, Instance& I) {
     if (ie > p.n_rstar - 2) ie = p.n_rstar - 2;
     I.i_e = ie;
     I.f_e = (p.rstar_ext - (p.rstar_min + ie * I.drs)) / I.drs;
-    I.pitch = (p.n_rstar + kPitchAlign - 1) / kPitchAlign * kPitchAlign;
+    I.pitch = (p.n_theta + kPitchAlign - 1) / kPitchAlign * kPitchAlign;
     I.wave_cap = p.wave_capacity > 0 ? p.wave_capacity : 4096;
     return "";
 }
@@ -177,22 +186,25 @@ InstDev dev_of(const teuk_ctx* c, const Instance& I) {
     return d;
 }
 
-int auto_chunk(const Instance& I) {
-    // at least 16 warp tasks per SM (152 SMs), chunks of at least 16 rows
-    int nstrip = (I.p.n_rstar - 2 + 29) / 30;
-    int chunk = I.p.n_theta;
-    while (chunk > 16 && (int64_t)nstrip * ((I.p.n_theta + chunk - 1) / chunk) < 152 * 16)
-        chunk /= 2;
-    return chunk;
+// Strip length so that the grid holds about 16 warps per SM on 152 SMs, at least
+// 8 columns (a strip reads 2 columns beyond its outputs).
+int auto_strip(const Instance& I) {
+    int warps_per_block = I.pitch / 32;
+    int64_t blocks = (int64_t)152 * 16 / (warps_per_block > 0 ? warps_per_block : 1);
+    int64_t cols = I.p.n_rstar - 2;
+    int64_t L = (cols + blocks - 1) / blocks;
+    if (L < 8) L = 8;
+    if (L > 512) L = 512;
+    return (int)L;
 }
 
-int eff_chunk(const teuk_ctx* c, const Instance& I) {
-    int ch = I.chunk > 0 ? I.chunk : (c->chunk > 0 ? c->chunk : auto_chunk(I));
-    return std::max(1, std::min(ch, I.p.n_theta));
+int eff_strip(const teuk_ctx* c, const Instance& I) {
+    int L = I.strip > 0 ? I.strip : (c->strip > 0 ? c->strip : auto_strip(I));
+    return std::max(1, std::min(L, I.p.n_rstar - 2));
 }
 
-void do_step(teuk_ctx* c, Instance& I, int chunk) {
-    launch_step(c->stream, dev_of(c, I), I.step, I.cur, chunk);
+void do_step(teuk_ctx* c, Instance& I, int strip) {
+    launch_step(c->stream, dev_of(c, I), I.step, I.cur, strip);
     c->launches++;
     I.cur = 1 - I.cur;
     I.step++;
@@ -272,14 +284,14 @@ extern "C" teuk_status teuk_create(const teuk_params* p, int n_instances, void* 
         const teuk_params& q = I.p;
         size_t es = q.prec == TEUK_FP64 ? sizeof(double2) : sizeof(float4);
         int nplanes = q.prec == TEUK_FP32 ? 1 : 2;
-        I.plane_bytes = (size_t)q.n_theta * I.pitch * es;
+        I.plane_bytes = (size_t)q.n_rstar * I.pitch * es;
         for (int b = 0; b < 2; ++b)
             for (int k = 0; k < nplanes; ++k) {
                 TK_CCUDA(cudaMallocAsync(&I.state[b][k], I.plane_bytes, c->stream));
                 TK_CCUDA(cudaMemsetAsync(I.state[b][k], 0, I.plane_bytes, c->stream));
             }
         size_t cs = q.prec == TEUK_FP64 ? sizeof(double) : sizeof(float);
-        size_t cbytes = (size_t)kNCoef * q.n_theta * I.pitch * cs;
+        size_t cbytes = (size_t)kNCoef * q.n_rstar * I.pitch * cs;
         TK_CCUDA(cudaMallocAsync(&I.coef_h, cbytes, c->stream));
         TK_CCUDA(cudaMallocAsync(&I.coef_i, cbytes, c->stream));
         TK_CCUDA(cudaMallocAsync((void**)&I.x_int, sizeof(double) * q.n_rstar, c->stream));
@@ -434,85 +446,121 @@ void invalidate_graph(teuk_ctx* c) {
 
 void enqueue_batched(teuk_ctx* c) {
     Batch& B = c->batch;
-    cudaMemsetAsync(B.d_counter, 0, sizeof(unsigned long long), c->stream);
-    cudaMemsetAsync(B.d_flags, 0, sizeof(int) * B.items_per_step, c->stream);
     cudaMemsetAsync(B.d_abort, 0, sizeof(int), c->stream);
-    launch_batched_step(c->stream, c->prec, B.bd, B.grid);
-    launch_batched_extract(c->stream, c->prec, B.bd, B.max_nth);
+    for (BatchClass& K : B.cls) {
+        cudaMemsetAsync(K.d_counter, 0, sizeof(unsigned long long), c->stream);
+        cudaMemsetAsync(K.d_flags, 0, sizeof(int) * K.items, c->stream);
+    }
+    for (BatchClass& K : B.cls) launch_batched_step(c->stream, c->prec, K.bd, K.grid, K.pitch);
+    for (BatchClass& K : B.cls) launch_batched_extract(c->stream, c->prec, K.bd, K.max_nth);
 }
 
-// All instances advance n steps in one persistent launch (captured once in a CUDA
-// graph and replayed; the per-call descriptors are uploaded before each replay).
+// All instances advance n steps: one persistent launch per block-size class, captured
+// once in a CUDA graph and replayed (the per-call descriptors are uploaded first).
 teuk_status batched_step(teuk_ctx* c, int64_t n) {
     Batch& B = c->batch;
     const int ni = (int)c->inst.size();
-    std::vector<int64_t> item_base(ni + 1, 0), base_step(ni);
-    std::vector<int> chunk(ni), nstrip(ni), base_bin(ni);
-    std::vector<InstDev> idev(ni);
-    int max_nth = 0;
-    for (int k = 0; k < ni; ++k) {
-        Instance& I = c->inst[k];
-        chunk[k] = std::max(2, eff_chunk(c, I));  // an item's 2-row halo must lie in the next chunk
-        nstrip[k] = (I.p.n_rstar - 2 + 29) / 30;
-        int nck = (I.p.n_theta + chunk[k] - 1) / chunk[k];
-        item_base[k + 1] = item_base[k] + (int64_t)nstrip[k] * nck;
-        base_step[k] = I.step;
-        base_bin[k] = I.cur;
-        idev[k] = dev_of(c, I);
-        max_nth = std::max(max_nth, I.p.n_theta);
+    if (B.cls.empty()) {
+        for (int k = 0; k < ni; ++k) {
+            int pitch = c->inst[k].pitch;
+            BatchClass* K = nullptr;
+            for (BatchClass& q : B.cls)
+                if (q.pitch == pitch) K = &q;
+            if (!K) {
+                B.cls.emplace_back();
+                K = &B.cls.back();
+                K->pitch = pitch;
+            }
+            K->members.push_back(k);
+        }
     }
-    const int64_t items = item_base[ni];
-    // blob layout: InstDev[ni] | item_base[ni+1] | base_step[ni] | n_steps | chunk[ni] | nstrip[ni] | base_bin[ni]
-    size_t off_inst = 0, off_ib = off_inst + sizeof(InstDev) * ni;
-    size_t off_bs = off_ib + sizeof(int64_t) * (ni + 1), off_n = off_bs + sizeof(int64_t) * ni;
-    size_t off_ch = off_n + sizeof(int64_t), off_ns = off_ch + sizeof(int) * ni;
-    size_t off_bb = off_ns + sizeof(int) * ni, bytes = off_bb + sizeof(int) * ni;
+    // per-class descriptor blocks:
+    // InstDev[m] | item_base[m+1] | base_step[m] | n_steps | strip[m] | nstrip[m] | base_bin[m]
+    std::vector<char> blob;
+    bool changed = false;
+    for (BatchClass& K : B.cls) {
+        const int m = (int)K.members.size();
+        size_t off = (blob.size() + 255) / 256 * 256;
+        K.off = off;
+        size_t o_inst = off, o_ib = o_inst + sizeof(InstDev) * m;
+        size_t o_bs = o_ib + sizeof(int64_t) * (m + 1), o_n = o_bs + sizeof(int64_t) * m;
+        size_t o_st = o_n + sizeof(int64_t), o_ns = o_st + sizeof(int) * m;
+        size_t o_bb = o_ns + sizeof(int) * m, end = o_bb + sizeof(int) * m;
+        blob.resize(end);
+        std::vector<int64_t> ib(m + 1, 0), bs(m);
+        std::vector<int> strip(m), nstrip(m), bb(m);
+        std::vector<InstDev> idev(m);
+        int max_nth = 0;
+        for (int q = 0; q < m; ++q) {
+            Instance& I = c->inst[K.members[q]];
+            strip[q] = eff_strip(c, I);
+            nstrip[q] = (I.p.n_rstar - 2 + strip[q] - 1) / strip[q];
+            ib[q + 1] = ib[q] + nstrip[q];
+            bs[q] = I.step;
+            bb[q] = I.cur;
+            idev[q] = dev_of(c, I);
+            max_nth = std::max(max_nth, I.p.n_theta);
+        }
+        std::memcpy(blob.data() + o_inst, idev.data(), sizeof(InstDev) * m);
+        std::memcpy(blob.data() + o_ib, ib.data(), sizeof(int64_t) * (m + 1));
+        std::memcpy(blob.data() + o_bs, bs.data(), sizeof(int64_t) * m);
+        std::memcpy(blob.data() + o_n, &n, sizeof(int64_t));
+        std::memcpy(blob.data() + o_st, strip.data(), sizeof(int) * m);
+        std::memcpy(blob.data() + o_ns, nstrip.data(), sizeof(int) * m);
+        std::memcpy(blob.data() + o_bb, bb.data(), sizeof(int) * m);
+        if (ib[m] != K.items || max_nth != K.max_nth) changed = true;
+        K.items = ib[m];
+        K.max_nth = max_nth;
+        K.bd.n_inst = m;
+        K.bd.items_per_step = K.items;
+        K.bd.status = c->status;
+        if (K.bd.spin_limit != c->spin_limit || K.bd.skip_release_item != c->inject_skip_item)
+            changed = true;
+        K.bd.spin_limit = c->spin_limit;          // default ~1.3 s of 64 ns sleeps per wait
+        K.bd.skip_release_item = c->inject_skip_item;
+        // pointers into the device blob (set below once it exists)
+        K.bd.inst = (const InstDev*)(uintptr_t)o_inst;
+        K.bd.item_base = (const int64_t*)(uintptr_t)o_ib;
+        K.bd.base_step = (const int64_t*)(uintptr_t)o_bs;
+        K.bd.n_steps = (const int64_t*)(uintptr_t)o_n;
+        K.bd.strip = (const int*)(uintptr_t)o_st;
+        K.bd.nstrip = (const int*)(uintptr_t)o_ns;
+        K.bd.base_bin = (const int*)(uintptr_t)o_bb;
+    }
     if (!B.alloc) {
-        TK_CUDA(c, cudaMallocAsync((void**)&B.d_blob, bytes, c->stream));
-        TK_CUDA(c, cudaMallocAsync((void**)&B.d_counter, sizeof(unsigned long long), c->stream));
+        TK_CUDA(c, cudaMallocAsync((void**)&B.d_blob, blob.size(), c->stream));
         TK_CUDA(c, cudaMallocAsync((void**)&B.d_abort, sizeof(int), c->stream));
-        B.blob_bytes = bytes;
-        B.grid = batched_grid(c->prec);
+        B.blob_bytes = blob.size();
+        for (BatchClass& K : B.cls) {
+            TK_CUDA(c, cudaMallocAsync((void**)&K.d_counter, sizeof(unsigned long long), c->stream));
+            K.grid = batched_grid(c->prec, K.pitch);
+        }
         B.alloc = true;
+        changed = true;
     }
-    if (items > B.flags_cap) {
-        if (B.d_flags) cudaFreeAsync(B.d_flags, c->stream);
-        TK_CUDA(c, cudaMallocAsync((void**)&B.d_flags, sizeof(int) * items, c->stream));
-        B.flags_cap = items;
-        invalidate_graph(c);
+    for (BatchClass& K : B.cls) {
+        if (K.items > K.flags_cap) {
+            if (K.d_flags) cudaFreeAsync(K.d_flags, c->stream);
+            TK_CUDA(c, cudaMallocAsync((void**)&K.d_flags, sizeof(int) * K.items, c->stream));
+            K.flags_cap = K.items;
+            changed = true;
+        }
+        char* base = B.d_blob;
+        K.bd.inst = (const InstDev*)(base + (uintptr_t)K.bd.inst);
+        K.bd.item_base = (const int64_t*)(base + (uintptr_t)K.bd.item_base);
+        K.bd.base_step = (const int64_t*)(base + (uintptr_t)K.bd.base_step);
+        K.bd.n_steps = (const int64_t*)(base + (uintptr_t)K.bd.n_steps);
+        K.bd.strip = (const int*)(base + (uintptr_t)K.bd.strip);
+        K.bd.nstrip = (const int*)(base + (uintptr_t)K.bd.nstrip);
+        K.bd.base_bin = (const int*)(base + (uintptr_t)K.bd.base_bin);
+        K.bd.counter = K.d_counter;
+        K.bd.flags = K.d_flags;
+        K.bd.abort = B.d_abort;
     }
-    if (items != B.items_per_step || max_nth != B.max_nth || c->spin_limit != B.bd.spin_limit ||
-        c->inject_skip_item != B.bd.skip_release_item)
-        invalidate_graph(c);
-    std::vector<char> blob(bytes);
-    std::memcpy(blob.data() + off_inst, idev.data(), sizeof(InstDev) * ni);
-    std::memcpy(blob.data() + off_ib, item_base.data(), sizeof(int64_t) * (ni + 1));
-    std::memcpy(blob.data() + off_bs, base_step.data(), sizeof(int64_t) * ni);
-    std::memcpy(blob.data() + off_n, &n, sizeof(int64_t));
-    std::memcpy(blob.data() + off_ch, chunk.data(), sizeof(int) * ni);
-    std::memcpy(blob.data() + off_ns, nstrip.data(), sizeof(int) * ni);
-    std::memcpy(blob.data() + off_bb, base_bin.data(), sizeof(int) * ni);
+    if (changed) invalidate_graph(c);
     // pageable source: the call returns once the host bytes are staged
-    TK_CUDA(c, cudaMemcpyAsync(B.d_blob, blob.data(), bytes, cudaMemcpyHostToDevice, c->stream));
-    BatchDev bd{};
-    bd.inst = (const InstDev*)(B.d_blob + off_inst);
-    bd.item_base = (const int64_t*)(B.d_blob + off_ib);
-    bd.base_step = (const int64_t*)(B.d_blob + off_bs);
-    bd.n_steps = (const int64_t*)(B.d_blob + off_n);
-    bd.chunk = (const int*)(B.d_blob + off_ch);
-    bd.nstrip = (const int*)(B.d_blob + off_ns);
-    bd.base_bin = (const int*)(B.d_blob + off_bb);
-    bd.n_inst = ni;
-    bd.items_per_step = items;
-    bd.counter = B.d_counter;
-    bd.flags = B.d_flags;
-    bd.abort = B.d_abort;
-    bd.status = c->status;
-    bd.spin_limit = c->spin_limit;   // default ~1.3 s of 64 ns sleeps per wait
-    bd.skip_release_item = c->inject_skip_item;
-    B.bd = bd;
-    B.items_per_step = items;
-    B.max_nth = max_nth;
+    TK_CUDA(c, cudaMemcpyAsync(B.d_blob, blob.data(), blob.size(), cudaMemcpyHostToDevice,
+                               c->stream));
     if (!B.exec && !B.graph_failed) {
         cudaGraph_t g = nullptr;
         if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
@@ -535,7 +583,7 @@ teuk_status batched_step(teuk_ctx* c, int64_t n) {
     } else {
         enqueue_batched(c);
     }
-    c->launches += 2;
+    c->launches += 2 * (int64_t)B.cls.size();
     for (Instance& I : c->inst) {
         int64_t s0 = I.step;
         I.step += n;
@@ -556,9 +604,9 @@ extern "C" teuk_status teuk_step_n(teuk_ctx* c, int64_t n) {
     if (n == 0) return TEUK_OK;
     if (c->inst.size() > 1 || c->steps_per_launch == 0) return batched_step(c, n);
     for (Instance& I : c->inst) {
-        int chunk = eff_chunk(c, I);
+        int strip = eff_strip(c, I);
         int64_t s0 = I.step;
-        for (int64_t k = 0; k < n; ++k) do_step(c, I, chunk);
+        for (int64_t k = 0; k < n; ++k) do_step(c, I, strip);
         do_extract(c, I);
         if (I.wave_hi != s0 + 1 || I.wave_lo == I.wave_hi) I.wave_lo = s0;
         I.wave_hi = I.step + 1;
@@ -630,11 +678,11 @@ extern "C" teuk_status teuk_get_time(const teuk_ctx* c, int instance, int64_t* s
 
 extern "C" teuk_status teuk_get_geometry(const teuk_ctx* c, int instance, double* out);
 
-extern "C" teuk_status teuk_set_tiling(teuk_ctx* c, int theta_chunk, int steps_per_launch) {
+extern "C" teuk_status teuk_set_tiling(teuk_ctx* c, int strip, int steps_per_launch) {
     if (!c) return TEUK_EINVAL;
-    if (theta_chunk < 0 || steps_per_launch < 0)
+    if (strip < 0 || steps_per_launch < 0)
         TK_FAIL(c, TEUK_EINVAL, "tiling parameters must be >= 0");
-    c->chunk = theta_chunk;
+    c->strip = strip;
     c->steps_per_launch = steps_per_launch;
     invalidate_graph(c);
     return TEUK_OK;
@@ -650,16 +698,16 @@ extern "C" teuk_status teuk_set_fault_injection(teuk_ctx* c, int64_t skip_releas
     return TEUK_OK;
 }
 
-extern "C" teuk_status teuk_set_instance_tiling(teuk_ctx* c, int instance, int theta_chunk) {
+extern "C" teuk_status teuk_set_instance_tiling(teuk_ctx* c, int instance, int strip) {
     teuk_status st = check_instance(c, instance);
     if (st) return st;
-    if (theta_chunk < 0) TK_FAIL(c, TEUK_EINVAL, "theta_chunk must be >= 0");
-    c->inst[instance].chunk = theta_chunk;
+    if (strip < 0) TK_FAIL(c, TEUK_EINVAL, "strip must be >= 0");
+    c->inst[instance].strip = strip;
     invalidate_graph(c);
     return TEUK_OK;
 }
 
-// Time each candidate theta chunk on a scratch copy of one instance of every
+// Time each candidate strip length on a scratch copy of one instance of every
 // distinct (n_theta, precision, n_rstar bucket) class and keep the fastest.
 extern "C" teuk_status teuk_autotune(teuk_ctx* c, int trial_steps, int* chosen) {
     if (!c) return TEUK_EINVAL;
@@ -684,7 +732,7 @@ extern "C" teuk_status teuk_autotune(teuk_ctx* c, int trial_steps, int* chosen) 
                                     c->stream) != cudaSuccess)
             err = TEUK_ENOMEM;
         float best_ms = 1e30f;
-        int best_chunk = auto_chunk(I);
+        int best_chunk = auto_strip(I);
         if (!err) {
             InstDev d = dev_of(c, I);
             d.wave = scr_wave;           // trial records must not touch the live ring
@@ -695,9 +743,9 @@ extern "C" teuk_status teuk_autotune(teuk_ctx* c, int trial_steps, int* chosen) 
                 d.buf[0][q] = scr[0][q];
                 d.buf[1][q] = scr[1][q];
             }
-            const int cand[] = {4, 8, 16, 32, 64, 128, 256, 512, 1024};
+            const int cand[] = {8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512};
             for (int ch : cand) {
-                if (ch > I.p.n_theta) break;
+                if (ch > I.p.n_rstar - 2) break;
                 for (int w = 0; w < 2; ++w) launch_step(c->stream, d, I.step + w, w & 1, ch);
                 cudaEventRecord(e0, c->stream);
                 for (int t = 0; t < trial_steps; ++t) launch_step(c->stream, d, I.step + t, t & 1, ch);
@@ -728,7 +776,7 @@ extern "C" teuk_status teuk_autotune(teuk_ctx* c, int trial_steps, int* chosen) 
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     for (int k = 0; k < ni; ++k) {
-        c->inst[k].chunk = best[k];
+        c->inst[k].strip = best[k];
         if (chosen) chosen[k] = best[k];
     }
     invalidate_graph(c);
@@ -744,9 +792,13 @@ extern "C" void teuk_destroy(teuk_ctx* c) {
         Batch& B = c->batch;
         if (B.exec) cudaGraphExecDestroy(B.exec);
         if (B.graph) cudaGraphDestroy(B.graph);
-        void* ptrs[] = {B.d_blob, B.d_counter, B.d_flags, B.d_abort};
+        void* ptrs[] = {B.d_blob, B.d_abort};
         for (void* q : ptrs)
             if (q) cudaFreeAsync(q, c->stream);
+        for (BatchClass& K : B.cls) {
+            if (K.d_counter) cudaFreeAsync(K.d_counter, c->stream);
+            if (K.d_flags) cudaFreeAsync(K.d_flags, c->stream);
+        }
     }
     for (Instance& I : c->inst) free_instance(c->stream, I);
     if (c->status) cudaFreeAsync(c->status, c->stream);
@@ -825,7 +877,7 @@ extern "C" teuk_status teuk_adjoint_n(teuk_ctx* c, int instance, int64_t step0, 
                 (long long)I.step, (long long)step0);
     cudaStream_t s = c->stream;
     const int nth = I.p.n_theta;
-    const size_t plane = (size_t)nth * I.pitch * sizeof(double2);
+    const size_t plane = (size_t)I.p.n_rstar * I.pitch * sizeof(double2);  // one [nr][pitch] plane
     AdjBuffers B(s);
     double2 *lam[2][2], *mu[2];
     for (int b = 0; b < 2; ++b)
@@ -855,7 +907,7 @@ extern "C" teuk_status teuk_adjoint_n(teuk_ctx* c, int instance, int64_t step0, 
         c->launches++;
         return cur;
     };
-    const int chunk = eff_chunk(c, I);
+    const int chunk = eff_strip(c, I);
     // the segment plan: segments [a_k, a_k + len_k) of the steps step0 .. step0+n-1
     int64_t K = (builtin && ckpt_every > 0) ? ckpt_every : n;
     int64_t nseg = (n + K - 1) / K;

@@ -11,10 +11,10 @@ namespace teuk {
 // about 2^-48 relative.
 template <class P>
 __global__ void import_state_kernel(InstDev d, int b, const double* u) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    int j = blockIdx.y;
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    int i = blockIdx.y;
     if (i >= d.nr || j >= d.nth) return;
-    size_t np = (size_t)d.nr * d.nth, q = (size_t)j * d.nr + i, o = (size_t)j * d.pitch + i;
+    size_t np = (size_t)d.nr * d.nth, q = (size_t)j * d.nr + i, o = node_index(d, i, j);
     double v[4] = {u[q], u[np + q], u[2 * np + q], u[3 * np + q]};
     if constexpr (sizeof(typename P::T) == 8) {
         ((double2*)d.buf[b][0])[o] = make_double2(v[0], v[1]);
@@ -34,10 +34,10 @@ __global__ void import_state_kernel(InstDev d, int b, const double* u) {
 
 template <class P>
 __global__ void export_state_kernel(InstDev d, int b, double* u) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    int j = blockIdx.y;
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    int i = blockIdx.y;
     if (i >= d.nr || j >= d.nth) return;
-    size_t np = (size_t)d.nr * d.nth, q = (size_t)j * d.nr + i, o = (size_t)j * d.pitch + i;
+    size_t np = (size_t)d.nr * d.nth, q = (size_t)j * d.nr + i, o = node_index(d, i, j);
     NodeV<P> n = Planes<P>::of(d, b).load(o);
     double v[4];
     if constexpr (P::kahan) {
@@ -52,10 +52,10 @@ __global__ void export_state_kernel(InstDev d, int b, double* u) {
 // Sets ST_NONFINITE if any state value of buffer b is NaN or infinite.
 template <class P>
 __global__ void scan_finite_kernel(InstDev d, int b) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    int j = blockIdx.y;
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    int i = blockIdx.y;
     if (i >= d.nr || j >= d.nth) return;
-    NodeV<P> n = Planes<P>::of(d, b).load((size_t)j * d.pitch + i);
+    NodeV<P> n = Planes<P>::of(d, b).load(node_index(d, i, j));
     bool ok = isfinite((double)n.F.re) && isfinite((double)n.F.im) && isfinite((double)n.Pp.re) &&
               isfinite((double)n.Pp.im);
     if constexpr (P::kahan)
@@ -86,21 +86,21 @@ __global__ void zero_kernel(double* p, size_t n) {
 }
 
 void launch_import_state(cudaStream_t st, const InstDev& d, int bin, const double* u) {
-    dim3 g((d.nr + 127) / 128, d.nth);
+    dim3 g((d.nth + 127) / 128, d.nr);
     if (d.prec == 0) import_state_kernel<P64><<<g, 128, 0, st>>>(d, bin, u);
     else if (d.prec == 1) import_state_kernel<P32><<<g, 128, 0, st>>>(d, bin, u);
     else import_state_kernel<PK><<<g, 128, 0, st>>>(d, bin, u);
 }
 
 void launch_export_state(cudaStream_t st, const InstDev& d, int bin, double* u) {
-    dim3 g((d.nr + 127) / 128, d.nth);
+    dim3 g((d.nth + 127) / 128, d.nr);
     if (d.prec == 0) export_state_kernel<P64><<<g, 128, 0, st>>>(d, bin, u);
     else if (d.prec == 1) export_state_kernel<P32><<<g, 128, 0, st>>>(d, bin, u);
     else export_state_kernel<PK><<<g, 128, 0, st>>>(d, bin, u);
 }
 
 void launch_scan_finite(cudaStream_t st, const InstDev& d, int bin) {
-    dim3 g((d.nr + 127) / 128, d.nth);
+    dim3 g((d.nth + 127) / 128, d.nr);
     if (d.prec == 0) scan_finite_kernel<P64><<<g, 128, 0, st>>>(d, bin);
     else if (d.prec == 1) scan_finite_kernel<P32><<<g, 128, 0, st>>>(d, bin);
     else scan_finite_kernel<PK><<<g, 128, 0, st>>>(d, bin);

@@ -1,14 +1,15 @@
 // teuk_internal.cuh -- device-side data structures shared by the library's kernels.
 //
-// HBM layout of one instance (r* is the fastest index; rows are padded to a pitch
-// that is a multiple of 32 elements so every row starts 512-byte aligned):
-//   state   two ping-pong buffers, each made of "planes" [n_theta][pitch]:
+// HBM layout of one instance (theta is the fastest index; each r* column of n_theta
+// nodes is padded to a pitch that is a multiple of 32 elements, so a column starts on
+// a 512-byte boundary and one thread block reads it in one coalesced sweep):
+//   state   two ping-pong buffers, each made of "planes" [n_rstar][pitch]:
 //             FP64        plane 0 = Phi (double2), plane 1 = Pi (double2)
 //             FP32        plane 0 = {Phi_R, Phi_I, Pi_R, Pi_I} (float4)
 //             FP32_KAHAN  plane 0 = hi {Phi, Pi} (float4), plane 1 = c {Phi, Pi} (float4),
 //                         the represented value being hi - c
-//   coef_h  [9][n_theta][pitch] coefficients of the predictor at half nodes (i+1/2, j)
-//   coef_i  [9][n_theta][pitch] coefficients of the corrector at integer nodes (i, j)
+//   coef_h  [9][n_rstar][pitch] FP64 path: predictor coefficients at half nodes (i+1/2, j)
+//   coef_i  [9][n_rstar][pitch] FP64 path: corrector coefficients at integer nodes (i, j)
 //   source  FP64 complex profile on a window of nodes around the particle
 //   wave    FP64 ring of waveform records [capacity][n_theta] (double2)
 #pragma once
@@ -64,7 +65,7 @@ struct InstDev {
     float ghost_f;            // +1 even |m|, -1 odd |m|
     double ghost;
     void* buf[2][2];          // [ping-pong buffer][plane]
-    const void* coef_h;       // [9][nth][pitch] (double or float)
+    const void* coef_h;       // [9][nr][pitch] (double or float)
     const void* coef_i;
     const RTab* rtab_h;       // [nr] FP32 paths: radial tables at half nodes i+1/2
     const RTab* rtab_i;       // [nr] at integer nodes
@@ -79,14 +80,14 @@ struct InstDev {
 
 enum StatusBits : unsigned int { ST_NONFINITE = 1u, ST_TIMEOUT = 2u, ST_BOUNDS = 4u };
 
-// Batched persistent launch over many instances (teuk_step.cu).  Work items are
-// (relative step s, instance k, theta chunk ck, strip) in that order of priority;
+// Batched persistent launch over many instances of one block-size class (teuk_step.cu).
+// Work items are (relative step s, instance k, r* strip) in that order of priority;
 // items of one step are numbered instance by instance from item_base[k].
 struct BatchDev {
     const InstDev* inst;        // [n_inst] descriptors of this call
     const int64_t* item_base;   // [n_inst + 1] first item of each instance within a step
-    const int* chunk;           // [n_inst] theta rows per item
-    const int* nstrip;          // [n_inst] strips per chunk row
+    const int* strip;           // [n_inst] r* columns per item
+    const int* nstrip;          // [n_inst] items per instance and step
     const int64_t* base_step;   // [n_inst] time level at the start of the call
     const int* base_bin;        // [n_inst] buffer holding that level
     const int64_t* n_steps;     // steps of this call (device scalar)
@@ -102,7 +103,12 @@ struct BatchDev {
 };
 
 __host__ __device__ inline size_t plane_elems(const InstDev& d) {
-    return (size_t)d.nth * (size_t)d.pitch;
+    return (size_t)d.nr * (size_t)d.pitch;
+}
+
+// Offset of node (i, j) = (r*_i, theta_j) in a plane.
+__host__ __device__ inline size_t node_index(const InstDev& d, int i, int j) {
+    return (size_t)i * (size_t)d.pitch + (size_t)j;
 }
 
 // ---- host launchers (each defined next to its kernels) ----
@@ -120,10 +126,10 @@ void launch_profile(cudaStream_t st, double M, double a, double rstar_min, doubl
                     double rs0, double sig_r, double sig_t, double drs0_dr0, const double* x_int,
                     const double* x_half, const SourceDev& src);
 // teuk_step.cu
-void launch_step(cudaStream_t st, const InstDev& d, int64_t step, int bin, int chunk);
+void launch_step(cudaStream_t st, const InstDev& d, int64_t step, int bin, int strip);
 void launch_extract(cudaStream_t st, const InstDev& d, int64_t step, int bin);
-void launch_batched_step(cudaStream_t st, int prec, const BatchDev& b, int grid);
-int batched_grid(int prec);
+void launch_batched_step(cudaStream_t st, int prec, const BatchDev& b, int grid, int threads);
+int batched_grid(int prec, int threads);
 void launch_batched_extract(cudaStream_t st, int prec, const BatchDev& b, int max_nth);
 // teuk_aux.cu
 void launch_import_state(cudaStream_t st, const InstDev& d, int bin, const double* u);

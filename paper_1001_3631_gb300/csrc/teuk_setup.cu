@@ -102,27 +102,26 @@ template <typename T>
 __global__ void coef_kernel(double M, double a, int s, int m, double rstar_min, double drs,
                             double dth, double dt, int nr, int nth, int pitch,
                             const double* x_int, const double* x_half, T* coef_h, T* coef_i) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    int j = blockIdx.y;
-    if (i >= pitch || j >= nth) return;
-    size_t pl = (size_t)nth * pitch;
-    size_t o = (size_t)j * pitch + i;
+    int j = blockIdx.x * blockDim.x + threadIdx.x;   // theta row (fastest in memory)
+    int i = blockIdx.y;                              // r* column
+    if (j >= pitch || i >= nr) return;
+    size_t pl = (size_t)nr * pitch;
+    size_t o = (size_t)i * pitch + j;
     double th = (j + 0.5) * dth;
     double c[kNCoef];
-    if (i < nr - 1) {
+    if (j < nth && i < nr - 1) {
         node_coefficients(M, a, s, m, x_half[i], th, dth, dt, drs, 0.5, c);
         for (int k = 0; k < kNCoef; ++k) coef_h[k * pl + o] = (T)c[k];
     } else {
         for (int k = 0; k < kNCoef; ++k) coef_h[k * pl + o] = (T)0;
     }
-    if (i < nr) {
+    if (j < nth) {
         node_coefficients(M, a, s, m, x_int[i], th, dth, dt, drs, 1.0, c);
         for (int k = 0; k < kNCoef; ++k) coef_i[k * pl + o] = (T)c[k];
     } else {
         for (int k = 0; k < kNCoef; ++k) coef_i[k * pl + o] = (T)0;
     }
 }
-
 
 // Source profile on the window: P = 4 pi (r^2 + a^2 cos^2) Delta / (Sigma^2 r^3) * G,
 // G = exp(-(dr^2/sig_r^2 + dth^2/sig_t^2)/2) / (2 pi sig_r sig_t), zero beyond 8 sigma;
@@ -240,7 +239,7 @@ void launch_coefficients(cudaStream_t st, int prec, double M, double a, int s, i
                          double rstar_min, double drs, double dth, double dt, int nr, int nth,
                          int pitch, const double* x_int, const double* x_half, void* coef_h,
                          void* coef_i) {
-    dim3 g((pitch + 127) / 128, nth);
+    dim3 g((pitch + 127) / 128, nr);
     if (prec == 0)
         coef_kernel<double><<<g, 128, 0, st>>>(M, a, s, m, rstar_min, drs, dth, dt, nr, nth, pitch,
                                                x_int, x_half, (double*)coef_h, (double*)coef_i);

@@ -1,20 +1,20 @@
 // teuk_step.cu -- the Lax-Wendroff step (Eqs. 13-14) as one fused kernel per step.
 //
-// Work decomposition: a warp owns a strip of 32 consecutive r* columns (lane L holds
-// column i = 30*strip + L) and streams down a chunk of theta rows.  Each lane
-// computes the predictor (Eq. 13) at its right half node i+1/2; the left half node
-// i-1/2 comes from lane L-1 through a warp shuffle, so lanes 1..30 produce the
-// corrector (Eq. 14) for 30 columns per strip.  In theta the warp keeps a 3-row
-// register ring of half-node results, so every input row is read from HBM once
-// per chunk (plus a 2-row halo at each chunk edge) and nothing goes through shared
-// memory.  The angular ghost rows of the pole boundary condition (Sec. 2.2) are
-// mirror images of row 0 / row n_theta-1 with sign +1 (even |m|) or -1 (odd |m|),
-// applied to the state for the predictor and to the half-node results for the
-// corrector.
+// Work decomposition: a thread block holds one whole theta column (thread j = row j,
+// blockDim = n_theta rounded up to a warp) and streams along r* over a strip of
+// columns [c0, c1).  At each column it loads u^n(i, j) (prefetched one column ahead),
+// computes the predictor (Eq. 13) at the half node just behind it and the corrector
+// (Eq. 14) at the column behind that, and stores u^{n+1}.  Radial neighbours are the
+// registers of the previous column; theta neighbours come from the lanes above and
+// below (warp shuffles, and shared memory across warp edges).  A strip reads two extra
+// columns, so every input is read from HBM about once per step.  The angular ghost
+// rows of the pole condition (Sec. 2.2) mirror row 0 / row n_theta-1 with sign +1
+// (even |m|) or -1 (odd |m|): on the averaged state in the predictor, on the half-node
+// results in the corrector.
 //
-// Arithmetic, in terms of differences so that the compensated FP32 state keeps
-// its accuracy (a difference of two (hi, c) pairs is formed as
-// (hi_a - hi_b) - (c_a - c_b) before anything cancels):
+// Arithmetic, in differences so that the compensated FP32 state keeps its accuracy (a
+// difference of two (hi, c) pairs is formed as (hi_a - hi_b) - (c_a - c_b) before
+// anything cancels):
 //   predictor at (i+1/2, j), with Fb = (Phi_i + Phi_{i+1})/2, dF = Phi_{i+1} - Phi_i,
 //   Dp(j) = Fb(j+1) - Fb(j) and the same for Pi:
 //     dh_Phi = -g dF + (dt/2) Pb
@@ -33,112 +33,212 @@
 
 namespace teuk {
 
-// One work item: the strip `strip` (columns 30*strip .. 30*strip+31) and the theta
-// chunk `ck` (rows ck*chunk .. ) of one step, executed by one whole warp.
-template <class P>
-__device__ __forceinline__ void step_item(const InstDev& d, int64_t step, int bin, int chunk,
-                                          int strip, int ck) {
-    using T = typename P::T;
-    using C = Cx<T>;
-    const int lane = threadIdx.x & 31;
-    const int i = 30 * strip + lane;
-    const bool col_ok = i < d.nr;
-    const bool half_ok = lane < 31 && i + 1 < d.nr;
-    const bool out_ok = lane >= 1 && lane <= 30 && i <= d.nr - 2;
-    const bool bnd = (i == 0 || i == d.nr - 1) && (lane <= 30);
-    const int j0 = ck * chunk, j1 = min(d.nth, j0 + chunk);
-    const int nth = d.nth, pitch = d.pitch;
-    const T g = (T)d.ghost;
-    const T hdt = (T)(0.5 * d.dt), fdt = (T)d.dt;
-    const int ex_strip = d.i_e >= 1 ? (d.i_e - 1) / 30 : 0;
-    const bool ex_warp = strip == ex_strip;
+// Values exchanged between neighbouring rows of one column: within a warp by shuffles,
+// across warp edges through shared memory.  Each exchange point owns its own buffer,
+// double-buffered by column parity, so a buffer is rewritten only after every thread
+// has passed a later barrier (no write can overtake a slow reader).
+template <typename T>
+struct Xchg {
+    T lo[2][kMaxWarps][4];   // lane 0 of each warp, read by lane 31 of the warp below
+    T hi[2][kMaxWarps][4];   // lane 31 of each warp, read by lane 0 of the warp above
+};
 
-    // source factors of this step: (dt/2) A_n e^{-i(omega t_n + phase0)} and
-    // dt A_n e^{-i(omega (t_n + dt/2) + phase0)}, FP64
-    // only warps whose columns and rows meet the source window need them
-    const int c_lo = 30 * strip, c_hi = 30 * strip + 31, r_lo = j0 - 1, r_hi = j1;
-    const SourceDev& sw = d.src;
-    const bool src_warp = sw.on && r_lo < sw.j_lo + sw.nj && r_hi >= sw.j_lo &&
-                          ((c_lo < sw.i_lo + sw.ni && c_hi >= sw.i_lo) ||
-                           (c_lo < sw.h_lo + sw.nh && c_hi >= sw.h_lo));
-    double2 sp_fac = make_double2(0.0, 0.0), sc_fac = make_double2(0.0, 0.0);
-    if (src_warp) source_factors(d, step, sp_fac, sc_fac);
+template <typename T>
+struct StepSmem {
+    Xchg<T> x1, x2, x3;
+};
 
-    const Planes<P> in = Planes<P>::of(d, bin), out = Planes<P>::of(d, 1 - bin);
-    ColTab<P> colh, coli;  // radial coefficient tables of this lane's column (FP32 paths)
-    colh.load(d.rtab_h, i, half_ok);
-    coli.load(d.rtab_i, i, col_ok);
-
-    NodeV<P> prev = NodeV<P>::zero();
-    Half<T> pend;           // Fb, Pb, dF, dP of the previous loaded row
-    C dp_prev = C::zero();  // Dp of row (previous loaded row - 1)
-    CRing<T> ring;          // corrector inputs of rows jc-1, jc, jc+1
-    int ring_n = 0;         // rows pushed so far
-    int ring_top = -3;      // row index of ring.c
-
-    const int jl_begin = max(j0 - 2, -1), jl_end = min(j1 + 1, nth);
-    const int jp_lo = max(j0 - 1, 0), jp_hi = min(j1, nth - 1);
-
-    for (int jl = jl_begin; jl <= jl_end; ++jl) {
-        // ---- load row jl of the own column (mirror rows outside [0, nth)) ----
-        const int jr = jl < 0 ? 0 : (jl >= nth ? nth - 1 : jl);
-        NodeV<P> own = col_ok ? in.load((size_t)jr * pitch + i) : NodeV<P>::zero();
-        if (jl < 0 || jl >= nth) own.scale(g);
-        const NodeV<P> nb = own.shfl_down();
-        Half<T> cur = half_prep<P>(own, nb);
-        C dp_cur = C::zero();
-        if (jl > jl_begin) {
-            // Dp(jl-1) = Fb(jl) - Fb(jl-1), from the columns' own theta differences
-            C delta = own.dphi(prev);
-            C delta_n = shfl_down_c(delta);
-            dp_cur = C::half_sum(delta, delta_n);
-        }
-        prev = own;
-
-        // ---- predictor at jp = jl - 1 ----
-        const int jp = jl - 1;
-        if (jl > jl_begin && jp >= jp_lo && jp <= jp_hi) {
-            T cf[kNCoef];
-            get_coefs<P>(d, colh, true, i, jp, half_ok, cf);
-            C src = C::zero();
-            if (src_warp) src = source_half<T>(d.src, sp_fac, i, jp);
-            HalfRec<T> rec = predictor<T>(pend, dp_cur, dp_prev, cf, hdt, src);
-            CRow<T> row = combine_lr<T>(rec);
-            if (jp == 0) {  // ghost row -1 of the half-node results
-                CRow<T> gr = row.mirror(g);
-                gr.DpS = C::half_sum(dp_prev, shfl_up_c(dp_prev));
-                ring.push(gr);
-                ++ring_n;
-                ring_top = -1;
-            }
-            ring.push(row);
-            ++ring_n;
-            ring_top = jp;
-            if (ring_n >= 3 && ring_top - 1 >= j0 && ring_top - 1 < j1)
-                corrector<P>(d, in, out, ring, ring_top - 1, i, out_ok, bnd, ex_warp, src_warp,
-                             coli, fdt, sc_fac, step);
-            if (jp == nth - 1) {  // ghost row nth
-                CRow<T> gr = row.mirror(g);
-                ring.push(gr);
-                ++ring_n;
-                ring_top = nth;
-                if (ring_n >= 3 && nth - 1 >= j0 && nth - 1 < j1)
-                    corrector<P>(d, in, out, ring, nth - 1, i, out_ok, bnd, ex_warp, src_warp,
-                                 coli, fdt, sc_fac, step);
-            }
-        }
-        pend = cur;
-        dp_prev = dp_cur;
+// down_out[k] = down_in[k] of row j+1, up_out[k] = up_in[k] of row j-1 (KD, KU values);
+// the top and bottom rows of the block receive garbage and apply the ghost rule.
+template <typename T, int KD, int KU>
+__device__ __forceinline__ void xchg(Xchg<T>& X, int par, const T* down_in, T* down_out,
+                                     const T* up_in, T* up_out) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < KD; ++k) down_out[k] = shfl_down_t(down_in[k]);
+#pragma unroll
+    for (int k = 0; k < KU; ++k) up_out[k] = shfl_up_t(up_in[k]);
+    if (nwarp > 1) {
+        if (lane == 0)
+#pragma unroll
+            for (int k = 0; k < KD; ++k) X.lo[par][warp][k] = down_in[k];
+        if (lane == 31)
+#pragma unroll
+            for (int k = 0; k < KU; ++k) X.hi[par][warp][k] = up_in[k];
+        __syncthreads();
+        if (lane == 31 && warp + 1 < nwarp)
+#pragma unroll
+            for (int k = 0; k < KD; ++k) down_out[k] = X.lo[par][warp + 1][k];
+        if (lane == 0 && warp > 0)
+#pragma unroll
+            for (int k = 0; k < KU; ++k) up_out[k] = X.hi[par][warp - 1][k];
     }
 }
 
+// One work item: the columns [c0, c1) of one instance for one step, one thread per row.
+// Per column c: (1) exchange Phi(c) with the rows above and below -> theta differences
+// dl(c) = Phi(j+1) - Phi(j) and dlm(c) = Phi(j) - Phi(j-1); (2) predictor at the half
+// node c-1/2; (3) exchange its results with the rows above and below; (4) corrector at
+// column c-1.  Two barriers per column.  The first two columns are peeled so the
+// steady-state loop has no per-column mode switches, and it is unrolled by three so the
+// rotation of the previous / current / prefetched column is register renaming.
 template <class P>
-__global__ void __launch_bounds__(128) step_kernel(InstDev d, int64_t step, int bin, int chunk) {
-    const int gw = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
-    const int nstrip = (d.nr - 2 + 29) / 30;
-    const int nck = (d.nth + chunk - 1) / chunk;
-    if (gw >= nstrip * nck) return;  // whole warps only
-    step_item<P>(d, step, bin, chunk, gw % nstrip, gw / nstrip);
+__device__ __forceinline__ void strip_step(const InstDev& d, int64_t step, int bin, int c0,
+                                           int c1, StepSmem<typename P::T>& sm) {
+    using T = typename P::T;
+    using C = Cx<T>;
+    constexpr int KF = P::kahan ? 4 : 2;   // Phi values exchanged: hi (and c)
+    constexpr bool kRT = sizeof(T) == 4;  // FP32 paths: radial tables, prefetched a column ahead
+    const int j = threadIdx.x;
+    const int nth = d.nth;
+    const bool row_ok = j < nth;
+    const bool bot = j == 0, top = j == nth - 1;
+    const T g = (T)d.ghost;
+    const T hdt = (T)(0.5 * d.dt), fdt = (T)d.dt;
+    const Planes<P> in = Planes<P>::of(d, bin), out = Planes<P>::of(d, 1 - bin);
+    RowTab<P> rt;
+    rt.load(d.thtab, j, row_ok);
+    const size_t pitch = (size_t)d.pitch;
+
+    // source: this block's columns against the window
+    const SourceDev& sw = d.src;
+    const bool src_blk = sw.on &&
+                         ((c0 - 1 < sw.i_lo + sw.ni && c1 >= sw.i_lo) ||
+                          (c0 - 1 < sw.h_lo + sw.nh && c1 >= sw.h_lo));
+    double2 sp_fac = make_double2(0.0, 0.0), sc_fac = make_double2(0.0, 0.0);
+    if (src_blk) source_factors(d, step, sp_fac, sc_fac);
+    const bool ex_blk = c0 - 1 <= d.i_e && d.i_e <= c1 - 1;
+
+    // radial boundary condition: Phi = Pi = 0 at i = 0 and i = nr - 1
+    if (row_ok && c0 == 1) out.store(node_index(d, 0, j), NodeV<P>::zero());
+    if (row_ok && c1 == d.nr - 1) out.store(node_index(d, d.nr - 1, j), NodeV<P>::zero());
+
+    // (1) theta differences of Phi in column u (ghost rows by the pole rule)
+    auto theta_diffs = [&](const NodeV<P>& u, int par, C& dl, C& dlm) {
+        T v[4] = {u.F.re, u.F.im, u.Fc.re, u.Fc.im}, vd[4], vu[4];
+        xchg<T, KF, KF>(sm.x1, par, v, vd, v, vu);
+        NodeV<P> dn = NodeV<P>::zero(), upn = NodeV<P>::zero();
+        dn.F = {vd[0], vd[1]};
+        upn.F = {vu[0], vu[1]};
+        if constexpr (P::kahan) {
+            dn.Fc = {vd[2], vd[3]};
+            upn.Fc = {vu[2], vu[3]};
+        }
+        if (top) { dn = u; dn.scale(g); }     // row nth   = g * row nth-1
+        if (bot) { upn = u; upn.scale(g); }   // row -1    = g * row 0
+        dl = dn.dphi(u);
+        dlm = u.dphi(upn);
+    };
+    // (2) predictor at the half node h between columns h (ul) and h+1 (ur)
+    auto predict = [&](const NodeV<P>& ul, const NodeV<P>& ur, C dll, C dlr, C dlml, C dlmr,
+                       const RTab& tab, int h) {
+        const Half<T> hp = half_prep<P>(ul, ur);
+        const C Dp = C::half_sum(dll, dlr);     // Fb(j+1) - Fb(j)
+        const C Dm = C::half_sum(dlml, dlmr);   // Fb(j) - Fb(j-1)
+        T cf[kNCoef];
+        get_coefs_pre<P>(d, rt, tab, true, h, j, row_ok, cf);
+        C src = C::zero();
+        if (src_blk) src = source_half<T>(sw, sp_fac, h, j);
+        return predictor<T>(hp, Dp, Dm, cf, hdt, src);
+    };
+    // (3)+(4) corrector at column cc from the half nodes L = cc-1/2 and R = cc+1/2
+    auto correct = [&](const HalfRec<T>& R, const HalfRec<T>& L, const NodeV<P>& uc,
+                       const RTab& tab, int cc, int par, size_t o) {
+        const CRow<T> row = combine_lr<T>(R, L);
+        T xd[2] = {row.Hs.re, row.Hs.im}, xdo[2];
+        T xu[4] = {row.Hs.re, row.Hs.im, row.DpS.re, row.DpS.im}, xuo[4];
+        xchg<T, 2, 4>(sm.x3, par, xd, xdo, xu, xuo);
+        C Hs_p = {xdo[0], xdo[1]};
+        C Hs_m = {xuo[0], xuo[1]}, DpS_m = {xuo[2], xuo[3]};
+        if (top) Hs_p = g * row.Hs;
+        if (bot) {
+            Hs_m = g * row.Hs;
+            DpS_m = (T(1) - g) * C::half_sum(R.Fb, L.Fb);  // (Dp_R(-1) + Dp_L(-1))/2
+        }
+        const C Dplus = row.DpS + (Hs_p - row.Hs);
+        const C Dminus = DpS_m + (row.Hs - Hs_m);
+        T cf[kNCoef];
+        get_coefs_pre<P>(d, rt, tab, false, cc, j, row_ok, cf);
+        C srcc = C::zero();
+        if (src_blk) srcc = source_int<T>(sw, sc_fac, cc, j);
+        C dPhi = rmac(rmac(C::zero(), -cf[C_G], row.dFc), fdt, row.PC);
+        C dPi = rmac(srcc, cf[C_G], row.dPc);
+        dPi = cmac(dPi, cf[C_E1R], cf[C_E1I], row.PC);
+        dPi = cmac(dPi, cf[C_E2R], cf[C_E2I], row.dFc);
+        dPi = rmac(dPi, cf[C_EP], Dplus);
+        dPi = rmac(dPi, -cf[C_EM], Dminus);
+        dPi = cmac(dPi, cf[C_E3R], cf[C_E3I], row.FC);
+        if (row_ok) {
+            NodeV<P> u = uc;
+            u.update(dPhi, dPi);
+            out.store(o, u);
+        }
+    };
+    // waveform record of the input level between columns i_e (ul) and i_e + 1 (ur)
+    auto extract = [&](const NodeV<P>& ul, const NodeV<P>& ur) {
+        if (!row_ok) return;
+        double2 a = ul.phi64(), b = ur.phi64();
+        double f = d.f_e;
+        double2 w = make_double2((1.0 - f) * a.x + f * b.x, (1.0 - f) * a.y + f * b.y);
+        d.wave[(size_t)(step % d.wave_cap) * nth + j] = w;
+        if (!isfinite(w.x) || !isfinite(w.y)) atomicOr(d.status, (unsigned)ST_NONFINITE);
+    };
+    auto load_col = [&](size_t o) { return row_ok ? in.load(o) : NodeV<P>::zero(); };
+    auto rtab_h = [&](int i) { RTab t{}; if constexpr (kRT) t = load_rtab(d.rtab_h, i); return t; };
+    auto rtab_i = [&](int i) { RTab t{}; if constexpr (kRT) t = load_rtab(d.rtab_i, i); return t; };
+
+    // prologue: columns c0-1 and c0
+    size_t o = node_index(d, c0 - 1, j);           // offset of the column being loaded
+    NodeV<P> u_prev = load_col(o);
+    NodeV<P> u_cur = load_col(o + pitch);
+    C dl_prev, dlm_prev, dl, dlm;
+    theta_diffs(u_prev, (c0 - 1) & 1, dl_prev, dlm_prev);
+    RTab th = rtab_h(c0 - 1);
+    theta_diffs(u_cur, c0 & 1, dl, dlm);
+    HalfRec<T> L = predict(u_prev, u_cur, dl_prev, dl, dlm_prev, dlm, th, c0 - 1);
+    if (ex_blk && d.i_e == c0 - 1) extract(u_prev, u_cur);
+    u_prev = u_cur;
+    dl_prev = dl;
+    dlm_prev = dlm;
+    o += 2 * pitch;                                // column c0 + 1
+    NodeV<P> u_next = c0 + 1 <= c1 ? load_col(o) : NodeV<P>::zero();
+
+    // steady state: column c loaded, predictor at c-1/2, corrector at c-1
+#pragma unroll 3
+    for (int c = c0 + 1; c <= c1; ++c) {
+        u_cur = u_next;
+        if (c < c1) u_next = load_col(o + pitch);
+        th = rtab_h(c - 1);
+        const RTab ti = rtab_i(c - 1);
+        const int par = c & 1;
+        theta_diffs(u_cur, par, dl, dlm);
+        const HalfRec<T> R = predict(u_prev, u_cur, dl_prev, dl, dlm_prev, dlm, th, c - 1);
+        correct(R, L, u_prev, ti, c - 1, par, o - pitch);
+        if (ex_blk && d.i_e == c - 1) extract(u_prev, u_cur);
+        L = R;
+        u_prev = u_cur;
+        dl_prev = dl;
+        dlm_prev = dlm;
+        o += pitch;
+    }
+}
+
+// Two register budgets: columns of up to 256 rows (the common case, room for two
+// blocks per SM at up to 128 registers) and of up to 1024 rows.
+template <class P>
+__global__ void __launch_bounds__(256, 2) step_kernel_s(InstDev d, int64_t step, int bin, int strip) {
+    __shared__ StepSmem<typename P::T> sm;
+    const int c0 = 1 + blockIdx.x * strip;
+    const int c1 = min(d.nr - 1, c0 + strip);
+    strip_step<P>(d, step, bin, c0, c1, sm);
+}
+
+template <class P>
+__global__ void __launch_bounds__(1024) step_kernel_l(InstDev d, int64_t step, int bin, int strip) {
+    __shared__ StepSmem<typename P::T> sm;
+    const int c0 = 1 + blockIdx.x * strip;
+    const int c1 = min(d.nr - 1, c0 + strip);
+    strip_step<P>(d, step, bin, c0, c1, sm);
 }
 
 // Waveform record of the state in buffer bin (time level `step`): one thread per row.
@@ -147,8 +247,8 @@ __global__ void extract_kernel(InstDev d, int64_t step, int bin) {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= d.nth) return;
     const Planes<P> in = Planes<P>::of(d, bin);
-    size_t o = (size_t)j * d.pitch + d.i_e;
-    double2 a = in.load(o).phi64(), b = in.load(o + 1).phi64();
+    double2 a = in.load(node_index(d, d.i_e, j)).phi64();
+    double2 b = in.load(node_index(d, d.i_e + 1, j)).phi64();
     double f = d.f_e;
     double2 w = make_double2((1.0 - f) * a.x + f * b.x, (1.0 - f) * a.y + f * b.y);
     d.wave[(size_t)(step % d.wave_cap) * d.nth + j] = w;
@@ -165,42 +265,52 @@ __device__ __forceinline__ void st_release(int* p, int v) {
     asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Wait until the items of the 3x3 neighbourhood (strips strip-1..strip+1, chunks
-// ck-1..ck+1) have completed relative step s-1.  That covers what this item reads
-// (halo of one column and two rows) and what it overwrites (the buffer the
-// neighbours of step s-1 read).  Lanes 0..8 each poll one neighbour with acquire
-// loads; the wait gives up after spin_limit polls.  Returns false on give-up or abort.
-__device__ bool wait_neighbours(const BatchDev& b, const int* fl, int nstrip, int nck, int strip,
-                                int ck, int64_t s) {
-    const int lane = threadIdx.x & 31;
-    bool ok = true;
-    if (lane < 9) {
-        int st = strip + lane % 3 - 1, c = ck + lane / 3 - 1;
-        if (st >= 0 && st < nstrip && c >= 0 && c < nck) {
-            const int* f = fl + (size_t)c * nstrip + st;
+// Wait until the strips st-1, st, st+1 of the previous step have completed.  That
+// covers what this strip reads (one column on each side) and what it overwrites (the
+// buffer its neighbours read).  Threads 0..2 poll one neighbour each with acquire
+// loads; a wait gives up after spin_limit polls.  Returns false on give-up or abort.
+__device__ bool wait_neighbours(const BatchDev& b, const int* fl, int nstrip, int st, int64_t s,
+                                int* flag_smem) {
+    const int t = threadIdx.x;
+    if (t == 0) *flag_smem = 1;
+    __syncthreads();
+    if (t < 3) {
+        int q = st + t - 1;
+        if (q >= 0 && q < nstrip) {
             long long it = 0;
-            while (ld_acquire(f) < (int)s) {
-                if (++it > b.spin_limit || *(volatile int*)b.abort) { ok = false; break; }
+            while (ld_acquire(fl + q) < (int)s) {
+                if (++it > b.spin_limit || *(volatile int*)b.abort) {
+                    *flag_smem = 0;
+                    break;
+                }
                 __nanosleep(64);
             }
         }
     }
-    ok = __all_sync(kFull, ok);
+    __syncthreads();
+    bool ok = *flag_smem != 0;
     __threadfence();
+    __syncthreads();
     return ok;
 }
 
-template <class P>
-__global__ void __launch_bounds__(128) batched_step_kernel(BatchDev b) {
-    const int lane = threadIdx.x & 31;
+// Persistent kernel of one block-size class: blocks grab (step, instance, strip) items
+// in step order; an item waits for its radial neighbours of the previous step.  Items
+// only wait on items grabbed earlier, so the launch cannot deadlock whatever the
+// number of resident blocks.
+template <class P, int kMaxThreads, int kMinBlocks>
+__global__ void __launch_bounds__(kMaxThreads, kMinBlocks) batched_step_kernel(BatchDev b) {
+    __shared__ StepSmem<typename P::T> sm;
+    __shared__ unsigned long long item;
+    __shared__ int flag;
     const int64_t nsteps = *b.n_steps;
     const int64_t total = b.items_per_step * nsteps;
     for (;;) {
-        unsigned long long g = 0;
-        if (lane == 0) g = atomicAdd(b.counter, 1ull);
-        g = __shfl_sync(kFull, g, 0);
-        if ((int64_t)g >= total) return;
-        if (*(volatile int*)b.abort) return;
+        __syncthreads();
+        if (threadIdx.x == 0) item = atomicAdd(b.counter, 1ull);
+        __syncthreads();
+        const unsigned long long g = item;
+        if ((int64_t)g >= total || *(volatile int*)b.abort) return;
         const int64_t s = (int64_t)g / b.items_per_step, r = (int64_t)g % b.items_per_step;
         int lo = 0, hi = b.n_inst - 1;
         while (lo < hi) {
@@ -208,27 +318,28 @@ __global__ void __launch_bounds__(128) batched_step_kernel(BatchDev b) {
             if (b.item_base[mid] <= r) lo = mid; else hi = mid - 1;
         }
         const int k = lo;
-        const int64_t local = r - b.item_base[k];
+        const int st = (int)(r - b.item_base[k]);
         const InstDev& d = b.inst[k];
-        const int nstrip = b.nstrip[k], chunk = b.chunk[k];
-        const int nck = (d.nth + chunk - 1) / chunk;
-        const int ck = (int)(local / nstrip), strip = (int)(local % nstrip);
+        const int strip = b.strip[k], nstrip = b.nstrip[k];
         int* fl = b.flags + b.item_base[k];
-        if (s > 0 && !wait_neighbours(b, fl, nstrip, nck, strip, ck, s)) {
-            if (lane == 0) {
+        if (s > 0 && !wait_neighbours(b, fl, nstrip, st, s, &flag)) {
+            if (threadIdx.x == 0) {
                 atomicOr(b.status, (unsigned)ST_TIMEOUT);
                 atomicExch(b.abort, 1);
             }
             return;
         }
-        step_item<P>(d, b.base_step[k] + s, (int)((b.base_bin[k] + s) & 1), chunk, strip, ck);
+        const int c0 = 1 + st * strip;
+        const int c1 = min(d.nr - 1, c0 + strip);
+        strip_step<P>(d, b.base_step[k] + s, (int)((b.base_bin[k] + s) & 1), c0, c1, sm);
         __threadfence();
-        __syncwarp();
-        if (lane == 0 && !(s == 0 && r == b.skip_release_item)) st_release(fl + local, (int)(s + 1));
+        __syncthreads();
+        if (threadIdx.x == 0 && !(s == 0 && r == b.skip_release_item))
+            st_release(fl + st, (int)(s + 1));
     }
 }
 
-// Waveform record of the final level of every instance (block row y = instance).
+// Waveform record of the final level of every instance of the class (block row y).
 template <class P>
 __global__ void batched_extract_kernel(BatchDev b) {
     const int k = blockIdx.y;
@@ -239,28 +350,42 @@ __global__ void batched_extract_kernel(BatchDev b) {
     const int bin = (int)((b.base_bin[k] + n) & 1);
     const int64_t step = b.base_step[k] + n;
     const Planes<P> in = Planes<P>::of(d, bin);
-    size_t o = (size_t)j * d.pitch + d.i_e;
-    double2 a = in.load(o).phi64(), c = in.load(o + 1).phi64();
+    double2 a = in.load(node_index(d, d.i_e, j)).phi64();
+    double2 c = in.load(node_index(d, d.i_e + 1, j)).phi64();
     double f = d.f_e;
     double2 w = make_double2((1.0 - f) * a.x + f * c.x, (1.0 - f) * a.y + f * c.y);
     d.wave[(size_t)(step % d.wave_cap) * d.nth + j] = w;
     if (!isfinite(w.x) || !isfinite(w.y)) atomicOr(d.status, (unsigned)ST_NONFINITE);
 }
 
-int batched_grid(int prec) {
+template <class P>
+static int grid_for(int threads) {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (prec == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batched_step_kernel<P64>, 128, 0);
-    else if (prec == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batched_step_kernel<P32>, 128, 0);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batched_step_kernel<PK>, 128, 0);
+    if (threads <= 256)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batched_step_kernel<P, 256, 2>, threads, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batched_step_kernel<P, 1024, 1>, threads, 0);
     return (per > 0 ? per : 1) * (sms > 0 ? sms : 1);
 }
 
-void launch_batched_step(cudaStream_t st, int prec, const BatchDev& b, int grid) {
-    if (prec == 0) batched_step_kernel<P64><<<grid, 128, 0, st>>>(b);
-    else if (prec == 1) batched_step_kernel<P32><<<grid, 128, 0, st>>>(b);
-    else batched_step_kernel<PK><<<grid, 128, 0, st>>>(b);
+int batched_grid(int prec, int threads) {
+    if (prec == 0) return grid_for<P64>(threads);
+    if (prec == 1) return grid_for<P32>(threads);
+    return grid_for<PK>(threads);
+}
+
+template <class P>
+static void launch_batched_p(cudaStream_t st, const BatchDev& b, int grid, int threads) {
+    if (threads <= 256) batched_step_kernel<P, 256, 2><<<grid, threads, 0, st>>>(b);
+    else batched_step_kernel<P, 1024, 1><<<grid, threads, 0, st>>>(b);
+}
+
+void launch_batched_step(cudaStream_t st, int prec, const BatchDev& b, int grid, int threads) {
+    if (prec == 0) launch_batched_p<P64>(st, b, grid, threads);
+    else if (prec == 1) launch_batched_p<P32>(st, b, grid, threads);
+    else launch_batched_p<PK>(st, b, grid, threads);
 }
 
 void launch_batched_extract(cudaStream_t st, int prec, const BatchDev& b, int max_nth) {
@@ -270,14 +395,18 @@ void launch_batched_extract(cudaStream_t st, int prec, const BatchDev& b, int ma
     else batched_extract_kernel<PK><<<g, 128, 0, st>>>(b);
 }
 
-void launch_step(cudaStream_t st, const InstDev& d, int64_t step, int bin, int chunk) {
-    int nstrip = (d.nr - 2 + 29) / 30;
-    int nck = (d.nth + chunk - 1) / chunk;
-    int64_t warps = (int64_t)nstrip * nck;
-    int blocks = (int)((warps * 32 + 127) / 128);
-    if (d.prec == 0) step_kernel<P64><<<blocks, 128, 0, st>>>(d, step, bin, chunk);
-    else if (d.prec == 1) step_kernel<P32><<<blocks, 128, 0, st>>>(d, step, bin, chunk);
-    else step_kernel<PK><<<blocks, 128, 0, st>>>(d, step, bin, chunk);
+template <class P>
+static void launch_step_p(cudaStream_t st, const InstDev& d, int64_t step, int bin, int strip) {
+    int blocks = (d.nr - 2 + strip - 1) / strip;
+    int threads = d.pitch;
+    if (threads <= 256) step_kernel_s<P><<<blocks, threads, 0, st>>>(d, step, bin, strip);
+    else step_kernel_l<P><<<blocks, threads, 0, st>>>(d, step, bin, strip);
+}
+
+void launch_step(cudaStream_t st, const InstDev& d, int64_t step, int bin, int strip) {
+    if (d.prec == 0) launch_step_p<P64>(st, d, step, bin, strip);
+    else if (d.prec == 1) launch_step_p<P32>(st, d, step, bin, strip);
+    else launch_step_p<PK>(st, d, step, bin, strip);
 }
 
 void launch_extract(cudaStream_t st, const InstDev& d, int64_t step, int bin) {

@@ -7,6 +7,7 @@
 namespace teuk {
 
 constexpr unsigned kFull = 0xffffffffu;
+constexpr int kMaxWarps = 32;     // a block holds one theta column of up to 1024 rows
 
 // ---------------------------------------------------------------- complex
 template <typename T>
@@ -23,15 +24,20 @@ template <typename T>
 __device__ __forceinline__ Cx<T> operator-(Cx<T> a, Cx<T> b) { return {a.re - b.re, a.im - b.im}; }
 template <typename T>
 __device__ __forceinline__ Cx<T> operator*(T s, Cx<T> a) { return {s * a.re, s * a.im}; }
+// Fused multiply-add in the type itself (a plain fma() call on floats would resolve to
+// the double overload and run on the FP64 pipe).
+__device__ __forceinline__ float tfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double tfma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 // acc + (cr + i ci) * z
 template <typename T>
 __device__ __forceinline__ Cx<T> cmac(Cx<T> acc, T cr, T ci, Cx<T> z) {
-    return {fma(cr, z.re, fma(-ci, z.im, acc.re)), fma(cr, z.im, fma(ci, z.re, acc.im))};
+    return {tfma(cr, z.re, tfma(-ci, z.im, acc.re)), tfma(cr, z.im, tfma(ci, z.re, acc.im))};
 }
 // acc + s * z (s real)
 template <typename T>
 __device__ __forceinline__ Cx<T> rmac(Cx<T> acc, T s, Cx<T> z) {
-    return {fma(s, z.re, acc.re), fma(s, z.im, acc.im)};
+    return {tfma(s, z.re, acc.re), tfma(s, z.im, acc.im)};
 }
 
 __device__ __forceinline__ float shfl_down_t(float v) { return __shfl_down_sync(kFull, v, 1); }
@@ -183,21 +189,22 @@ struct HalfRec { Cx<T> Fb, Pb, dF, dP, Dp, hF, hP; };
 template <typename T>
 struct CRow {
     Cx<T> Hs;        // (dh_Phi_R + dh_Phi_L)/2
-    Cx<T> DpS;       // (Dp_R + Dp_L)/2 = u~-averaged theta difference to the next row, minus the Hs part
+    Cx<T> DpS;       // (Dp_R + Dp_L)/2
     Cx<T> FC, PC;    // u~ = (h_R + h_L)/2 for Phi and Pi
     Cx<T> dFc, dPc;  // h_R - h_L for Phi and Pi
-    __device__ __forceinline__ CRow mirror(T g) const {
-        CRow r;
-        r.Hs = g * Hs; r.DpS = g * DpS; r.FC = g * FC; r.PC = g * PC; r.dFc = g * dFc; r.dPc = g * dPc;
-        return r;
-    }
 };
 
 template <typename T>
-struct CRing {
-    CRow<T> a, b, c;  // rows jc-1, jc, jc+1 once full
-    __device__ __forceinline__ void push(const CRow<T>& r) { a = b; b = c; c = r; }
-};
+__device__ __forceinline__ CRow<T> combine_lr(const HalfRec<T>& R, const HalfRec<T>& L) {
+    CRow<T> c;
+    c.Hs = Cx<T>::half_sum(R.hF, L.hF);
+    c.DpS = Cx<T>::half_sum(R.Dp, L.Dp);
+    c.FC = Cx<T>::half_sum(R.Fb, L.Fb) + c.Hs;
+    c.PC = Cx<T>::half_sum(R.Pb, L.Pb) + Cx<T>::half_sum(R.hP, L.hP);
+    c.dFc = Cx<T>::half_sum(R.dF, L.dF) + (R.hF - L.hF);
+    c.dPc = Cx<T>::half_sum(R.dP, L.dP) + (R.hP - L.hP);
+    return c;
+}
 
 template <typename T>
 __device__ __forceinline__ void load_coefs(const T* tab, size_t pl, size_t o, bool ok, T* cf) {
@@ -208,7 +215,8 @@ __device__ __forceinline__ void load_coefs(const T* tab, size_t pl, size_t o, bo
 // FP32 coefficients of one node from its radial table and its theta row (see RTab).
 __device__ __forceinline__ void form_coefs(const RTab& t, const ThTab& h, float* cf) {
     float sig2 = fmaf(-t.aD, h.sin2, t.R2);
-    float iS = __frcp_rn(sig2);
+    float iS = __fdividef(1.0f, sig2);             // hardware estimate, then one Newton step
+    iS = fmaf(iS, fmaf(-sig2, iS, 1.0f), iS);
     float rs = rsqrtf(sig2);
     rs = rs * fmaf(-0.5f * sig2 * rs, rs, 1.5f);  // one Newton step on 1/sqrt
     float g = t.Rd * rs;
@@ -227,40 +235,49 @@ __device__ __forceinline__ void form_coefs(const RTab& t, const ThTab& h, float*
     cf[C_E3I] = t.qi * iS;
 }
 
-// The radial table of one column, held in registers for a whole work item (FP32 paths;
-// empty for FP64, which reads 2D tables).
+__device__ __forceinline__ RTab load_rtab(const RTab* tab, int i) {
+    const float4* q = (const float4*)(tab + i);
+    const float4 a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + 2), e = __ldg(q + 3);
+    return RTab{a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w, e.x, 0.f, 0.f, 0.f};
+}
+
+// The theta table of one row, held in registers by its thread for a whole work item
+// (FP32 paths; empty for FP64, which reads 2D tables).
 template <class P>
-struct ColTab {
-    RTab t;
-    __device__ __forceinline__ void load(const RTab* tab, int i, bool ok) {
+struct RowTab {
+    ThTab t;
+    __device__ __forceinline__ void load(const ThTab* tab, int j, bool ok) {
         if constexpr (sizeof(typename P::T) == 4) {
-            if (ok) {
-                const float4* q = (const float4*)(tab + i);
-                float4 a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + 2), e = __ldg(q + 3);
-                t = RTab{a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w, e.x, 0.f, 0.f, 0.f};
-            } else {
-                t = RTab{};
-            }
+            t = ok ? tab[j] : ThTab{};
         }
     }
 };
 
 // Coefficients of the predictor (half = true, node i+1/2) or the corrector (node i) at
 // row j: read from the 2D FP64 tables, or formed in registers on the FP32 paths from
-// the column's radial table and the row's theta table.
+// the column's radial table (the same address for the whole block) and the row's
+// theta table.
 template <class P>
-__device__ __forceinline__ void get_coefs(const InstDev& d, const ColTab<P>& col, bool half, int i,
-                                          int j, bool ok, typename P::T* cf) {
+__device__ __forceinline__ void get_coefs(const InstDev& d, const RowTab<P>& row, bool half,
+                                          int i, int j, bool ok, typename P::T* cf) {
     if constexpr (sizeof(typename P::T) == 8) {
         load_coefs((const double*)(half ? d.coef_h : d.coef_i), plane_elems(d),
-                   (size_t)j * d.pitch + i, ok, cf);
+                   node_index(d, i, j), ok, cf);
     } else {
-        const ThTab h = d.thtab[j];
-        form_coefs(col.t, h, cf);
-        if (!ok) {
-#pragma unroll
-            for (int k = 0; k < kNCoef; ++k) cf[k] = 0.f;
-        }
+        form_coefs(load_rtab(half ? d.rtab_h : d.rtab_i, i), row.t, cf);
+    }
+}
+
+// Same, from a radial table already in registers (prefetched by the caller).
+template <class P>
+__device__ __forceinline__ void get_coefs_pre(const InstDev& d, const RowTab<P>& row, const RTab& t,
+                                              bool half, int i, int j, bool ok,
+                                              typename P::T* cf) {
+    if constexpr (sizeof(typename P::T) == 8) {
+        load_coefs((const double*)(half ? d.coef_h : d.coef_i), plane_elems(d),
+                   node_index(d, i, j), ok, cf);
+    } else {
+        form_coefs(t, row.t, cf);
     }
 }
 
@@ -279,23 +296,6 @@ __device__ __forceinline__ HalfRec<T> predictor(const Half<T>& h, Cx<T> Dp, Cx<T
     a = cmac(a, cf[C_E3R], cf[C_E3I], h.Fb);
     r.hP = a;
     return r;
-}
-
-template <typename T>
-__device__ __forceinline__ CRow<T> combine_lr(const HalfRec<T>& R) {
-    HalfRec<T> L;
-    L.Fb = shfl_up_c(R.Fb); L.Pb = shfl_up_c(R.Pb);
-    L.dF = shfl_up_c(R.dF); L.dP = shfl_up_c(R.dP);
-    L.Dp = shfl_up_c(R.Dp);
-    L.hF = shfl_up_c(R.hF); L.hP = shfl_up_c(R.hP);
-    CRow<T> c;
-    c.Hs = Cx<T>::half_sum(R.hF, L.hF);
-    c.DpS = Cx<T>::half_sum(R.Dp, L.Dp);
-    c.FC = Cx<T>::half_sum(R.Fb, L.Fb) + c.Hs;
-    c.PC = Cx<T>::half_sum(R.Pb, L.Pb) + Cx<T>::half_sum(R.hP, L.hP);
-    c.dFc = Cx<T>::half_sum(R.dF, L.dF) + (R.hF - L.hF);
-    c.dPc = Cx<T>::half_sum(R.dP, L.dP) + (R.hP - L.hP);
-    return c;
 }
 
 // ---------------------------------------------------------------- source
@@ -330,53 +330,6 @@ __device__ __forceinline__ Cx<T> source_int(const SourceDev& s, double2 fac, int
     if ((unsigned)a < (unsigned)s.ni && (unsigned)b < (unsigned)s.nj)
         return cmul_cast<T>(fac, s.P_int[(size_t)b * s.ni + a]);
     return Cx<T>::zero();
-}
-
-// Eq. (14) for row jc of the own column, store of u^{n+1}, and the waveform
-// record of the input state (time level `step`) when this warp holds r*_ext.
-template <class P>
-__device__ __forceinline__ void corrector(const InstDev& d, const Planes<P>& in,
-                                          const Planes<P>& out, const CRing<typename P::T>& ring,
-                                          int jc, int i, bool out_ok, bool bnd, bool ex_warp,
-                                          bool src_warp, const ColTab<P>& coli,
-                                          typename P::T fdt, double2 sc_fac, int64_t step) {
-    using T = typename P::T;
-    using C = Cx<T>;
-    const CRow<T>& a = ring.a;
-    const CRow<T>& b = ring.b;
-    const CRow<T>& c = ring.c;
-    const bool col_ok = i < d.nr;
-    C Dplus = b.DpS + (c.Hs - b.Hs);
-    C Dminus = a.DpS + (b.Hs - a.Hs);
-    const size_t o = (size_t)jc * d.pitch + i;
-    T cf[kNCoef];
-    get_coefs<P>(d, coli, false, i, jc, col_ok, cf);
-    C src = C::zero();
-    if (src_warp) src = source_int<T>(d.src, sc_fac, i, jc);
-    C dPhi = rmac(rmac(C::zero(), -cf[C_G], b.dFc), fdt, b.PC);
-    C dPi = rmac(src, cf[C_G], b.dPc);
-    dPi = cmac(dPi, cf[C_E1R], cf[C_E1I], b.PC);
-    dPi = cmac(dPi, cf[C_E2R], cf[C_E2I], b.dFc);
-    dPi = rmac(dPi, cf[C_EP], Dplus);
-    dPi = rmac(dPi, -cf[C_EM], Dminus);
-    dPi = cmac(dPi, cf[C_E3R], cf[C_E3I], b.FC);
-    NodeV<P> u = col_ok ? in.load(o) : NodeV<P>::zero();
-    if (ex_warp) {
-        double2 ph = u.phi64();
-        double2 phn = make_double2(__shfl_down_sync(kFull, ph.x, 1), __shfl_down_sync(kFull, ph.y, 1));
-        if (i == d.i_e) {
-            double f = d.f_e;
-            double2 w = make_double2((1.0 - f) * ph.x + f * phn.x, (1.0 - f) * ph.y + f * phn.y);
-            d.wave[(size_t)(step % d.wave_cap) * d.nth + jc] = w;
-            if (!isfinite(w.x) || !isfinite(w.y)) atomicOr(d.status, (unsigned)ST_NONFINITE);
-        }
-    }
-    if (out_ok) {
-        u.update(dPhi, dPi);
-        out.store(o, u);
-    } else if (bnd) {
-        out.store(o, NodeV<P>::zero());
-    }
 }
 
 }  // namespace teuk
