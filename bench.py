@@ -325,20 +325,81 @@ def cpu_baseline(cfg, budget_s=12.0):
 
 
 def run_reference(args, world, rank):
+    """The reference arm: the oracle (single-threaded FP64 C, the only reference this
+    paper has) on the host cores, on the same 16384 x 256 workload.  One bench step is
+    one full time step; the per-step time comes from two run lengths (warmup and
+    warmup + steps) so the oracle's setup is excluded."""
     if rank != 0:
         return 0
+    from oracle import teuk_oracle as orc
     from paper_1001_3631_gb300 import inputs
     cfg = inputs.PAPER_SCALE_16384x256
-    cb = cpu_baseline(cfg, budget_s=8.0)
-    line = {"impl": "reference", "metric": "grid-point updates/s", "value": cb["value"],
-            "unit": "updates/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "impl": "oracle on host cores"},
+    p = orc.params(**cfg["params"], r0=cfg["r0"])
+    src = orc.orbit_source(p)
+    W, K = max(1, args.warmup), max(1, args.steps)
+    t0 = time.perf_counter()
+    orc.run(p, None, W, src, wave=False)
+    t1 = time.perf_counter()
+    orc.run(p, None, W + K, src, wave=False)
+    t2 = time.perf_counter()
+    per_step = max((t2 - t1) - (t1 - t0), 1e-9) / K
+    npts = p.n_rstar * p.n_theta
+    value = npts / per_step
+    cb = {"value": value, "unit": "updates/s", "cores": 1, "kind": "oracle",
+          "sample": "%d timed full steps of the %dx%d grid (setup excluded by differencing)"
+                    % (K, p.n_rstar, p.n_theta)}
+    line = {"impl": "reference", "metric": "grid-point updates/s", "value": value,
+            "unit": "updates/s", "n_gpus": args.gpus, "steps": K, "warmup": W,
+            "ms_per_step": per_step * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "impl": "oracle on host cores",
+                       "time_steps_per_bench_step": 1},
             "cpu_baseline": cb,
-            "e2e": {"value": cb["value"], "unit": "updates/s", "h2d_bytes_per_step": 0,
+            "e2e": {"value": value, "unit": "updates/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
+
+
+def precision_sweep(steps=100000, every=1000):
+    """Long run of the 8192 x 128 single mode at a = 0.99: waveform relative error of the
+    FP32 and FP32-Kahan paths against the FP64 path every `every` steps, at the stated
+    extraction radius r* = 400 and at a near-zone probe r* = 30 (the signal of the
+    particle at r*(8M) = 10.2 does not reach r* = 400 within steps * dt = 204 M)."""
+    import numpy as np
+    import torch
+
+    from paper_1001_3631_gb300 import TeukSolver, inputs
+    cfg = inputs.LONG_RUN_8192x128
+    out = {"workload": "long run 8192x128 (s=-2, m=2, a=0.99, r0=8M), %d steps" % steps,
+           "every": every}
+    waves = {}
+    for prec in ("fp64", "fp32", "fp32_kahan"):
+        ctxs = []
+        for ext in (400.0, 30.0):
+            s = TeukSolver(dict(cfg["params"], prec=prec, rstar_ext=ext, wave_capacity=steps + 1))
+            s.set_source(cfg["r0"])
+            ctxs.append(s)
+        t0 = time.perf_counter()
+        for s in ctxs:
+            s.step(steps)
+        torch.cuda.synchronize()
+        out["seconds_" + prec] = time.perf_counter() - t0
+        waves[prec] = [s.extract(cap=steps + 1)[0] for s in ctxs]
+        for s in ctxs:
+            s.close()
+    for prec in ("fp32", "fp32_kahan"):
+        for k, ext in enumerate((400.0, 30.0)):
+            ref, got = waves["fp64"][k], waves[prec][k]
+            errs = []
+            for n in range(every, steps + 1, every):
+                a, b = got[:n + 1], ref[:n + 1]
+                nb = np.linalg.norm(b)
+                errs.append(float(np.linalg.norm(a - b) / nb) if nb > 0 else None)
+            out["%s_r%d" % (prec, int(ext))] = {"rel_err_every": errs,
+                                               "final": errs[-1], "max": max(e for e in errs if e is not None) if any(e is not None for e in errs) else None,
+                                               "ref_norm": float(np.linalg.norm(ref))}
+    return out
 
 
 def main():
@@ -354,6 +415,8 @@ def main():
     ap.add_argument("--only", choices=["fp32_kahan", "fp64"], default=None,
                     help="time one path only (for profiler captures)")
     ap.add_argument("--accuracy-steps", type=int, default=4000)
+    ap.add_argument("--precision-sweep", action="store_true",
+                    help="run the 8192x128 long-run precision sweep and print its JSON")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
@@ -362,6 +425,11 @@ def main():
 
     import torch
     torch.cuda.set_device(local)
+    if args.precision_sweep:
+        from paper_1001_3631_gb300 import build as b
+        b.build()
+        print(json.dumps(precision_sweep()))
+        return 0
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
