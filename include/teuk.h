@@ -167,21 +167,22 @@ teuk_status teuk_get_time(const teuk_ctx* ctx, int instance, int64_t* step, doub
  * W = (1 - f_e) Phi_{i_e} + f_e Phi_{i_e + 1}. */
 teuk_status teuk_get_geometry(const teuk_ctx* ctx, int instance, double* out);
 
-/* Launch configuration: theta rows per work item for every instance (0 = automatic;
- * a per-instance choice from teuk_set_instance_tiling / teuk_autotune wins), and the
+/* Launch configuration: r* columns per thread block ("strip"; a block holds one whole
+ * theta column and streams along r*) for every instance (0 = automatic; a
+ * per-instance choice from teuk_set_instance_tiling / teuk_autotune wins), and the
  * launch mode: steps_per_launch >= 1 launches one fused kernel per step (single-instance
  * contexts); 0 sends a single-instance context through the persistent batched kernel
  * that multi-instance contexts always use.  Results do not depend on either choice
  * (the per-point arithmetic is fixed). */
-teuk_status teuk_set_tiling(teuk_ctx* ctx, int theta_chunk, int steps_per_launch);
+teuk_status teuk_set_tiling(teuk_ctx* ctx, int strip, int steps_per_launch);
 
-/* Theta rows per work item of one instance (0 = back to the context default). */
-teuk_status teuk_set_instance_tiling(teuk_ctx* ctx, int instance, int theta_chunk);
+/* Strip length (r* columns per block) of one instance (0 = back to the context default). */
+teuk_status teuk_set_instance_tiling(teuk_ctx* ctx, int instance, int strip);
 
 /* Autotuner: for every distinct (n_theta, precision, n_rstar rounded up to a power of
- * two) class of the context, time trial_steps steps of each candidate theta chunk
- * (4 .. n_theta, powers of two) on a scratch copy of one instance of the class and keep
- * the fastest for all its instances.  chosen (may be NULL) receives the chunk of each
+ * two) class of the context, time trial_steps steps of each candidate strip length
+ * (8 .. 512 columns) on a scratch copy of one instance of the class and keep the
+ * fastest for all its instances.  chosen (may be NULL) receives the strip of each
  * instance.  The state and the waveform records are not changed.  Synchronizes. */
 teuk_status teuk_autotune(teuk_ctx* ctx, int trial_steps, int* chosen);
 

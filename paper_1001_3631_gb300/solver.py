@@ -142,21 +142,23 @@ class TeukSolver:
         return dict(drs=out[0], dth=out[1], dt=out[2], rp=out[3], rm=out[4], r_ext=out[5],
                     i_e=int(out[6]), f_e=out[7])
 
-    def set_tiling(self, theta_chunk=0, steps_per_launch=0):
-        check(_lib.load().teuk_set_tiling(self.ctx, theta_chunk, steps_per_launch), self.ctx)
+    def set_tiling(self, strip=0, steps_per_launch=1):
+        """strip: r* columns per thread block (0 = automatic); steps_per_launch 0 sends a
+        single-instance context through the persistent batched kernel."""
+        check(_lib.load().teuk_set_tiling(self.ctx, strip, steps_per_launch), self.ctx)
 
     def kernel_launches(self):
         return _lib.load().teuk_kernel_launches(self.ctx)
 
-    def set_instance_tiling(self, instance, theta_chunk):
-        check(_lib.load().teuk_set_instance_tiling(self.ctx, instance, theta_chunk), self.ctx)
+    def set_instance_tiling(self, instance, strip):
+        check(_lib.load().teuk_set_instance_tiling(self.ctx, instance, strip), self.ctx)
 
     def set_fault_injection(self, skip_release_item=-1, spin_limit=0):
         check(_lib.load().teuk_set_fault_injection(self.ctx, skip_release_item, spin_limit),
               self.ctx)
 
     def autotune(self, trial_steps=10, cache_path=None):
-        """Theta chunk per instance from a cached table keyed by (GPU, n_theta, precision,
+        """Strip length per instance from a cached table keyed by (GPU, n_theta, precision,
         n_rstar bucket); classes missing from the table are timed by teuk_autotune."""
         import torch
         path = cache_path or os.environ.get("TEUK_TUNE_CACHE") or os.path.join(

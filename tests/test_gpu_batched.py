@@ -26,9 +26,9 @@ def rel(a, b):
     return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
 
 
-def run_single(inst, prec, steps, chunk, persistent=False):
+def run_single(inst, prec, steps, strip, persistent=False):
     with TeukSolver(dict(inst["params"], prec=prec)) as s:
-        s.set_tiling(chunk, 0 if persistent else 1)
+        s.set_tiling(strip, 0 if persistent else 1)
         s.set_source(inst["r0"], inputs.amplitudes(100, seed=inst["step0"] + 1))
         u0 = inputs.random_state(inst["params"]["n_theta"], inst["params"]["n_rstar"], seed=2)
         s.set_state(u0, inst["step0"])
@@ -40,9 +40,9 @@ def run_single(inst, prec, steps, chunk, persistent=False):
     return u, w, first
 
 
-def run_batched(prec, steps, chunk, stream=None):
+def run_batched(prec, steps, strip, stream=None):
     with TeukSolver([dict(i["params"], prec=prec) for i in INST], stream=stream) as s:
-        s.set_tiling(chunk, 1)
+        s.set_tiling(strip, 1)
         for k, inst in enumerate(INST):
             s.set_source(inst["r0"], inputs.amplitudes(100, seed=inst["step0"] + 1), instance=k)
             u0 = inputs.random_state(inst["params"]["n_theta"], inst["params"]["n_rstar"], seed=2)

@@ -18,10 +18,10 @@ def rel(a, b):
     return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
 
 
-def gpu_run(params, r0, nsteps, u0=None, amps=None, prec="fp64", chunk=0, step0=0,
-            sigma_abs=None):
+def gpu_run(params, r0, nsteps, u0=None, amps=None, prec="fp64", strip=0, step0=0,
+            sigma_abs=None, persistent=False):
     with TeukSolver(dict(params, prec=prec)) as s:
-        s.set_tiling(chunk)
+        s.set_tiling(strip, 0 if persistent else 1)
         if r0 is not None:
             if sigma_abs:
                 s.set_source(r0, amps, sigma_rstar_abs=sigma_abs[0], sigma_theta_abs=sigma_abs[1])
@@ -46,11 +46,13 @@ def oracle_run(orc, params, r0, nsteps, u0=None, amps=None, step0=0, sigma_abs=N
 
 
 SMALL = [
-    # (n_rstar, n_theta, m, a, rstar range, r0, ext)  ragged sizes on purpose
+    # (n_rstar, n_theta, m, a, rstar range, r0, ext)  ragged sizes on purpose;
+    # n_theta = 300 runs the kernel variant for columns of more than 256 rows
     (97, 12, 2, 0.9, (-10.0, 30.0), 6.0, 20.0),
     (151, 33, 3, 0.7, (-20.0, 40.0), 8.0, 35.0),
     (64, 8, 1, 0.0, (-10.0, 30.0), 7.0, 29.9),
     (8, 4, 2, 0.5, (-2.0, 12.0), 6.0, 10.0),
+    (45, 300, 2, 0.6, (-10.0, 30.0), 6.0, 22.0),
 ]
 
 
@@ -63,11 +65,12 @@ def test_fp64_small_grids_random_state_and_source(orc, case):
     amps = inputs.amplitudes(40, seed=nr)
     uo, wo = oracle_run(orc, params, r0, 37, u0, amps)
     ref = None
-    for chunk in (0, 5, nth):
-        ug, wg, first = gpu_run(params, r0, 37, u0, amps, chunk=chunk)
+    # one fused launch per step with three strip lengths, then the persistent kernel
+    for strip, pers in ((0, False), (5, False), (nth, False), (0, True), (7, True)):
+        ug, wg, first = gpu_run(params, r0, 37, u0, amps, strip=strip, persistent=pers)
         assert first == 0 and wg.shape == wo.shape
-        assert rel(ug, uo) <= FP64_TOL, (chunk, rel(ug, uo))
-        assert rel(wg, wo) <= FP64_TOL, (chunk, rel(wg, wo))
+        assert rel(ug, uo) <= FP64_TOL, (strip, pers, rel(ug, uo))
+        assert rel(wg, wo) <= FP64_TOL, (strip, pers, rel(wg, wo))
         if ref is None:
             ref = (ug, wg)
         else:  # the per-point arithmetic does not depend on the tiling
@@ -105,9 +108,10 @@ def test_fp32_paths_single_mode(orc, prec, tol_state, tol_wave):
     assert es <= tol_state and ew <= tol_wave
 
 
+@pytest.mark.parametrize("case", [SMALL[1], SMALL[4]])
 @pytest.mark.parametrize("prec", ["fp32", "fp32_kahan"])
-def test_fp32_paths_small_grids(orc, prec):
-    nr, nth, m, a, (lo, hi), r0, ext = SMALL[1]
+def test_fp32_paths_small_grids(orc, prec, case):
+    nr, nth, m, a, (lo, hi), r0, ext = case
     params = dict(s=-2, m=m, a=a, rstar_min=lo, rstar_max=hi, n_rstar=nr, n_theta=nth,
                   rstar_ext=ext, dt_rule=1, courant=0.5)
     u0 = inputs.smooth_state(nth, nr, seed=3)
