@@ -278,6 +278,7 @@ extern "C" teuk_status teuk_create(const teuk_params* p, int n_instances, void* 
             return fail(_e == cudaErrorMemoryAllocation ? TEUK_ENOMEM : TEUK_ECUDA); \
         }                                                                         \
     } while (0)
+    TK_CCUDA(prepare_step_kernels());
     TK_CCUDA(cudaMallocAsync((void**)&c->status, sizeof(unsigned), c->stream));
     TK_CCUDA(cudaMemsetAsync(c->status, 0, sizeof(unsigned), c->stream));
     for (Instance& I : c->inst) {

@@ -126,6 +126,7 @@ void launch_profile(cudaStream_t st, double M, double a, double rstar_min, doubl
                     double rs0, double sig_r, double sig_t, double drs0_dr0, const double* x_int,
                     const double* x_half, const SourceDev& src);
 // teuk_step.cu
+cudaError_t prepare_step_kernels();
 void launch_step(cudaStream_t st, const InstDev& d, int64_t step, int bin, int strip);
 void launch_extract(cudaStream_t st, const InstDev& d, int64_t step, int bin);
 void launch_batched_step(cudaStream_t st, int prec, const BatchDev& b, int grid, int threads);

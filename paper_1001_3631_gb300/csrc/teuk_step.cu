@@ -2,7 +2,8 @@
 //
 // Work decomposition: a thread block holds one whole theta column (thread j = row j,
 // blockDim = n_theta rounded up to a warp) and streams along r* over a strip of
-// columns [c0, c1).  At each column it loads u^n(i, j) (prefetched one column ahead),
+// columns [c0, c1).  The columns of u^n arrive in a ring of shared-memory slots, filled
+// by bulk-async (TMA) copies several columns ahead of use; at each column the block
 // computes the predictor (Eq. 13) at the half node just behind it and the corrector
 // (Eq. 14) at the column behind that, and stores u^{n+1}.  Radial neighbours are the
 // registers of the previous column; theta neighbours come from the lanes above and
@@ -75,27 +76,162 @@ __device__ __forceinline__ void xchg(Xchg<T>& X, int par, const T* down_in, T* d
     }
 }
 
+// ---------------------------------------------------------------- column ring
+// PTX wrappers: mbarrier and the bulk-async copy global -> shared (TMA, untiled form).
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* b) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(b)) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(b)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* b, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsigned bytes,
+                                              uint64_t* b) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(b))
+        : "memory");
+}
+// Orders this thread's view of global memory (generic proxy) before its later bulk copies.
+__device__ __forceinline__ void fence_proxy_async_global() {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+// Columns of the input level (every plane, plus on the FP32 paths the column's two
+// radial tables) are copied into kRing shared-memory slots by one thread, kRing - 2
+// columns ahead of use; each slot has an mbarrier that its copy completes.  A column's
+// state is read when it arrives and its radial tables one column later, so its slot is
+// refilled after the first barrier two columns on, when every thread has finished with
+// it.  Copies start on 16-byte boundaries with sizes in multiples of 16 bytes: a column
+// is n_theta 16-byte nodes at a 512-byte aligned offset, a radial table 64 bytes.
+constexpr int kRing = 6;
+constexpr unsigned long long kRingWaitNs = 1000000000ull;  // a slot wait gives up after 1 s
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+template <class P>
+struct ColumnRing {
+    static constexpr bool kTabs = sizeof(typename P::T) == 4;
+    __host__ __device__ static unsigned slot_bytes(int threads) {
+        return (unsigned)P::planes * (unsigned)threads * 16u + (kTabs ? 2u * (unsigned)sizeof(RTab) : 0u);
+    }
+    __host__ __device__ static unsigned ring_bytes(int threads) { return kRing * slot_bytes(threads); }
+
+    unsigned char* base;  // kRing slots: planes [P::planes][stride] of 16-byte nodes, tables
+    uint64_t* mbar;       // [kRing]
+    unsigned stride;      // nodes per plane in a slot (the block size)
+    unsigned sbytes;
+    unsigned phase;       // bit s: parity of the next completion awaited on slot s
+    bool late;            // a wait gave up
+
+    __device__ __forceinline__ ColumnRing(unsigned char* b, uint64_t* m)
+        : base(b), mbar(m), stride(blockDim.x), sbytes(slot_bytes(blockDim.x)), phase(0), late(false) {}
+
+    // One thread, once per block, before any fill; the block synchronizes afterwards.
+    __device__ __forceinline__ void init() const {
+        for (int k = 0; k < kRing; ++k) mbar_init(mbar + k);
+        mbar_init_fence();
+    }
+    __device__ __forceinline__ unsigned char* slot(int s) const { return base + (size_t)s * sbytes; }
+    // One thread: copy column col of buffer bin (and its radial tables) into slot s.
+    __device__ __forceinline__ void fill(const InstDev& d, int bin, int col, int s) const {
+        unsigned char* dst = slot(s);
+        const unsigned nb = (unsigned)d.nth * 16u;
+        mbar_expect_tx(mbar + s, P::planes * nb + (kTabs ? 2u * (unsigned)sizeof(RTab) : 0u));
+        const size_t off = (size_t)col * (size_t)d.pitch * 16u;
+#pragma unroll
+        for (int q = 0; q < P::planes; ++q)
+            bulk_copy_g2s(dst + q * stride * 16u, (const unsigned char*)d.buf[bin][q] + off, nb, mbar + s);
+        if constexpr (kTabs) {
+            unsigned char* t = dst + P::planes * stride * 16u;
+            bulk_copy_g2s(t, d.rtab_h + col, sizeof(RTab), mbar + s);
+            bulk_copy_g2s(t + sizeof(RTab), d.rtab_i + col, sizeof(RTab), mbar + s);
+        }
+    }
+    // Wait for the next copy into slot s.  Once a wait has given up, the thread waits
+    // no more (its results are void and the status word says so).
+    __device__ __forceinline__ void wait(int s) {
+        const unsigned par = (phase >> s) & 1u;
+        phase ^= 1u << s;
+        if (mbar_try_wait(mbar + s, par) || late) return;
+        const unsigned long long t0 = global_ns();
+        while (!mbar_try_wait(mbar + s, par))
+            if (global_ns() - t0 > kRingWaitNs) { late = true; return; }
+    }
+    __device__ __forceinline__ NodeV<P> node(int s, int j, bool ok) const {
+        return ok ? Planes<P>::at(slot(s), stride).load((size_t)j) : NodeV<P>::zero();
+    }
+    // Radial table of the column in slot s: which = 0 half node i+1/2, 1 node i.
+    __device__ __forceinline__ RTab tab(int s, int which) const {
+        RTab t{};
+        if constexpr (kTabs) {
+            const float4* q = (const float4*)(slot(s) + P::planes * stride * 16u) + 4 * which;
+            const float4 a = q[0], b = q[1], c = q[2], e = q[3];
+            t = RTab{a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w, e.x, 0.f, 0.f, 0.f};
+        }
+        return t;
+    }
+    // After a wait gave up: give every copy still in flight (bounded) time to land, so
+    // the block never exits with a copy into its shared memory outstanding.
+    __device__ void drain() const {
+        const unsigned long long t0 = global_ns();
+        for (int k = 0; k < kRing; ++k)
+            while (!mbar_try_wait(mbar + k, ((phase >> k) & 1u) ^ 1u))
+                if (global_ns() - t0 > kRingWaitNs) return;
+    }
+};
+
 // One work item: the columns [c0, c1) of one instance for one step, one thread per row.
 // Per column c: (1) exchange Phi(c) with the rows above and below -> theta differences
 // dl(c) = Phi(j+1) - Phi(j) and dlm(c) = Phi(j) - Phi(j-1); (2) predictor at the half
 // node c-1/2; (3) exchange its results with the rows above and below; (4) corrector at
 // column c-1.  Two barriers per column.  The first two columns are peeled so the
 // steady-state loop has no per-column mode switches, and it is unrolled by three so the
-// rotation of the previous / current / prefetched column is register renaming.
+// rotation of the previous / current column is register renaming.  Columns c0-1 .. c1
+// are read, through the ring.
 template <class P>
 __device__ __forceinline__ void strip_step(const InstDev& d, int64_t step, int bin, int c0,
-                                           int c1, StepSmem<typename P::T>& sm) {
+                                           int c1, StepSmem<typename P::T>& sm,
+                                           ColumnRing<P>& ring) {
     using T = typename P::T;
     using C = Cx<T>;
     constexpr int KF = P::kahan ? 4 : 2;   // Phi values exchanged: hi (and c)
-    constexpr bool kRT = sizeof(T) == 4;  // FP32 paths: radial tables, prefetched a column ahead
     const int j = threadIdx.x;
     const int nth = d.nth;
     const bool row_ok = j < nth;
     const bool bot = j == 0, top = j == nth - 1;
+    const bool one_warp = blockDim.x <= 32;
     const T g = (T)d.ghost;
     const T hdt = (T)(0.5 * d.dt), fdt = (T)d.dt;
-    const Planes<P> in = Planes<P>::of(d, bin), out = Planes<P>::of(d, 1 - bin);
+    const Planes<P> out = Planes<P>::of(d, 1 - bin);
+    const int ncols = c1 - c0 + 2;
+    if (threadIdx.x == 0) {
+        fence_proxy_async_global();
+        for (int k = 0; k < ncols && k < kRing; ++k) ring.fill(d, bin, c0 - 1 + k, k);
+    }
     RowTab<P> rt;
     rt.load(d.thtab, j, row_ok);
     const size_t pitch = (size_t)d.pitch;
@@ -136,7 +272,7 @@ __device__ __forceinline__ void strip_step(const InstDev& d, int64_t step, int b
         const C Dp = C::half_sum(dll, dlr);     // Fb(j+1) - Fb(j)
         const C Dm = C::half_sum(dlml, dlmr);   // Fb(j) - Fb(j-1)
         T cf[kNCoef];
-        get_coefs_pre<P>(d, rt, tab, true, h, j, row_ok, cf);
+        get_coefs<P>(d, rt, tab, true, h, j, row_ok, cf);
         C src = C::zero();
         if (src_blk) src = source_half<T>(sw, sp_fac, h, j);
         return predictor<T>(hp, Dp, Dm, cf, hdt, src);
@@ -158,7 +294,7 @@ __device__ __forceinline__ void strip_step(const InstDev& d, int64_t step, int b
         const C Dplus = row.DpS + (Hs_p - row.Hs);
         const C Dminus = DpS_m + (row.Hs - Hs_m);
         T cf[kNCoef];
-        get_coefs_pre<P>(d, rt, tab, false, cc, j, row_ok, cf);
+        get_coefs<P>(d, rt, tab, false, cc, j, row_ok, cf);
         C srcc = C::zero();
         if (src_blk) srcc = source_int<T>(sw, sc_fac, cc, j);
         C dPhi = rmac(rmac(C::zero(), -cf[C_G], row.dFc), fdt, row.PC);
@@ -183,62 +319,85 @@ __device__ __forceinline__ void strip_step(const InstDev& d, int64_t step, int b
         d.wave[(size_t)(step % d.wave_cap) * nth + j] = w;
         if (!isfinite(w.x) || !isfinite(w.y)) atomicOr(d.status, (unsigned)ST_NONFINITE);
     };
-    auto load_col = [&](size_t o) { return row_ok ? in.load(o) : NodeV<P>::zero(); };
-    auto rtab_h = [&](int i) { RTab t{}; if constexpr (kRT) t = load_rtab(d.rtab_h, i); return t; };
-    auto rtab_i = [&](int i) { RTab t{}; if constexpr (kRT) t = load_rtab(d.rtab_i, i); return t; };
 
-    // prologue: columns c0-1 and c0
-    size_t o = node_index(d, c0 - 1, j);           // offset of the column being loaded
-    NodeV<P> u_prev = load_col(o);
-    NodeV<P> u_cur = load_col(o + pitch);
+    // prologue: columns c0-1 (slot 0) and c0 (slot 1)
     C dl_prev, dlm_prev, dl, dlm;
+    ring.wait(0);
+    NodeV<P> u_prev = ring.node(0, j, row_ok);
     theta_diffs(u_prev, (c0 - 1) & 1, dl_prev, dlm_prev);
-    RTab th = rtab_h(c0 - 1);
+    ring.wait(1);
+    NodeV<P> u_cur = ring.node(1, j, row_ok);
     theta_diffs(u_cur, c0 & 1, dl, dlm);
-    HalfRec<T> L = predict(u_prev, u_cur, dl_prev, dl, dlm_prev, dlm, th, c0 - 1);
+    HalfRec<T> L = predict(u_prev, u_cur, dl_prev, dl, dlm_prev, dlm, ring.tab(0, 0), c0 - 1);
     if (ex_blk && d.i_e == c0 - 1) extract(u_prev, u_cur);
     u_prev = u_cur;
     dl_prev = dl;
     dlm_prev = dlm;
-    o += 2 * pitch;                                // column c0 + 1
-    NodeV<P> u_next = c0 + 1 <= c1 ? load_col(o) : NodeV<P>::zero();
+    size_t o = node_index(d, c0, j);               // output offset of the corrector's column
 
-    // steady state: column c loaded, predictor at c-1/2, corrector at c-1
+    // steady state: column c arrives, predictor at c-1/2, corrector at c-1; the slots
+    // hold columns c-2 (sf, free once the first barrier is passed), c-1 (sp) and c (sc)
+    int sf = 0, sp = 1, sc = 2;
 #pragma unroll 3
     for (int c = c0 + 1; c <= c1; ++c) {
-        u_cur = u_next;
-        if (c < c1) u_next = load_col(o + pitch);
-        th = rtab_h(c - 1);
-        const RTab ti = rtab_i(c - 1);
+        ring.wait(sc);
+        u_cur = ring.node(sc, j, row_ok);
         const int par = c & 1;
         theta_diffs(u_cur, par, dl, dlm);
-        const HalfRec<T> R = predict(u_prev, u_cur, dl_prev, dl, dlm_prev, dlm, th, c - 1);
-        correct(R, L, u_prev, ti, c - 1, par, o - pitch);
+        if (one_warp) __syncwarp();
+        if (threadIdx.x == 0 && c - 2 + kRing <= c1) ring.fill(d, bin, c - 2 + kRing, sf);
+        const HalfRec<T> R = predict(u_prev, u_cur, dl_prev, dl, dlm_prev, dlm, ring.tab(sp, 0), c - 1);
+        correct(R, L, u_prev, ring.tab(sp, 1), c - 1, par, o);
         if (ex_blk && d.i_e == c - 1) extract(u_prev, u_cur);
         L = R;
         u_prev = u_cur;
         dl_prev = dl;
         dlm_prev = dlm;
         o += pitch;
+        sf = sp;
+        sp = sc;
+        sc = sc + 1 == kRing ? 0 : sc + 1;
+    }
+    if (__syncthreads_or(ring.late)) {
+        if (threadIdx.x == 0) {
+            ring.drain();
+            atomicOr(d.status, (unsigned)ST_TIMEOUT);
+        }
+        __syncthreads();
+        ring.late = false;
     }
 }
 
 // Two register budgets: columns of up to 256 rows (the common case, room for two
-// blocks per SM at up to 128 registers) and of up to 1024 rows.
+// blocks per SM at up to 128 registers) and of up to 1024 rows.  Dynamic shared memory:
+// the column ring, ColumnRing<P>::ring_bytes(blockDim.x).
 template <class P>
-__global__ void __launch_bounds__(256, 2) step_kernel_s(InstDev d, int64_t step, int bin, int strip) {
+__device__ __forceinline__ void step_body(const InstDev& d, int64_t step, int bin, int strip) {
+    extern __shared__ __align__(128) unsigned char ring_smem[];
     __shared__ StepSmem<typename P::T> sm;
+    __shared__ uint64_t mbar[kRing];
+    __shared__ int skip;
+    ColumnRing<P> ring(ring_smem, mbar);
+    if (threadIdx.x == 0) {
+        // a bounded wait of an earlier launch gave up: the state is void until it is reset
+        skip = (*(volatile unsigned*)d.status & ST_TIMEOUT) != 0;
+        if (!skip) ring.init();
+    }
+    __syncthreads();
+    if (skip) return;
     const int c0 = 1 + blockIdx.x * strip;
     const int c1 = min(d.nr - 1, c0 + strip);
-    strip_step<P>(d, step, bin, c0, c1, sm);
+    strip_step<P>(d, step, bin, c0, c1, sm, ring);
+}
+
+template <class P>
+__global__ void __launch_bounds__(256, 2) step_kernel_s(InstDev d, int64_t step, int bin, int strip) {
+    step_body<P>(d, step, bin, strip);
 }
 
 template <class P>
 __global__ void __launch_bounds__(1024) step_kernel_l(InstDev d, int64_t step, int bin, int strip) {
-    __shared__ StepSmem<typename P::T> sm;
-    const int c0 = 1 + blockIdx.x * strip;
-    const int c1 = min(d.nr - 1, c0 + strip);
-    strip_step<P>(d, step, bin, c0, c1, sm);
+    step_body<P>(d, step, bin, strip);
 }
 
 // Waveform record of the state in buffer bin (time level `step`): one thread per row.
@@ -300,9 +459,13 @@ __device__ bool wait_neighbours(const BatchDev& b, const int* fl, int nstrip, in
 // number of resident blocks.
 template <class P, int kMaxThreads, int kMinBlocks>
 __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) batched_step_kernel(BatchDev b) {
+    extern __shared__ __align__(128) unsigned char ring_smem[];
     __shared__ StepSmem<typename P::T> sm;
+    __shared__ uint64_t mbar[kRing];
     __shared__ unsigned long long item;
     __shared__ int flag;
+    ColumnRing<P> ring(ring_smem, mbar);
+    if (threadIdx.x == 0) ring.init();
     const int64_t nsteps = *b.n_steps;
     const int64_t total = b.items_per_step * nsteps;
     for (;;) {
@@ -331,7 +494,7 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) batched_step_kernel(B
         }
         const int c0 = 1 + st * strip;
         const int c1 = min(d.nr - 1, c0 + strip);
-        strip_step<P>(d, b.base_step[k] + s, (int)((b.base_bin[k] + s) & 1), c0, c1, sm);
+        strip_step<P>(d, b.base_step[k] + s, (int)((b.base_bin[k] + s) & 1), c0, c1, sm, ring);
         __threadfence();
         __syncthreads();
         if (threadIdx.x == 0 && !(s == 0 && r == b.skip_release_item))
@@ -363,10 +526,11 @@ static int grid_for(int threads) {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t smem = ColumnRing<P>::ring_bytes(threads);
     if (threads <= 256)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batched_step_kernel<P, 256, 2>, threads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batched_step_kernel<P, 256, 2>, threads, smem);
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batched_step_kernel<P, 1024, 1>, threads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batched_step_kernel<P, 1024, 1>, threads, smem);
     return (per > 0 ? per : 1) * (sms > 0 ? sms : 1);
 }
 
@@ -378,8 +542,9 @@ int batched_grid(int prec, int threads) {
 
 template <class P>
 static void launch_batched_p(cudaStream_t st, const BatchDev& b, int grid, int threads) {
-    if (threads <= 256) batched_step_kernel<P, 256, 2><<<grid, threads, 0, st>>>(b);
-    else batched_step_kernel<P, 1024, 1><<<grid, threads, 0, st>>>(b);
+    const size_t smem = ColumnRing<P>::ring_bytes(threads);
+    if (threads <= 256) batched_step_kernel<P, 256, 2><<<grid, threads, smem, st>>>(b);
+    else batched_step_kernel<P, 1024, 1><<<grid, threads, smem, st>>>(b);
 }
 
 void launch_batched_step(cudaStream_t st, int prec, const BatchDev& b, int grid, int threads) {
@@ -399,14 +564,35 @@ template <class P>
 static void launch_step_p(cudaStream_t st, const InstDev& d, int64_t step, int bin, int strip) {
     int blocks = (d.nr - 2 + strip - 1) / strip;
     int threads = d.pitch;
-    if (threads <= 256) step_kernel_s<P><<<blocks, threads, 0, st>>>(d, step, bin, strip);
-    else step_kernel_l<P><<<blocks, threads, 0, st>>>(d, step, bin, strip);
+    const size_t smem = ColumnRing<P>::ring_bytes(threads);
+    if (threads <= 256) step_kernel_s<P><<<blocks, threads, smem, st>>>(d, step, bin, strip);
+    else step_kernel_l<P><<<blocks, threads, smem, st>>>(d, step, bin, strip);
 }
 
 void launch_step(cudaStream_t st, const InstDev& d, int64_t step, int bin, int strip) {
     if (d.prec == 0) launch_step_p<P64>(st, d, step, bin, strip);
     else if (d.prec == 1) launch_step_p<P32>(st, d, step, bin, strip);
     else launch_step_p<PK>(st, d, step, bin, strip);
+}
+
+// Opt the step kernels in to the dynamic shared memory of their largest ring (on the
+// current device; called when a context is created).
+template <class P>
+static cudaError_t prepare_p() {
+    const int s = (int)ColumnRing<P>::ring_bytes(256), l = (int)ColumnRing<P>::ring_bytes(1024);
+    const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    cudaError_t e = cudaFuncSetAttribute(step_kernel_s<P>, a, s);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(step_kernel_l<P>, a, l);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(batched_step_kernel<P, 256, 2>, a, s);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(batched_step_kernel<P, 1024, 1>, a, l);
+    return e;
+}
+
+cudaError_t prepare_step_kernels() {
+    cudaError_t e = prepare_p<P64>();
+    if (e == cudaSuccess) e = prepare_p<P32>();
+    if (e == cudaSuccess) e = prepare_p<PK>();
+    return e;
 }
 
 void launch_extract(cudaStream_t st, const InstDev& d, int64_t step, int bin) {

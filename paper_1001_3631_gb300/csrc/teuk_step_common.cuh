@@ -50,9 +50,10 @@ template <typename T>
 __device__ __forceinline__ Cx<T> shfl_up_c(Cx<T> a) { return {shfl_up_t(a.re), shfl_up_t(a.im)}; }
 
 // ---------------------------------------------------------------- precisions
-struct P64 { using T = double; static constexpr bool kahan = false; };
-struct P32 { using T = float; static constexpr bool kahan = false; };
-struct PK  { using T = float; static constexpr bool kahan = true; };
+// planes: 16-byte planes per state buffer (the layout in teuk_internal.cuh)
+struct P64 { using T = double; static constexpr bool kahan = false; static constexpr int planes = 2; };
+struct P32 { using T = float; static constexpr bool kahan = false; static constexpr int planes = 1; };
+struct PK  { using T = float; static constexpr bool kahan = true; static constexpr int planes = 2; };
 
 // Compensated add (Kahan 1965): the represented value is hi - c.
 __device__ __forceinline__ void kahan_add(float& hi, float& c, float delta) {
@@ -115,6 +116,10 @@ template <> struct Planes<P64> {
     __device__ __forceinline__ static Planes of(const InstDev& d, int b) {
         return {(double2*)d.buf[b][0], (double2*)d.buf[b][1]};
     }
+    // planes of one column copied to shared memory, `stride` nodes apart
+    __device__ __forceinline__ static Planes at(void* base, unsigned stride) {
+        return {(double2*)base, (double2*)base + stride};
+    }
     __device__ __forceinline__ NodeV<P64> load(size_t o) const {
         NodeV<P64> n;
         double2 a = phi[o], b = pi[o];
@@ -130,6 +135,7 @@ template <> struct Planes<P64> {
 template <> struct Planes<P32> {
     float4* u;
     __device__ __forceinline__ static Planes of(const InstDev& d, int b) { return {(float4*)d.buf[b][0]}; }
+    __device__ __forceinline__ static Planes at(void* base, unsigned) { return {(float4*)base}; }
     __device__ __forceinline__ NodeV<P32> load(size_t o) const {
         NodeV<P32> n;
         float4 a = u[o];
@@ -145,6 +151,9 @@ template <> struct Planes<PK> {
     float4* hi; float4* c;
     __device__ __forceinline__ static Planes of(const InstDev& d, int b) {
         return {(float4*)d.buf[b][0], (float4*)d.buf[b][1]};
+    }
+    __device__ __forceinline__ static Planes at(void* base, unsigned stride) {
+        return {(float4*)base, (float4*)base + stride};
     }
     __device__ __forceinline__ NodeV<PK> load(size_t o) const {
         NodeV<PK> n;
@@ -235,12 +244,6 @@ __device__ __forceinline__ void form_coefs(const RTab& t, const ThTab& h, float*
     cf[C_E3I] = t.qi * iS;
 }
 
-__device__ __forceinline__ RTab load_rtab(const RTab* tab, int i) {
-    const float4* q = (const float4*)(tab + i);
-    const float4 a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + 2), e = __ldg(q + 3);
-    return RTab{a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w, e.x, 0.f, 0.f, 0.f};
-}
-
 // The theta table of one row, held in registers by its thread for a whole work item
 // (FP32 paths; empty for FP64, which reads 2D tables).
 template <class P>
@@ -255,24 +258,11 @@ struct RowTab {
 
 // Coefficients of the predictor (half = true, node i+1/2) or the corrector (node i) at
 // row j: read from the 2D FP64 tables, or formed in registers on the FP32 paths from
-// the column's radial table (the same address for the whole block) and the row's
-// theta table.
+// the column's radial table t (one copy in shared memory for the whole block) and the
+// row's theta table.
 template <class P>
-__device__ __forceinline__ void get_coefs(const InstDev& d, const RowTab<P>& row, bool half,
-                                          int i, int j, bool ok, typename P::T* cf) {
-    if constexpr (sizeof(typename P::T) == 8) {
-        load_coefs((const double*)(half ? d.coef_h : d.coef_i), plane_elems(d),
-                   node_index(d, i, j), ok, cf);
-    } else {
-        form_coefs(load_rtab(half ? d.rtab_h : d.rtab_i, i), row.t, cf);
-    }
-}
-
-// Same, from a radial table already in registers (prefetched by the caller).
-template <class P>
-__device__ __forceinline__ void get_coefs_pre(const InstDev& d, const RowTab<P>& row, const RTab& t,
-                                              bool half, int i, int j, bool ok,
-                                              typename P::T* cf) {
+__device__ __forceinline__ void get_coefs(const InstDev& d, const RowTab<P>& row, const RTab& t,
+                                          bool half, int i, int j, bool ok, typename P::T* cf) {
     if constexpr (sizeof(typename P::T) == 8) {
         load_coefs((const double*)(half ? d.coef_h : d.coef_i), plane_elems(d),
                    node_index(d, i, j), ok, cf);
