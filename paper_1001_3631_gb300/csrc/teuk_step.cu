@@ -6,9 +6,10 @@
 // by bulk-async (TMA) copies several columns ahead of use; at each column the block
 // computes the predictor (Eq. 13) at the half node just behind it and the corrector
 // (Eq. 14) at the column behind that, and stores u^{n+1}.  Radial neighbours are the
-// registers of the previous column; theta neighbours come from the lanes above and
-// below (warp shuffles, and shared memory across warp edges).  A strip reads two extra
-// columns, so every input is read from HBM about once per step.  The angular ghost
+// registers of the previous column; the theta neighbours of the input state are read
+// from the ring slot, and those of the predictor's results through a small shared
+// exchange buffer (one barrier per column).  A strip reads two extra columns, so every
+// input is read from HBM about once per step.  The angular ghost
 // rows of the pole condition (Sec. 2.2) mirror row 0 / row n_theta-1 with sign +1
 // (even |m|) or -1 (odd |m|): on the averaged state in the predictor, on the half-node
 // results in the corrector.
@@ -33,48 +34,6 @@
 #include "teuk_step_common.cuh"
 
 namespace teuk {
-
-// Values exchanged between neighbouring rows of one column: within a warp by shuffles,
-// across warp edges through shared memory.  Each exchange point owns its own buffer,
-// double-buffered by column parity, so a buffer is rewritten only after every thread
-// has passed a later barrier (no write can overtake a slow reader).
-template <typename T>
-struct Xchg {
-    T lo[2][kMaxWarps][4];   // lane 0 of each warp, read by lane 31 of the warp below
-    T hi[2][kMaxWarps][4];   // lane 31 of each warp, read by lane 0 of the warp above
-};
-
-template <typename T>
-struct StepSmem {
-    Xchg<T> x1, x2, x3;
-};
-
-// down_out[k] = down_in[k] of row j+1, up_out[k] = up_in[k] of row j-1 (KD, KU values);
-// the top and bottom rows of the block receive garbage and apply the ghost rule.
-template <typename T, int KD, int KU>
-__device__ __forceinline__ void xchg(Xchg<T>& X, int par, const T* down_in, T* down_out,
-                                     const T* up_in, T* up_out) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-#pragma unroll
-    for (int k = 0; k < KD; ++k) down_out[k] = shfl_down_t(down_in[k]);
-#pragma unroll
-    for (int k = 0; k < KU; ++k) up_out[k] = shfl_up_t(up_in[k]);
-    if (nwarp > 1) {
-        if (lane == 0)
-#pragma unroll
-            for (int k = 0; k < KD; ++k) X.lo[par][warp][k] = down_in[k];
-        if (lane == 31)
-#pragma unroll
-            for (int k = 0; k < KU; ++k) X.hi[par][warp][k] = up_in[k];
-        __syncthreads();
-        if (lane == 31 && warp + 1 < nwarp)
-#pragma unroll
-            for (int k = 0; k < KD; ++k) down_out[k] = X.lo[par][warp + 1][k];
-        if (lane == 0 && warp > 0)
-#pragma unroll
-            for (int k = 0; k < KU; ++k) up_out[k] = X.hi[par][warp - 1][k];
-    }
-}
 
 // ---------------------------------------------------------------- column ring
 // PTX wrappers: mbarrier and the bulk-async copy global -> shared (TMA, untiled form).
@@ -115,33 +74,32 @@ __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsign
 __device__ __forceinline__ void fence_proxy_async_global() {
     asm volatile("fence.proxy.async.global;" ::: "memory");
 }
-
-// Columns of the input level (every plane, plus on the FP32 paths the column's two
-// radial tables) are copied into kRing shared-memory slots by one thread, kRing - 2
-// columns ahead of use; each slot has an mbarrier that its copy completes.  A column's
-// state is read when it arrives and its radial tables one column later, so its slot is
-// refilled after the first barrier two columns on, when every thread has finished with
-// it.  Copies start on 16-byte boundaries with sizes in multiples of 16 bytes: a column
-// is n_theta 16-byte nodes at a 512-byte aligned offset, a radial table 64 bytes.
-constexpr int kRing = 6;
-constexpr unsigned long long kRingWaitNs = 1000000000ull;  // a slot wait gives up after 1 s
-
 __device__ __forceinline__ unsigned long long global_ns() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
     return t;
 }
 
-template <class P>
+constexpr unsigned long long kRingWaitNs = 1000000000ull;  // a slot wait gives up after 1 s
+
+// Columns of the input level (every plane, plus on the FP32 paths the column's two
+// radial tables) are copied into R shared-memory slots by one thread, R - 2 columns
+// ahead of use; each slot has an mbarrier that its copy completes.  A column is read
+// (own node and theta neighbours) when it arrives and its radial tables one column
+// later, so its slot is refilled after the barrier two columns on, when every thread
+// has finished with it.  Copies start on 16-byte boundaries with sizes in multiples of
+// 16 bytes: a column is n_theta 16-byte nodes at a 512-byte aligned offset, a radial
+// table 64 bytes.
+template <class P, int R>
 struct ColumnRing {
+    static constexpr int kSlots = R;
     static constexpr bool kTabs = sizeof(typename P::T) == 4;
     __host__ __device__ static unsigned slot_bytes(int threads) {
         return (unsigned)P::planes * (unsigned)threads * 16u + (kTabs ? 2u * (unsigned)sizeof(RTab) : 0u);
     }
-    __host__ __device__ static unsigned ring_bytes(int threads) { return kRing * slot_bytes(threads); }
 
-    unsigned char* base;  // kRing slots: planes [P::planes][stride] of 16-byte nodes, tables
-    uint64_t* mbar;       // [kRing]
+    unsigned char* base;  // R slots: planes [P::planes][stride] of 16-byte nodes, then tables
+    uint64_t* mbar;       // [R]
     unsigned stride;      // nodes per plane in a slot (the block size)
     unsigned sbytes;
     unsigned phase;       // bit s: parity of the next completion awaited on slot s
@@ -152,10 +110,11 @@ struct ColumnRing {
 
     // One thread, once per block, before any fill; the block synchronizes afterwards.
     __device__ __forceinline__ void init() const {
-        for (int k = 0; k < kRing; ++k) mbar_init(mbar + k);
+        for (int k = 0; k < R; ++k) mbar_init(mbar + k);
         mbar_init_fence();
     }
     __device__ __forceinline__ unsigned char* slot(int s) const { return base + (size_t)s * sbytes; }
+    __device__ __forceinline__ Planes<P> planes(int s) const { return Planes<P>::at(slot(s), stride); }
     // One thread: copy column col of buffer bin (and its radial tables) into slot s.
     __device__ __forceinline__ void fill(const InstDev& d, int bin, int col, int s) const {
         unsigned char* dst = slot(s);
@@ -181,9 +140,6 @@ struct ColumnRing {
         while (!mbar_try_wait(mbar + s, par))
             if (global_ns() - t0 > kRingWaitNs) { late = true; return; }
     }
-    __device__ __forceinline__ NodeV<P> node(int s, int j, bool ok) const {
-        return ok ? Planes<P>::at(slot(s), stride).load((size_t)j) : NodeV<P>::zero();
-    }
     // Radial table of the column in slot s: which = 0 half node i+1/2, 1 node i.
     __device__ __forceinline__ RTab tab(int s, int which) const {
         RTab t{};
@@ -198,39 +154,56 @@ struct ColumnRing {
     // the block never exits with a copy into its shared memory outstanding.
     __device__ void drain() const {
         const unsigned long long t0 = global_ns();
-        for (int k = 0; k < kRing; ++k)
+        for (int k = 0; k < R; ++k)
             while (!mbar_try_wait(mbar + k, ((phase >> k) & 1u) ^ 1u))
                 if (global_ns() - t0 > kRingWaitNs) return;
     }
 };
 
+// Shared memory of a step block: the ring, then the exchange buffer of the predictor's
+// results, [2 (column parity)][threads + 2][4] values (row j at entry j + 1; the
+// entries 0 and threads + 1 are never written and stand for rows that the pole rule
+// replaces).
+template <class P, int R>
+struct StepShared {
+    using T = typename P::T;
+    __host__ __device__ static unsigned xbuf_elems(int threads) { return 2u * ((unsigned)threads + 2u) * 4u; }
+    __host__ __device__ static unsigned bytes(int threads) {
+        return R * ColumnRing<P, R>::slot_bytes(threads) + xbuf_elems(threads) * (unsigned)sizeof(T);
+    }
+    __device__ __forceinline__ static T* xbuf(unsigned char* base) {
+        return (T*)(base + R * ColumnRing<P, R>::slot_bytes(blockDim.x));
+    }
+};
+
+// Slots of the ring: six for blocks of up to 256 rows, four for larger blocks (whose
+// slots are four times bigger).
+constexpr int kRingS = 6, kRingL = 4;
+
 // One work item: the columns [c0, c1) of one instance for one step, one thread per row.
-// Per column c: (1) exchange Phi(c) with the rows above and below -> theta differences
-// dl(c) = Phi(j+1) - Phi(j) and dlm(c) = Phi(j) - Phi(j-1); (2) predictor at the half
-// node c-1/2; (3) exchange its results with the rows above and below; (4) corrector at
-// column c-1.  Two barriers per column.  The first two columns are peeled so the
-// steady-state loop has no per-column mode switches, and it is unrolled by three so the
-// rotation of the previous / current column is register renaming.  Columns c0-1 .. c1
-// are read, through the ring.
-template <class P>
+// Per column c: theta differences of Phi(c), dl = Phi(j+1) - Phi(j) and dlm = Phi(j) -
+// Phi(j-1), from the ring slot; predictor at the half node c-1/2; exchange of its
+// results with the rows above and below (the one barrier of the column); corrector at
+// column c-1.  The first two columns are peeled so the steady-state loop has no
+// per-column mode switches, and it is unrolled by three so the rotation of the
+// previous / current column is register renaming.  Columns c0-1 .. c1 are read.
+template <class P, int R>
 __device__ __forceinline__ void strip_step(const InstDev& d, int64_t step, int bin, int c0,
-                                           int c1, StepSmem<typename P::T>& sm,
-                                           ColumnRing<P>& ring) {
+                                           int c1, ColumnRing<P, R>& ring, typename P::T* xbuf) {
     using T = typename P::T;
     using C = Cx<T>;
-    constexpr int KF = P::kahan ? 4 : 2;   // Phi values exchanged: hi (and c)
     const int j = threadIdx.x;
     const int nth = d.nth;
     const bool row_ok = j < nth;
     const bool bot = j == 0, top = j == nth - 1;
-    const bool one_warp = blockDim.x <= 32;
+    const int jp = j + 1 < nth ? j + 1 : j, jm = j > 0 ? j - 1 : 0;  // in-slot neighbours
     const T g = (T)d.ghost;
     const T hdt = (T)(0.5 * d.dt), fdt = (T)d.dt;
     const Planes<P> out = Planes<P>::of(d, 1 - bin);
-    const int ncols = c1 - c0 + 2;
+    const unsigned xstride = 4u * (blockDim.x + 2u);
     if (threadIdx.x == 0) {
         fence_proxy_async_global();
-        for (int k = 0; k < ncols && k < kRing; ++k) ring.fill(d, bin, c0 - 1 + k, k);
+        for (int k = 0; k < c1 - c0 + 2 && k < R; ++k) ring.fill(d, bin, c0 - 1 + k, k);
     }
     RowTab<P> rt;
     rt.load(d.thtab, j, row_ok);
@@ -249,23 +222,19 @@ __device__ __forceinline__ void strip_step(const InstDev& d, int64_t step, int b
     if (row_ok && c0 == 1) out.store(node_index(d, 0, j), NodeV<P>::zero());
     if (row_ok && c1 == d.nr - 1) out.store(node_index(d, d.nr - 1, j), NodeV<P>::zero());
 
-    // (1) theta differences of Phi in column u (ghost rows by the pole rule)
-    auto theta_diffs = [&](const NodeV<P>& u, int par, C& dl, C& dlm) {
-        T v[4] = {u.F.re, u.F.im, u.Fc.re, u.Fc.im}, vd[4], vu[4];
-        xchg<T, KF, KF>(sm.x1, par, v, vd, v, vu);
-        NodeV<P> dn = NodeV<P>::zero(), upn = NodeV<P>::zero();
-        dn.F = {vd[0], vd[1]};
-        upn.F = {vu[0], vu[1]};
-        if constexpr (P::kahan) {
-            dn.Fc = {vd[2], vd[3]};
-            upn.Fc = {vu[2], vu[3]};
-        }
+    // own node of the column in slot s
+    auto node = [&](int s) { return row_ok ? ring.planes(s).load((size_t)j) : NodeV<P>::zero(); };
+    // theta differences of Phi in the column in slot s (own node u; ghost rows by the
+    // pole rule)
+    auto theta_diffs = [&](int s, const NodeV<P>& u, C& dl, C& dlm) {
+        const Planes<P> pl = ring.planes(s);
+        NodeV<P> dn = pl.load_phi((size_t)jp), upn = pl.load_phi((size_t)jm);
         if (top) { dn = u; dn.scale(g); }     // row nth   = g * row nth-1
         if (bot) { upn = u; upn.scale(g); }   // row -1    = g * row 0
         dl = dn.dphi(u);
         dlm = u.dphi(upn);
     };
-    // (2) predictor at the half node h between columns h (ul) and h+1 (ur)
+    // predictor at the half node h between columns h (ul) and h+1 (ur)
     auto predict = [&](const NodeV<P>& ul, const NodeV<P>& ur, C dll, C dlr, C dlml, C dlmr,
                        const RTab& tab, int h) {
         const Half<T> hp = half_prep<P>(ul, ur);
@@ -277,19 +246,37 @@ __device__ __forceinline__ void strip_step(const InstDev& d, int64_t step, int b
         if (src_blk) src = source_half<T>(sw, sp_fac, h, j);
         return predictor<T>(hp, Dp, Dm, cf, hdt, src);
     };
-    // (3)+(4) corrector at column cc from the half nodes L = cc-1/2 and R = cc+1/2
-    auto correct = [&](const HalfRec<T>& R, const HalfRec<T>& L, const NodeV<P>& uc,
-                       const RTab& tab, int cc, int par, size_t o) {
-        const CRow<T> row = combine_lr<T>(R, L);
-        T xd[2] = {row.Hs.re, row.Hs.im}, xdo[2];
-        T xu[4] = {row.Hs.re, row.Hs.im, row.DpS.re, row.DpS.im}, xuo[4];
-        xchg<T, 2, 4>(sm.x3, par, xd, xdo, xu, xuo);
-        C Hs_p = {xdo[0], xdo[1]};
-        C Hs_m = {xuo[0], xuo[1]}, DpS_m = {xuo[2], xuo[3]};
+    // corrector at column cc from the half nodes L = cc-1/2 and R = cc+1/2; hs is the
+    // exchange buffer of this column's parity
+    auto correct = [&](const HalfRec<T>& Rh, const HalfRec<T>& Lh, const NodeV<P>& uc,
+                       const RTab& tab, int cc, T* xb, size_t o) {
+        const CRow<T> row = combine_lr<T>(Rh, Lh);
+        T* mine = xb + 4 * (j + 1);
+        if constexpr (sizeof(T) == 4) {
+            *(float4*)mine = make_float4(row.Hs.re, row.Hs.im, row.DpS.re, row.DpS.im);
+        } else {
+            ((double2*)mine)[0] = make_double2(row.Hs.re, row.Hs.im);
+            ((double2*)mine)[1] = make_double2(row.DpS.re, row.DpS.im);
+        }
+        __syncthreads();
+        C Hs_p, Hs_m, DpS_m;
+        if constexpr (sizeof(T) == 4) {
+            const float2 a = *(const float2*)(mine + 4);
+            const float4 b = *(const float4*)(mine - 4);
+            Hs_p = {a.x, a.y};
+            Hs_m = {b.x, b.y};
+            DpS_m = {b.z, b.w};
+        } else {
+            const double2 a = *(const double2*)(mine + 4);
+            const double2 b0 = ((const double2*)(mine - 4))[0], b1 = ((const double2*)(mine - 4))[1];
+            Hs_p = {a.x, a.y};
+            Hs_m = {b0.x, b0.y};
+            DpS_m = {b1.x, b1.y};
+        }
         if (top) Hs_p = g * row.Hs;
         if (bot) {
             Hs_m = g * row.Hs;
-            DpS_m = (T(1) - g) * C::half_sum(R.Fb, L.Fb);  // (Dp_R(-1) + Dp_L(-1))/2
+            DpS_m = (T(1) - g) * C::half_sum(Rh.Fb, Lh.Fb);  // (Dp_R(-1) + Dp_L(-1))/2
         }
         const C Dplus = row.DpS + (Hs_p - row.Hs);
         const C Dminus = DpS_m + (row.Hs - Hs_m);
@@ -323,11 +310,11 @@ __device__ __forceinline__ void strip_step(const InstDev& d, int64_t step, int b
     // prologue: columns c0-1 (slot 0) and c0 (slot 1)
     C dl_prev, dlm_prev, dl, dlm;
     ring.wait(0);
-    NodeV<P> u_prev = ring.node(0, j, row_ok);
-    theta_diffs(u_prev, (c0 - 1) & 1, dl_prev, dlm_prev);
+    NodeV<P> u_prev = node(0);
+    theta_diffs(0, u_prev, dl_prev, dlm_prev);
     ring.wait(1);
-    NodeV<P> u_cur = ring.node(1, j, row_ok);
-    theta_diffs(u_cur, c0 & 1, dl, dlm);
+    NodeV<P> u_cur = node(1);
+    theta_diffs(1, u_cur, dl, dlm);
     HalfRec<T> L = predict(u_prev, u_cur, dl_prev, dl, dlm_prev, dlm, ring.tab(0, 0), c0 - 1);
     if (ex_blk && d.i_e == c0 - 1) extract(u_prev, u_cur);
     u_prev = u_cur;
@@ -336,27 +323,26 @@ __device__ __forceinline__ void strip_step(const InstDev& d, int64_t step, int b
     size_t o = node_index(d, c0, j);               // output offset of the corrector's column
 
     // steady state: column c arrives, predictor at c-1/2, corrector at c-1; the slots
-    // hold columns c-2 (sf, free once the first barrier is passed), c-1 (sp) and c (sc)
+    // hold columns c-2 (sf, free once the column's barrier is passed), c-1 (sp) and c (sc)
     int sf = 0, sp = 1, sc = 2;
 #pragma unroll 3
     for (int c = c0 + 1; c <= c1; ++c) {
         ring.wait(sc);
-        u_cur = ring.node(sc, j, row_ok);
-        const int par = c & 1;
-        theta_diffs(u_cur, par, dl, dlm);
-        if (one_warp) __syncwarp();
-        if (threadIdx.x == 0 && c - 2 + kRing <= c1) ring.fill(d, bin, c - 2 + kRing, sf);
-        const HalfRec<T> R = predict(u_prev, u_cur, dl_prev, dl, dlm_prev, dlm, ring.tab(sp, 0), c - 1);
-        correct(R, L, u_prev, ring.tab(sp, 1), c - 1, par, o);
+        u_cur = node(sc);
+        theta_diffs(sc, u_cur, dl, dlm);
+        const RTab th = ring.tab(sp, 0);
+        const HalfRec<T> Rh = predict(u_prev, u_cur, dl_prev, dl, dlm_prev, dlm, th, c - 1);
+        correct(Rh, L, u_prev, ring.tab(sp, 1), c - 1, xbuf + (c & 1) * xstride, o);
+        if (threadIdx.x == 0 && c - 2 + R <= c1) ring.fill(d, bin, c - 2 + R, sf);
         if (ex_blk && d.i_e == c - 1) extract(u_prev, u_cur);
-        L = R;
+        L = Rh;
         u_prev = u_cur;
         dl_prev = dl;
         dlm_prev = dlm;
         o += pitch;
         sf = sp;
         sp = sc;
-        sc = sc + 1 == kRing ? 0 : sc + 1;
+        sc = sc + 1 == R ? 0 : sc + 1;
     }
     if (__syncthreads_or(ring.late)) {
         if (threadIdx.x == 0) {
@@ -370,14 +356,13 @@ __device__ __forceinline__ void strip_step(const InstDev& d, int64_t step, int b
 
 // Two register budgets: columns of up to 256 rows (the common case, room for two
 // blocks per SM at up to 128 registers) and of up to 1024 rows.  Dynamic shared memory:
-// the column ring, ColumnRing<P>::ring_bytes(blockDim.x).
-template <class P>
+// StepShared<P, R>::bytes(blockDim.x).
+template <class P, int R>
 __device__ __forceinline__ void step_body(const InstDev& d, int64_t step, int bin, int strip) {
-    extern __shared__ __align__(128) unsigned char ring_smem[];
-    __shared__ StepSmem<typename P::T> sm;
-    __shared__ uint64_t mbar[kRing];
+    extern __shared__ __align__(128) unsigned char step_smem[];
+    __shared__ uint64_t mbar[R];
     __shared__ int skip;
-    ColumnRing<P> ring(ring_smem, mbar);
+    ColumnRing<P, R> ring(step_smem, mbar);
     if (threadIdx.x == 0) {
         // a bounded wait of an earlier launch gave up: the state is void until it is reset
         skip = (*(volatile unsigned*)d.status & ST_TIMEOUT) != 0;
@@ -387,17 +372,17 @@ __device__ __forceinline__ void step_body(const InstDev& d, int64_t step, int bi
     if (skip) return;
     const int c0 = 1 + blockIdx.x * strip;
     const int c1 = min(d.nr - 1, c0 + strip);
-    strip_step<P>(d, step, bin, c0, c1, sm, ring);
+    strip_step<P, R>(d, step, bin, c0, c1, ring, StepShared<P, R>::xbuf(step_smem));
 }
 
 template <class P>
 __global__ void __launch_bounds__(256, 2) step_kernel_s(InstDev d, int64_t step, int bin, int strip) {
-    step_body<P>(d, step, bin, strip);
+    step_body<P, kRingS>(d, step, bin, strip);
 }
 
 template <class P>
 __global__ void __launch_bounds__(1024) step_kernel_l(InstDev d, int64_t step, int bin, int strip) {
-    step_body<P>(d, step, bin, strip);
+    step_body<P, kRingL>(d, step, bin, strip);
 }
 
 // Waveform record of the state in buffer bin (time level `step`): one thread per row.
@@ -457,14 +442,14 @@ __device__ bool wait_neighbours(const BatchDev& b, const int* fl, int nstrip, in
 // in step order; an item waits for its radial neighbours of the previous step.  Items
 // only wait on items grabbed earlier, so the launch cannot deadlock whatever the
 // number of resident blocks.
-template <class P, int kMaxThreads, int kMinBlocks>
+template <class P, int kMaxThreads, int kMinBlocks, int R>
 __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) batched_step_kernel(BatchDev b) {
-    extern __shared__ __align__(128) unsigned char ring_smem[];
-    __shared__ StepSmem<typename P::T> sm;
-    __shared__ uint64_t mbar[kRing];
+    extern __shared__ __align__(128) unsigned char step_smem[];
+    __shared__ uint64_t mbar[R];
     __shared__ unsigned long long item;
     __shared__ int flag;
-    ColumnRing<P> ring(ring_smem, mbar);
+    ColumnRing<P, R> ring(step_smem, mbar);
+    typename P::T* xbuf = StepShared<P, R>::xbuf(step_smem);
     if (threadIdx.x == 0) ring.init();
     const int64_t nsteps = *b.n_steps;
     const int64_t total = b.items_per_step * nsteps;
@@ -494,7 +479,7 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) batched_step_kernel(B
         }
         const int c0 = 1 + st * strip;
         const int c1 = min(d.nr - 1, c0 + strip);
-        strip_step<P>(d, b.base_step[k] + s, (int)((b.base_bin[k] + s) & 1), c0, c1, sm, ring);
+        strip_step<P, R>(d, b.base_step[k] + s, (int)((b.base_bin[k] + s) & 1), c0, c1, ring, xbuf);
         __threadfence();
         __syncthreads();
         if (threadIdx.x == 0 && !(s == 0 && r == b.skip_release_item))
@@ -526,11 +511,12 @@ static int grid_for(int threads) {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const size_t smem = ColumnRing<P>::ring_bytes(threads);
     if (threads <= 256)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batched_step_kernel<P, 256, 2>, threads, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batched_step_kernel<P, 256, 2, kRingS>, threads,
+                                                      StepShared<P, kRingS>::bytes(threads));
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batched_step_kernel<P, 1024, 1>, threads, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batched_step_kernel<P, 1024, 1, kRingL>, threads,
+                                                      StepShared<P, kRingL>::bytes(threads));
     return (per > 0 ? per : 1) * (sms > 0 ? sms : 1);
 }
 
@@ -542,9 +528,10 @@ int batched_grid(int prec, int threads) {
 
 template <class P>
 static void launch_batched_p(cudaStream_t st, const BatchDev& b, int grid, int threads) {
-    const size_t smem = ColumnRing<P>::ring_bytes(threads);
-    if (threads <= 256) batched_step_kernel<P, 256, 2><<<grid, threads, smem, st>>>(b);
-    else batched_step_kernel<P, 1024, 1><<<grid, threads, smem, st>>>(b);
+    if (threads <= 256)
+        batched_step_kernel<P, 256, 2, kRingS><<<grid, threads, StepShared<P, kRingS>::bytes(threads), st>>>(b);
+    else
+        batched_step_kernel<P, 1024, 1, kRingL><<<grid, threads, StepShared<P, kRingL>::bytes(threads), st>>>(b);
 }
 
 void launch_batched_step(cudaStream_t st, int prec, const BatchDev& b, int grid, int threads) {
@@ -564,9 +551,10 @@ template <class P>
 static void launch_step_p(cudaStream_t st, const InstDev& d, int64_t step, int bin, int strip) {
     int blocks = (d.nr - 2 + strip - 1) / strip;
     int threads = d.pitch;
-    const size_t smem = ColumnRing<P>::ring_bytes(threads);
-    if (threads <= 256) step_kernel_s<P><<<blocks, threads, smem, st>>>(d, step, bin, strip);
-    else step_kernel_l<P><<<blocks, threads, smem, st>>>(d, step, bin, strip);
+    if (threads <= 256)
+        step_kernel_s<P><<<blocks, threads, StepShared<P, kRingS>::bytes(threads), st>>>(d, step, bin, strip);
+    else
+        step_kernel_l<P><<<blocks, threads, StepShared<P, kRingL>::bytes(threads), st>>>(d, step, bin, strip);
 }
 
 void launch_step(cudaStream_t st, const InstDev& d, int64_t step, int bin, int strip) {
@@ -575,16 +563,16 @@ void launch_step(cudaStream_t st, const InstDev& d, int64_t step, int bin, int s
     else launch_step_p<PK>(st, d, step, bin, strip);
 }
 
-// Opt the step kernels in to the dynamic shared memory of their largest ring (on the
+// Opt the step kernels in to the dynamic shared memory of their largest blocks (on the
 // current device; called when a context is created).
 template <class P>
 static cudaError_t prepare_p() {
-    const int s = (int)ColumnRing<P>::ring_bytes(256), l = (int)ColumnRing<P>::ring_bytes(1024);
+    const int s = (int)StepShared<P, kRingS>::bytes(256), l = (int)StepShared<P, kRingL>::bytes(1024);
     const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
     cudaError_t e = cudaFuncSetAttribute(step_kernel_s<P>, a, s);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(step_kernel_l<P>, a, l);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(batched_step_kernel<P, 256, 2>, a, s);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(batched_step_kernel<P, 1024, 1>, a, l);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(batched_step_kernel<P, 256, 2, kRingS>, a, s);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(batched_step_kernel<P, 1024, 1, kRingL>, a, l);
     return e;
 }
 

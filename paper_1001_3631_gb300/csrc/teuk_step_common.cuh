@@ -6,8 +6,7 @@
 
 namespace teuk {
 
-constexpr unsigned kFull = 0xffffffffu;
-constexpr int kMaxWarps = 32;     // a block holds one theta column of up to 1024 rows
+constexpr int kMaxRows = 1024;   // a block holds one theta column of up to 1024 rows
 
 // ---------------------------------------------------------------- complex
 template <typename T>
@@ -40,15 +39,6 @@ __device__ __forceinline__ Cx<T> rmac(Cx<T> acc, T s, Cx<T> z) {
     return {tfma(s, z.re, acc.re), tfma(s, z.im, acc.im)};
 }
 
-__device__ __forceinline__ float shfl_down_t(float v) { return __shfl_down_sync(kFull, v, 1); }
-__device__ __forceinline__ double shfl_down_t(double v) { return __shfl_down_sync(kFull, v, 1); }
-__device__ __forceinline__ float shfl_up_t(float v) { return __shfl_up_sync(kFull, v, 1); }
-__device__ __forceinline__ double shfl_up_t(double v) { return __shfl_up_sync(kFull, v, 1); }
-template <typename T>
-__device__ __forceinline__ Cx<T> shfl_down_c(Cx<T> a) { return {shfl_down_t(a.re), shfl_down_t(a.im)}; }
-template <typename T>
-__device__ __forceinline__ Cx<T> shfl_up_c(Cx<T> a) { return {shfl_up_t(a.re), shfl_up_t(a.im)}; }
-
 // ---------------------------------------------------------------- precisions
 // planes: 16-byte planes per state buffer (the layout in teuk_internal.cuh)
 struct P64 { using T = double; static constexpr bool kahan = false; static constexpr int planes = 2; };
@@ -77,13 +67,6 @@ struct NodeV {
     __device__ __forceinline__ void scale(T s) {  // s = +-1: exact
         F = s * F; Pp = s * Pp;
         if constexpr (P::kahan) { Fc = s * Fc; Pc = s * Pc; }
-    }
-    __device__ __forceinline__ NodeV shfl_down() const {
-        NodeV n;
-        n.F = shfl_down_c(F); n.Pp = shfl_down_c(Pp);
-        if constexpr (P::kahan) { n.Fc = shfl_down_c(Fc); n.Pc = shfl_down_c(Pc); }
-        else { n.Fc = n.Pc = Cx<T>::zero(); }
-        return n;
     }
     // Phi(this) - Phi(o), accurate for compensated pairs
     __device__ __forceinline__ Cx<T> dphi(const NodeV& o) const {
@@ -127,6 +110,13 @@ template <> struct Planes<P64> {
         n.Fc = n.Pc = Cx<double>::zero();
         return n;
     }
+    // Phi alone (the theta neighbours of a node)
+    __device__ __forceinline__ NodeV<P64> load_phi(size_t o) const {
+        NodeV<P64> n = NodeV<P64>::zero();
+        double2 a = phi[o];
+        n.F = {a.x, a.y};
+        return n;
+    }
     __device__ __forceinline__ void store(size_t o, const NodeV<P64>& n) const {
         phi[o] = make_double2(n.F.re, n.F.im);
         pi[o] = make_double2(n.Pp.re, n.Pp.im);
@@ -141,6 +131,12 @@ template <> struct Planes<P32> {
         float4 a = u[o];
         n.F = {a.x, a.y}; n.Pp = {a.z, a.w};
         n.Fc = n.Pc = Cx<float>::zero();
+        return n;
+    }
+    __device__ __forceinline__ NodeV<P32> load_phi(size_t o) const {
+        NodeV<P32> n = NodeV<P32>::zero();
+        float2 a = *(const float2*)(u + o);
+        n.F = {a.x, a.y};
         return n;
     }
     __device__ __forceinline__ void store(size_t o, const NodeV<P32>& n) const {
@@ -160,6 +156,13 @@ template <> struct Planes<PK> {
         float4 a = hi[o], b = c[o];
         n.F = {a.x, a.y}; n.Pp = {a.z, a.w};
         n.Fc = {b.x, b.y}; n.Pc = {b.z, b.w};
+        return n;
+    }
+    __device__ __forceinline__ NodeV<PK> load_phi(size_t o) const {
+        NodeV<PK> n = NodeV<PK>::zero();
+        float2 a = *(const float2*)(hi + o), b = *(const float2*)(c + o);
+        n.F = {a.x, a.y};
+        n.Fc = {b.x, b.y};
         return n;
     }
     __device__ __forceinline__ void store(size_t o, const NodeV<PK>& n) const {
