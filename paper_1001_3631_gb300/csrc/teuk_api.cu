@@ -44,6 +44,7 @@ struct Instance {
     int i_e = 0;
     double f_e = 0, r_ext = 0;
     int strip = 0;      // r* columns per work item chosen for this instance (0 = context default)
+    int resident = 0;   // blocks of its step kernel the GPU holds at once
 };
 
 // Device side of the batched persistent launch of one context: one persistent kernel
@@ -188,9 +189,10 @@ InstDev dev_of(const teuk_ctx* c, const Instance& I) {
 
 // Strip length so that the grid holds about 16 warps per SM on 152 SMs, at least
 // 8 columns (a strip reads 2 columns beyond its outputs).
+// Strip length that gives one wave of resident blocks (at least 8 columns per block,
+// so the ring's start-up is amortised; at most 512).
 int auto_strip(const Instance& I) {
-    int warps_per_block = I.pitch / 32;
-    int64_t blocks = (int64_t)152 * 16 / (warps_per_block > 0 ? warps_per_block : 1);
+    int64_t blocks = I.resident > 0 ? I.resident : 1;
     int64_t cols = I.p.n_rstar - 2;
     int64_t L = (cols + blocks - 1) / blocks;
     if (L < 8) L = 8;
@@ -279,6 +281,7 @@ extern "C" teuk_status teuk_create(const teuk_params* p, int n_instances, void* 
         }                                                                         \
     } while (0)
     TK_CCUDA(prepare_step_kernels());
+    for (Instance& I : c->inst) I.resident = step_resident_blocks((int)I.p.prec, I.pitch);
     TK_CCUDA(cudaMallocAsync((void**)&c->status, sizeof(unsigned), c->stream));
     TK_CCUDA(cudaMemsetAsync(c->status, 0, sizeof(unsigned), c->stream));
     for (Instance& I : c->inst) {
@@ -733,7 +736,7 @@ extern "C" teuk_status teuk_autotune(teuk_ctx* c, int trial_steps, int* chosen) 
                                     c->stream) != cudaSuccess)
             err = TEUK_ENOMEM;
         float best_ms = 1e30f;
-        int best_chunk = auto_strip(I);
+        int best_strip = auto_strip(I);
         if (!err) {
             InstDev d = dev_of(c, I);
             d.wave = scr_wave;           // trial records must not touch the live ring
@@ -755,7 +758,7 @@ extern "C" teuk_status teuk_autotune(teuk_ctx* c, int trial_steps, int* chosen) 
                 float ms = 0.f;
                 cudaEventElapsedTime(&ms, e0, e1);
                 c->launches += trial_steps + 2;
-                if (ms < best_ms) { best_ms = ms; best_chunk = ch; }
+                if (ms < best_ms) { best_ms = ms; best_strip = ch; }
             }
         }
         for (int b = 0; b < 2; ++b)
@@ -771,7 +774,7 @@ extern "C" teuk_status teuk_autotune(teuk_ctx* c, int trial_steps, int* chosen) 
             Instance& J = c->inst[k2];
             if (J.p.n_theta == I.p.n_theta && J.p.prec == I.p.prec &&
                 bucket(J.p.n_rstar) == bucket(I.p.n_rstar) && !best[k2])
-                best[k2] = best_chunk;
+                best[k2] = best_strip;
         }
     }
     cudaEventDestroy(e0);

@@ -127,6 +127,7 @@ void launch_profile(cudaStream_t st, double M, double a, double rstar_min, doubl
                     const double* x_half, const SourceDev& src);
 // teuk_step.cu
 cudaError_t prepare_step_kernels();
+int step_resident_blocks(int prec, int threads);  // blocks of the step kernel the GPU holds at once
 void launch_step(cudaStream_t st, const InstDev& d, int64_t step, int bin, int strip);
 void launch_extract(cudaStream_t st, const InstDev& d, int64_t step, int bin);
 void launch_batched_step(cudaStream_t st, int prec, const BatchDev& b, int grid, int threads);

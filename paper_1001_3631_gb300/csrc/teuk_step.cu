@@ -161,9 +161,8 @@ struct ColumnRing {
 };
 
 // Shared memory of a step block: the ring, then the exchange buffer of the predictor's
-// results, [2 (column parity)][threads + 2][4] values (row j at entry j + 1; the
-// entries 0 and threads + 1 are never written and stand for rows that the pole rule
-// replaces).
+// results, [2 (column parity)][threads + 2][4] values (row j at entry j + 1; entries 0
+// and n_theta + 1 hold the ghost rows of the pole rule).
 template <class P, int R>
 struct StepShared {
     using T = typename P::T;
@@ -196,8 +195,11 @@ __device__ __forceinline__ void strip_step(const InstDev& d, int64_t step, int b
     const int nth = d.nth;
     const bool row_ok = j < nth;
     const bool bot = j == 0, top = j == nth - 1;
-    const int jp = j + 1 < nth ? j + 1 : j, jm = j > 0 ? j - 1 : 0;  // in-slot neighbours
+    // theta neighbours in the slot, the pole rows standing in for the ghost rows: row
+    // nth = g * row nth-1 and row -1 = g * row 0 (gp, gm the factors)
+    const int jp = j + 1 < nth ? j + 1 : j, jm = j > 0 ? j - 1 : 0;
     const T g = (T)d.ghost;
+    const T gp = top ? g : T(1), gm = bot ? g : T(1);
     const T hdt = (T)(0.5 * d.dt), fdt = (T)d.dt;
     const Planes<P> out = Planes<P>::of(d, 1 - bin);
     const unsigned xstride = 4u * (blockDim.x + 2u);
@@ -222,17 +224,15 @@ __device__ __forceinline__ void strip_step(const InstDev& d, int64_t step, int b
     if (row_ok && c0 == 1) out.store(node_index(d, 0, j), NodeV<P>::zero());
     if (row_ok && c1 == d.nr - 1) out.store(node_index(d, d.nr - 1, j), NodeV<P>::zero());
 
-    // own node of the column in slot s
-    auto node = [&](int s) { return row_ok ? ring.planes(s).load((size_t)j) : NodeV<P>::zero(); };
-    // theta differences of Phi in the column in slot s (own node u; ghost rows by the
-    // pole rule)
+    // own node of the column in slot s (rows past nth read slot padding: their results
+    // are never stored or exchanged)
+    auto node = [&](int s) { return ring.planes(s).load((size_t)j); };
+    // theta differences of Phi in the column in slot s (own node u)
     auto theta_diffs = [&](int s, const NodeV<P>& u, C& dl, C& dlm) {
         const Planes<P> pl = ring.planes(s);
-        NodeV<P> dn = pl.load_phi((size_t)jp), upn = pl.load_phi((size_t)jm);
-        if (top) { dn = u; dn.scale(g); }     // row nth   = g * row nth-1
-        if (bot) { upn = u; upn.scale(g); }   // row -1    = g * row 0
-        dl = dn.dphi(u);
-        dlm = u.dphi(upn);
+        const NodeV<P> dn = pl.load_phi((size_t)jp), upn = pl.load_phi((size_t)jm);
+        dl = dn.dphi_sl(gp, u);
+        dlm = u.dphi_sr(gm, upn);
     };
     // predictor at the half node h between columns h (ul) and h+1 (ur)
     auto predict = [&](const NodeV<P>& ul, const NodeV<P>& ur, C dll, C dlr, C dlml, C dlmr,
@@ -241,7 +241,7 @@ __device__ __forceinline__ void strip_step(const InstDev& d, int64_t step, int b
         const C Dp = C::half_sum(dll, dlr);     // Fb(j+1) - Fb(j)
         const C Dm = C::half_sum(dlml, dlmr);   // Fb(j) - Fb(j-1)
         T cf[kNCoef];
-        get_coefs<P>(d, rt, tab, true, h, j, row_ok, cf);
+        get_coefs<P>(d, rt, tab, true, h, j, cf);
         C src = C::zero();
         if (src_blk) src = source_half<T>(sw, sp_fac, h, j);
         return predictor<T>(hp, Dp, Dm, cf, hdt, src);
@@ -251,13 +251,21 @@ __device__ __forceinline__ void strip_step(const InstDev& d, int64_t step, int b
     auto correct = [&](const HalfRec<T>& Rh, const HalfRec<T>& Lh, const NodeV<P>& uc,
                        const RTab& tab, int cc, T* xb, size_t o) {
         const CRow<T> row = combine_lr<T>(Rh, Lh);
+        // publish {Hs, DpS} of this row at entry j + 1; the pole rows also write the
+        // ghost entries: row nth (entry nth + 1) Hs = g Hs(nth-1), row -1 (entry 0)
+        // Hs = g Hs(0) and DpS = (Dp_R(-1) + Dp_L(-1))/2 = (1 - g) (Fb_R + Fb_L)(0)/2
         T* mine = xb + 4 * (j + 1);
-        if constexpr (sizeof(T) == 4) {
-            *(float4*)mine = make_float4(row.Hs.re, row.Hs.im, row.DpS.re, row.DpS.im);
-        } else {
-            ((double2*)mine)[0] = make_double2(row.Hs.re, row.Hs.im);
-            ((double2*)mine)[1] = make_double2(row.DpS.re, row.DpS.im);
-        }
+        auto put = [](T* e, C a, C b) {
+            if constexpr (sizeof(T) == 4) {
+                *(float4*)e = make_float4(a.re, a.im, b.re, b.im);
+            } else {
+                ((double2*)e)[0] = make_double2(a.re, a.im);
+                ((double2*)e)[1] = make_double2(b.re, b.im);
+            }
+        };
+        if (row_ok) put(mine, row.Hs, row.DpS);
+        if (top) put(mine + 4, g * row.Hs, C::zero());
+        if (bot) put(xb, g * row.Hs, (T(1) - g) * C::half_sum(Rh.Fb, Lh.Fb));
         __syncthreads();
         C Hs_p, Hs_m, DpS_m;
         if constexpr (sizeof(T) == 4) {
@@ -273,15 +281,10 @@ __device__ __forceinline__ void strip_step(const InstDev& d, int64_t step, int b
             Hs_m = {b0.x, b0.y};
             DpS_m = {b1.x, b1.y};
         }
-        if (top) Hs_p = g * row.Hs;
-        if (bot) {
-            Hs_m = g * row.Hs;
-            DpS_m = (T(1) - g) * C::half_sum(Rh.Fb, Lh.Fb);  // (Dp_R(-1) + Dp_L(-1))/2
-        }
         const C Dplus = row.DpS + (Hs_p - row.Hs);
         const C Dminus = DpS_m + (row.Hs - Hs_m);
         T cf[kNCoef];
-        get_coefs<P>(d, rt, tab, false, cc, j, row_ok, cf);
+        get_coefs<P>(d, rt, tab, false, cc, j, cf);
         C srcc = C::zero();
         if (src_blk) srcc = source_int<T>(sw, sc_fac, cc, j);
         C dPhi = rmac(rmac(C::zero(), -cf[C_G], row.dFc), fdt, row.PC);
@@ -354,8 +357,8 @@ __device__ __forceinline__ void strip_step(const InstDev& d, int64_t step, int b
     }
 }
 
-// Two register budgets: columns of up to 256 rows (the common case, room for two
-// blocks per SM at up to 128 registers) and of up to 1024 rows.  Dynamic shared memory:
+// Two register budgets: columns of up to 256 rows (the common case, P::blocks256
+// blocks per SM) and of up to 1024 rows.  Dynamic shared memory:
 // StepShared<P, R>::bytes(blockDim.x).
 template <class P, int R>
 __device__ __forceinline__ void step_body(const InstDev& d, int64_t step, int bin, int strip) {
@@ -376,7 +379,7 @@ __device__ __forceinline__ void step_body(const InstDev& d, int64_t step, int bi
 }
 
 template <class P>
-__global__ void __launch_bounds__(256, 2) step_kernel_s(InstDev d, int64_t step, int bin, int strip) {
+__global__ void __launch_bounds__(256, P::blocks256) step_kernel_s(InstDev d, int64_t step, int bin, int strip) {
     step_body<P, kRingS>(d, step, bin, strip);
 }
 
@@ -512,7 +515,7 @@ static int grid_for(int threads) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (threads <= 256)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batched_step_kernel<P, 256, 2, kRingS>, threads,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batched_step_kernel<P, 256, P::blocks256, kRingS>, threads,
                                                       StepShared<P, kRingS>::bytes(threads));
     else
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batched_step_kernel<P, 1024, 1, kRingL>, threads,
@@ -529,7 +532,7 @@ int batched_grid(int prec, int threads) {
 template <class P>
 static void launch_batched_p(cudaStream_t st, const BatchDev& b, int grid, int threads) {
     if (threads <= 256)
-        batched_step_kernel<P, 256, 2, kRingS><<<grid, threads, StepShared<P, kRingS>::bytes(threads), st>>>(b);
+        batched_step_kernel<P, 256, P::blocks256, kRingS><<<grid, threads, StepShared<P, kRingS>::bytes(threads), st>>>(b);
     else
         batched_step_kernel<P, 1024, 1, kRingL><<<grid, threads, StepShared<P, kRingL>::bytes(threads), st>>>(b);
 }
@@ -557,6 +560,26 @@ static void launch_step_p(cudaStream_t st, const InstDev& d, int64_t step, int b
         step_kernel_l<P><<<blocks, threads, StepShared<P, kRingL>::bytes(threads), st>>>(d, step, bin, strip);
 }
 
+template <class P>
+static int resident_p(int threads) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (threads <= 256)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, step_kernel_s<P>, threads,
+                                                      StepShared<P, kRingS>::bytes(threads));
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, step_kernel_l<P>, threads,
+                                                      StepShared<P, kRingL>::bytes(threads));
+    return (per > 0 ? per : 1) * (sms > 0 ? sms : 1);
+}
+
+int step_resident_blocks(int prec, int threads) {
+    if (prec == 0) return resident_p<P64>(threads);
+    if (prec == 1) return resident_p<P32>(threads);
+    return resident_p<PK>(threads);
+}
+
 void launch_step(cudaStream_t st, const InstDev& d, int64_t step, int bin, int strip) {
     if (d.prec == 0) launch_step_p<P64>(st, d, step, bin, strip);
     else if (d.prec == 1) launch_step_p<P32>(st, d, step, bin, strip);
@@ -571,7 +594,7 @@ static cudaError_t prepare_p() {
     const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
     cudaError_t e = cudaFuncSetAttribute(step_kernel_s<P>, a, s);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(step_kernel_l<P>, a, l);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(batched_step_kernel<P, 256, 2, kRingS>, a, s);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(batched_step_kernel<P, 256, P::blocks256, kRingS>, a, s);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(batched_step_kernel<P, 1024, 1, kRingL>, a, l);
     return e;
 }

@@ -40,10 +40,25 @@ __device__ __forceinline__ Cx<T> rmac(Cx<T> acc, T s, Cx<T> z) {
 }
 
 // ---------------------------------------------------------------- precisions
-// planes: 16-byte planes per state buffer (the layout in teuk_internal.cuh)
-struct P64 { using T = double; static constexpr bool kahan = false; static constexpr int planes = 2; };
-struct P32 { using T = float; static constexpr bool kahan = false; static constexpr int planes = 1; };
-struct PK  { using T = float; static constexpr bool kahan = true; static constexpr int planes = 2; };
+// planes: 16-byte planes per state buffer (the layout in teuk_internal.cuh);
+// blocks256: resident blocks per SM that the register budget of the step kernel for
+// columns of up to 256 rows aims at (two: at three the FP32 paths fit in 80 registers
+// but run no faster, being issue-bound)
+struct P64 {
+    using T = double;
+    static constexpr bool kahan = false;
+    static constexpr int planes = 2, blocks256 = 2;
+};
+struct P32 {
+    using T = float;
+    static constexpr bool kahan = false;
+    static constexpr int planes = 1, blocks256 = 2;
+};
+struct PK {
+    using T = float;
+    static constexpr bool kahan = true;
+    static constexpr int planes = 2, blocks256 = 2;
+};
 
 // Compensated add (Kahan 1965): the represented value is hi - c.
 __device__ __forceinline__ void kahan_add(float& hi, float& c, float delta) {
@@ -64,14 +79,22 @@ struct NodeV {
         n.F = n.Pp = n.Fc = n.Pc = Cx<T>::zero();
         return n;
     }
-    __device__ __forceinline__ void scale(T s) {  // s = +-1: exact
-        F = s * F; Pp = s * Pp;
-        if constexpr (P::kahan) { Fc = s * Fc; Pc = s * Pc; }
-    }
     // Phi(this) - Phi(o), accurate for compensated pairs
     __device__ __forceinline__ Cx<T> dphi(const NodeV& o) const {
         if constexpr (P::kahan) return (F - o.F) - (Fc - o.Fc);
         else return F - o.F;
+    }
+    // gs Phi(this) - Phi(o) and Phi(this) - gs Phi(o) for gs = +-1 (an exact scaling, so
+    // these round exactly as dphi of the scaled node)
+    __device__ __forceinline__ Cx<T> dphi_sl(T gs, const NodeV& o) const {
+        const Cx<T> a = {tfma(gs, F.re, -o.F.re), tfma(gs, F.im, -o.F.im)};
+        if constexpr (P::kahan) return a - Cx<T>{tfma(gs, Fc.re, -o.Fc.re), tfma(gs, Fc.im, -o.Fc.im)};
+        else return a;
+    }
+    __device__ __forceinline__ Cx<T> dphi_sr(T gs, const NodeV& o) const {
+        const Cx<T> a = {tfma(-gs, o.F.re, F.re), tfma(-gs, o.F.im, F.im)};
+        if constexpr (P::kahan) return a - Cx<T>{tfma(-gs, o.Fc.re, Fc.re), tfma(-gs, o.Fc.im, Fc.im)};
+        else return a;
     }
     __device__ __forceinline__ Cx<T> dpi(const NodeV& o) const {
         if constexpr (P::kahan) return (Pp - o.Pp) - (Pc - o.Pc);
@@ -218,19 +241,19 @@ __device__ __forceinline__ CRow<T> combine_lr(const HalfRec<T>& R, const HalfRec
     return c;
 }
 
+// (rows past n_theta read the padding of the tables: in bounds, never used)
 template <typename T>
-__device__ __forceinline__ void load_coefs(const T* tab, size_t pl, size_t o, bool ok, T* cf) {
+__device__ __forceinline__ void load_coefs(const T* tab, size_t pl, size_t o, T* cf) {
 #pragma unroll
-    for (int k = 0; k < kNCoef; ++k) cf[k] = ok ? __ldg(tab + k * pl + o) : T(0);
+    for (int k = 0; k < kNCoef; ++k) cf[k] = __ldg(tab + k * pl + o);
 }
 
 // FP32 coefficients of one node from its radial table and its theta row (see RTab).
 __device__ __forceinline__ void form_coefs(const RTab& t, const ThTab& h, float* cf) {
     float sig2 = fmaf(-t.aD, h.sin2, t.R2);
-    float iS = __fdividef(1.0f, sig2);             // hardware estimate, then one Newton step
-    iS = fmaf(iS, fmaf(-sig2, iS, 1.0f), iS);
     float rs = rsqrtf(sig2);
     rs = rs * fmaf(-0.5f * sig2 * rs, rs, 1.5f);  // one Newton step on 1/sqrt
+    float iS = rs * rs;                           // 1/Sigma^2 within a few ulp
     float g = t.Rd * rs;
     float ctre = t.ctr * iS;
     float ctim = fmaf(t.ctc, h.cs, t.cti) * iS;
@@ -265,10 +288,10 @@ struct RowTab {
 // row's theta table.
 template <class P>
 __device__ __forceinline__ void get_coefs(const InstDev& d, const RowTab<P>& row, const RTab& t,
-                                          bool half, int i, int j, bool ok, typename P::T* cf) {
+                                          bool half, int i, int j, typename P::T* cf) {
     if constexpr (sizeof(typename P::T) == 8) {
         load_coefs((const double*)(half ? d.coef_h : d.coef_i), plane_elems(d),
-                   node_index(d, i, j), ok, cf);
+                   node_index(d, i, j), cf);
     } else {
         form_coefs(t, row.t, cf);
     }
