@@ -35,7 +35,7 @@ struct Instance {
     bool src_on = false;
     teuk_orbit orbit{};
     double rs0 = 0, sig_r = 0, sig_t = 0, drs0_dr0 = 0;
-    double2* P_win = nullptr;   // P_int | P_half | dP_int | dP_half
+    double2* P_win = nullptr;   // P_int | P_half | dP_int | dP_half | Q_int | Q_half
     double* amps = nullptr;
     SourceDev sd{};
     // waveform ring: time levels [wave_lo, wave_hi) are held
@@ -370,11 +370,18 @@ extern "C" teuk_status teuk_set_source(teuk_ctx* c, int instance, const teuk_orb
     if (I.P_win) { cudaFreeAsync(I.P_win, c->stream); I.P_win = nullptr; }
     if (I.amps) { cudaFreeAsync(I.amps, c->stream); I.amps = nullptr; }
     size_t nwi = (size_t)sd.nj * sd.ni, nwh = (size_t)sd.nj * sd.nh;
-    TK_CUDA(c, cudaMallocAsync((void**)&I.P_win, sizeof(double2) * 2 * (nwi + nwh), c->stream));
+    // P, P_half, dP, dP_half (double2), then the step kernels' copies Q_int, Q_half
+    const size_t qe = q.prec == TEUK_FP64 ? sizeof(double2) : sizeof(float2);
+    sd.q_stride = q.prec == TEUK_FP64 ? sd.nj : (sd.nj + 1) / 2 * 2;
+    const size_t qi_bytes = qe * sd.q_stride * sd.ni, qh_bytes = qe * sd.q_stride * sd.nh;
+    TK_CUDA(c, cudaMallocAsync((void**)&I.P_win, sizeof(double2) * 2 * (nwi + nwh) + qi_bytes + qh_bytes,
+                               c->stream));
     sd.P_int = I.P_win;
     sd.P_half = I.P_win + nwi;
     sd.dP_int = I.P_win + nwi + nwh;
     sd.dP_half = I.P_win + 2 * nwi + nwh;
+    sd.Q_int = I.P_win + 2 * (nwi + nwh);
+    sd.Q_half = (const char*)sd.Q_int + qi_bytes;
     if (n_amps > 0) {
         TK_CUDA(c, cudaMallocAsync((void**)&I.amps, sizeof(double) * n_amps, c->stream));
         TK_CUDA(c, cudaMemcpyAsync(I.amps, amps, sizeof(double) * n_amps, cudaMemcpyHostToDevice,
@@ -387,7 +394,7 @@ extern "C" teuk_status teuk_set_source(teuk_ctx* c, int instance, const teuk_orb
     I.sig_t = stt;
     I.drs0_dr0 = (r0 * r0 + q.a * q.a) / Delta0;
     launch_profile(c->stream, q.M, q.a, q.rstar_min, I.drs, I.dth, rs0, sr, stt, I.drs0_dr0,
-                   I.x_int, I.x_half, sd);
+                   I.x_int, I.x_half, sd, (int)q.prec);
     c->launches++;
     TK_CUDA(c, cudaGetLastError());
     I.sd = sd;

@@ -40,6 +40,13 @@ struct SourceDev {
     const double2* P_half;   // [nj][nh]
     const double2* dP_int;   // [nj][ni]   dP/dr0
     const double2* dP_half;  // [nj][nh]
+    // P again for the step kernels: column-major ([ni][q_stride], [nh][q_stride]) so that
+    // the rows of one column are contiguous, in the state's arithmetic type (double2 on
+    // the FP64 path, float2 on the FP32 paths); q_stride >= nj makes every column a
+    // 16-byte aligned multiple of 16 bytes (the step kernel prefetches columns into L2)
+    const void* Q_int;
+    const void* Q_half;
+    int q_stride;
     double omega, phase0;    // tau = A_n exp(-i (omega t + phase0)) P
     double domega, dphase0;  // d omega/d r0, d phase0/d r0
     const double* amps;      // A_n for n < n_amps, else 1
@@ -124,7 +131,7 @@ void launch_tables_1d(cudaStream_t st, double M, double a, int s, int m, double 
                       RTab* rtab_h, RTab* rtab_i, ThTab* thtab);
 void launch_profile(cudaStream_t st, double M, double a, double rstar_min, double drs, double dth,
                     double rs0, double sig_r, double sig_t, double drs0_dr0, const double* x_int,
-                    const double* x_half, const SourceDev& src);
+                    const double* x_half, const SourceDev& src, int prec);
 // teuk_step.cu
 cudaError_t prepare_step_kernels();
 int step_resident_blocks(int prec, int threads);  // blocks of the step kernel the GPU holds at once

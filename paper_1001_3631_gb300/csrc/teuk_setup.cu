@@ -155,21 +155,29 @@ __global__ void profile_kernel(double M, double a, double rstar_min, double drs,
                                double rs0, double sig_r, double sig_t, double drs0_dr0,
                                const double* x_int, const double* x_half, SourceDev src,
                                double2* P_int, double2* P_half, double2* dP_int,
-                               double2* dP_half) {
+                               double2* dP_half, int prec) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     int jj = blockIdx.y;
     if (jj >= src.nj) return;
     double th = (src.j_lo + jj + 0.5) * dth;
+    // column-major copy for the step kernels, in their arithmetic type
+    auto put_q = [&](const void* q, size_t idx, double2 v) {
+        if (prec == 0) ((double2*)q)[idx] = v;
+        else ((float2*)q)[idx] = make_float2((float)v.x, (float)v.y);
+    };
     if (k < src.ni) {
         int i = src.i_lo + k;
+        double2* p = &P_int[(size_t)jj * src.ni + k];
         profile_point(M, a, x_int[i], rstar_min + i * drs, th, rs0, sig_r, sig_t, drs0_dr0,
-                      &P_int[(size_t)jj * src.ni + k], &dP_int[(size_t)jj * src.ni + k]);
+                      p, &dP_int[(size_t)jj * src.ni + k]);
+        put_q(src.Q_int, (size_t)k * src.q_stride + jj, *p);
     }
     if (k < src.nh) {
         int i = src.h_lo + k;
+        double2* p = &P_half[(size_t)jj * src.nh + k];
         profile_point(M, a, x_half[i], rstar_min + (i + 0.5) * drs, th, rs0, sig_r, sig_t,
-                      drs0_dr0, &P_half[(size_t)jj * src.nh + k],
-                      &dP_half[(size_t)jj * src.nh + k]);
+                      drs0_dr0, p, &dP_half[(size_t)jj * src.nh + k]);
+        put_q(src.Q_half, (size_t)k * src.q_stride + jj, *p);
     }
 }
 
@@ -250,12 +258,12 @@ void launch_coefficients(cudaStream_t st, int prec, double M, double a, int s, i
 
 void launch_profile(cudaStream_t st, double M, double a, double rstar_min, double drs, double dth,
                     double rs0, double sig_r, double sig_t, double drs0_dr0, const double* x_int,
-                    const double* x_half, const SourceDev& src) {
+                    const double* x_half, const SourceDev& src, int prec) {
     dim3 g(((src.ni > src.nh ? src.ni : src.nh) + 127) / 128, src.nj);
     profile_kernel<<<g, 128, 0, st>>>(M, a, rstar_min, drs, dth, rs0, sig_r, sig_t, drs0_dr0,
                                       x_int, x_half, src, (double2*)src.P_int,
                                       (double2*)src.P_half, (double2*)src.dP_int,
-                                      (double2*)src.dP_half);
+                                      (double2*)src.dP_half, prec);
 }
 
 }  // namespace teuk

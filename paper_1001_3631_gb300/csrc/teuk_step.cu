@@ -70,6 +70,10 @@ __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsign
         "l"(src), "r"(bytes), "r"(smem_addr(b))
         : "memory");
 }
+// Bulk prefetch of a global range into L2 (16-byte aligned, size a multiple of 16).
+__device__ __forceinline__ void bulk_prefetch_l2(const void* src, unsigned bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
 // Orders this thread's view of global memory (generic proxy) before its later bulk copies.
 __device__ __forceinline__ void fence_proxy_async_global() {
     asm volatile("fence.proxy.async.global;" ::: "memory");
@@ -115,8 +119,17 @@ struct ColumnRing {
     }
     __device__ __forceinline__ unsigned char* slot(int s) const { return base + (size_t)s * sbytes; }
     __device__ __forceinline__ Planes<P> planes(int s) const { return Planes<P>::at(slot(s), stride); }
-    // One thread: copy column col of buffer bin (and its radial tables) into slot s.
+    // One thread: copy column col of buffer bin (and its radial tables) into slot s, and
+    // prefetch the column's slices of the source profile into L2 (read once per step,
+    // they would otherwise come from DRAM, evicted by the state streaming through L2).
     __device__ __forceinline__ void fill(const InstDev& d, int bin, int col, int s) const {
+        if (d.src.on) {
+            const SourceDev& w = d.src;
+            const unsigned cb = (unsigned)w.q_stride * (unsigned)sizeof(typename V2T<typename P::T>::V);
+            const int a = col - w.i_lo, h = col - w.h_lo;
+            if ((unsigned)a < (unsigned)w.ni) bulk_prefetch_l2((const char*)w.Q_int + (size_t)a * cb, cb);
+            if ((unsigned)h < (unsigned)w.nh) bulk_prefetch_l2((const char*)w.Q_half + (size_t)h * cb, cb);
+        }
         unsigned char* dst = slot(s);
         const unsigned nb = (unsigned)d.nth * 16u;
         mbar_expect_tx(mbar + s, P::planes * nb + (kTabs ? 2u * (unsigned)sizeof(RTab) : 0u));
@@ -216,8 +229,18 @@ __device__ __forceinline__ void strip_step(const InstDev& d, int64_t step, int b
     const bool src_blk = sw.on &&
                          ((c0 - 1 < sw.i_lo + sw.ni && c1 >= sw.i_lo) ||
                           (c0 - 1 < sw.h_lo + sw.nh && c1 >= sw.h_lo));
-    double2 sp_fac = make_double2(0.0, 0.0), sc_fac = make_double2(0.0, 0.0);
-    if (src_blk) source_factors(d, step, sp_fac, sc_fac);
+    // the step's two source factors, computed once (FP64 sincos) and shared
+    __shared__ double2 sfac[2];
+    C sp_fac = C::zero(), sc_fac = C::zero();
+    if (src_blk) {
+        // two warps, one factor each (FP64 sincos is a long dependent chain)
+        const int w1 = blockDim.x > 32 ? 32 : 0;
+        if (threadIdx.x == 0) sfac[0] = source_factor(d, step, 0.0, 0.5 * d.dt);
+        if (threadIdx.x == w1) sfac[1] = source_factor(d, step, 0.5, d.dt);
+        __syncthreads();
+        sp_fac = {(T)sfac[0].x, (T)sfac[0].y};
+        sc_fac = {(T)sfac[1].x, (T)sfac[1].y};
+    }
     const bool ex_blk = c0 - 1 <= d.i_e && d.i_e <= c1 - 1;
 
     // radial boundary condition: Phi = Pi = 0 at i = 0 and i = nr - 1
@@ -236,20 +259,18 @@ __device__ __forceinline__ void strip_step(const InstDev& d, int64_t step, int b
     };
     // predictor at the half node h between columns h (ul) and h+1 (ur)
     auto predict = [&](const NodeV<P>& ul, const NodeV<P>& ur, C dll, C dlr, C dlml, C dlmr,
-                       const RTab& tab, int h) {
+                       const RTab& tab, int h, C src) {
         const Half<T> hp = half_prep<P>(ul, ur);
         const C Dp = C::half_sum(dll, dlr);     // Fb(j+1) - Fb(j)
         const C Dm = C::half_sum(dlml, dlmr);   // Fb(j) - Fb(j-1)
         T cf[kNCoef];
         get_coefs<P>(d, rt, tab, true, h, j, cf);
-        C src = C::zero();
-        if (src_blk) src = source_half<T>(sw, sp_fac, h, j);
         return predictor<T>(hp, Dp, Dm, cf, hdt, src);
     };
-    // corrector at column cc from the half nodes L = cc-1/2 and R = cc+1/2; hs is the
-    // exchange buffer of this column's parity
+    // corrector at column cc from the half nodes L = cc-1/2 and R = cc+1/2; xb is the
+    // exchange buffer of this column's parity, srcc the source term at (cc, j)
     auto correct = [&](const HalfRec<T>& Rh, const HalfRec<T>& Lh, const NodeV<P>& uc,
-                       const RTab& tab, int cc, T* xb, size_t o) {
+                       const RTab& tab, int cc, T* xb, size_t o, C srcc) {
         const CRow<T> row = combine_lr<T>(Rh, Lh);
         // publish {Hs, DpS} of this row at entry j + 1; the pole rows also write the
         // ghost entries: row nth (entry nth + 1) Hs = g Hs(nth-1), row -1 (entry 0)
@@ -285,8 +306,6 @@ __device__ __forceinline__ void strip_step(const InstDev& d, int64_t step, int b
         const C Dminus = DpS_m + (row.Hs - Hs_m);
         T cf[kNCoef];
         get_coefs<P>(d, rt, tab, false, cc, j, cf);
-        C srcc = C::zero();
-        if (src_blk) srcc = source_int<T>(sw, sc_fac, cc, j);
         C dPhi = rmac(rmac(C::zero(), -cf[C_G], row.dFc), fdt, row.PC);
         C dPi = rmac(srcc, cf[C_G], row.dPc);
         dPi = cmac(dPi, cf[C_E1R], cf[C_E1I], row.PC);
@@ -318,7 +337,12 @@ __device__ __forceinline__ void strip_step(const InstDev& d, int64_t step, int b
     ring.wait(1);
     NodeV<P> u_cur = node(1);
     theta_diffs(1, u_cur, dl, dlm);
-    HalfRec<T> L = predict(u_prev, u_cur, dl_prev, dl, dlm_prev, dlm, ring.tab(0, 0), c0 - 1);
+    // source terms at the half node c-1/2 and the node c-1 of the next column, loaded
+    // one column ahead (source blocks only)
+    auto src_h = [&](int h) { return src_blk ? source_half<T>(sw, sp_fac, h, j) : C::zero(); };
+    auto src_i = [&](int i) { return src_blk ? source_int<T>(sw, sc_fac, i, j) : C::zero(); };
+    HalfRec<T> L = predict(u_prev, u_cur, dl_prev, dl, dlm_prev, dlm, ring.tab(0, 0), c0 - 1, src_h(c0 - 1));
+    C nxt_h = src_h(c0), nxt_i = src_i(c0);
     if (ex_blk && d.i_e == c0 - 1) extract(u_prev, u_cur);
     u_prev = u_cur;
     dl_prev = dl;
@@ -330,12 +354,17 @@ __device__ __forceinline__ void strip_step(const InstDev& d, int64_t step, int b
     int sf = 0, sp = 1, sc = 2;
 #pragma unroll 3
     for (int c = c0 + 1; c <= c1; ++c) {
+        const C s_h = nxt_h, s_i = nxt_i;
+        if (c < c1) {
+            nxt_h = src_h(c);
+            nxt_i = src_i(c);
+        }
         ring.wait(sc);
         u_cur = node(sc);
         theta_diffs(sc, u_cur, dl, dlm);
         const RTab th = ring.tab(sp, 0);
-        const HalfRec<T> Rh = predict(u_prev, u_cur, dl_prev, dl, dlm_prev, dlm, th, c - 1);
-        correct(Rh, L, u_prev, ring.tab(sp, 1), c - 1, xbuf + (c & 1) * xstride, o);
+        const HalfRec<T> Rh = predict(u_prev, u_cur, dl_prev, dl, dlm_prev, dlm, th, c - 1, s_h);
+        correct(Rh, L, u_prev, ring.tab(sp, 1), c - 1, xbuf + (c & 1) * xstride, o, s_i);
         if (threadIdx.x == 0 && c - 2 + R <= c1) ring.fill(d, bin, c - 2 + R, sf);
         if (ex_blk && d.i_e == c - 1) extract(u_prev, u_cur);
         L = Rh;

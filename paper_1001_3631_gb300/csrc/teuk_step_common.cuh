@@ -315,36 +315,43 @@ __device__ __forceinline__ HalfRec<T> predictor(const Half<T>& h, Cx<T> Dp, Cx<T
 }
 
 // ---------------------------------------------------------------- source
-__device__ __forceinline__ void source_factors(const InstDev& d, int64_t step, double2& sp,
-                                               double2& sc) {
+// dt_sub A_n e^{-i (omega t + phase0)} at t = t_n + off * dt: the predictor's factor
+// (off = 0, dt_sub = dt/2) or the corrector's (off = 1/2, dt_sub = dt)
+__device__ __forceinline__ double2 source_factor(const InstDev& d, int64_t step, double off,
+                                                 double dt_sub) {
     double A = (d.src.amps != nullptr && step < d.src.n_amps) ? d.src.amps[step] : 1.0;
     double t = (double)step * d.dt;
-    double s1, c1, s2, c2;
-    sincos(d.src.omega * t + d.src.phase0, &s1, &c1);
-    sincos(d.src.omega * (t + 0.5 * d.dt) + d.src.phase0, &s2, &c2);
-    double hp = 0.5 * d.dt * A, hc = d.dt * A;
-    sp = make_double2(hp * c1, -hp * s1);
-    sc = make_double2(hc * c2, -hc * s2);
+    double sn, cs;
+    sincos(d.src.omega * (t + off * d.dt) + d.src.phase0, &sn, &cs);
+    double h = dt_sub * A;
+    return make_double2(h * cs, -h * sn);
+}
+
+// tau at a window node: factor (A e^{-i(omega t + phase0)} and the sub-step's share of
+// dt) times the profile, from the column-major copy in the arithmetic type
+template <typename T> struct V2T;
+template <> struct V2T<float> { using V = float2; };
+template <> struct V2T<double> { using V = double2; };
+
+template <typename T>
+__device__ __forceinline__ Cx<T> source_at(const void* q, int stride, Cx<T> fac, int a, int b) {
+    const typename V2T<T>::V p = ((const typename V2T<T>::V*)q)[(size_t)a * stride + b];
+    return {fac.re * p.x - fac.im * p.y, fac.re * p.y + fac.im * p.x};
 }
 
 template <typename T>
-__device__ __forceinline__ Cx<T> cmul_cast(double2 f, double2 p) {
-    return {(T)(f.x * p.x - f.y * p.y), (T)(f.x * p.y + f.y * p.x)};
-}
-
-template <typename T>
-__device__ __forceinline__ Cx<T> source_half(const SourceDev& s, double2 fac, int i, int j) {
+__device__ __forceinline__ Cx<T> source_half(const SourceDev& s, Cx<T> fac, int i, int j) {
     int a = i - s.h_lo, b = j - s.j_lo;
     if ((unsigned)a < (unsigned)s.nh && (unsigned)b < (unsigned)s.nj)
-        return cmul_cast<T>(fac, s.P_half[(size_t)b * s.nh + a]);
+        return source_at<T>(s.Q_half, s.q_stride, fac, a, b);
     return Cx<T>::zero();
 }
 
 template <typename T>
-__device__ __forceinline__ Cx<T> source_int(const SourceDev& s, double2 fac, int i, int j) {
+__device__ __forceinline__ Cx<T> source_int(const SourceDev& s, Cx<T> fac, int i, int j) {
     int a = i - s.i_lo, b = j - s.j_lo;
     if ((unsigned)a < (unsigned)s.ni && (unsigned)b < (unsigned)s.nj)
-        return cmul_cast<T>(fac, s.P_int[(size_t)b * s.ni + a]);
+        return source_at<T>(s.Q_int, s.q_stride, fac, a, b);
     return Cx<T>::zero();
 }
 
