@@ -30,6 +30,8 @@
 // sub-steps differ only by the factor 1/2 versus 1 of dt).  This is Eqs. (13)-(14)
 // with S_Pi = -c_t Pi + P* Phi_* + w Theta[Phi] + q Phi + tau, rearranged, not
 // approximated.
+#include <type_traits>
+
 #include "teuk_internal.cuh"
 #include "teuk_step_common.cuh"
 
@@ -229,17 +231,25 @@ __device__ __forceinline__ void strip_step(const InstDev& d, int64_t step, int b
     const bool src_blk = sw.on &&
                          ((c0 - 1 < sw.i_lo + sw.ni && c1 >= sw.i_lo) ||
                           (c0 - 1 < sw.h_lo + sw.nh && c1 >= sw.h_lo));
-    // the step's two source factors, computed once (FP64 sincos) and shared
-    __shared__ double2 sfac[2];
+    // the step's two source factors, computed once in FP64 (sincos) by two warps, one
+    // factor each, and shared already rounded to the arithmetic type
+    __shared__ T sfac[4];
     C sp_fac = C::zero(), sc_fac = C::zero();
     if (src_blk) {
-        // two warps, one factor each (FP64 sincos is a long dependent chain)
         const int w1 = blockDim.x > 32 ? 32 : 0;
-        if (threadIdx.x == 0) sfac[0] = source_factor(d, step, 0.0, 0.5 * d.dt);
-        if (threadIdx.x == w1) sfac[1] = source_factor(d, step, 0.5, d.dt);
+        if (threadIdx.x == 0) {
+            const double2 f = source_factor(d, step, 0.0, 0.5 * d.dt);
+            sfac[0] = (T)f.x;
+            sfac[1] = (T)f.y;
+        }
+        if (threadIdx.x == w1) {
+            const double2 f = source_factor(d, step, 0.5, d.dt);
+            sfac[2] = (T)f.x;
+            sfac[3] = (T)f.y;
+        }
         __syncthreads();
-        sp_fac = {(T)sfac[0].x, (T)sfac[0].y};
-        sc_fac = {(T)sfac[1].x, (T)sfac[1].y};
+        sp_fac = {sfac[0], sfac[1]};
+        sc_fac = {sfac[2], sfac[3]};
     }
     const bool ex_blk = c0 - 1 <= d.i_e && d.i_e <= c1 - 1;
 
@@ -337,12 +347,11 @@ __device__ __forceinline__ void strip_step(const InstDev& d, int64_t step, int b
     ring.wait(1);
     NodeV<P> u_cur = node(1);
     theta_diffs(1, u_cur, dl, dlm);
-    // source terms at the half node c-1/2 and the node c-1 of the next column, loaded
-    // one column ahead (source blocks only)
-    auto src_h = [&](int h) { return src_blk ? source_half<T>(sw, sp_fac, h, j) : C::zero(); };
-    auto src_i = [&](int i) { return src_blk ? source_int<T>(sw, sc_fac, i, j) : C::zero(); };
-    HalfRec<T> L = predict(u_prev, u_cur, dl_prev, dl, dlm_prev, dlm, ring.tab(0, 0), c0 - 1, src_h(c0 - 1));
-    C nxt_h = src_h(c0), nxt_i = src_i(c0);
+    // source terms at the half node h and the node i (source blocks only)
+    auto src_h = [&](int h) { return source_half<T>(sw, sp_fac, h, j); };
+    auto src_i = [&](int i) { return source_int<T>(sw, sc_fac, i, j); };
+    HalfRec<T> L = predict(u_prev, u_cur, dl_prev, dl, dlm_prev, dlm, ring.tab(0, 0), c0 - 1,
+                           src_blk ? src_h(c0 - 1) : C::zero());
     if (ex_blk && d.i_e == c0 - 1) extract(u_prev, u_cur);
     u_prev = u_cur;
     dl_prev = dl;
@@ -350,32 +359,46 @@ __device__ __forceinline__ void strip_step(const InstDev& d, int64_t step, int b
     size_t o = node_index(d, c0, j);               // output offset of the corrector's column
 
     // steady state: column c arrives, predictor at c-1/2, corrector at c-1; the slots
-    // hold columns c-2 (sf, free once the column's barrier is passed), c-1 (sp) and c (sc)
-    int sf = 0, sp = 1, sc = 2;
-#pragma unroll 3
-    for (int c = c0 + 1; c <= c1; ++c) {
-        const C s_h = nxt_h, s_i = nxt_i;
-        if (c < c1) {
-            nxt_h = src_h(c);
-            nxt_i = src_i(c);
+    // hold columns c-2 (sf, free once the column's barrier is passed), c-1 (sp) and c (sc).
+    // Two instances of the loop: blocks without source nodes carry no source code; the
+    // source blocks load the next column's source terms one column ahead.
+    auto steady = [&](auto has_src) {
+        constexpr bool kSrc = decltype(has_src)::value;
+        C nxt_h = C::zero(), nxt_i = C::zero();
+        if constexpr (kSrc) {
+            nxt_h = src_h(c0);
+            nxt_i = src_i(c0);
         }
-        ring.wait(sc);
-        u_cur = node(sc);
-        theta_diffs(sc, u_cur, dl, dlm);
-        const RTab th = ring.tab(sp, 0);
-        const HalfRec<T> Rh = predict(u_prev, u_cur, dl_prev, dl, dlm_prev, dlm, th, c - 1, s_h);
-        correct(Rh, L, u_prev, ring.tab(sp, 1), c - 1, xbuf + (c & 1) * xstride, o, s_i);
-        if (threadIdx.x == 0 && c - 2 + R <= c1) ring.fill(d, bin, c - 2 + R, sf);
-        if (ex_blk && d.i_e == c - 1) extract(u_prev, u_cur);
-        L = Rh;
-        u_prev = u_cur;
-        dl_prev = dl;
-        dlm_prev = dlm;
-        o += pitch;
-        sf = sp;
-        sp = sc;
-        sc = sc + 1 == R ? 0 : sc + 1;
-    }
+        int sf = 0, sp = 1, sc = 2;
+#pragma unroll 3
+        for (int c = c0 + 1; c <= c1; ++c) {
+            const C s_h = nxt_h, s_i = nxt_i;
+            if constexpr (kSrc) {
+                if (c < c1) {
+                    nxt_h = src_h(c);
+                    nxt_i = src_i(c);
+                }
+            }
+            ring.wait(sc);
+            u_cur = node(sc);
+            theta_diffs(sc, u_cur, dl, dlm);
+            const RTab th = ring.tab(sp, 0);
+            const HalfRec<T> Rh = predict(u_prev, u_cur, dl_prev, dl, dlm_prev, dlm, th, c - 1, s_h);
+            correct(Rh, L, u_prev, ring.tab(sp, 1), c - 1, xbuf + (c & 1) * xstride, o, s_i);
+            if (threadIdx.x == 0 && c - 2 + R <= c1) ring.fill(d, bin, c - 2 + R, sf);
+            if (ex_blk && d.i_e == c - 1) extract(u_prev, u_cur);
+            L = Rh;
+            u_prev = u_cur;
+            dl_prev = dl;
+            dlm_prev = dlm;
+            o += pitch;
+            sf = sp;
+            sp = sc;
+            sc = sc + 1 == R ? 0 : sc + 1;
+        }
+    };
+    if (src_blk) steady(std::true_type{});
+    else steady(std::false_type{});
     if (__syncthreads_or(ring.late)) {
         if (threadIdx.x == 0) {
             ring.drain();
