@@ -80,6 +80,13 @@ __device__ __forceinline__ void bulk_prefetch_l2(const void* src, unsigned bytes
 __device__ __forceinline__ void fence_proxy_async_global() {
     asm volatile("fence.proxy.async.global;" ::: "memory");
 }
+// Programmatic dependent launch: wait for the previous grid in the stream (complete and
+// its memory visible; a no-op for launches without the attribute), and allow the next
+// grid to launch.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch_dependents() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
 __device__ __forceinline__ unsigned long long global_ns() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
@@ -201,8 +208,11 @@ constexpr int kRingS = 6, kRingL = 4;
 // column c-1.  The first two columns are peeled so the steady-state loop has no
 // per-column mode switches, and it is unrolled by three so the rotation of the
 // previous / current column is register renaming.  Columns c0-1 .. c1 are read.
-template <class P, int R>
-__device__ __forceinline__ void strip_step(const InstDev& d, int64_t step, int bin, int c0,
+// kPerStep: the block belongs to a per-step launch (programmatic dependent launch: the
+// part before griddepcontrol.wait overlaps the previous step, and the block returns at
+// once when a bounded wait of an earlier launch gave up).  Returns false in that case.
+template <class P, int R, bool kPerStep>
+__device__ __forceinline__ bool strip_step(const InstDev& d, int64_t step, int bin, int c0,
                                            int c1, ColumnRing<P, R>& ring, typename P::T* xbuf) {
     using T = typename P::T;
     using C = Cx<T>;
@@ -218,10 +228,6 @@ __device__ __forceinline__ void strip_step(const InstDev& d, int64_t step, int b
     const T hdt = (T)(0.5 * d.dt), fdt = (T)d.dt;
     const Planes<P> out = Planes<P>::of(d, 1 - bin);
     const unsigned xstride = 4u * (blockDim.x + 2u);
-    if (threadIdx.x == 0) {
-        fence_proxy_async_global();
-        for (int k = 0; k < c1 - c0 + 2 && k < R; ++k) ring.fill(d, bin, c0 - 1 + k, k);
-    }
     RowTab<P> rt;
     rt.load(d.thtab, j, row_ok);
     const size_t pitch = (size_t)d.pitch;
@@ -234,7 +240,7 @@ __device__ __forceinline__ void strip_step(const InstDev& d, int64_t step, int b
     // the step's two source factors, computed once in FP64 (sincos) by two warps, one
     // factor each, and shared already rounded to the arithmetic type
     __shared__ T sfac[4];
-    C sp_fac = C::zero(), sc_fac = C::zero();
+    __shared__ int skip;
     if (src_blk) {
         const int w1 = blockDim.x > 32 ? 32 : 0;
         if (threadIdx.x == 0) {
@@ -247,7 +253,22 @@ __device__ __forceinline__ void strip_step(const InstDev& d, int64_t step, int b
             sfac[2] = (T)f.x;
             sfac[3] = (T)f.y;
         }
-        __syncthreads();
+    }
+    // Everything above reads only constant data; the state of the previous step (read
+    // by the ring, overwritten by this step's stores) is touched only below.
+    if constexpr (kPerStep) griddep_wait();
+    if (threadIdx.x == 0) {
+        // a bounded wait of an earlier launch gave up: the state is void until it is reset
+        skip = kPerStep ? (*(volatile unsigned*)d.status & ST_TIMEOUT) != 0 : 0;
+        if (!skip) {
+            fence_proxy_async_global();
+            for (int k = 0; k < c1 - c0 + 2 && k < R; ++k) ring.fill(d, bin, c0 - 1 + k, k);
+        }
+    }
+    __syncthreads();
+    if (kPerStep && skip) return false;
+    C sp_fac = C::zero(), sc_fac = C::zero();
+    if (src_blk) {
         sp_fac = {sfac[0], sfac[1]};
         sc_fac = {sfac[2], sfac[3]};
     }
@@ -407,6 +428,7 @@ __device__ __forceinline__ void strip_step(const InstDev& d, int64_t step, int b
         __syncthreads();
         ring.late = false;
     }
+    return true;
 }
 
 // Two register budgets: columns of up to 256 rows (the common case, P::blocks256
@@ -416,18 +438,15 @@ template <class P, int R>
 __device__ __forceinline__ void step_body(const InstDev& d, int64_t step, int bin, int strip) {
     extern __shared__ __align__(128) unsigned char step_smem[];
     __shared__ uint64_t mbar[R];
-    __shared__ int skip;
+    // the next step's launch may begin now: its blocks become resident as ours retire and
+    // run their set-up while this step drains
+    griddep_launch_dependents();
     ColumnRing<P, R> ring(step_smem, mbar);
-    if (threadIdx.x == 0) {
-        // a bounded wait of an earlier launch gave up: the state is void until it is reset
-        skip = (*(volatile unsigned*)d.status & ST_TIMEOUT) != 0;
-        if (!skip) ring.init();
-    }
+    if (threadIdx.x == 0) ring.init();
     __syncthreads();
-    if (skip) return;
     const int c0 = 1 + blockIdx.x * strip;
     const int c1 = min(d.nr - 1, c0 + strip);
-    strip_step<P, R>(d, step, bin, c0, c1, ring, StepShared<P, R>::xbuf(step_smem));
+    strip_step<P, R, true>(d, step, bin, c0, c1, ring, StepShared<P, R>::xbuf(step_smem));
 }
 
 template <class P>
@@ -534,7 +553,7 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) batched_step_kernel(B
         }
         const int c0 = 1 + st * strip;
         const int c1 = min(d.nr - 1, c0 + strip);
-        strip_step<P, R>(d, b.base_step[k] + s, (int)((b.base_bin[k] + s) & 1), c0, c1, ring, xbuf);
+        strip_step<P, R, false>(d, b.base_step[k] + s, (int)((b.base_bin[k] + s) & 1), c0, c1, ring, xbuf);
         __threadfence();
         __syncthreads();
         if (threadIdx.x == 0 && !(s == 0 && r == b.skip_release_item))
@@ -606,10 +625,23 @@ template <class P>
 static void launch_step_p(cudaStream_t st, const InstDev& d, int64_t step, int bin, int strip) {
     int blocks = (d.nr - 2 + strip - 1) / strip;
     int threads = d.pitch;
-    if (threads <= 256)
-        step_kernel_s<P><<<blocks, threads, StepShared<P, kRingS>::bytes(threads), st>>>(d, step, bin, strip);
-    else
-        step_kernel_l<P><<<blocks, threads, StepShared<P, kRingL>::bytes(threads), st>>>(d, step, bin, strip);
+    // programmatic dependent launch (see step_body)
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(blocks);
+    cfg.blockDim = dim3(threads);
+    cfg.stream = st;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    if (threads <= 256) {
+        cfg.dynamicSmemBytes = StepShared<P, kRingS>::bytes(threads);
+        cudaLaunchKernelEx(&cfg, step_kernel_s<P>, d, step, bin, strip);
+    } else {
+        cfg.dynamicSmemBytes = StepShared<P, kRingL>::bytes(threads);
+        cudaLaunchKernelEx(&cfg, step_kernel_l<P>, d, step, bin, strip);
+    }
 }
 
 template <class P>
