@@ -117,10 +117,13 @@ teuk_status teuk_set_source(teuk_ctx* ctx, int instance, const teuk_orbit* orbit
 
 /* Replace the state of one instance from host memory in u-layout (copied) and
  * set its time level to step0 (t = step0 dt).  Clears that instance's
- * waveform records. */
+ * waveform records.  Synchronizes.  The first call of teuk_set_state or
+ * teuk_get_state on an instance allocates a device staging buffer of
+ * 32 n_rstar n_theta bytes, kept until teuk_destroy. */
 teuk_status teuk_set_state(teuk_ctx* ctx, int instance, const double* host_u, int64_t step0);
 
-/* Copy the state of one instance to host memory in u-layout.  Synchronizes. */
+/* Copy the state of one instance to host memory in u-layout (through the staging
+ * buffer described at teuk_set_state).  Synchronizes. */
 teuk_status teuk_get_state(teuk_ctx* ctx, int instance, double* host_u);
 
 /* Advance every instance by n full Lax-Wendroff steps (Eqs. 13-14), recording the

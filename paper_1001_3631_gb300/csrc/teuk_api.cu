@@ -45,6 +45,7 @@ struct Instance {
     double f_e = 0, r_ext = 0;
     int strip = 0;      // r* columns per work item chosen for this instance (0 = context default)
     int resident = 0;   // blocks of its step kernel the GPU holds at once
+    double* stage = nullptr;    // u-layout staging of set/get_state, allocated on first use
 };
 
 // Device side of the batched persistent launch of one context: one persistent kernel
@@ -88,6 +89,8 @@ struct teuk_ctx {
     Batch batch;
     int64_t inject_skip_item = -1;   // testing aid: a work item that never releases its flag
     long long spin_limit = 20000000LL;
+    double2* sum_buf = nullptr;      // teuk_extract's summed records, grown on demand
+    int64_t sum_cap = 0;
 };
 
 static std::string g_create_err = "no error";
@@ -221,7 +224,8 @@ void free_instance(cudaStream_t s, Instance& I) {
     for (int b = 0; b < 2; ++b)
         for (int k = 0; k < 2; ++k)
             if (I.state[b][k]) cudaFreeAsync(I.state[b][k], s);
-    void* ptrs[] = {I.coef_h, I.coef_i, I.x_int, I.x_half, I.P_win, I.amps, I.wave, I.rtab, I.thtab};
+    void* ptrs[] = {I.coef_h, I.coef_i, I.x_int, I.x_half, I.P_win, I.amps, I.wave, I.rtab, I.thtab,
+                    I.stage};
     for (void* q : ptrs)
         if (q) cudaFreeAsync(q, s);
     I = Instance();
@@ -413,13 +417,11 @@ extern "C" teuk_status teuk_set_state(teuk_ctx* c, int instance, const double* h
     if (!host_u || step0 < 0) TK_FAIL(c, TEUK_EINVAL, "host_u is NULL or step0 < 0");
     Instance& I = c->inst[instance];
     size_t bytes = sizeof(double) * 4 * (size_t)I.p.n_rstar * I.p.n_theta;
-    double* du = nullptr;
-    TK_CUDA(c, cudaMallocAsync((void**)&du, bytes, c->stream));
-    TK_CUDA(c, cudaMemcpyAsync(du, host_u, bytes, cudaMemcpyHostToDevice, c->stream));
-    launch_import_state(c->stream, dev_of(c, I), I.cur, du);
+    if (!I.stage) TK_CUDA(c, cudaMallocAsync((void**)&I.stage, bytes, c->stream));
+    TK_CUDA(c, cudaMemcpyAsync(I.stage, host_u, bytes, cudaMemcpyHostToDevice, c->stream));
+    launch_import_state(c->stream, dev_of(c, I), I.cur, I.stage);
     c->launches++;
     TK_CUDA(c, cudaGetLastError());
-    TK_CUDA(c, cudaFreeAsync(du, c->stream));
     TK_CUDA(c, cudaStreamSynchronize(c->stream));  // the host buffer may go away after return
     I.step = step0;
     I.wave_lo = I.wave_hi = step0;
@@ -432,13 +434,11 @@ extern "C" teuk_status teuk_get_state(teuk_ctx* c, int instance, double* host_u)
     if (!host_u) TK_FAIL(c, TEUK_EINVAL, "host_u is NULL");
     Instance& I = c->inst[instance];
     size_t bytes = sizeof(double) * 4 * (size_t)I.p.n_rstar * I.p.n_theta;
-    double* du = nullptr;
-    TK_CUDA(c, cudaMallocAsync((void**)&du, bytes, c->stream));
-    launch_export_state(c->stream, dev_of(c, I), I.cur, du);
+    if (!I.stage) TK_CUDA(c, cudaMallocAsync((void**)&I.stage, bytes, c->stream));
+    launch_export_state(c->stream, dev_of(c, I), I.cur, I.stage);
     c->launches++;
     TK_CUDA(c, cudaGetLastError());
-    TK_CUDA(c, cudaMemcpyAsync(host_u, du, bytes, cudaMemcpyDeviceToHost, c->stream));
-    TK_CUDA(c, cudaFreeAsync(du, c->stream));
+    TK_CUDA(c, cudaMemcpyAsync(host_u, I.stage, bytes, cudaMemcpyDeviceToHost, c->stream));
     TK_CUDA(c, cudaStreamSynchronize(c->stream));
     return TEUK_OK;
 }
@@ -648,14 +648,18 @@ extern "C" teuk_status teuk_extract(teuk_ctx* c, int instance, double* out, doub
         done += run;
     }
     if (out_scalar && k > 0) {
-        double2* tmp = nullptr;
-        TK_CUDA(c, cudaMallocAsync((void**)&tmp, sizeof(double2) * k, c->stream));
-        launch_wave_sum(c->stream, I.wave, I.wave_cap, nth, I.dth, lvl0, k, tmp);
+        if (k > c->sum_cap) {
+            if (c->sum_buf) TK_CUDA(c, cudaFreeAsync(c->sum_buf, c->stream));
+            c->sum_buf = nullptr;
+            c->sum_cap = 0;
+            TK_CUDA(c, cudaMallocAsync((void**)&c->sum_buf, sizeof(double2) * k, c->stream));
+            c->sum_cap = k;
+        }
+        launch_wave_sum(c->stream, I.wave, I.wave_cap, nth, I.dth, lvl0, k, c->sum_buf);
         c->launches++;
         TK_CUDA(c, cudaGetLastError());
-        TK_CUDA(c, cudaMemcpyAsync(out_scalar, tmp, sizeof(double2) * k, cudaMemcpyDeviceToHost,
+        TK_CUDA(c, cudaMemcpyAsync(out_scalar, c->sum_buf, sizeof(double2) * k, cudaMemcpyDeviceToHost,
                                    c->stream));
-        TK_CUDA(c, cudaFreeAsync(tmp, c->stream));
     }
     TK_CUDA(c, cudaStreamSynchronize(c->stream));
     if (n_written) *n_written = k;
@@ -800,6 +804,7 @@ extern "C" int64_t teuk_kernel_launches(const teuk_ctx* c) { return c ? c->launc
 extern "C" void teuk_destroy(teuk_ctx* c) {
     if (!c) return;
     {
+        if (c->sum_buf) cudaFreeAsync(c->sum_buf, c->stream);
         Batch& B = c->batch;
         if (B.exec) cudaGraphExecDestroy(B.exec);
         if (B.graph) cudaGraphDestroy(B.graph);
