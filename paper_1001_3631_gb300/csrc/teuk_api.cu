@@ -46,6 +46,11 @@ struct Instance {
     int strip = 0;      // r* columns per work item chosen for this instance (0 = context default)
     int resident = 0;   // blocks of its step kernel the GPU holds at once
     double* stage = nullptr;    // u-layout staging of set/get_state, allocated on first use
+    // column partition of the per-step launch for strip length part_strip (see
+    // refresh_partition); d_part holds n_rstar ints
+    int* d_part = nullptr;
+    std::vector<int> h_part;
+    int part_strip = 0;
 };
 
 // Device side of the batched persistent launch of one context: one persistent kernel
@@ -208,8 +213,59 @@ int eff_strip(const teuk_ctx* c, const Instance& I) {
     return std::max(1, std::min(L, I.p.n_rstar - 2));
 }
 
+// Column partition of the per-step launch: the same number of blocks as uniform strips
+// of the effective length, cut so that the blocks have about equal cost.  A column costs
+// 1, a column of the source window 1 + alpha (its source terms; alpha = 0.25 on the FP32
+// paths, 0.1 on the FP64 path, measured per column on GB300) and the extraction column
+// 2 more (the FP64 waveform record).  Without it the blocks holding the source window
+// finish last and every step waits for them.  Built on the host whenever the strip
+// length or the source changes, so a step never allocates or copies.
+teuk_status refresh_partition(teuk_ctx* c, Instance& I) {
+    const int strip = eff_strip(c, I);
+    const int nr = I.p.n_rstar;
+    const int nb = (nr - 2 + strip - 1) / strip;
+    const double alpha = I.p.prec == TEUK_FP64 ? 0.1 : 0.25;
+    int wlo = nr, whi = 0;
+    if (I.src_on) {
+        wlo = std::min(I.sd.i_lo, I.sd.h_lo + 1);
+        whi = std::max(I.sd.i_lo + I.sd.ni, I.sd.h_lo + I.sd.nh + 1);
+    }
+    std::vector<double> cum(nr, 0.0);  // cum[col] = cost of the columns 1 .. col-1
+    for (int col = 2; col <= nr - 1; ++col) {
+        const int q = col - 1;
+        cum[col] = cum[col - 1] + 1.0 + ((q >= wlo && q < whi) ? alpha : 0.0) + (q == I.i_e ? 2.0 : 0.0);
+    }
+    const double total = cum[nr - 1];
+    I.h_part.assign(nb + 1, 0);
+    I.h_part[0] = 1;
+    I.h_part[nb] = nr - 1;
+    int col = 1;
+    for (int k = 1; k < nb; ++k) {
+        const double t = total * k / nb;
+        const int lo = I.h_part[k - 1] + 1, hi = nr - 1 - (nb - k);
+        col = std::max(col, lo);
+        while (col < hi && cum[col + 1] <= t) ++col;
+        if (col < hi && t - cum[col] > cum[col + 1] - t) ++col;
+        I.h_part[k] = col;
+    }
+    if (!I.d_part) TK_CUDA(c, cudaMallocAsync((void**)&I.d_part, sizeof(int) * nr, c->stream));
+    // (from pageable memory: staged before the call returns, so h_part may change after)
+    TK_CUDA(c, cudaMemcpyAsync(I.d_part, I.h_part.data(), sizeof(int) * (nb + 1), cudaMemcpyHostToDevice,
+                               c->stream));
+    I.part_strip = strip;
+    return TEUK_OK;
+}
+
+teuk_status refresh_partitions(teuk_ctx* c) {
+    for (Instance& I : c->inst) {
+        teuk_status st = refresh_partition(c, I);
+        if (st) return st;
+    }
+    return TEUK_OK;
+}
+
 void do_step(teuk_ctx* c, Instance& I, int strip) {
-    launch_step(c->stream, dev_of(c, I), I.step, I.cur, strip);
+    launch_step(c->stream, dev_of(c, I), I.step, I.cur, strip, I.part_strip == strip ? I.d_part : nullptr);
     c->launches++;
     I.cur = 1 - I.cur;
     I.step++;
@@ -225,7 +281,7 @@ void free_instance(cudaStream_t s, Instance& I) {
         for (int k = 0; k < 2; ++k)
             if (I.state[b][k]) cudaFreeAsync(I.state[b][k], s);
     void* ptrs[] = {I.coef_h, I.coef_i, I.x_int, I.x_half, I.P_win, I.amps, I.wave, I.rtab, I.thtab,
-                    I.stage};
+                    I.stage, I.d_part};
     for (void* q : ptrs)
         if (q) cudaFreeAsync(q, s);
     I = Instance();
@@ -322,6 +378,7 @@ extern "C" teuk_status teuk_create(const teuk_params* p, int n_instances, void* 
         TK_CCUDA(cudaGetLastError());
         I.r_ext = 0;  // filled lazily from x at r*_ext when needed (adjoint loss)
     }
+    if (refresh_partitions(c) != TEUK_OK) return fail(TEUK_ECUDA);
 #undef TK_CCUDA
     *out = c;
     return TEUK_OK;
@@ -404,6 +461,8 @@ extern "C" teuk_status teuk_set_source(teuk_ctx* c, int instance, const teuk_orb
     I.sd = sd;
     I.orbit = *orbit;
     I.src_on = true;
+    st = refresh_partition(c, I);
+    if (st) return st;
     if (n_amps > 0) TK_CUDA(c, cudaStreamSynchronize(c->stream));  // host amps may be freed
     return TEUK_OK;
 }
@@ -700,7 +759,7 @@ extern "C" teuk_status teuk_set_tiling(teuk_ctx* c, int strip, int steps_per_lau
     c->strip = strip;
     c->steps_per_launch = steps_per_launch;
     invalidate_graph(c);
-    return TEUK_OK;
+    return refresh_partitions(c);
 }
 
 extern "C" teuk_status teuk_set_fault_injection(teuk_ctx* c, int64_t skip_release_item,
@@ -719,7 +778,7 @@ extern "C" teuk_status teuk_set_instance_tiling(teuk_ctx* c, int instance, int s
     if (strip < 0) TK_FAIL(c, TEUK_EINVAL, "strip must be >= 0");
     c->inst[instance].strip = strip;
     invalidate_graph(c);
-    return TEUK_OK;
+    return refresh_partition(c, c->inst[instance]);
 }
 
 // Time each candidate strip length on a scratch copy of one instance of every
@@ -796,7 +855,7 @@ extern "C" teuk_status teuk_autotune(teuk_ctx* c, int trial_steps, int* chosen) 
     }
     invalidate_graph(c);
     TK_CUDA(c, cudaGetLastError());
-    return TEUK_OK;
+    return refresh_partitions(c);
 }
 
 extern "C" int64_t teuk_kernel_launches(const teuk_ctx* c) { return c ? c->launches : 0; }
@@ -913,9 +972,9 @@ extern "C" teuk_status teuk_adjoint_n(teuk_ctx* c, int instance, int64_t step0, 
     // forward-sweep helpers ------------------------------------------------
     // run `count` steps on the buffers of dv (which start in buffer cur), recording
     // levels into the ring of dv; returns the buffer holding the result.
-    auto forward = [&](InstDev dv, int cur, int64_t level, int64_t count, int chunk) {
+    auto forward = [&](InstDev dv, int cur, int64_t level, int64_t count, int strip) {
         for (int64_t k = 0; k < count; ++k) {
-            launch_step(s, dv, level + k, cur, chunk);
+            launch_step(s, dv, level + k, cur, strip);
             c->launches++;
             cur = 1 - cur;
         }
@@ -923,7 +982,7 @@ extern "C" teuk_status teuk_adjoint_n(teuk_ctx* c, int instance, int64_t step0, 
         c->launches++;
         return cur;
     };
-    const int chunk = eff_strip(c, I);
+    const int strip = eff_strip(c, I);
     // the segment plan: segments [a_k, a_k + len_k) of the steps step0 .. step0+n-1
     int64_t K = (builtin && ckpt_every > 0) ? ckpt_every : n;
     int64_t nseg = (n + K - 1) / K;
@@ -955,7 +1014,7 @@ extern "C" teuk_status teuk_adjoint_n(teuk_ctx* c, int instance, int64_t step0, 
             fw = dev_of(c, I);
             fw.wave = segrec;
             fw.wave_cap = K + 1;
-            I.cur = forward(fw, I.cur, a, len, chunk);
+            I.cur = forward(fw, I.cur, a, len, strip);
             I.step = a + len;
             if (!ckpt) {  // one segment holds everything: take the loss now
                 launch_loss_records(s, segrec, K + 1, nth, a + 1, len, r6, lossrec + (a - step0),
@@ -985,7 +1044,7 @@ extern "C" teuk_status teuk_adjoint_n(teuk_ctx* c, int instance, int64_t step0, 
             }
             rv.wave = segrec;
             rv.wave_cap = K + 1;
-            forward(rv, 0, a, len, chunk);
+            forward(rv, 0, a, len, strip);
             // records a+1 .. a+len, and also record a (the last record of the previous
             // segment), which this segment's first reverse step needs before the
             // previous segment is recomputed; writing it twice stores the same value

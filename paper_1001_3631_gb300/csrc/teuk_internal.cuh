@@ -135,7 +135,10 @@ void launch_profile(cudaStream_t st, double M, double a, double rstar_min, doubl
 // teuk_step.cu
 cudaError_t prepare_step_kernels();
 int step_resident_blocks(int prec, int threads);  // blocks of the step kernel the GPU holds at once
-void launch_step(cudaStream_t st, const InstDev& d, int64_t step, int bin, int strip);
+// part (device, may be null): block b covers the columns [part[b], part[b+1]) of a
+// partition into ceil((n_rstar - 2) / strip) pieces, instead of uniform strips
+void launch_step(cudaStream_t st, const InstDev& d, int64_t step, int bin, int strip,
+                 const int* part = nullptr);
 void launch_extract(cudaStream_t st, const InstDev& d, int64_t step, int bin);
 void launch_batched_step(cudaStream_t st, int prec, const BatchDev& b, int grid, int threads);
 int batched_grid(int prec, int threads);

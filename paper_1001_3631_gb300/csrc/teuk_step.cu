@@ -434,8 +434,12 @@ __device__ __forceinline__ bool strip_step(const InstDev& d, int64_t step, int b
 // Two register budgets: columns of up to 256 rows (the common case, P::blocks256
 // blocks per SM) and of up to 1024 rows.  Dynamic shared memory:
 // StepShared<P, R>::bytes(blockDim.x).
+// part (may be null): the block's columns are [part[b], part[b+1]) instead of the uniform
+// strips; it is written by the host before the launch sequence and never changes while
+// a step runs, so it is read before griddepcontrol.wait.
 template <class P, int R>
-__device__ __forceinline__ void step_body(const InstDev& d, int64_t step, int bin, int strip) {
+__device__ __forceinline__ void step_body(const InstDev& d, int64_t step, int bin, int strip,
+                                          const int* part) {
     extern __shared__ __align__(128) unsigned char step_smem[];
     __shared__ uint64_t mbar[R];
     // the next step's launch may begin now: its blocks become resident as ours retire and
@@ -444,19 +448,27 @@ __device__ __forceinline__ void step_body(const InstDev& d, int64_t step, int bi
     ColumnRing<P, R> ring(step_smem, mbar);
     if (threadIdx.x == 0) ring.init();
     __syncthreads();
-    const int c0 = 1 + blockIdx.x * strip;
-    const int c1 = min(d.nr - 1, c0 + strip);
+    int c0, c1;
+    if (part) {
+        c0 = part[blockIdx.x];
+        c1 = part[blockIdx.x + 1];
+    } else {
+        c0 = 1 + blockIdx.x * strip;
+        c1 = min(d.nr - 1, c0 + strip);
+    }
     strip_step<P, R, true>(d, step, bin, c0, c1, ring, StepShared<P, R>::xbuf(step_smem));
 }
 
 template <class P>
-__global__ void __launch_bounds__(256, P::blocks256) step_kernel_s(InstDev d, int64_t step, int bin, int strip) {
-    step_body<P, kRingS>(d, step, bin, strip);
+__global__ void __launch_bounds__(256, P::blocks256) step_kernel_s(InstDev d, int64_t step, int bin, int strip,
+                                                                  const int* part) {
+    step_body<P, kRingS>(d, step, bin, strip, part);
 }
 
 template <class P>
-__global__ void __launch_bounds__(1024) step_kernel_l(InstDev d, int64_t step, int bin, int strip) {
-    step_body<P, kRingL>(d, step, bin, strip);
+__global__ void __launch_bounds__(1024) step_kernel_l(InstDev d, int64_t step, int bin, int strip,
+                                                     const int* part) {
+    step_body<P, kRingL>(d, step, bin, strip, part);
 }
 
 // Waveform record of the state in buffer bin (time level `step`): one thread per row.
@@ -622,7 +634,8 @@ void launch_batched_extract(cudaStream_t st, int prec, const BatchDev& b, int ma
 }
 
 template <class P>
-static void launch_step_p(cudaStream_t st, const InstDev& d, int64_t step, int bin, int strip) {
+static void launch_step_p(cudaStream_t st, const InstDev& d, int64_t step, int bin, int strip,
+                          const int* part) {
     int blocks = (d.nr - 2 + strip - 1) / strip;
     int threads = d.pitch;
     // programmatic dependent launch (see step_body)
@@ -637,10 +650,10 @@ static void launch_step_p(cudaStream_t st, const InstDev& d, int64_t step, int b
     cfg.numAttrs = 1;
     if (threads <= 256) {
         cfg.dynamicSmemBytes = StepShared<P, kRingS>::bytes(threads);
-        cudaLaunchKernelEx(&cfg, step_kernel_s<P>, d, step, bin, strip);
+        cudaLaunchKernelEx(&cfg, step_kernel_s<P>, d, step, bin, strip, part);
     } else {
         cfg.dynamicSmemBytes = StepShared<P, kRingL>::bytes(threads);
-        cudaLaunchKernelEx(&cfg, step_kernel_l<P>, d, step, bin, strip);
+        cudaLaunchKernelEx(&cfg, step_kernel_l<P>, d, step, bin, strip, part);
     }
 }
 
@@ -664,10 +677,11 @@ int step_resident_blocks(int prec, int threads) {
     return resident_p<PK>(threads);
 }
 
-void launch_step(cudaStream_t st, const InstDev& d, int64_t step, int bin, int strip) {
-    if (d.prec == 0) launch_step_p<P64>(st, d, step, bin, strip);
-    else if (d.prec == 1) launch_step_p<P32>(st, d, step, bin, strip);
-    else launch_step_p<PK>(st, d, step, bin, strip);
+void launch_step(cudaStream_t st, const InstDev& d, int64_t step, int bin, int strip,
+                 const int* part) {
+    if (d.prec == 0) launch_step_p<P64>(st, d, step, bin, strip, part);
+    else if (d.prec == 1) launch_step_p<P32>(st, d, step, bin, strip, part);
+    else launch_step_p<PK>(st, d, step, bin, strip, part);
 }
 
 // Opt the step kernels in to the dynamic shared memory of their largest blocks (on the
