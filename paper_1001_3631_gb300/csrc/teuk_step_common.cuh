@@ -38,6 +38,43 @@ template <typename T>
 __device__ __forceinline__ Cx<T> rmac(Cx<T> acc, T s, Cx<T> z) {
     return {tfma(s, z.re, acc.re), tfma(s, z.im, acc.im)};
 }
+// -a
+template <typename T>
+__device__ __forceinline__ Cx<T> neg(Cx<T> a) { return {-a.re, -a.im}; }
+
+// FP32 complex values in paired instructions (sm_100 and later: FADD2 / FMUL2 / FFMA2
+// act on both components of a register pair).  Each component rounds exactly as the
+// scalar round-to-nearest operation, so these overloads change no result, only the
+// instruction count.
+__device__ __forceinline__ float2 pk(Cx<float> a) { return make_float2(a.re, a.im); }
+__device__ __forceinline__ Cx<float> up(float2 v) { return {v.x, v.y}; }
+__device__ __forceinline__ float2 bc(float s) { return make_float2(s, s); }
+__device__ __forceinline__ Cx<float> operator+(Cx<float> a, Cx<float> b) {
+    return up(__fadd2_rn(pk(a), pk(b)));
+}
+// a - b as b * (-1) + a: the product is exact, so this rounds as the subtraction
+__device__ __forceinline__ Cx<float> operator-(Cx<float> a, Cx<float> b) {
+    return up(__ffma2_rn(bc(-1.0f), pk(b), pk(a)));
+}
+__device__ __forceinline__ Cx<float> neg(Cx<float> a) { return up(__fmul2_rn(bc(-1.0f), pk(a))); }
+__device__ __forceinline__ Cx<float> operator*(float s, Cx<float> a) {
+    return up(__fmul2_rn(bc(s), pk(a)));
+}
+template <>
+__device__ __forceinline__ Cx<float> Cx<float>::half_sum(Cx<float> a, Cx<float> b) {
+    return up(__fmul2_rn(bc(0.5f), __fadd2_rn(pk(a), pk(b))));
+}
+// (a + b)/2 + c (the halving is exact, so one fused operation rounds the same)
+template <typename T>
+__device__ __forceinline__ Cx<T> half_sum_add(Cx<T> a, Cx<T> b, Cx<T> c) {
+    return Cx<T>::half_sum(a, b) + c;
+}
+__device__ __forceinline__ Cx<float> half_sum_add(Cx<float> a, Cx<float> b, Cx<float> c) {
+    return up(__ffma2_rn(bc(0.5f), __fadd2_rn(pk(a), pk(b)), pk(c)));
+}
+__device__ __forceinline__ Cx<float> rmac(Cx<float> acc, float s, Cx<float> z) {
+    return up(__ffma2_rn(bc(s), pk(z), pk(acc)));
+}
 
 // ---------------------------------------------------------------- precisions
 // planes: 16-byte planes per state buffer (the layout in teuk_internal.cuh);
@@ -60,11 +97,12 @@ struct PK {
     static constexpr int planes = 2, blocks256 = 2;
 };
 
-// Compensated add (Kahan 1965): the represented value is hi - c.
-__device__ __forceinline__ void kahan_add(float& hi, float& c, float delta) {
-    float y = __fsub_rn(delta, c);
-    float t = __fadd_rn(hi, y);
-    c = __fsub_rn(__fsub_rn(t, hi), y);
+// Compensated add (Kahan 1965) of both components of a complex value: the represented
+// value is hi - c.
+__device__ __forceinline__ void kahan_add(Cx<float>& hi, Cx<float>& c, Cx<float> delta) {
+    const Cx<float> y = delta - c;
+    const Cx<float> t = hi + y;
+    c = (t - hi) - y;
     hi = t;
 }
 
@@ -87,13 +125,13 @@ struct NodeV {
     // gs Phi(this) - Phi(o) and Phi(this) - gs Phi(o) for gs = +-1 (an exact scaling, so
     // these round exactly as dphi of the scaled node)
     __device__ __forceinline__ Cx<T> dphi_sl(T gs, const NodeV& o) const {
-        const Cx<T> a = {tfma(gs, F.re, -o.F.re), tfma(gs, F.im, -o.F.im)};
-        if constexpr (P::kahan) return a - Cx<T>{tfma(gs, Fc.re, -o.Fc.re), tfma(gs, Fc.im, -o.Fc.im)};
+        const Cx<T> a = rmac(neg(o.F), gs, F);
+        if constexpr (P::kahan) return a - rmac(neg(o.Fc), gs, Fc);
         else return a;
     }
     __device__ __forceinline__ Cx<T> dphi_sr(T gs, const NodeV& o) const {
-        const Cx<T> a = {tfma(-gs, o.F.re, F.re), tfma(-gs, o.F.im, F.im)};
-        if constexpr (P::kahan) return a - Cx<T>{tfma(-gs, o.Fc.re, Fc.re), tfma(-gs, o.Fc.im, Fc.im)};
+        const Cx<T> a = rmac(F, -gs, o.F);
+        if constexpr (P::kahan) return a - rmac(Fc, -gs, o.Fc);
         else return a;
     }
     __device__ __forceinline__ Cx<T> dpi(const NodeV& o) const {
@@ -107,8 +145,8 @@ struct NodeV {
     }
     __device__ __forceinline__ void update(Cx<T> dF, Cx<T> dP) {
         if constexpr (P::kahan) {
-            kahan_add(F.re, Fc.re, dF.re); kahan_add(F.im, Fc.im, dF.im);
-            kahan_add(Pp.re, Pc.re, dP.re); kahan_add(Pp.im, Pc.im, dP.im);
+            kahan_add(F, Fc, dF);
+            kahan_add(Pp, Pc, dP);
         } else {
             F = F + dF; Pp = Pp + dP;
         }
@@ -234,10 +272,10 @@ __device__ __forceinline__ CRow<T> combine_lr(const HalfRec<T>& R, const HalfRec
     CRow<T> c;
     c.Hs = Cx<T>::half_sum(R.hF, L.hF);
     c.DpS = Cx<T>::half_sum(R.Dp, L.Dp);
-    c.FC = Cx<T>::half_sum(R.Fb, L.Fb) + c.Hs;
-    c.PC = Cx<T>::half_sum(R.Pb, L.Pb) + Cx<T>::half_sum(R.hP, L.hP);
-    c.dFc = Cx<T>::half_sum(R.dF, L.dF) + (R.hF - L.hF);
-    c.dPc = Cx<T>::half_sum(R.dP, L.dP) + (R.hP - L.hP);
+    c.FC = half_sum_add(R.Fb, L.Fb, c.Hs);
+    c.PC = half_sum_add(R.Pb, L.Pb, Cx<T>::half_sum(R.hP, L.hP));
+    c.dFc = half_sum_add(R.dF, L.dF, R.hF - L.hF);
+    c.dPc = half_sum_add(R.dP, L.dP, R.hP - L.hP);
     return c;
 }
 
