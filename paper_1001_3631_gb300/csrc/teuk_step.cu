@@ -206,8 +206,9 @@ constexpr int kRingS = 6, kRingL = 4;
 // Phi(j-1), from the ring slot; predictor at the half node c-1/2; exchange of its
 // results with the rows above and below (the one barrier of the column); corrector at
 // column c-1.  The first two columns are peeled so the steady-state loop has no
-// per-column mode switches, and it is unrolled by three so the rotation of the
-// previous / current column is register renaming.  Columns c0-1 .. c1 are read.
+// per-column mode switches, and it is unrolled by two so the rotation of the
+// previous / current column is register renaming (by two: measured faster than one,
+// three or six on GB300).  Columns c0-1 .. c1 are read.
 // kPerStep: the block belongs to a per-step launch (programmatic dependent launch: the
 // part before griddepcontrol.wait overlaps the previous step, and the block returns at
 // once when a bounded wait of an earlier launch gave up).  Returns false in that case.
@@ -391,7 +392,7 @@ __device__ __forceinline__ bool strip_step(const InstDev& d, int64_t step, int b
             nxt_i = src_i(c0);
         }
         int sf = 0, sp = 1, sc = 2;
-#pragma unroll 3
+#pragma unroll 2
         for (int c = c0 + 1; c <= c1; ++c) {
             const C s_h = nxt_h, s_i = nxt_i;
             if constexpr (kSrc) {
