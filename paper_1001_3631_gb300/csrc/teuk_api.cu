@@ -29,7 +29,7 @@ struct Instance {
     void* coef_i = nullptr;
     double* x_int = nullptr;
     double* x_half = nullptr;
-    RTab* rtab = nullptr;       // [2][nr]: half nodes, then integer nodes (FP32 paths)
+    RTab2* rtab = nullptr;      // [nr] (half node, node) per column (FP32 paths)
     ThTab* thtab = nullptr;     // [nth]
     // source
     bool src_on = false;
@@ -182,8 +182,7 @@ InstDev dev_of(const teuk_ctx* c, const Instance& I) {
         for (int k = 0; k < 2; ++k) d.buf[b][k] = I.state[b][k];
     d.coef_h = I.coef_h;
     d.coef_i = I.coef_i;
-    d.rtab_h = I.rtab;
-    d.rtab_i = I.rtab ? I.rtab + I.p.n_rstar : nullptr;
+    d.rtab = I.rtab;
     d.thtab = I.thtab;
     d.src = I.sd;
     d.src.on = I.src_on ? 1 : 0;
@@ -368,10 +367,10 @@ extern "C" teuk_status teuk_create(const teuk_params* p, int n_instances, void* 
                             I.dt, q.n_rstar, q.n_theta, I.pitch, I.x_int, I.x_half, I.coef_h,
                             I.coef_i);
         if (q.prec != TEUK_FP64) {
-            TK_CCUDA(cudaMallocAsync((void**)&I.rtab, sizeof(RTab) * 2 * q.n_rstar, c->stream));
+            TK_CCUDA(cudaMallocAsync((void**)&I.rtab, sizeof(RTab2) * q.n_rstar, c->stream));
             TK_CCUDA(cudaMallocAsync((void**)&I.thtab, sizeof(ThTab) * q.n_theta, c->stream));
             launch_tables_1d(c->stream, q.M, q.a, q.s, q.m, I.drs, I.dth, I.dt, q.n_rstar,
-                             q.n_theta, I.x_int, I.x_half, I.rtab, I.rtab + q.n_rstar, I.thtab);
+                             q.n_theta, I.x_int, I.x_half, I.rtab, I.thtab);
             c->launches++;
         }
         c->launches += 2;

@@ -53,16 +53,18 @@ struct SourceDev {
     int64_t n_amps;
 };
 
-// FP32 paths form their coefficients in registers from these 1D tables (rounded from
-// FP64 at setup), instead of reading 2D tables every step.  Per radial node and
-// sub-step fraction s (1/2 at half nodes, 1 at integer nodes), sdt = s dt:
-//   Sigma^2 = R2 - aD sin^2,  iS = 1/Sigma^2,  rs = Sigma^{-1}
-//   g  = Rd * rs                                     (Rd = sdt R / dr*)
-//   c_t = (ctr iS, (cti + ctc cos) iS),  E1 = -sdt c_t
-//   E2 = c_t g + ((pr - bb sin^2 iS) iS, pi iS)      (pr, pi, bb scaled by sdt/dr*)
-//   ep, em = Ds iS (1/dth^2 +- cot/(2 dth))          (Ds = sdt Delta)
-//   E3 = ((qr - Ds V) iS, qi iS)                      (qr, qi scaled by sdt)
-struct RTab { float R2, aD, Rd, ctr, cti, ctc, pr, pi, bb, Ds, qr, qi, sdt, pad0, pad1, pad2; };
+// FP32 paths form their coefficients in registers from 1D tables (rounded from FP64 at
+// setup), instead of reading 2D tables every step.  The entry of radial column i holds
+// the values of the half node i+1/2 in .x (sub-step fraction s = 1/2) and of the node i
+// in .y (s = 1), so that both coefficient sets of a column are formed together in
+// paired FP32 instructions.  With sdt = s dt:
+//   Sigma^2 = R2 + naD sin^2 (naD = -a^2 Delta),  iS = 1/Sigma^2,  rs = Sigma^{-1}
+//   g  = Rd * rs                                      (Rd = sdt R / dr*)
+//   c_t = (ctr iS, (cti + ctc cos) iS),  E1 = nsdt c_t   (nsdt = -sdt)
+//   E2 = c_t g + ((pr + nbb sin^2 iS) iS, pi iS)       (pr, pi, nbb = -bb scaled by sdt/dr*)
+//   ep, em = Ds iS (1/dth^2 +- cot/(2 dth))           (Ds = sdt Delta)
+//   E3 = ((qr + nDs V) iS, qi iS)                      (qr, qi scaled by sdt; nDs = -Ds)
+struct RTab2 { float2 R2, naD, Rd, ctr, cti, ctc, pr, pi, nbb, Ds, nDs, qr, qi, nsdt, pad0, pad1; };
 // Per theta row: sin^2, cos, V = (m + s cos)^2/sin^2 - s, th_p, th_m = 1/dth^2 +- cot/(2 dth)
 struct ThTab { float sin2, cs, V, thp, thm, pad0, pad1, pad2; };
 
@@ -74,8 +76,7 @@ struct InstDev {
     void* buf[2][2];          // [ping-pong buffer][plane]
     const void* coef_h;       // [9][nr][pitch] (double or float)
     const void* coef_i;
-    const RTab* rtab_h;       // [nr] FP32 paths: radial tables at half nodes i+1/2
-    const RTab* rtab_i;       // [nr] at integer nodes
+    const RTab2* rtab;        // [nr] FP32 paths: radial tables (half node, node) per column
     const ThTab* thtab;       // [nth]
     SourceDev src;
     int i_e;                  // extraction between i_e and i_e + 1
@@ -128,7 +129,7 @@ void launch_coefficients(cudaStream_t st, int prec, double M, double a, int s, i
                          void* coef_i);
 void launch_tables_1d(cudaStream_t st, double M, double a, int s, int m, double drs, double dth,
                       double dt, int nr, int nth, const double* x_int, const double* x_half,
-                      RTab* rtab_h, RTab* rtab_i, ThTab* thtab);
+                      RTab2* rtab, ThTab* thtab);
 void launch_profile(cudaStream_t st, double M, double a, double rstar_min, double drs, double dth,
                     double rs0, double sig_r, double sig_t, double drs0_dr0, const double* x_int,
                     const double* x_half, const SourceDev& src, int prec);

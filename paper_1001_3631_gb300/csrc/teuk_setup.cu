@@ -181,39 +181,62 @@ __global__ void profile_kernel(double M, double a, double rstar_min, double drs,
     }
 }
 
-// 1D tables of the FP32 paths (see RTab / ThTab), computed in FP64 and rounded once.
-__device__ RTab radial_table(double M, double a, int s_, int m_, double x, double drs, double sdt) {
+// 1D tables of the FP32 paths (see RTab2 / ThTab), computed in FP64 and rounded once.
+struct RadialVals { double R2, naD, Rd, ctr, cti, ctc, pr, pi, nbb, Ds, nDs, qr, qi, nsdt; };
+
+__device__ RadialVals radial_vals(double M, double a, int s_, int m_, double x, double drs, double sdt) {
     double d = sqrt(M * M - a * a);
     double rp = M + d, rm = M - d;
     double s = (double)s_, m = (double)m_;
     double r = rp + x;
     double Delta = x * (x + rp - rm);
     double R = r * r + a * a;
-    RTab t;
-    t.R2 = (float)(R * R);
-    t.aD = (float)(a * a * Delta);
-    t.Rd = (float)(sdt * R / drs);
-    t.ctr = (float)(2.0 * s * (r * Delta - M * (r * r - a * a)));
-    t.cti = (float)(4.0 * M * a * m * r);
-    t.ctc = (float)(2.0 * s * a * Delta);
-    t.pr = (float)(sdt / drs * (Delta * (6.0 * R / r + 2.0 * r) + 2.0 * R * s * (r - M)));
-    t.pi = (float)(sdt / drs * (2.0 * R * m * a));
-    t.bb = (float)(sdt / drs * (a * a * Delta * (2.0 * R * (r - M) - 4.0 * r * Delta) * 0.5));
-    t.Ds = (float)(sdt * Delta);
-    t.qr = (float)(sdt * (6.0 * Delta * Delta / (r * r) + 6.0 * Delta * (s + 1.0) * (r - M) / r));
-    t.qi = (float)(sdt * (6.0 * Delta * m * a / r + 4.0 * s * m * a * (r - M)));
-    t.sdt = (float)sdt;
-    t.pad0 = t.pad1 = t.pad2 = 0.f;
+    RadialVals t;
+    t.R2 = R * R;
+    t.naD = -(a * a * Delta);
+    t.Rd = sdt * R / drs;
+    t.ctr = 2.0 * s * (r * Delta - M * (r * r - a * a));
+    t.cti = 4.0 * M * a * m * r;
+    t.ctc = 2.0 * s * a * Delta;
+    t.pr = sdt / drs * (Delta * (6.0 * R / r + 2.0 * r) + 2.0 * R * s * (r - M));
+    t.pi = sdt / drs * (2.0 * R * m * a);
+    t.nbb = -(sdt / drs * (a * a * Delta * (2.0 * R * (r - M) - 4.0 * r * Delta) * 0.5));
+    t.Ds = sdt * Delta;
+    t.nDs = -t.Ds;
+    t.qr = sdt * (6.0 * Delta * Delta / (r * r) + 6.0 * Delta * (s + 1.0) * (r - M) / r);
+    t.qi = sdt * (6.0 * Delta * m * a / r + 4.0 * s * m * a * (r - M));
+    t.nsdt = -sdt;
     return t;
 }
 
+__device__ float2 pair_f(double h, double i) { return make_float2((float)h, (float)i); }
+
 __global__ void tables_1d_kernel(double M, double a, int s, int m, double drs, double dth,
                                  double dt, int nr, int nth, const double* x_int,
-                                 const double* x_half, RTab* rtab_h, RTab* rtab_i, ThTab* thtab) {
+                                 const double* x_half, RTab2* rtab, ThTab* thtab) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < nr) rtab_i[k] = radial_table(M, a, s, m, x_int[k], drs, dt);
-    if (k < nr - 1) rtab_h[k] = radial_table(M, a, s, m, x_half[k], drs, 0.5 * dt);
-    if (k == nr - 1) rtab_h[k] = RTab{};
+    if (k < nr) {
+        // the half node nr-1/2 lies outside the grid: zeros
+        const RadialVals h = k < nr - 1 ? radial_vals(M, a, s, m, x_half[k], drs, 0.5 * dt) : RadialVals{};
+        const RadialVals i = radial_vals(M, a, s, m, x_int[k], drs, dt);
+        RTab2 t;
+        t.R2 = pair_f(h.R2, i.R2);
+        t.naD = pair_f(h.naD, i.naD);
+        t.Rd = pair_f(h.Rd, i.Rd);
+        t.ctr = pair_f(h.ctr, i.ctr);
+        t.cti = pair_f(h.cti, i.cti);
+        t.ctc = pair_f(h.ctc, i.ctc);
+        t.pr = pair_f(h.pr, i.pr);
+        t.pi = pair_f(h.pi, i.pi);
+        t.nbb = pair_f(h.nbb, i.nbb);
+        t.Ds = pair_f(h.Ds, i.Ds);
+        t.nDs = pair_f(h.nDs, i.nDs);
+        t.qr = pair_f(h.qr, i.qr);
+        t.qi = pair_f(h.qi, i.qi);
+        t.nsdt = pair_f(h.nsdt, i.nsdt);
+        t.pad0 = t.pad1 = make_float2(0.f, 0.f);
+        rtab[k] = t;
+    }
     if (k < nth) {
         double th = (k + 0.5) * dth, sn, cs;
         sincos(th, &sn, &cs);
@@ -231,10 +254,10 @@ __global__ void tables_1d_kernel(double M, double a, int s, int m, double drs, d
 
 void launch_tables_1d(cudaStream_t st, double M, double a, int s, int m, double drs, double dth,
                       double dt, int nr, int nth, const double* x_int, const double* x_half,
-                      RTab* rtab_h, RTab* rtab_i, ThTab* thtab) {
+                      RTab2* rtab, ThTab* thtab) {
     int n = nr > nth ? nr : nth;
     tables_1d_kernel<<<(n + 127) / 128, 128, 0, st>>>(M, a, s, m, drs, dth, dt, nr, nth, x_int,
-                                                      x_half, rtab_h, rtab_i, thtab);
+                                                      x_half, rtab, thtab);
 }
 
 void launch_invert_tortoise(cudaStream_t st, double M, double a, double rstar_min, double drs,

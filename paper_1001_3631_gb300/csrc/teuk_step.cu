@@ -95,23 +95,23 @@ __device__ __forceinline__ unsigned long long global_ns() {
 
 constexpr unsigned long long kRingWaitNs = 1000000000ull;  // a slot wait gives up after 1 s
 
-// Columns of the input level (every plane, plus on the FP32 paths the column's two
-// radial tables) are copied into R shared-memory slots by one thread, R - 2 columns
+// Columns of the input level (every plane, plus on the FP32 paths the column's radial
+// table) are copied into R shared-memory slots by one thread, R - 2 columns
 // ahead of use; each slot has an mbarrier that its copy completes.  A column is read
 // (own node and theta neighbours) when it arrives and its radial tables one column
 // later, so its slot is refilled after the barrier two columns on, when every thread
 // has finished with it.  Copies start on 16-byte boundaries with sizes in multiples of
 // 16 bytes: a column is n_theta 16-byte nodes at a 512-byte aligned offset, a radial
-// table 64 bytes.
+// table 128 bytes.
 template <class P, int R>
 struct ColumnRing {
     static constexpr int kSlots = R;
     static constexpr bool kTabs = sizeof(typename P::T) == 4;
     __host__ __device__ static unsigned slot_bytes(int threads) {
-        return (unsigned)P::planes * (unsigned)threads * 16u + (kTabs ? 2u * (unsigned)sizeof(RTab) : 0u);
+        return (unsigned)P::planes * (unsigned)threads * 16u + (kTabs ? (unsigned)sizeof(RTab2) : 0u);
     }
 
-    unsigned char* base;  // R slots: planes [P::planes][stride] of 16-byte nodes, then tables
+    unsigned char* base;  // R slots: planes [P::planes][stride] of 16-byte nodes, then RTab2
     uint64_t* mbar;       // [R]
     unsigned stride;      // nodes per plane in a slot (the block size)
     unsigned sbytes;
@@ -141,15 +141,13 @@ struct ColumnRing {
         }
         unsigned char* dst = slot(s);
         const unsigned nb = (unsigned)d.nth * 16u;
-        mbar_expect_tx(mbar + s, P::planes * nb + (kTabs ? 2u * (unsigned)sizeof(RTab) : 0u));
+        mbar_expect_tx(mbar + s, P::planes * nb + (kTabs ? (unsigned)sizeof(RTab2) : 0u));
         const size_t off = (size_t)col * (size_t)d.pitch * 16u;
 #pragma unroll
         for (int q = 0; q < P::planes; ++q)
             bulk_copy_g2s(dst + q * stride * 16u, (const unsigned char*)d.buf[bin][q] + off, nb, mbar + s);
         if constexpr (kTabs) {
-            unsigned char* t = dst + P::planes * stride * 16u;
-            bulk_copy_g2s(t, d.rtab_h + col, sizeof(RTab), mbar + s);
-            bulk_copy_g2s(t + sizeof(RTab), d.rtab_i + col, sizeof(RTab), mbar + s);
+            bulk_copy_g2s(dst + P::planes * stride * 16u, d.rtab + col, sizeof(RTab2), mbar + s);
         }
     }
     // Wait for the next copy into slot s.  Once a wait has given up, the thread waits
@@ -162,13 +160,21 @@ struct ColumnRing {
         while (!mbar_try_wait(mbar + s, par))
             if (global_ns() - t0 > kRingWaitNs) { late = true; return; }
     }
-    // Radial table of the column in slot s: which = 0 half node i+1/2, 1 node i.
-    __device__ __forceinline__ RTab tab(int s, int which) const {
-        RTab t{};
+    // Radial table of the column in slot s (FP32 paths).
+    __device__ __forceinline__ RTab2 tab2(int s) const {
+        RTab2 t{};
         if constexpr (kTabs) {
-            const float4* q = (const float4*)(slot(s) + P::planes * stride * 16u) + 4 * which;
-            const float4 a = q[0], b = q[1], c = q[2], e = q[3];
-            t = RTab{a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w, e.x, 0.f, 0.f, 0.f};
+            const float4* q = (const float4*)(slot(s) + P::planes * stride * 16u);
+            float4 v[7];
+#pragma unroll
+            for (int k = 0; k < 7; ++k) v[k] = q[k];
+            t.R2 = {v[0].x, v[0].y};   t.naD = {v[0].z, v[0].w};
+            t.Rd = {v[1].x, v[1].y};   t.ctr = {v[1].z, v[1].w};
+            t.cti = {v[2].x, v[2].y};  t.ctc = {v[2].z, v[2].w};
+            t.pr = {v[3].x, v[3].y};   t.pi = {v[3].z, v[3].w};
+            t.nbb = {v[4].x, v[4].y};  t.Ds = {v[4].z, v[4].w};
+            t.nDs = {v[5].x, v[5].y};  t.qr = {v[5].z, v[5].w};
+            t.qi = {v[6].x, v[6].y};   t.nsdt = {v[6].z, v[6].w};
         }
         return t;
     }
@@ -217,6 +223,7 @@ __device__ __forceinline__ bool strip_step(const InstDev& d, int64_t step, int b
                                            int c1, ColumnRing<P, R>& ring, typename P::T* xbuf) {
     using T = typename P::T;
     using C = Cx<T>;
+    constexpr bool kTabsPath = sizeof(T) == 4;   // FP32 paths: coefficients from 1D tables
     const int j = threadIdx.x;
     const int nth = d.nth;
     const bool row_ok = j < nth;
@@ -291,18 +298,32 @@ __device__ __forceinline__ bool strip_step(const InstDev& d, int64_t step, int b
     };
     // predictor at the half node h between columns h (ul) and h+1 (ur)
     auto predict = [&](const NodeV<P>& ul, const NodeV<P>& ur, C dll, C dlr, C dlml, C dlmr,
-                       const RTab& tab, int h, C src) {
+                       const T* cf, C src) {
         const Half<T> hp = half_prep<P>(ul, ur);
         const C Dp = C::half_sum(dll, dlr);     // Fb(j+1) - Fb(j)
         const C Dm = C::half_sum(dlml, dlmr);   // Fb(j) - Fb(j-1)
-        T cf[kNCoef];
-        get_coefs<P>(d, rt, tab, true, h, j, cf);
         return predictor<T>(hp, Dp, Dm, cf, hdt, src);
     };
+    // coefficients of column col: the half node col+1/2 into cfh and, on the FP32 paths
+    // (formed together in paired instructions), the node col into cfi
+    auto coefs = [&](int slot, int col, T* cfh, T* cfi) {
+        if constexpr (kTabsPath) {
+            float2 cf2[kNCoef];
+            form_coefs2(ring.tab2(slot), rt.t, cf2);
+#pragma unroll
+            for (int k = 0; k < kNCoef; ++k) {
+                cfh[k] = cf2[k].x;
+                cfi[k] = cf2[k].y;
+            }
+        } else {
+            coefs64(d, true, col, j, (double*)cfh);
+        }
+    };
     // corrector at column cc from the half nodes L = cc-1/2 and R = cc+1/2; xb is the
-    // exchange buffer of this column's parity, srcc the source term at (cc, j)
+    // exchange buffer of this column's parity, srcc the source term at (cc, j); cfi the
+    // node's coefficients on the FP32 paths (the FP64 path reads them here)
     auto correct = [&](const HalfRec<T>& Rh, const HalfRec<T>& Lh, const NodeV<P>& uc,
-                       const RTab& tab, int cc, T* xb, size_t o, C srcc) {
+                       const T* cfi, int cc, T* xb, size_t o, C srcc) {
         const CRow<T> row = combine_lr<T>(Rh, Lh);
         // publish {Hs, DpS} of this row at entry j + 1; the pole rows also write the
         // ghost entries: row nth (entry nth + 1) Hs = g Hs(nth-1), row -1 (entry 0)
@@ -337,7 +358,12 @@ __device__ __forceinline__ bool strip_step(const InstDev& d, int64_t step, int b
         const C Dplus = row.DpS + (Hs_p - row.Hs);
         const C Dminus = DpS_m + (row.Hs - Hs_m);
         T cf[kNCoef];
-        get_coefs<P>(d, rt, tab, false, cc, j, cf);
+        if constexpr (kTabsPath) {
+#pragma unroll
+            for (int k = 0; k < kNCoef; ++k) cf[k] = cfi[k];
+        } else {
+            coefs64(d, false, cc, j, (double*)cf);
+        }
         C dPhi = rmac(rmac(C::zero(), -cf[C_G], row.dFc), fdt, row.PC);
         C dPi = rmac(srcc, cf[C_G], row.dPc);
         dPi = cmac(dPi, cf[C_E1R], cf[C_E1I], row.PC);
@@ -372,8 +398,9 @@ __device__ __forceinline__ bool strip_step(const InstDev& d, int64_t step, int b
     // source terms at the half node h and the node i (source blocks only)
     auto src_h = [&](int h) { return source_half<T>(sw, sp_fac, h, j); };
     auto src_i = [&](int i) { return source_int<T>(sw, sc_fac, i, j); };
-    HalfRec<T> L = predict(u_prev, u_cur, dl_prev, dl, dlm_prev, dlm, ring.tab(0, 0), c0 - 1,
-                           src_blk ? src_h(c0 - 1) : C::zero());
+    T cfh[kNCoef], cfi[kNCoef];
+    coefs(0, c0 - 1, cfh, cfi);
+    HalfRec<T> L = predict(u_prev, u_cur, dl_prev, dl, dlm_prev, dlm, cfh, src_blk ? src_h(c0 - 1) : C::zero());
     if (ex_blk && d.i_e == c0 - 1) extract(u_prev, u_cur);
     u_prev = u_cur;
     dl_prev = dl;
@@ -404,9 +431,9 @@ __device__ __forceinline__ bool strip_step(const InstDev& d, int64_t step, int b
             ring.wait(sc);
             u_cur = node(sc);
             theta_diffs(sc, u_cur, dl, dlm);
-            const RTab th = ring.tab(sp, 0);
-            const HalfRec<T> Rh = predict(u_prev, u_cur, dl_prev, dl, dlm_prev, dlm, th, c - 1, s_h);
-            correct(Rh, L, u_prev, ring.tab(sp, 1), c - 1, xbuf + (c & 1) * xstride, o, s_i);
+            coefs(sp, c - 1, cfh, cfi);
+            const HalfRec<T> Rh = predict(u_prev, u_cur, dl_prev, dl, dlm_prev, dlm, cfh, s_h);
+            correct(Rh, L, u_prev, cfi, c - 1, xbuf + (c & 1) * xstride, o, s_i);
             if (threadIdx.x == 0 && c - 2 + R <= c1) ring.fill(d, bin, c - 2 + R, sf);
             if (ex_blk && d.i_e == c - 1) extract(u_prev, u_cur);
             L = Rh;

@@ -286,53 +286,50 @@ __device__ __forceinline__ void load_coefs(const T* tab, size_t pl, size_t o, T*
     for (int k = 0; k < kNCoef; ++k) cf[k] = __ldg(tab + k * pl + o);
 }
 
-// FP32 coefficients of one node from its radial table and its theta row (see RTab).
-__device__ __forceinline__ void form_coefs(const RTab& t, const ThTab& h, float* cf) {
-    float sig2 = fmaf(-t.aD, h.sin2, t.R2);
-    float rs = rsqrtf(sig2);
-    rs = rs * fmaf(-0.5f * sig2 * rs, rs, 1.5f);  // one Newton step on 1/sqrt
-    float iS = rs * rs;                           // 1/Sigma^2 within a few ulp
-    float g = t.Rd * rs;
-    float ctre = t.ctr * iS;
-    float ctim = fmaf(t.ctc, h.cs, t.cti) * iS;
-    cf[C_G] = g;
-    cf[C_E1R] = -t.sdt * ctre;
-    cf[C_E1I] = -t.sdt * ctim;
-    float bbt = t.bb * h.sin2 * iS;
-    cf[C_E2R] = fmaf(ctre, g, (t.pr - bbt) * iS);
-    cf[C_E2I] = fmaf(ctim, g, t.pi * iS);
-    float ws = t.Ds * iS;
-    cf[C_EP] = ws * h.thp;
-    cf[C_EM] = ws * h.thm;
-    cf[C_E3R] = fmaf(-t.Ds, h.V, t.qr) * iS;
-    cf[C_E3I] = t.qi * iS;
-}
-
-// The theta table of one row, held in registers by its thread for a whole work item
-// (FP32 paths; empty for FP64, which reads 2D tables).
+// The theta table of one row as broadcast pairs (x, x), held in registers by its thread
+// for a whole work item (FP32 paths; empty for FP64, which reads 2D tables).
+struct ThPair { float2 sin2, cs, V, thp, thm; };
 template <class P>
 struct RowTab {
-    ThTab t;
+    ThPair t;
     __device__ __forceinline__ void load(const ThTab* tab, int j, bool ok) {
         if constexpr (sizeof(typename P::T) == 4) {
-            t = ok ? tab[j] : ThTab{};
+            const ThTab h = ok ? tab[j] : ThTab{};
+            t = ThPair{bc(h.sin2), bc(h.cs), bc(h.V), bc(h.thp), bc(h.thm)};
         }
     }
 };
 
-// Coefficients of the predictor (half = true, node i+1/2) or the corrector (node i) at
-// row j: read from the 2D FP64 tables, or formed in registers on the FP32 paths from
-// the column's radial table t (one copy in shared memory for the whole block) and the
-// row's theta table.
-template <class P>
-__device__ __forceinline__ void get_coefs(const InstDev& d, const RowTab<P>& row, const RTab& t,
-                                          bool half, int i, int j, typename P::T* cf) {
-    if constexpr (sizeof(typename P::T) == 8) {
-        load_coefs((const double*)(half ? d.coef_h : d.coef_i), plane_elems(d),
-                   node_index(d, i, j), cf);
-    } else {
-        form_coefs(t, row.t, cf);
-    }
+// FP32 coefficients of the half node i+1/2 (.x) and of the node i (.y) of one column,
+// from the column's radial table and the row's theta table (see RTab2), in paired
+// instructions.
+__device__ __forceinline__ void form_coefs2(const RTab2& t, const ThPair& h, float2* cf) {
+    const float2 sig2 = __ffma2_rn(t.naD, h.sin2, t.R2);
+    float2 rs = make_float2(rsqrtf(sig2.x), rsqrtf(sig2.y));
+    // one Newton step on 1/sqrt: rs (1.5 - (sig2 / 2) rs^2)
+    const float2 hr = __fmul2_rn(__fmul2_rn(bc(-0.5f), sig2), rs);
+    rs = __fmul2_rn(rs, __ffma2_rn(hr, rs, bc(1.5f)));
+    const float2 iS = __fmul2_rn(rs, rs);                // 1/Sigma^2 within a few ulp
+    const float2 g = __fmul2_rn(t.Rd, rs);
+    const float2 ctre = __fmul2_rn(t.ctr, iS);
+    const float2 ctim = __fmul2_rn(__ffma2_rn(t.ctc, h.cs, t.cti), iS);
+    cf[C_G] = g;
+    cf[C_E1R] = __fmul2_rn(t.nsdt, ctre);
+    cf[C_E1I] = __fmul2_rn(t.nsdt, ctim);
+    const float2 pb = __ffma2_rn(__fmul2_rn(t.nbb, h.sin2), iS, t.pr);   // pr - bb sin^2 iS
+    cf[C_E2R] = __ffma2_rn(ctre, g, __fmul2_rn(pb, iS));
+    cf[C_E2I] = __ffma2_rn(ctim, g, __fmul2_rn(t.pi, iS));
+    const float2 ws = __fmul2_rn(t.Ds, iS);
+    cf[C_EP] = __fmul2_rn(ws, h.thp);
+    cf[C_EM] = __fmul2_rn(ws, h.thm);
+    cf[C_E3R] = __fmul2_rn(__ffma2_rn(t.nDs, h.V, t.qr), iS);
+    cf[C_E3I] = __fmul2_rn(t.qi, iS);
+}
+
+// FP64 coefficients of the predictor (half = true, node i+1/2) or the corrector (node i)
+// at row j, from the 2D tables.
+__device__ __forceinline__ void coefs64(const InstDev& d, bool half, int i, int j, double* cf) {
+    load_coefs((const double*)(half ? d.coef_h : d.coef_i), plane_elems(d), node_index(d, i, j), cf);
 }
 
 // Eq. (13) at the own half node, as an increment on the averaged state.
