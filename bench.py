@@ -250,17 +250,19 @@ def batched_leg(n_calls=4, steps_per_call=25, warm_calls=2):
         s = TeukSolver([dict(i["params"], prec="fp32_kahan") for i in insts], stream=stream)
         for k, inst in enumerate(insts):
             s.set_source(inst["r0"], instance=k)
-        chunks = s.autotune(trial_steps=5)
+        chunks = s.autotune(trial_steps=5)   # strips timed on the whole batch
         for _ in range(warm_calls):
             s.step(steps_per_call)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         stream.synchronize()
+        l0 = s.kernel_launches()
         e0.record(stream)
         for _ in range(n_calls):
             s.step(steps_per_call)
         e1.record(stream)
         stream.synchronize()
         ms = e0.elapsed_time(e1)
+        launches = (s.kernel_launches() - l0) // n_calls
         s.sync()
         npts = sum(i["params"]["n_rstar"] * i["params"]["n_theta"] for i in insts)
         s.close()
@@ -268,8 +270,8 @@ def batched_leg(n_calls=4, steps_per_call=25, warm_calls=2):
                         "N_theta in {64,128,256} (seed 3003), FP32-Kahan",
             "value": npts * n_calls * steps_per_call / (ms * 1e-3), "unit": "updates/s",
             "points": npts, "steps_timed": n_calls * steps_per_call,
-            "ms_per_call": ms / n_calls, "launches_per_call": 2,
-            "distinct_chunks": sorted(set(chunks))}
+            "ms_per_call": ms / n_calls, "launches_per_call": int(launches),
+            "distinct_strips": sorted(set(chunks))}
 
 
 def single_mode_leg(steps=2000):
@@ -298,6 +300,37 @@ def single_mode_leg(steps=2000):
                 s.close()
             out["%s_%s" % (prec, mode)] = 51200 * steps / (ms * 1e-3)
     out["unit"] = "updates/s"
+    return out
+
+
+def adjoint_leg():
+    """The adjoint workload (4096 x 128, 10000 steps, A_n ~ N(1, 0.1) seed 5005, checkpoint
+    every 100 steps, loss at a near-zone probe r* = 12.5): the forward run alone and the
+    full gradient call (checkpointed forward, recomputation, backward sweep with the FP64
+    co-state, FP64 gradient sums), each timed on the host around a synchronising call."""
+    import numpy as np
+
+    from paper_1001_3631_gb300 import TeukSolver, inputs
+    cfg = inputs.ADJOINT_4096x128
+    p = dict(cfg["params"], rstar_ext=12.5)
+    n, npts = cfg["steps"], cfg["params"]["n_rstar"] * cfg["params"]["n_theta"]
+    amps = inputs.amplitudes(n, seed=cfg["amp_seed"])
+    out = {"workload": "adjoint 4096x128, %d steps, checkpoint every %d" % (n, cfg["ckpt_every"])}
+    for prec in ("fp64", "fp32_kahan"):
+        with TeukSolver(dict(p, prec=prec)) as s:
+            s.set_source(cfg["r0"], amps)
+            s.set_state(np.zeros(s.shape()), 0)
+            t0 = time.perf_counter()
+            s.step(n)
+            s.sync()
+            tf = time.perf_counter() - t0
+            s.set_state(np.zeros(s.shape()), 0)
+            t0 = time.perf_counter()
+            s.adjoint(n, step0=0, ckpt_every=cfg["ckpt_every"])
+            ta = time.perf_counter() - t0
+        out[prec] = {"forward_s": tf, "gradient_s": ta, "gradient_over_forward": ta / tf,
+                     "gradient_updates_per_s": npts * n / ta}
+    out["unit_note"] = "gradient_updates_per_s = forward point-updates covered per second of the gradient call"
     return out
 
 
@@ -497,6 +530,7 @@ def main():
         line["single_mode_800x64"] = single_mode_leg()
         line["accuracy"] = accuracy(cfg, n_steps=args.accuracy_steps)
         line["e2e"] = e2e_path("fp32_kahan", cfg, S, max(2, K // 2), 1)
+        line["adjoint"] = adjoint_leg()
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(cfg)
     print(json.dumps(line))

@@ -182,11 +182,15 @@ teuk_status teuk_set_tiling(teuk_ctx* ctx, int strip, int steps_per_launch);
 /* Strip length (r* columns per block) of one instance (0 = back to the context default). */
 teuk_status teuk_set_instance_tiling(teuk_ctx* ctx, int instance, int strip);
 
-/* Autotuner: for every distinct (n_theta, precision, n_rstar rounded up to a power of
- * two) class of the context, time trial_steps steps of each candidate strip length
- * (8 .. 512 columns) on a scratch copy of one instance of the class and keep the
- * fastest for all its instances.  chosen (may be NULL) receives the strip of each
- * instance.  The state and the waveform records are not changed.  Synchronizes. */
+/* Autotuner of the strip length (r* columns per block), written to every instance
+ * (chosen, may be NULL, receives them).  A single instance stepped one launch per step:
+ * trial_steps steps of each candidate (8 .. 512 columns) on a scratch copy of the
+ * instance.  Contexts that run the persistent kernels (several instances, or one with
+ * steps_per_launch = 0): trial_steps steps of the whole context per candidate (16 .. 512),
+ * one length for all instances first, then block-size class by class, on the live state,
+ * which is restored afterwards from a snapshot (device memory for one copy of every
+ * instance's state and waveform ring while the call runs).  The state, the time levels
+ * and the waveform records are unchanged on return.  Synchronizes. */
 teuk_status teuk_autotune(teuk_ctx* ctx, int trial_steps, int* chosen);
 
 /* Testing aid for the bounded device waits of the batched kernel: work item

@@ -780,11 +780,145 @@ extern "C" teuk_status teuk_set_instance_tiling(teuk_ctx* c, int instance, int s
     return refresh_partition(c, c->inst[instance]);
 }
 
-// Time each candidate strip length on a scratch copy of one instance of every
-// distinct (n_theta, precision, n_rstar bucket) class and keep the fastest.
+// Contexts that step through the persistent kernels (several instances, or one in
+// persistent mode) run one launch per block-size class over all its instances, so a
+// strip length is judged in that setting: trial_steps steps of the whole context are
+// timed for each candidate, first with one length for every instance, then class by
+// class with the others held at their best, on the live state; afterwards every
+// instance's state, time level and waveform records are restored from a snapshot.
+// (Timing one instance alone favours short strips, which fill the GPU with one
+// instance but, in the batch, pay the ring's start-up every few columns.)
+static teuk_status autotune_batched(teuk_ctx* c, int trial_steps, int* chosen) {
+    const int ni = (int)c->inst.size();
+    struct Snap {
+        void* st[2] = {nullptr, nullptr};
+        double2* wave = nullptr;
+        int64_t step = 0, lo = 0, hi = 0;
+        int cur = 0;
+    };
+    std::vector<Snap> snap(ni);
+    auto release = [&]() {
+        for (Snap& q : snap) {
+            for (void* p : q.st)
+                if (p) cudaFreeAsync(p, c->stream);
+            if (q.wave) cudaFreeAsync(q.wave, c->stream);
+        }
+    };
+    teuk_status err = TEUK_OK;
+    for (int k = 0; k < ni && !err; ++k) {
+        Instance& I = c->inst[k];
+        const int nplanes = I.p.prec == TEUK_FP32 ? 1 : 2;
+        Snap& q = snap[k];
+        q.step = I.step;
+        q.cur = I.cur;
+        q.lo = I.wave_lo;
+        q.hi = I.wave_hi;
+        for (int pl = 0; pl < nplanes && !err; ++pl) {
+            if (cudaMallocAsync(&q.st[pl], I.plane_bytes, c->stream) != cudaSuccess) err = TEUK_ENOMEM;
+            else cudaMemcpyAsync(q.st[pl], I.state[I.cur][pl], I.plane_bytes, cudaMemcpyDeviceToDevice, c->stream);
+        }
+        const size_t wb = sizeof(double2) * (size_t)I.wave_cap * (size_t)I.p.n_theta;
+        if (!err) {
+            if (cudaMallocAsync((void**)&q.wave, wb, c->stream) != cudaSuccess) err = TEUK_ENOMEM;
+            else cudaMemcpyAsync(q.wave, I.wave, wb, cudaMemcpyDeviceToDevice, c->stream);
+        }
+    }
+    if (err) {
+        release();
+        cudaGetLastError();
+        TK_FAIL(c, err, "autotune: snapshot allocation failed");
+    }
+    cudaEvent_t e0, e1;
+    TK_CUDA(c, cudaEventCreate(&e0));
+    TK_CUDA(c, cudaEventCreate(&e1));
+    auto trial = [&](float& ms) -> teuk_status {
+        teuk_status st = batched_step(c, trial_steps);   // warm-up (and graph capture)
+        if (st) return st;
+        cudaEventRecord(e0, c->stream);
+        st = batched_step(c, trial_steps);
+        if (st) return st;
+        cudaEventRecord(e1, c->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) return TEUK_ECUDA;
+        cudaEventElapsedTime(&ms, e0, e1);
+        return TEUK_OK;
+    };
+    auto set_strip = [&](const std::vector<int>& members, int L) {
+        for (int k : members) c->inst[k].strip = std::max(1, std::min(L, c->inst[k].p.n_rstar - 2));
+    };
+    // block-size classes, as batched_step forms them (instances with the same pitch)
+    std::vector<std::vector<int>> cls;
+    std::vector<int> cls_pitch, all(ni);
+    for (int k = 0; k < ni; ++k) {
+        all[k] = k;
+        int q = 0;
+        while (q < (int)cls.size() && cls_pitch[q] != c->inst[k].pitch) ++q;
+        if (q == (int)cls.size()) {
+            cls.emplace_back();
+            cls_pitch.push_back(c->inst[k].pitch);
+        }
+        cls[q].push_back(k);
+    }
+    const int cand[] = {16, 32, 64, 128, 256, 512};
+    float best_ms = 1e30f;
+    int best_all = 128;
+    teuk_status st = TEUK_OK;
+    for (int L : cand) {
+        set_strip(all, L);
+        float ms = 0.f;
+        if ((st = trial(ms))) break;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best_all = L;
+        }
+    }
+    set_strip(all, best_all);
+    if (!st && cls.size() > 1) {
+        for (const std::vector<int>& members : cls) {
+            int best_c = best_all;
+            for (int L : cand) {
+                if (L == best_all) continue;
+                set_strip(members, L);
+                float ms = 0.f;
+                if ((st = trial(ms))) break;
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best_c = L;
+                }
+            }
+            set_strip(members, best_c);
+            if (st) break;
+        }
+    }
+    // restore the state, time level and waveform records of every instance
+    for (int k = 0; k < ni; ++k) {
+        Instance& I = c->inst[k];
+        const Snap& q = snap[k];
+        const int nplanes = I.p.prec == TEUK_FP32 ? 1 : 2;
+        for (int pl = 0; pl < nplanes; ++pl)
+            cudaMemcpyAsync(I.state[q.cur][pl], q.st[pl], I.plane_bytes, cudaMemcpyDeviceToDevice, c->stream);
+        cudaMemcpyAsync(I.wave, q.wave, sizeof(double2) * (size_t)I.wave_cap * (size_t)I.p.n_theta,
+                        cudaMemcpyDeviceToDevice, c->stream);
+        I.step = q.step;
+        I.cur = q.cur;
+        I.wave_lo = q.lo;
+        I.wave_hi = q.hi;
+        if (chosen) chosen[k] = I.strip;
+    }
+    release();
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    invalidate_graph(c);
+    if (st) return st;
+    TK_CUDA(c, cudaStreamSynchronize(c->stream));
+    return refresh_partitions(c);
+}
+
+// Single instance stepped one launch per step: time each candidate strip length on a
+// scratch copy of the instance and keep the fastest.  Otherwise see autotune_batched.
 extern "C" teuk_status teuk_autotune(teuk_ctx* c, int trial_steps, int* chosen) {
     if (!c) return TEUK_EINVAL;
     if (trial_steps < 1) TK_FAIL(c, TEUK_EINVAL, "trial_steps must be >= 1");
+    if (c->inst.size() > 1 || c->steps_per_launch == 0) return autotune_batched(c, trial_steps, chosen);
     const int ni = (int)c->inst.size();
     std::vector<int> best(ni, 0);
     cudaEvent_t e0, e1;

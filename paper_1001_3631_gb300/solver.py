@@ -56,6 +56,7 @@ class TeukSolver:
         st = lib.teuk_create(arr, self.n, ctypes.c_void_p(_stream_handle(stream)), ctypes.byref(h))
         check(st, None)
         self.ctx = h
+        self._steps_per_launch = 1
 
     # -- lifetime
     def close(self):
@@ -146,6 +147,7 @@ class TeukSolver:
         """strip: r* columns per thread block (0 = automatic); steps_per_launch 0 sends a
         single-instance context through the persistent batched kernel."""
         check(_lib.load().teuk_set_tiling(self.ctx, strip, steps_per_launch), self.ctx)
+        self._steps_per_launch = steps_per_launch
 
     def kernel_launches(self):
         return _lib.load().teuk_kernel_launches(self.ctx)
@@ -158,13 +160,23 @@ class TeukSolver:
               self.ctx)
 
     def autotune(self, trial_steps=10, cache_path=None):
-        """Strip length per instance from a cached table keyed by (GPU, n_theta, precision,
-        n_rstar bucket); classes missing from the table are timed by teuk_autotune."""
+        """Strip length per instance from a cached table keyed by (GPU, launch mode, n_theta,
+        precision, n_rstar bucket); entries missing from the table are timed by
+        teuk_autotune.  The launch mode is "step" for one instance stepped one launch per
+        step, and for contexts that run the persistent kernels a signature of the whole
+        set of instances (their best strips depend on one another)."""
+        import hashlib
+
         import torch
         path = cache_path or os.environ.get("TEUK_TUNE_CACHE") or os.path.join(
             os.path.expanduser("~"), ".cache", "teuk_gb300", "tune.json")
         gpu = torch.cuda.get_device_name()
-        keys = ["%s|%d|%d|%d" % (gpu, p.n_theta, p.prec, int(np.ceil(np.log2(p.n_rstar))))
+        if self.n == 1 and self._steps_per_launch != 0:
+            mode = "step"
+        else:
+            shapes = sorted((p.n_rstar, p.n_theta, p.prec) for p in self.params)
+            mode = "batch:" + hashlib.sha1(repr(shapes).encode()).hexdigest()[:12]
+        keys = ["%s|%s|%d|%d|%d" % (gpu, mode, p.n_theta, p.prec, int(np.ceil(np.log2(p.n_rstar))))
                 for p in self.params]
         table = {}
         if os.path.exists(path):

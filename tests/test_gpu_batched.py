@@ -128,6 +128,14 @@ def test_autotune_keeps_results_and_state(tmp_path):
         # a second solver reads the cached table without timing
         with TeukSolver([dict(i["params"], prec="fp32_kahan") for i in INST]) as s2:
             assert s2.autotune(cache_path=str(tmp_path / "tune.json")) == chosen
+        # time levels and buffers were restored: two more steps equal an untuned run
+        s.step(2)
+        with TeukSolver([dict(i["params"], prec="fp32_kahan") for i in INST]) as s3:
+            for k, inst in enumerate(INST):
+                s3.set_source(inst["r0"], instance=k)
+            s3.step(6)
+            for k in range(len(INST)):
+                assert np.array_equal(s3.get_state(k), s.get_state(k))
 
 
 def test_batched_uneven_workload_128_instances(orc):
