@@ -152,7 +152,9 @@ teuk_status teuk_extract(teuk_ctx* ctx, int instance, double* out, double* out_s
  *     segment's waveform from its checkpoint.  The state ends at step0 + n.
  * Out (host): grad_amps[k] = dL/dA_{step0+k} (n values, may be NULL),
  *   *grad_r0 = dL/dr0 (may be NULL), *loss (built-in loss only, may be NULL).
- * Synchronizes. */
+ * The co-state is FP64 for TEUK_FP64 instances and compensated FP32 (the Kahan
+ * scheme of the forward state) for the FP32 precisions; the gradient and loss sums
+ * are FP64.  Synchronizes. */
 teuk_status teuk_adjoint_n(teuk_ctx* ctx, int instance, int64_t step0, int64_t n,
                            int64_t ckpt_every, const double* grad_wave, double* grad_amps,
                            double* grad_r0, double* loss);

@@ -17,44 +17,87 @@
 // Coefficients are the scaled tables of teuk_setup.cu (g, E1, E2, ep, em, E3); in
 // the corrector's angular term  ep Phi~(j+1) + em Phi~(j-1) + (E3 - ep - em) Phi~(j)
 // the ghost rows fold back onto rows 0 and n_theta-1 with the sign of the pole
-// condition.  lam and mu are FP64 whatever the forward precision.
+// condition.  The co-state lam and mu are FP64 for FP64 instances; for FP32 instances
+// they are FP32, lam compensated like the forward state (value hi - c, each step's
+// increment added with Kahan's compensated sum), the gradient sums FP64 either way.
 #include "teuk_internal.cuh"
 
 namespace teuk {
 
-struct Z { double x, y; };
-__device__ __forceinline__ Z zld(const double2* p, size_t o) { double2 v = p[o]; return {v.x, v.y}; }
-__device__ __forceinline__ Z zadd(Z a, Z b) { return {a.x + b.x, a.y + b.y}; }
-__device__ __forceinline__ Z zscale(double s, Z a) { return {s * a.x, s * a.y}; }
+template <typename R>
+struct Z { R x, y; };
+template <typename R>
+__device__ __forceinline__ Z<R> zadd(Z<R> a, Z<R> b) { return {a.x + b.x, a.y + b.y}; }
+template <typename R>
+__device__ __forceinline__ Z<R> zscale(R s, Z<R> a) { return {s * a.x, s * a.y}; }
 // conj(cr + i ci) * z
-__device__ __forceinline__ Z zconjmul(double cr, double ci, Z z) {
+template <typename R>
+__device__ __forceinline__ Z<R> zconjmul(R cr, R ci, Z<R> z) {
     return {cr * z.x + ci * z.y, cr * z.y - ci * z.x};
 }
 
-template <typename T>
-__device__ __forceinline__ double cget(const T* tab, size_t pl, int k, size_t o) {
-    return (double)tab[(size_t)k * pl + o];
+template <typename R> struct R2T;
+template <> struct R2T<double> { using V = double2; };
+template <> struct R2T<float> { using V = float2; };
+
+// One co-state plane (complex, [nr][pitch]) and, for FP32, its compensation plane.
+template <typename R>
+struct CoPlane {
+    typename R2T<R>::V* v;
+    float2* c;   // FP32 only: value = v - c
+    __device__ __forceinline__ Z<R> ld(size_t o) const {
+        const typename R2T<R>::V a = v[o];
+        if constexpr (sizeof(R) == 4) {
+            const float2 b = c[o];
+            return {a.x - b.x, a.y - b.y};
+        } else {
+            return {a.x, a.y};
+        }
+    }
+};
+template <typename R>
+__device__ __forceinline__ CoPlane<R> coplane(const CoLevel& L, int k) {
+    return {(typename R2T<R>::V*)(k == 0 ? L.F : L.P), (float2*)(k == 0 ? L.Fc : L.Pc)};
+}
+template <typename R>
+__device__ __forceinline__ Z<R> ldv(const void* p, size_t o) {
+    const typename R2T<R>::V a = ((const typename R2T<R>::V*)p)[o];
+    return {a.x, a.y};
+}
+template <typename R>
+__device__ __forceinline__ void stv(void* p, size_t o, Z<R> z) {
+    ((typename R2T<R>::V*)p)[o] = {z.x, z.y};
+}
+template <typename R>
+__device__ __forceinline__ Z<R> gld(const double2* p, size_t o) {
+    const double2 a = p[o];
+    return {(R)a.x, (R)a.y};
+}
+
+template <typename T, typename R>
+__device__ __forceinline__ R cget(const T* tab, size_t pl, int k, size_t o) {
+    return (R)tab[(size_t)k * pl + o];
 }
 
 // Cotangent of the averaged Phi~ at (col, j) produced by the angular term of the
-// sub-step whose coefficients are `tab` and whose Pi cotangents are L (col fixed).
-template <typename T>
-__device__ __forceinline__ Z theta_cotangent(const T* tab, size_t pl, const double2* LP,
-                                             const InstDev& d, int col, int j, double g) {
+// sub-step whose coefficients are `tab` and whose Pi cotangents are LP (col fixed).
+template <typename T, typename R, class LD>
+__device__ __forceinline__ Z<R> theta_cotangent(const T* tab, size_t pl, const LD& LP,
+                                                const InstDev& d, int col, int j, R g) {
     const int nth = d.nth;
     size_t o = node_index(d, col, j);
-    Z l0 = zld(LP, o);
-    double ep0 = cget(tab, pl, C_EP, o), em0 = cget(tab, pl, C_EM, o);
-    Z r = zconjmul(cget(tab, pl, C_E3R, o) - ep0 - em0, cget(tab, pl, C_E3I, o), l0);
+    Z<R> l0 = LP(o);
+    R ep0 = cget<T, R>(tab, pl, C_EP, o), em0 = cget<T, R>(tab, pl, C_EM, o);
+    Z<R> r = zconjmul(cget<T, R>(tab, pl, C_E3R, o) - ep0 - em0, cget<T, R>(tab, pl, C_E3I, o), l0);
     if (j >= 1) {
         size_t om = o - 1;   // row j-1
-        r = zadd(r, zscale(cget(tab, pl, C_EP, om), zld(LP, om)));
+        r = zadd(r, zscale(cget<T, R>(tab, pl, C_EP, om), LP(om)));
     } else {
         r = zadd(r, zscale(g * em0, l0));   // ghost row -1 = g * row 0
     }
     if (j + 1 < nth) {
         size_t op = o + 1;   // row j+1
-        r = zadd(r, zscale(cget(tab, pl, C_EM, op), zld(LP, op)));
+        r = zadd(r, zscale(cget<T, R>(tab, pl, C_EM, op), LP(op)));
     } else {
         r = zadd(r, zscale(g * ep0, l0));   // ghost row nth = g * row nth-1
     }
@@ -62,44 +105,54 @@ __device__ __forceinline__ Z theta_cotangent(const T* tab, size_t pl, const doub
 }
 
 // mu = C^T P lam  at half node (h, j), h in [0, nr-2].
-template <typename T>
-__global__ void adj_corrector_kernel(InstDev d, const double2* lF, const double2* lP, double2* mF,
-                                     double2* mP) {
+template <typename T, typename R>
+__global__ void adj_corrector_kernel(InstDev d, CoLevel lam, CoMu mu) {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     int h = blockIdx.y;
     if (h > d.nr - 2 || j >= d.nth) return;
     const T* ci = (const T*)d.coef_i;
     const size_t pl = plane_elems(d);
-    Z muF = {0, 0}, muP = {0, 0};
+    const CoPlane<R> lF = coplane<R>(lam, 0), lP = coplane<R>(lam, 1);
+    auto LPf = [&](size_t o) { return lP.ld(o); };
+    Z<R> muF = {0, 0}, muP = {0, 0};
     // integer node h (this half node is its right neighbour R, sign +1) and
     // integer node h+1 (this half node is its left neighbour L, sign -1)
     for (int side = 0; side < 2; ++side) {
         int col = h + side;
         if (col < 1 || col > d.nr - 2) continue;   // P: boundary columns carry no cotangent
-        double sR = side == 0 ? 1.0 : -1.0;
+        R sR = side == 0 ? R(1) : R(-1);
         size_t o = node_index(d, col, j);
-        Z LF = zld(lF, o), LPi = zld(lP, o);
-        double G = cget(ci, pl, C_G, o);
-        Z tc = theta_cotangent<T>(ci, pl, lP, d, col, j, d.ghost);
+        Z<R> LF = lF.ld(o), LPi = lP.ld(o);
+        R G = cget<T, R>(ci, pl, C_G, o);
+        Z<R> tc = theta_cotangent<T, R>(ci, pl, LPf, d, col, j, (R)d.ghost);
         // Delta Phi = -G (hF_R - hF_L) + dt (hP_R + hP_L)/2
         // Delta Pi  =  G (hP_R - hP_L) + E1 (hP_R + hP_L)/2 + E2 (hF_R - hF_L) + angular(Phi~)
         muF = zadd(muF, zscale(-sR * G, LF));
-        muF = zadd(muF, zscale(sR, zconjmul(cget(ci, pl, C_E2R, o), cget(ci, pl, C_E2I, o), LPi)));
-        muF = zadd(muF, zscale(0.5, tc));
-        muP = zadd(muP, zscale(0.5 * d.dt, LF));
+        muF = zadd(muF, zscale(sR, zconjmul(cget<T, R>(ci, pl, C_E2R, o), cget<T, R>(ci, pl, C_E2I, o), LPi)));
+        muF = zadd(muF, zscale(R(0.5), tc));
+        muP = zadd(muP, zscale((R)(0.5 * d.dt), LF));
         muP = zadd(muP, zscale(sR * G, LPi));
-        muP = zadd(muP, zscale(0.5, zconjmul(cget(ci, pl, C_E1R, o), cget(ci, pl, C_E1I, o), LPi)));
+        muP = zadd(muP, zscale(R(0.5), zconjmul(cget<T, R>(ci, pl, C_E1R, o), cget<T, R>(ci, pl, C_E1I, o), LPi)));
     }
     size_t oh = node_index(d, h, j);
-    mF[oh] = make_double2(muF.x, muF.y);
-    mP[oh] = make_double2(muP.x, muP.y);
+    stv<R>(mu.F, oh, muF);
+    stv<R>(mu.P, oh, muP);
+}
+
+// Compensated add of an increment to one co-state node (FP32): value = v - c.
+__device__ __forceinline__ void kahan_node(float2& v, float2& c, Z<float> dlt) {
+    float yx = __fsub_rn(dlt.x, c.x), yy = __fsub_rn(dlt.y, c.y);
+    float tx = __fadd_rn(v.x, yx), ty = __fadd_rn(v.y, yy);
+    c.x = __fsub_rn(__fsub_rn(tx, v.x), yx);
+    c.y = __fsub_rn(__fsub_rn(ty, v.y), yy);
+    v.x = tx;
+    v.y = ty;
 }
 
 // lam^n = P lam^{n+1} + H^T mu (+ E^T gbar) at node (i, j).
-template <typename T>
-__global__ void adj_predictor_kernel(InstDev d, const double2* lF, const double2* lP,
-                                     const double2* mF, const double2* mP, const double2* gbar,
-                                     double2* oF, double2* oP) {
+template <typename T, typename R>
+__global__ void adj_predictor_kernel(InstDev d, CoLevel lin, CoMu mu, const double2* gbar,
+                                     CoLevel lout) {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     int i = blockIdx.y;
     if (i >= d.nr || j >= d.nth) return;
@@ -107,74 +160,107 @@ __global__ void adj_predictor_kernel(InstDev d, const double2* lF, const double2
     const size_t pl = plane_elems(d);
     const size_t o = node_index(d, i, j);
     const bool interior = i >= 1 && i <= d.nr - 2;
-    Z aF = interior ? zld(lF, o) : Z{0, 0};
-    Z aP = interior ? zld(lP, o) : Z{0, 0};
-    const double hdt = 0.5 * d.dt;
+    constexpr bool kComp = sizeof(R) == 4;
+    // FP64: the sum starts from P lam^{n+1}; FP32: the increment alone, added to the
+    // compensated lam^{n+1} at the end
+    Z<R> aF = {0, 0}, aP = {0, 0};
+    if constexpr (!kComp) {
+        if (interior) {
+            aF = ldv<R>(lin.F, o);
+            aP = ldv<R>(lin.P, o);
+        }
+    }
+    const R hdt = (R)(0.5 * d.dt);
+    auto MPf = [&](size_t q) { return ldv<R>(mu.P, q); };
     // half node i-1/2 (index i-1, this column is its right input R, sign +1) and
     // half node i+1/2 (index i, this column is its left input L, sign -1)
     for (int side = 0; side < 2; ++side) {
         int h = i - 1 + side;
         if (h < 0 || h > d.nr - 2) continue;
-        double sR = side == 0 ? 1.0 : -1.0;
+        R sR = side == 0 ? R(1) : R(-1);
         size_t oh = node_index(d, h, j);
-        Z MF = zld(mF, oh), MP = zld(mP, oh);
-        double G = cget(ch, pl, C_G, oh);
-        Z tc = theta_cotangent<T>(ch, pl, mP, d, h, j, d.ghost);
+        Z<R> MF = ldv<R>(mu.F, oh), MP = ldv<R>(mu.P, oh);
+        R G = cget<T, R>(ch, pl, C_G, oh);
+        Z<R> tc = theta_cotangent<T, R>(ch, pl, MPf, d, h, j, (R)d.ghost);
         // hF = (F_L + F_R)/2 - G (F_R - F_L) + hdt (P_L + P_R)/2
         // hP = (P_L + P_R)/2 + G (P_R - P_L) + E1 (P_L + P_R)/2 + E2 (F_R - F_L) + angular(Fbar)
-        aF = zadd(aF, zscale(0.5 - sR * G, MF));
-        aF = zadd(aF, zscale(sR, zconjmul(cget(ch, pl, C_E2R, oh), cget(ch, pl, C_E2I, oh), MP)));
-        aF = zadd(aF, zscale(0.5, tc));
-        aP = zadd(aP, zscale(0.5 * hdt, MF));
-        aP = zadd(aP, zscale(0.5 + sR * G, MP));
-        aP = zadd(aP, zscale(0.5, zconjmul(cget(ch, pl, C_E1R, oh), cget(ch, pl, C_E1I, oh), MP)));
+        aF = zadd(aF, zscale(R(0.5) - sR * G, MF));
+        aF = zadd(aF, zscale(sR, zconjmul(cget<T, R>(ch, pl, C_E2R, oh), cget<T, R>(ch, pl, C_E2I, oh), MP)));
+        aF = zadd(aF, zscale(R(0.5), tc));
+        aP = zadd(aP, zscale(R(0.5) * hdt, MF));
+        aP = zadd(aP, zscale(R(0.5) + sR * G, MP));
+        aP = zadd(aP, zscale(R(0.5), zconjmul(cget<T, R>(ch, pl, C_E1R, oh), cget<T, R>(ch, pl, C_E1I, oh), MP)));
     }
     if (gbar) {  // transpose of the linear extraction between i_e and i_e + 1
-        if (i == d.i_e) aF = zadd(aF, zscale(1.0 - d.f_e, zld(gbar, j)));
-        if (i == d.i_e + 1) aF = zadd(aF, zscale(d.f_e, zld(gbar, j)));
+        if (i == d.i_e) aF = zadd(aF, zscale((R)(1.0 - d.f_e), gld<R>(gbar, j)));
+        if (i == d.i_e + 1) aF = zadd(aF, zscale((R)d.f_e, gld<R>(gbar, j)));
     }
-    oF[o] = make_double2(aF.x, aF.y);
-    oP[o] = make_double2(aP.x, aP.y);
+    if constexpr (kComp) {
+        float2 vF = {0.f, 0.f}, cF = {0.f, 0.f}, vP = {0.f, 0.f}, cP = {0.f, 0.f};
+        if (interior) {
+            vF = ((const float2*)lin.F)[o];
+            cF = ((const float2*)lin.Fc)[o];
+            vP = ((const float2*)lin.P)[o];
+            cP = ((const float2*)lin.Pc)[o];
+        }
+        kahan_node(vF, cF, aF);
+        kahan_node(vP, cP, aP);
+        ((float2*)lout.F)[o] = vF;
+        ((float2*)lout.Fc)[o] = cF;
+        ((float2*)lout.P)[o] = vP;
+        ((float2*)lout.Pc)[o] = cP;
+    } else {
+        stv<R>(lout.F, o, aF);
+        stv<R>(lout.P, o, aP);
+    }
 }
 
 // lam = E^T gbar (the start of the reverse sweep).
-__global__ void adj_init_kernel(InstDev d, const double2* gbar, double2* oF, double2* oP) {
+template <typename R>
+__global__ void adj_init_kernel(InstDev d, const double2* gbar, CoLevel out) {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     int i = blockIdx.y;
     if (j >= d.pitch || i >= d.nr) return;
     size_t o = node_index(d, i, j);
-    Z a = {0, 0};
-    if (gbar && i == d.i_e) a = zscale(1.0 - d.f_e, zld(gbar, j));
-    if (gbar && i == d.i_e + 1) a = zscale(d.f_e, zld(gbar, j));
-    oF[o] = make_double2(a.x, a.y);
-    oP[o] = make_double2(0.0, 0.0);
+    Z<double> a = {0, 0};
+    if (gbar && i == d.i_e) a = zscale(1.0 - d.f_e, gld<double>(gbar, j));
+    if (gbar && i == d.i_e + 1) a = zscale(d.f_e, gld<double>(gbar, j));
+    stv<R>(out.F, o, Z<R>{(R)a.x, (R)a.y});
+    stv<R>(out.P, o, Z<R>{0, 0});
+    if constexpr (sizeof(R) == 4) {
+        ((float2*)out.Fc)[o] = make_float2(0.f, 0.f);
+        ((float2*)out.Pc)[o] = make_float2(0.f, 0.f);
+    }
 }
 
-// Source gradients of step n: one block, fixed-order reduction.
-__global__ void adj_source_kernel(InstDev d, int64_t n, const double2* lP, const double2* mP,
-                                  double* gA, double* gR) {
+// Source gradients of step n: one block, fixed-order reduction (FP64 sums).
+template <typename R>
+__global__ void adj_source_kernel(InstDev d, int64_t n, CoLevel lam, CoMu mu, double* gA,
+                                  double* gR) {
     __shared__ double sA[256], sR[256];
     const SourceDev& s = d.src;
+    const CoPlane<R> lP = coplane<R>(lam, 1);
     double A = (s.amps != nullptr && n < s.n_amps) ? s.amps[n] : 1.0;
     double tp = (double)n * d.dt, tc = tp + 0.5 * d.dt;
     double sp, cp, sc, cc;
     sincos(s.omega * tp + s.phase0, &sp, &cp);
     sincos(s.omega * tc + s.phase0, &sc, &cc);
-    Z ep = {cp, -sp}, ec = {cc, -sc};
+    Z<double> ep = {cp, -sp}, ec = {cc, -sc};
     // d/dr0 e^{-i phi} = -i (dphi/dr0) e^{-i phi}
     double kp = tp * s.domega + s.dphase0, kc = tc * s.domega + s.dphase0;
     // (-i k)(x + i y) = k y - i k x
-    Z dep = {kp * ep.y, -kp * ep.x}, dec = {kc * ec.y, -kc * ec.x};
+    Z<double> dep = {kp * ep.y, -kp * ep.x}, dec = {kc * ec.y, -kc * ec.x};
     double accA = 0.0, accR = 0.0;
     const double hdt = 0.5 * d.dt;
     int nh_tot = s.nj * s.nh, ni_tot = s.nj * s.ni;
     for (int k = threadIdx.x; k < nh_tot + ni_tot; k += blockDim.x) {
-        Z lam, P, dP, e, de;
+        Z<double> lam_v, P, dP, e, de;
         double w;
         if (k < nh_tot) {
             int jj = k / s.nh, hh = k % s.nh;
             size_t o = node_index(d, s.h_lo + hh, s.j_lo + jj);
-            lam = zld(mP, o);
+            const Z<R> m = ldv<R>(mu.P, o);
+            lam_v = {(double)m.x, (double)m.y};
             P = {s.P_half[k].x, s.P_half[k].y};
             dP = {s.dP_half[k].x, s.dP_half[k].y};
             e = ep; de = dep; w = hdt;
@@ -184,17 +270,18 @@ __global__ void adj_source_kernel(InstDev d, int64_t n, const double2* lP, const
             int col = s.i_lo + ii;
             if (col < 1 || col > d.nr - 2) continue;
             size_t o = node_index(d, col, s.j_lo + jj);
-            lam = zld(lP, o);
+            const Z<R> l = lP.ld(o);
+            lam_v = {(double)l.x, (double)l.y};
             P = {s.P_int[kk].x, s.P_int[kk].y};
             dP = {s.dP_int[kk].x, s.dP_int[kk].y};
             e = ec; de = dec; w = d.dt;
         }
         // e P and (de P + e dP)
-        Z eP = {e.x * P.x - e.y * P.y, e.x * P.y + e.y * P.x};
-        Z dd = {de.x * P.x - de.y * P.y + e.x * dP.x - e.y * dP.y,
-                de.x * P.y + de.y * P.x + e.x * dP.y + e.y * dP.x};
-        accA += w * (lam.x * eP.x + lam.y * eP.y);
-        accR += w * (lam.x * dd.x + lam.y * dd.y);
+        Z<double> eP = {e.x * P.x - e.y * P.y, e.x * P.y + e.y * P.x};
+        Z<double> dd = {de.x * P.x - de.y * P.y + e.x * dP.x - e.y * dP.y,
+                        de.x * P.y + de.y * P.x + e.x * dP.y + e.y * dP.x};
+        accA += w * (lam_v.x * eP.x + lam_v.y * eP.y);
+        accR += w * (lam_v.x * dd.x + lam_v.y * dd.y);
     }
     sA[threadIdx.x] = accA;
     sR[threadIdx.x] = accR;
@@ -238,32 +325,29 @@ __global__ void ordered_sum_kernel(const double* v, int64_t n, double* out) {
 
 // ------------------------------------------------------------------ launchers
 
-void launch_adj_corrector(cudaStream_t st, const InstDev& d, const double2* lF, const double2* lP,
-                          double2* mF, double2* mP) {
+void launch_adj_corrector(cudaStream_t st, const InstDev& d, const CoLevel& lam, const CoMu& mu) {
     dim3 g((d.nth + 127) / 128, d.nr - 1);
-    if (d.prec == 0) adj_corrector_kernel<double><<<g, 128, 0, st>>>(d, lF, lP, mF, mP);
-    else adj_corrector_kernel<float><<<g, 128, 0, st>>>(d, lF, lP, mF, mP);
+    if (d.prec == 0) adj_corrector_kernel<double, double><<<g, 128, 0, st>>>(d, lam, mu);
+    else adj_corrector_kernel<float, float><<<g, 128, 0, st>>>(d, lam, mu);
 }
 
-void launch_adj_predictor(cudaStream_t st, const InstDev& d, const double2* lF, const double2* lP,
-                          const double2* mF, const double2* mP, const double2* gbar, double2* oF,
-                          double2* oP) {
+void launch_adj_predictor(cudaStream_t st, const InstDev& d, const CoLevel& lin, const CoMu& mu,
+                          const double2* gbar, const CoLevel& lout) {
     dim3 g((d.nth + 127) / 128, d.nr);
-    if (d.prec == 0)
-        adj_predictor_kernel<double><<<g, 128, 0, st>>>(d, lF, lP, mF, mP, gbar, oF, oP);
-    else
-        adj_predictor_kernel<float><<<g, 128, 0, st>>>(d, lF, lP, mF, mP, gbar, oF, oP);
+    if (d.prec == 0) adj_predictor_kernel<double, double><<<g, 128, 0, st>>>(d, lin, mu, gbar, lout);
+    else adj_predictor_kernel<float, float><<<g, 128, 0, st>>>(d, lin, mu, gbar, lout);
 }
 
-void launch_adj_init(cudaStream_t st, const InstDev& d, const double2* gbar, double2* oF,
-                     double2* oP) {
+void launch_adj_init(cudaStream_t st, const InstDev& d, const double2* gbar, const CoLevel& out) {
     dim3 g((d.pitch + 127) / 128, d.nr);
-    adj_init_kernel<<<g, 128, 0, st>>>(d, gbar, oF, oP);
+    if (d.prec == 0) adj_init_kernel<double><<<g, 128, 0, st>>>(d, gbar, out);
+    else adj_init_kernel<float><<<g, 128, 0, st>>>(d, gbar, out);
 }
 
-void launch_adj_source(cudaStream_t st, const InstDev& d, int64_t n, const double2* lP,
-                       const double2* mP, double* gA, double* gR) {
-    adj_source_kernel<<<1, 256, 0, st>>>(d, n, lP, mP, gA, gR);
+void launch_adj_source(cudaStream_t st, const InstDev& d, int64_t n, const CoLevel& lam,
+                       const CoMu& mu, double* gA, double* gR) {
+    if (d.prec == 0) adj_source_kernel<double><<<1, 256, 0, st>>>(d, n, lam, mu, gA, gR);
+    else adj_source_kernel<float><<<1, 256, 0, st>>>(d, n, lam, mu, gA, gR);
 }
 
 void launch_loss_records(cudaStream_t st, const double2* wave, int64_t cap, int nth,

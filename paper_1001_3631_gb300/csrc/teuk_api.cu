@@ -1085,12 +1085,23 @@ extern "C" teuk_status teuk_adjoint_n(teuk_ctx* c, int instance, int64_t step0, 
                 (long long)I.step, (long long)step0);
     cudaStream_t s = c->stream;
     const int nth = I.p.n_theta;
-    const size_t plane = (size_t)I.p.n_rstar * I.pitch * sizeof(double2);  // one [nr][pitch] plane
+    // co-state planes ([nr][pitch] complex): FP64 for FP64 instances, else FP32 with
+    // compensation planes for lam
+    const bool co32 = I.p.prec != TEUK_FP64;
+    const size_t plane = (size_t)I.p.n_rstar * I.pitch * (co32 ? sizeof(float2) : sizeof(double2));
     AdjBuffers B(s);
-    double2 *lam[2][2], *mu[2];
-    for (int b = 0; b < 2; ++b)
-        for (int k = 0; k < 2; ++k) TK_CUDA(c, B.get((void**)&lam[b][k], plane));
-    for (int k = 0; k < 2; ++k) TK_CUDA(c, B.get((void**)&mu[k], plane));
+    CoLevel lam[2] = {};
+    CoMu mu = {};
+    for (int b = 0; b < 2; ++b) {
+        TK_CUDA(c, B.get(&lam[b].F, plane));
+        TK_CUDA(c, B.get(&lam[b].P, plane));
+        if (co32) {
+            TK_CUDA(c, B.get(&lam[b].Fc, plane));
+            TK_CUDA(c, B.get(&lam[b].Pc, plane));
+        }
+    }
+    TK_CUDA(c, B.get(&mu.F, plane));
+    TK_CUDA(c, B.get(&mu.P, plane));
     double *gA = nullptr, *gR = nullptr, *lossrec = nullptr, *scal = nullptr;
     double2* gbar = nullptr;
     TK_CUDA(c, B.get((void**)&gA, sizeof(double) * n));
@@ -1106,8 +1117,9 @@ extern "C" teuk_status teuk_adjoint_n(teuk_ctx* c, int instance, int64_t step0, 
     // run `count` steps on the buffers of dv (which start in buffer cur), recording
     // levels into the ring of dv; returns the buffer holding the result.
     auto forward = [&](InstDev dv, int cur, int64_t level, int64_t count, int strip) {
+        const int* part = I.part_strip == strip ? I.d_part : nullptr;
         for (int64_t k = 0; k < count; ++k) {
-            launch_step(s, dv, level + k, cur, strip);
+            launch_step(s, dv, level + k, cur, strip, part);
             c->launches++;
             cur = 1 - cur;
         }
@@ -1189,19 +1201,18 @@ extern "C" teuk_status teuk_adjoint_n(teuk_ctx* c, int instance, int64_t step0, 
         for (int64_t m = a + len - 1; m >= a; --m) {
             const int64_t k = m - step0;  // step index within the call
             if (!started) {
-                launch_adj_init(s, d, gbar + (size_t)(n - 1) * nth, lam[cur][0], lam[cur][1]);
+                launch_adj_init(s, d, gbar + (size_t)(n - 1) * nth, lam[cur]);
                 c->launches++;
                 started = true;
             }
-            launch_adj_corrector(s, d, lam[cur][0], lam[cur][1], mu[0], mu[1]);
+            launch_adj_corrector(s, d, lam[cur], mu);
             c->launches++;
             if (I.src_on) {
-                launch_adj_source(s, d, m, lam[cur][1], mu[1], gA + k, gR + k);
+                launch_adj_source(s, d, m, lam[cur], mu, gA + k, gR + k);
                 c->launches++;
             }
             const double2* gb = k >= 1 ? gbar + (size_t)(k - 1) * nth : nullptr;
-            launch_adj_predictor(s, d, lam[cur][0], lam[cur][1], mu[0], mu[1], gb,
-                                 lam[1 - cur][0], lam[1 - cur][1]);
+            launch_adj_predictor(s, d, lam[cur], mu, gb, lam[1 - cur]);
             c->launches++;
             cur = 1 - cur;
         }

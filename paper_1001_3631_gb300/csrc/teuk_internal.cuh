@@ -151,15 +151,18 @@ void launch_scan_finite(cudaStream_t st, const InstDev& d, int bin);
 void launch_wave_sum(cudaStream_t st, const double2* wave, int64_t cap, int nth, double dth,
                      int64_t level0, int64_t k_count, double2* out);
 // teuk_adjoint.cu
-void launch_adj_corrector(cudaStream_t st, const InstDev& d, const double2* lF, const double2* lP,
-                          double2* mF, double2* mP);
-void launch_adj_predictor(cudaStream_t st, const InstDev& d, const double2* lF, const double2* lP,
-                          const double2* mF, const double2* mP, const double2* gbar, double2* oF,
-                          double2* oP);
-void launch_adj_init(cudaStream_t st, const InstDev& d, const double2* gbar, double2* oF,
-                     double2* oP);
-void launch_adj_source(cudaStream_t st, const InstDev& d, int64_t n, const double2* lP,
-                       const double2* mP, double* gA, double* gR);
+// Co-state of one time level (teuk_adjoint.cu): F and P planes ([nr][pitch] complex,
+// double2 for FP64 instances, float2 otherwise) and, for FP32, their compensation
+// planes (float2; the value is v - c).  mu: the half-node cotangents (same type, no
+// compensation).
+struct CoLevel { void* F; void* P; void* Fc; void* Pc; };
+struct CoMu { void* F; void* P; };
+void launch_adj_corrector(cudaStream_t st, const InstDev& d, const CoLevel& lam, const CoMu& mu);
+void launch_adj_predictor(cudaStream_t st, const InstDev& d, const CoLevel& lin, const CoMu& mu,
+                          const double2* gbar, const CoLevel& lout);
+void launch_adj_init(cudaStream_t st, const InstDev& d, const double2* gbar, const CoLevel& out);
+void launch_adj_source(cudaStream_t st, const InstDev& d, int64_t n, const CoLevel& lam,
+                       const CoMu& mu, double* gA, double* gR);
 void launch_loss_records(cudaStream_t st, const double2* wave, int64_t cap, int nth,
                          int64_t level0, int64_t count, double r6, double* lossrec,
                          double2* gbar);

@@ -38,6 +38,28 @@ def test_cotangent_mode_matches_oracle_adjoint(orc, m):
     assert gr == pytest.approx(gr_o, rel=1e-11)
 
 
+# FP32 instances run the co-state in compensated FP32.  Against the oracle's FP64
+# adjoint (cotangent mode: no forward run, so only the FP32 rounding of the coefficient
+# tables and of the co-state arithmetic separate them) the gradients agree to ~1e-6
+# relative (measured up to 9.4e-7 for dL/dA and 3.1e-6 for dL/dr0 on these grids); the
+# bounds leave a factor of ~10.
+@pytest.mark.parametrize("prec", ["fp32_kahan", "fp32"])
+@pytest.mark.parametrize("m", [2, 1])
+def test_fp32_costate_matches_oracle_adjoint(orc, prec, m):
+    params = dict(SMALL, m=m, n_rstar=201, n_theta=16, rstar_min=-20.0, rstar_max=40.0,
+                  rstar_ext=11.0)
+    n, r0 = 200, 8.0
+    amps = inputs.amplitudes(n, seed=5005)
+    gw = np.random.default_rng(12).standard_normal((n, 16, 2))
+    p = oracle_params(orc, params, r0)
+    ga_o, gr_o, _ = orc.adjoint(p, orc.orbit_source(p), gw, amps=amps)
+    with TeukSolver(dict(params, prec=prec, wave_capacity=n + 1)) as s:
+        s.set_source(r0, amps)
+        ga, gr, _ = s.adjoint(n, step0=0, grad_wave=gw)
+    assert rel(ga, ga_o) <= 1e-5
+    assert gr == pytest.approx(gr_o, rel=3e-5)
+
+
 def _host_loss(s, n):
     w, first = s.extract(cap=n + 1)
     assert first == 0
@@ -118,6 +140,22 @@ def test_adjoint_workload_4096x128_full_size():
         assert ga[k] == pytest.approx(fd, rel=1e-5, abs=1e-8 * abs(L))
     fdr = (_fd_loss(params, r0 + h, amps, n) - _fd_loss(params, r0 - h, amps, n)) / (2 * h)
     assert gr == pytest.approx(fdr, rel=1e-5)
+
+
+def test_fp32_kahan_gradient_full_size_close_to_fp64():
+    # the full adjoint workload on an FP32-Kahan instance (compensated FP32 co-state)
+    # against the FP64 instance: measured 2.8e-7 (dL/dA), 1.5e-6 (dL/dr0), 3.2e-7 (loss)
+    cfg = inputs.ADJOINT_4096x128
+    params, n, r0 = dict(cfg["params"], rstar_ext=12.5), cfg["steps"], cfg["r0"]
+    amps = inputs.amplitudes(n, seed=cfg["amp_seed"])
+    res = {}
+    for prec in ("fp64", "fp32_kahan"):
+        with TeukSolver(dict(params, prec=prec)) as s:
+            s.set_source(r0, amps)
+            res[prec] = s.adjoint(n, step0=0, ckpt_every=cfg["ckpt_every"])
+    assert rel(res["fp32_kahan"][0], res["fp64"][0]) <= 3e-6
+    assert res["fp32_kahan"][1] == pytest.approx(res["fp64"][1], rel=2e-5)
+    assert res["fp32_kahan"][2] == pytest.approx(res["fp64"][2], rel=3e-6)
 
 
 def test_autograd_function_matches_builtin_adjoint():
