@@ -233,70 +233,91 @@ __global__ void adj_init_kernel(InstDev d, const double2* gbar, CoLevel out) {
     }
 }
 
-// Source gradients of step n: one block, fixed-order reduction (FP64 sums).
+// Source gradients of step n.  With e = e^{-i phi} the phase of a sub-step and
+// de = d e / d r0,
+//   dL/dA_n  = Re( (dt/2) e_p S_h + dt e_c S_i ),
+//   dL/dr0  += A_n Re( (dt/2) (de_p S_h + e_p S'_h) + dt (de_c S_i + e_c S'_i) ),
+// where S_h = sum conj(mu_Pi) P_half and S'_h = sum conj(mu_Pi) dP_half over the
+// half-node window, S_i and S'_i the same with lam'_Pi over the integer-node window
+// (interior columns only).  The four complex sums are FP64: each block reduces a fixed
+// slice of the window in a fixed order, and the last block to finish adds the blocks'
+// partial sums in index order and applies the phases, so the result does not depend
+// on the scheduling.
+constexpr int kSrcThreads = 256;
 template <typename R>
-__global__ void adj_source_kernel(InstDev d, int64_t n, CoLevel lam, CoMu mu, double* gA,
-                                  double* gR) {
-    __shared__ double sA[256], sR[256];
+__global__ void adj_source_kernel(InstDev d, int64_t n, CoLevel lam, CoMu mu, double* part,
+                                  unsigned* done, double* gA, double* gR) {
+    __shared__ double red[8][kSrcThreads];
+    __shared__ bool last;
     const SourceDev& s = d.src;
     const CoPlane<R> lP = coplane<R>(lam, 1);
-    double A = (s.amps != nullptr && n < s.n_amps) ? s.amps[n] : 1.0;
-    double tp = (double)n * d.dt, tc = tp + 0.5 * d.dt;
-    double sp, cp, sc, cc;
-    sincos(s.omega * tp + s.phase0, &sp, &cp);
-    sincos(s.omega * tc + s.phase0, &sc, &cc);
-    Z<double> ep = {cp, -sp}, ec = {cc, -sc};
-    // d/dr0 e^{-i phi} = -i (dphi/dr0) e^{-i phi}
-    double kp = tp * s.domega + s.dphase0, kc = tc * s.domega + s.dphase0;
-    // (-i k)(x + i y) = k y - i k x
-    Z<double> dep = {kp * ep.y, -kp * ep.x}, dec = {kc * ec.y, -kc * ec.x};
-    double accA = 0.0, accR = 0.0;
-    const double hdt = 0.5 * d.dt;
-    int nh_tot = s.nj * s.nh, ni_tot = s.nj * s.ni;
-    for (int k = threadIdx.x; k < nh_tot + ni_tot; k += blockDim.x) {
-        Z<double> lam_v, P, dP, e, de;
-        double w;
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // S_h, S'_h, S_i, S'_i (re, im)
+    const int nh_tot = s.nj * s.nh, ni_tot = s.nj * s.ni;
+    const int stride = gridDim.x * kSrcThreads;
+    for (int k = blockIdx.x * kSrcThreads + threadIdx.x; k < nh_tot + ni_tot; k += stride) {
+        Z<double> l, P, dP;
+        int q;
         if (k < nh_tot) {
             int jj = k / s.nh, hh = k % s.nh;
-            size_t o = node_index(d, s.h_lo + hh, s.j_lo + jj);
-            const Z<R> m = ldv<R>(mu.P, o);
-            lam_v = {(double)m.x, (double)m.y};
+            const Z<R> m = ldv<R>(mu.P, node_index(d, s.h_lo + hh, s.j_lo + jj));
+            l = {(double)m.x, (double)m.y};
             P = {s.P_half[k].x, s.P_half[k].y};
             dP = {s.dP_half[k].x, s.dP_half[k].y};
-            e = ep; de = dep; w = hdt;
+            q = 0;
         } else {
             int kk = k - nh_tot;
             int jj = kk / s.ni, ii = kk % s.ni;
             int col = s.i_lo + ii;
             if (col < 1 || col > d.nr - 2) continue;
-            size_t o = node_index(d, col, s.j_lo + jj);
-            const Z<R> l = lP.ld(o);
-            lam_v = {(double)l.x, (double)l.y};
+            const Z<R> v = lP.ld(node_index(d, col, s.j_lo + jj));
+            l = {(double)v.x, (double)v.y};
             P = {s.P_int[kk].x, s.P_int[kk].y};
             dP = {s.dP_int[kk].x, s.dP_int[kk].y};
-            e = ec; de = dec; w = d.dt;
+            q = 4;
         }
-        // e P and (de P + e dP)
-        Z<double> eP = {e.x * P.x - e.y * P.y, e.x * P.y + e.y * P.x};
-        Z<double> dd = {de.x * P.x - de.y * P.y + e.x * dP.x - e.y * dP.y,
-                        de.x * P.y + de.y * P.x + e.x * dP.y + e.y * dP.x};
-        accA += w * (lam_v.x * eP.x + lam_v.y * eP.y);
-        accR += w * (lam_v.x * dd.x + lam_v.y * dd.y);
+        // conj(l) P and conj(l) dP
+        acc[q + 0] += l.x * P.x + l.y * P.y;
+        acc[q + 1] += l.x * P.y - l.y * P.x;
+        acc[q + 2] += l.x * dP.x + l.y * dP.y;
+        acc[q + 3] += l.x * dP.y - l.y * dP.x;
     }
-    sA[threadIdx.x] = accA;
-    sR[threadIdx.x] = accR;
+#pragma unroll
+    for (int v = 0; v < 8; ++v) red[v][threadIdx.x] = acc[v];
     __syncthreads();
-    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
-        if (threadIdx.x < st) {
-            sA[threadIdx.x] += sA[threadIdx.x + st];
-            sR[threadIdx.x] += sR[threadIdx.x + st];
-        }
+    for (int st = kSrcThreads / 2; st > 0; st >>= 1) {
+        if (threadIdx.x < st)
+#pragma unroll
+            for (int v = 0; v < 8; ++v) red[v][threadIdx.x] += red[v][threadIdx.x + st];
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        *gA = sA[0];
-        *gR = A * sR[0];
+#pragma unroll
+        for (int v = 0; v < 8; ++v) part[blockIdx.x * 8 + v] = red[v][0];
+        __threadfence();
+        last = atomicAdd(done, 1u) == gridDim.x - 1;
     }
+    __syncthreads();
+    if (!last || threadIdx.x != 0) return;
+    __threadfence();
+    double S[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int b = 0; b < (int)gridDim.x; ++b)
+#pragma unroll
+        for (int v = 0; v < 8; ++v) S[v] += ((volatile double*)part)[b * 8 + v];
+    *done = 0;   // ready for the next step's launch (stream-ordered)
+    double A = (s.amps != nullptr && n < s.n_amps) ? s.amps[n] : 1.0;
+    double tp = (double)n * d.dt, tc = tp + 0.5 * d.dt;
+    double sp, cp, sc, cc;
+    sincos(s.omega * tp + s.phase0, &sp, &cp);
+    sincos(s.omega * tc + s.phase0, &sc, &cc);
+    // e = (cos, -sin); de = -i k e with k = d phi / d r0
+    double kp = tp * s.domega + s.dphase0, kc = tc * s.domega + s.dphase0;
+    Z<double> ep = {cp, -sp}, ec = {cc, -sc};
+    Z<double> dep = {kp * ep.y, -kp * ep.x}, dec = {kc * ec.y, -kc * ec.x};
+    auto re_mul = [](Z<double> a, double bx, double by) { return a.x * bx - a.y * by; };
+    const double hdt = 0.5 * d.dt;
+    *gA = hdt * re_mul(ep, S[0], S[1]) + d.dt * re_mul(ec, S[4], S[5]);
+    *gR = A * (hdt * (re_mul(dep, S[0], S[1]) + re_mul(ep, S[2], S[3])) +
+               d.dt * (re_mul(dec, S[4], S[5]) + re_mul(ec, S[6], S[7])));
 }
 
 // Loss of the built-in |r_ext^3 W|^2: per record, lossrec[k] = r^6 sum_j |W_k[j]|^2 (j
@@ -344,10 +365,17 @@ void launch_adj_init(cudaStream_t st, const InstDev& d, const double2* gbar, con
     else adj_init_kernel<float><<<g, 128, 0, st>>>(d, gbar, out);
 }
 
+int adj_source_blocks(const InstDev& d) {
+    const int tot = d.src.nj * (d.src.nh + d.src.ni);
+    const int b = (tot + kSrcThreads - 1) / kSrcThreads;
+    return b < 1 ? 1 : (b > kAdjSourceMaxBlocks ? kAdjSourceMaxBlocks : b);
+}
+
 void launch_adj_source(cudaStream_t st, const InstDev& d, int64_t n, const CoLevel& lam,
-                       const CoMu& mu, double* gA, double* gR) {
-    if (d.prec == 0) adj_source_kernel<double><<<1, 256, 0, st>>>(d, n, lam, mu, gA, gR);
-    else adj_source_kernel<float><<<1, 256, 0, st>>>(d, n, lam, mu, gA, gR);
+                       const CoMu& mu, double* part, unsigned* done, double* gA, double* gR) {
+    const int nb = adj_source_blocks(d);
+    if (d.prec == 0) adj_source_kernel<double><<<nb, kSrcThreads, 0, st>>>(d, n, lam, mu, part, done, gA, gR);
+    else adj_source_kernel<float><<<nb, kSrcThreads, 0, st>>>(d, n, lam, mu, part, done, gA, gR);
 }
 
 void launch_loss_records(cudaStream_t st, const double2* wave, int64_t cap, int nth,

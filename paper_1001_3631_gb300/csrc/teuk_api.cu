@@ -1102,6 +1102,11 @@ extern "C" teuk_status teuk_adjoint_n(teuk_ctx* c, int instance, int64_t step0, 
     }
     TK_CUDA(c, B.get(&mu.F, plane));
     TK_CUDA(c, B.get(&mu.P, plane));
+    double* src_part = nullptr;
+    unsigned* src_done = nullptr;
+    TK_CUDA(c, B.get((void**)&src_part, sizeof(double) * 8 * kAdjSourceMaxBlocks));
+    TK_CUDA(c, B.get((void**)&src_done, sizeof(unsigned)));
+    TK_CUDA(c, cudaMemsetAsync(src_done, 0, sizeof(unsigned), s));
     double *gA = nullptr, *gR = nullptr, *lossrec = nullptr, *scal = nullptr;
     double2* gbar = nullptr;
     TK_CUDA(c, B.get((void**)&gA, sizeof(double) * n));
@@ -1208,7 +1213,7 @@ extern "C" teuk_status teuk_adjoint_n(teuk_ctx* c, int instance, int64_t step0, 
             launch_adj_corrector(s, d, lam[cur], mu);
             c->launches++;
             if (I.src_on) {
-                launch_adj_source(s, d, m, lam[cur], mu, gA + k, gR + k);
+                launch_adj_source(s, d, m, lam[cur], mu, src_part, src_done, gA + k, gR + k);
                 c->launches++;
             }
             const double2* gb = k >= 1 ? gbar + (size_t)(k - 1) * nth : nullptr;

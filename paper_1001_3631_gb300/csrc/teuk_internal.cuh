@@ -161,8 +161,12 @@ void launch_adj_corrector(cudaStream_t st, const InstDev& d, const CoLevel& lam,
 void launch_adj_predictor(cudaStream_t st, const InstDev& d, const CoLevel& lin, const CoMu& mu,
                           const double2* gbar, const CoLevel& lout);
 void launch_adj_init(cudaStream_t st, const InstDev& d, const double2* gbar, const CoLevel& out);
+// source gradients of one step: part holds 8 doubles per block (at most
+// kAdjSourceMaxBlocks blocks), done one zero-initialised counter (left zero)
+constexpr int kAdjSourceMaxBlocks = 64;
+int adj_source_blocks(const InstDev& d);
 void launch_adj_source(cudaStream_t st, const InstDev& d, int64_t n, const CoLevel& lam,
-                       const CoMu& mu, double* gA, double* gR);
+                       const CoMu& mu, double* part, unsigned* done, double* gA, double* gR);
 void launch_loss_records(cudaStream_t st, const double2* wave, int64_t cap, int nth,
                          int64_t level0, int64_t count, double r6, double* lossrec,
                          double2* gbar);
