@@ -508,7 +508,7 @@ def main():
         "dtype": "f32-kahan", "data": "synthetic",
         "config": {"workload": WORKLOAD, "time_steps_per_bench_step": S,
                    "precision": "FP32 stencil, Kahan-compensated state; FP64 tables/source/extraction",
-                   "l2": "inputs larger than L2 (state 268 MB + coefficient tables 302 MB)",
+                   "l2": "inputs larger than L2 (ping-pong state 268 MB FP32-Kahan, 268 MB + 604 MB tables FP64)",
                    "parallelism": "replica per GPU" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": ach_k, "peak": peak, "unit": "GB/s",
                      "frac": ach_k / peak, "traffic": traffic,

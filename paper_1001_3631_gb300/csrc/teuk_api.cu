@@ -263,6 +263,24 @@ teuk_status refresh_partitions(teuk_ctx* c) {
     return TEUK_OK;
 }
 
+// The 2D coefficient tables [9][n_rstar][pitch] at half and integer nodes, in the
+// instance's precision: read by the FP64 step kernel and by the adjoint.  FP64 instances
+// build them at creation, FP32 instances (whose step kernels form their coefficients
+// from 1D tables) on the first adjoint call.
+teuk_status coef_tables(teuk_ctx* c, Instance& I) {
+    if (I.coef_h) return TEUK_OK;
+    const teuk_params& q = I.p;
+    const size_t cs = q.prec == TEUK_FP64 ? sizeof(double) : sizeof(float);
+    const size_t cbytes = (size_t)kNCoef * q.n_rstar * I.pitch * cs;
+    TK_CUDA(c, cudaMallocAsync(&I.coef_h, cbytes, c->stream));
+    TK_CUDA(c, cudaMallocAsync(&I.coef_i, cbytes, c->stream));
+    launch_coefficients(c->stream, q.prec, q.M, q.a, q.s, q.m, q.rstar_min, I.drs, I.dth, I.dt,
+                        q.n_rstar, q.n_theta, I.pitch, I.x_int, I.x_half, I.coef_h, I.coef_i);
+    c->launches++;
+    TK_CUDA(c, cudaGetLastError());
+    return TEUK_OK;
+}
+
 void do_step(teuk_ctx* c, Instance& I, int strip) {
     launch_step(c->stream, dev_of(c, I), I.step, I.cur, strip, I.part_strip == strip ? I.d_part : nullptr);
     c->launches++;
@@ -353,27 +371,23 @@ extern "C" teuk_status teuk_create(const teuk_params* p, int n_instances, void* 
                 TK_CCUDA(cudaMallocAsync(&I.state[b][k], I.plane_bytes, c->stream));
                 TK_CCUDA(cudaMemsetAsync(I.state[b][k], 0, I.plane_bytes, c->stream));
             }
-        size_t cs = q.prec == TEUK_FP64 ? sizeof(double) : sizeof(float);
-        size_t cbytes = (size_t)kNCoef * q.n_rstar * I.pitch * cs;
-        TK_CCUDA(cudaMallocAsync(&I.coef_h, cbytes, c->stream));
-        TK_CCUDA(cudaMallocAsync(&I.coef_i, cbytes, c->stream));
         TK_CCUDA(cudaMallocAsync((void**)&I.x_int, sizeof(double) * q.n_rstar, c->stream));
         TK_CCUDA(cudaMallocAsync((void**)&I.x_half, sizeof(double) * q.n_rstar, c->stream));
         TK_CCUDA(cudaMallocAsync((void**)&I.wave, sizeof(double2) * I.wave_cap * q.n_theta,
                                  c->stream));
         launch_invert_tortoise(c->stream, q.M, q.a, q.rstar_min, I.drs, q.n_rstar, I.x_int,
                                I.x_half);
-        launch_coefficients(c->stream, q.prec, q.M, q.a, q.s, q.m, q.rstar_min, I.drs, I.dth,
-                            I.dt, q.n_rstar, q.n_theta, I.pitch, I.x_int, I.x_half, I.coef_h,
-                            I.coef_i);
-        if (q.prec != TEUK_FP64) {
+        c->launches++;
+        if (q.prec == TEUK_FP64) {  // the FP32 paths build theirs on the first adjoint call
+            const teuk_status e = coef_tables(c, I);
+            if (e != TEUK_OK) return fail(e);
+        } else {
             TK_CCUDA(cudaMallocAsync((void**)&I.rtab, sizeof(RTab2) * q.n_rstar, c->stream));
             TK_CCUDA(cudaMallocAsync((void**)&I.thtab, sizeof(ThTab) * q.n_theta, c->stream));
             launch_tables_1d(c->stream, q.M, q.a, q.s, q.m, I.drs, I.dth, I.dt, q.n_rstar,
                              q.n_theta, I.x_int, I.x_half, I.rtab, I.thtab);
             c->launches++;
         }
-        c->launches += 2;
         TK_CCUDA(cudaGetLastError());
         I.r_ext = 0;  // filled lazily from x at r*_ext when needed (adjoint loss)
     }
@@ -1085,6 +1099,8 @@ extern "C" teuk_status teuk_adjoint_n(teuk_ctx* c, int instance, int64_t step0, 
                 (long long)I.step, (long long)step0);
     cudaStream_t s = c->stream;
     const int nth = I.p.n_theta;
+    st = coef_tables(c, I);
+    if (st) return st;
     // co-state planes ([nr][pitch] complex): FP64 for FP64 instances, else FP32 with
     // compensation planes for lam
     const bool co32 = I.p.prec != TEUK_FP64;
