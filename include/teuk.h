@@ -186,7 +186,7 @@ teuk_status teuk_set_instance_tiling(teuk_ctx* ctx, int instance, int strip);
 
 /* Autotuner of the strip length (r* columns per block), written to every instance
  * (chosen, may be NULL, receives them).  A single instance stepped one launch per step:
- * trial_steps steps of each candidate (8 .. 512 columns) on a scratch copy of the
+ * trial_steps steps of each candidate (1 .. 512 columns) on a scratch copy of the
  * instance.  Contexts that run the persistent kernels (several instances, or one with
  * steps_per_launch = 0): trial_steps steps of the whole context per candidate (16 .. 512),
  * one length for all instances first, then block-size class by class, on the live state,

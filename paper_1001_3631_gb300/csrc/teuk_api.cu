@@ -196,13 +196,15 @@ InstDev dev_of(const teuk_ctx* c, const Instance& I) {
 
 // Strip length so that the grid holds about 16 warps per SM on 152 SMs, at least
 // 8 columns (a strip reads 2 columns beyond its outputs).
-// Strip length that gives one wave of resident blocks (at least 8 columns per block,
-// so the ring's start-up is amortised; at most 512).
+// Strip length that gives one wave of resident blocks (at most 512 columns).  Grids too
+// small to fill the GPU get one column per block: the step time is then the ring's
+// start-up plus the strip, so the shortest strip is fastest (800 x 64 on GB300: 4.2 us
+// per step at one column, 8.2 us at eight).
 int auto_strip(const Instance& I) {
     int64_t blocks = I.resident > 0 ? I.resident : 1;
     int64_t cols = I.p.n_rstar - 2;
     int64_t L = (cols + blocks - 1) / blocks;
-    if (L < 8) L = 8;
+    if (L < 1) L = 1;
     if (L > 512) L = 512;
     return (int)L;
 }
@@ -964,7 +966,7 @@ extern "C" teuk_status teuk_autotune(teuk_ctx* c, int trial_steps, int* chosen) 
                 d.buf[0][q] = scr[0][q];
                 d.buf[1][q] = scr[1][q];
             }
-            const int cand[] = {8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512};
+            const int cand[] = {1, 2, 4, 8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512};
             for (int ch : cand) {
                 if (ch > I.p.n_rstar - 2) break;
                 for (int w = 0; w < 2; ++w) launch_step(c->stream, d, I.step + w, w & 1, ch);
