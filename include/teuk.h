@@ -51,7 +51,10 @@ typedef enum {
 typedef enum {
     TEUK_FP64 = 0,        /* state, coefficients and arithmetic in FP64 */
     TEUK_FP32 = 1,        /* state and arithmetic in FP32 (coefficients rounded from FP64) */
-    TEUK_FP32_KAHAN = 2   /* FP32 arithmetic, state as compensated (hi, c) FP32 pairs */
+    TEUK_FP32_KAHAN = 2,  /* FP32 arithmetic, state as compensated (hi, c) FP32 pairs */
+    TEUK_FP64_DF = 3      /* FP64-equivalent: state, coefficients and arithmetic in
+                           * double-float (hi + lo FP32 pairs, ~48 significant bits)
+                           * on the FP32 units; the adjoint uses an FP64 co-state */
 } teuk_precision;
 
 /*

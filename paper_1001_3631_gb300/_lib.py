@@ -13,7 +13,7 @@ LIB_PATH = os.path.join(HERE, "libteuk.so")
 HEADER = os.path.join(ROOT, "include", "teuk.h")
 
 TEUK_OK, TEUK_EINVAL, TEUK_ENOMEM, TEUK_ECUDA, TEUK_EUNSTABLE, TEUK_ETIMEOUT, TEUK_ESTATE = range(7)
-TEUK_FP64, TEUK_FP32, TEUK_FP32_KAHAN = 0, 1, 2
+TEUK_FP64, TEUK_FP32, TEUK_FP32_KAHAN, TEUK_FP64_DF = 0, 1, 2, 3
 STATUS_NAMES = {0: "TEUK_OK", 1: "TEUK_EINVAL", 2: "TEUK_ENOMEM", 3: "TEUK_ECUDA",
                 4: "TEUK_EUNSTABLE", 5: "TEUK_ETIMEOUT", 6: "TEUK_ESTATE"}
 

@@ -20,6 +20,9 @@
 // condition.  The co-state lam and mu are FP64 for FP64 instances; for FP32 instances
 // they are FP32, lam compensated like the forward state (value hi - c, each step's
 // increment added with Kahan's compensated sum), the gradient sums FP64 either way.
+#include <type_traits>
+
+#include "teuk_df.cuh"
 #include "teuk_internal.cuh"
 
 namespace teuk {
@@ -76,7 +79,8 @@ __device__ __forceinline__ Z<R> gld(const double2* p, size_t o) {
 
 template <typename T, typename R>
 __device__ __forceinline__ R cget(const T* tab, size_t pl, int k, size_t o) {
-    return (R)tab[(size_t)k * pl + o];
+    if constexpr (std::is_same<T, DF>::value) return (R)tab[(size_t)k * pl + o].to_double();
+    else return (R)tab[(size_t)k * pl + o];
 }
 
 // Cotangent of the averaged Phi~ at (col, j) produced by the angular term of the
@@ -349,6 +353,7 @@ __global__ void ordered_sum_kernel(const double* v, int64_t n, double* out) {
 void launch_adj_corrector(cudaStream_t st, const InstDev& d, const CoLevel& lam, const CoMu& mu) {
     dim3 g((d.nth + 127) / 128, d.nr - 1);
     if (d.prec == 0) adj_corrector_kernel<double, double><<<g, 128, 0, st>>>(d, lam, mu);
+    else if (d.prec == 3) adj_corrector_kernel<DF, double><<<g, 128, 0, st>>>(d, lam, mu);
     else adj_corrector_kernel<float, float><<<g, 128, 0, st>>>(d, lam, mu);
 }
 
@@ -356,12 +361,13 @@ void launch_adj_predictor(cudaStream_t st, const InstDev& d, const CoLevel& lin,
                           const double2* gbar, const CoLevel& lout) {
     dim3 g((d.nth + 127) / 128, d.nr);
     if (d.prec == 0) adj_predictor_kernel<double, double><<<g, 128, 0, st>>>(d, lin, mu, gbar, lout);
+    else if (d.prec == 3) adj_predictor_kernel<DF, double><<<g, 128, 0, st>>>(d, lin, mu, gbar, lout);
     else adj_predictor_kernel<float, float><<<g, 128, 0, st>>>(d, lin, mu, gbar, lout);
 }
 
 void launch_adj_init(cudaStream_t st, const InstDev& d, const double2* gbar, const CoLevel& out) {
     dim3 g((d.pitch + 127) / 128, d.nr);
-    if (d.prec == 0) adj_init_kernel<double><<<g, 128, 0, st>>>(d, gbar, out);
+    if (d.prec == 0 || d.prec == 3) adj_init_kernel<double><<<g, 128, 0, st>>>(d, gbar, out);
     else adj_init_kernel<float><<<g, 128, 0, st>>>(d, gbar, out);
 }
 
@@ -374,7 +380,8 @@ int adj_source_blocks(const InstDev& d) {
 void launch_adj_source(cudaStream_t st, const InstDev& d, int64_t n, const CoLevel& lam,
                        const CoMu& mu, double* part, unsigned* done, double* gA, double* gR) {
     const int nb = adj_source_blocks(d);
-    if (d.prec == 0) adj_source_kernel<double><<<nb, kSrcThreads, 0, st>>>(d, n, lam, mu, part, done, gA, gR);
+    if (d.prec == 0 || d.prec == 3)
+        adj_source_kernel<double><<<nb, kSrcThreads, 0, st>>>(d, n, lam, mu, part, done, gA, gR);
     else adj_source_kernel<float><<<nb, kSrcThreads, 0, st>>>(d, n, lam, mu, part, done, gA, gR);
 }
 

@@ -137,7 +137,8 @@ std::string derive(const teuk_params& p, Instance& I) {
     if (p.n_theta < 4 || p.n_theta > 1024) return "n_theta must be in [4, 1024]";
     if ((int64_t)p.n_rstar * p.n_theta > (int64_t)1 << 30) return "grid too large";
     if (!(p.rstar_max > p.rstar_min)) return "need rstar_max > rstar_min";
-    if (p.prec < 0 || p.prec > 2) return "prec must be TEUK_FP64, TEUK_FP32 or TEUK_FP32_KAHAN";
+    if (p.prec < 0 || p.prec > 3)
+        return "prec must be TEUK_FP64, TEUK_FP32, TEUK_FP32_KAHAN or TEUK_FP64_DF";
     if (p.wave_capacity < 0) return "wave_capacity must be >= 0";
     I.p = p;
     I.drs = (p.rstar_max - p.rstar_min) / (double)(p.n_rstar - 1);
@@ -225,7 +226,7 @@ teuk_status refresh_partition(teuk_ctx* c, Instance& I) {
     const int strip = eff_strip(c, I);
     const int nr = I.p.n_rstar;
     const int nb = (nr - 2 + strip - 1) / strip;
-    const double alpha = I.p.prec == TEUK_FP64 ? 0.1 : 0.25;
+    const double alpha = (I.p.prec == TEUK_FP64 || I.p.prec == TEUK_FP64_DF) ? 0.1 : 0.25;
     int wlo = nr, whi = 0;
     if (I.src_on) {
         wlo = std::min(I.sd.i_lo, I.sd.h_lo + 1);
@@ -272,7 +273,7 @@ teuk_status refresh_partitions(teuk_ctx* c) {
 teuk_status coef_tables(teuk_ctx* c, Instance& I) {
     if (I.coef_h) return TEUK_OK;
     const teuk_params& q = I.p;
-    const size_t cs = q.prec == TEUK_FP64 ? sizeof(double) : sizeof(float);
+    const size_t cs = q.prec == TEUK_FP64 ? sizeof(double) : q.prec == TEUK_FP64_DF ? sizeof(float2) : sizeof(float);
     const size_t cbytes = (size_t)kNCoef * q.n_rstar * I.pitch * cs;
     TK_CUDA(c, cudaMallocAsync(&I.coef_h, cbytes, c->stream));
     TK_CUDA(c, cudaMallocAsync(&I.coef_i, cbytes, c->stream));
@@ -380,7 +381,7 @@ extern "C" teuk_status teuk_create(const teuk_params* p, int n_instances, void* 
         launch_invert_tortoise(c->stream, q.M, q.a, q.rstar_min, I.drs, q.n_rstar, I.x_int,
                                I.x_half);
         c->launches++;
-        if (q.prec == TEUK_FP64) {  // the FP32 paths build theirs on the first adjoint call
+        if (q.prec == TEUK_FP64 || q.prec == TEUK_FP64_DF) {  // the FP32 paths build theirs on the first adjoint call
             const teuk_status e = coef_tables(c, I);
             if (e != TEUK_OK) return fail(e);
         } else {
@@ -447,8 +448,9 @@ extern "C" teuk_status teuk_set_source(teuk_ctx* c, int instance, const teuk_orb
     if (I.amps) { cudaFreeAsync(I.amps, c->stream); I.amps = nullptr; }
     size_t nwi = (size_t)sd.nj * sd.ni, nwh = (size_t)sd.nj * sd.nh;
     // P, P_half, dP, dP_half (double2), then the step kernels' copies Q_int, Q_half
-    const size_t qe = q.prec == TEUK_FP64 ? sizeof(double2) : sizeof(float2);
-    sd.q_stride = q.prec == TEUK_FP64 ? sd.nj : (sd.nj + 1) / 2 * 2;
+    const bool q16 = q.prec == TEUK_FP64 || q.prec == TEUK_FP64_DF;   // 16-byte profile entries
+    const size_t qe = q16 ? 16 : sizeof(float2);
+    sd.q_stride = q16 ? sd.nj : (sd.nj + 1) / 2 * 2;
     const size_t qi_bytes = qe * sd.q_stride * sd.ni, qh_bytes = qe * sd.q_stride * sd.nh;
     TK_CUDA(c, cudaMallocAsync((void**)&I.P_win, sizeof(double2) * 2 * (nwi + nwh) + qi_bytes + qh_bytes,
                                c->stream));
@@ -1105,7 +1107,7 @@ extern "C" teuk_status teuk_adjoint_n(teuk_ctx* c, int instance, int64_t step0, 
     if (st) return st;
     // co-state planes ([nr][pitch] complex): FP64 for FP64 instances, else FP32 with
     // compensation planes for lam
-    const bool co32 = I.p.prec != TEUK_FP64;
+    const bool co32 = I.p.prec == TEUK_FP32 || I.p.prec == TEUK_FP32_KAHAN;
     const size_t plane = (size_t)I.p.n_rstar * I.pitch * (co32 ? sizeof(float2) : sizeof(double2));
     AdjBuffers B(s);
     CoLevel lam[2] = {};

@@ -8,7 +8,7 @@ namespace teuk {
 
 // u-layout [4][nth][nr] (Phi_R, Phi_I, Pi_R, Pi_I) -> planes of buffer b.  The
 // compensated state is split as hi = fl32(v), c = fl32(hi - v), so hi - c = v to
-// about 2^-48 relative.
+// about 2^-48 relative; the double-float state as hi = fl32(v), lo = fl32(v - hi).
 template <class P>
 __global__ void import_state_kernel(InstDev d, int b, const double* u) {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -16,7 +16,12 @@ __global__ void import_state_kernel(InstDev d, int b, const double* u) {
     if (i >= d.nr || j >= d.nth) return;
     size_t np = (size_t)d.nr * d.nth, q = (size_t)j * d.nr + i, o = node_index(d, i, j);
     double v[4] = {u[q], u[np + q], u[2 * np + q], u[3 * np + q]};
-    if constexpr (sizeof(typename P::T) == 8) {
+    if constexpr (P::kind == kDF) {
+        DF h[4];
+        for (int k = 0; k < 4; ++k) h[k] = DF(v[k]);
+        ((float4*)d.buf[b][0])[o] = make_float4(h[0].hi, h[1].hi, h[2].hi, h[3].hi);
+        ((float4*)d.buf[b][1])[o] = make_float4(h[0].lo, h[1].lo, h[2].lo, h[3].lo);
+    } else if constexpr (P::kind == kFP64) {
         ((double2*)d.buf[b][0])[o] = make_double2(v[0], v[1]);
         ((double2*)d.buf[b][1])[o] = make_double2(v[2], v[3]);
     } else if constexpr (!P::kahan) {
@@ -40,12 +45,7 @@ __global__ void export_state_kernel(InstDev d, int b, double* u) {
     size_t np = (size_t)d.nr * d.nth, q = (size_t)j * d.nr + i, o = node_index(d, i, j);
     NodeV<P> n = Planes<P>::of(d, b).load(o);
     double v[4];
-    if constexpr (P::kahan) {
-        v[0] = (double)n.F.re - (double)n.Fc.re; v[1] = (double)n.F.im - (double)n.Fc.im;
-        v[2] = (double)n.Pp.re - (double)n.Pc.re; v[3] = (double)n.Pp.im - (double)n.Pc.im;
-    } else {
-        v[0] = (double)n.F.re; v[1] = (double)n.F.im; v[2] = (double)n.Pp.re; v[3] = (double)n.Pp.im;
-    }
+    n.v64(v);
     u[q] = v[0]; u[np + q] = v[1]; u[2 * np + q] = v[2]; u[3 * np + q] = v[3];
 }
 
@@ -56,8 +56,9 @@ __global__ void scan_finite_kernel(InstDev d, int b) {
     int i = blockIdx.y;
     if (i >= d.nr || j >= d.nth) return;
     NodeV<P> n = Planes<P>::of(d, b).load(node_index(d, i, j));
-    bool ok = isfinite((double)n.F.re) && isfinite((double)n.F.im) && isfinite((double)n.Pp.re) &&
-              isfinite((double)n.Pp.im);
+    double v[4];
+    n.v64(v);
+    bool ok = isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2]) && isfinite(v[3]);
     if constexpr (P::kahan)
         ok = ok && isfinite(n.Fc.re) && isfinite(n.Fc.im) && isfinite(n.Pc.re) && isfinite(n.Pc.im);
     if (!ok) atomicOr(d.status, (unsigned)ST_NONFINITE);
@@ -89,6 +90,7 @@ void launch_import_state(cudaStream_t st, const InstDev& d, int bin, const doubl
     dim3 g((d.nth + 127) / 128, d.nr);
     if (d.prec == 0) import_state_kernel<P64><<<g, 128, 0, st>>>(d, bin, u);
     else if (d.prec == 1) import_state_kernel<P32><<<g, 128, 0, st>>>(d, bin, u);
+    else if (d.prec == 3) import_state_kernel<PD><<<g, 128, 0, st>>>(d, bin, u);
     else import_state_kernel<PK><<<g, 128, 0, st>>>(d, bin, u);
 }
 
@@ -96,6 +98,7 @@ void launch_export_state(cudaStream_t st, const InstDev& d, int bin, double* u) 
     dim3 g((d.nth + 127) / 128, d.nr);
     if (d.prec == 0) export_state_kernel<P64><<<g, 128, 0, st>>>(d, bin, u);
     else if (d.prec == 1) export_state_kernel<P32><<<g, 128, 0, st>>>(d, bin, u);
+    else if (d.prec == 3) export_state_kernel<PD><<<g, 128, 0, st>>>(d, bin, u);
     else export_state_kernel<PK><<<g, 128, 0, st>>>(d, bin, u);
 }
 
@@ -103,6 +106,7 @@ void launch_scan_finite(cudaStream_t st, const InstDev& d, int bin) {
     dim3 g((d.nth + 127) / 128, d.nr);
     if (d.prec == 0) scan_finite_kernel<P64><<<g, 128, 0, st>>>(d, bin);
     else if (d.prec == 1) scan_finite_kernel<P32><<<g, 128, 0, st>>>(d, bin);
+    else if (d.prec == 3) scan_finite_kernel<PD><<<g, 128, 0, st>>>(d, bin);
     else scan_finite_kernel<PK><<<g, 128, 0, st>>>(d, bin);
 }
 

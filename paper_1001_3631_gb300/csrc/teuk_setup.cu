@@ -15,6 +15,7 @@
 //   Theta[F] = F_thth + cot F_th - V F,  V = (m + s cos)^2 / sin^2 - s
 // evaluated at r = r_+ + x with x from the inversion of Eq. (2), so that
 // Delta = x (x + r_+ - r_-) keeps full relative precision next to the horizon.
+#include "teuk_df.cuh"
 #include "teuk_internal.cuh"
 
 namespace teuk {
@@ -162,8 +163,14 @@ __global__ void profile_kernel(double M, double a, double rstar_min, double drs,
     double th = (src.j_lo + jj + 0.5) * dth;
     // column-major copy for the step kernels, in their arithmetic type
     auto put_q = [&](const void* q, size_t idx, double2 v) {
-        if (prec == 0) ((double2*)q)[idx] = v;
-        else ((float2*)q)[idx] = make_float2((float)v.x, (float)v.y);
+        if (prec == 0) {
+            ((double2*)q)[idx] = v;
+        } else if (prec == 3) {   // double-float: re.hi, re.lo, im.hi, im.lo
+            const DF x(v.x), y(v.y);
+            ((float4*)q)[idx] = make_float4(x.hi, x.lo, y.hi, y.lo);
+        } else {
+            ((float2*)q)[idx] = make_float2((float)v.x, (float)v.y);
+        }
     };
     if (k < src.ni) {
         int i = src.i_lo + k;
@@ -274,6 +281,9 @@ void launch_coefficients(cudaStream_t st, int prec, double M, double a, int s, i
     if (prec == 0)
         coef_kernel<double><<<g, 128, 0, st>>>(M, a, s, m, rstar_min, drs, dth, dt, nr, nth, pitch,
                                                x_int, x_half, (double*)coef_h, (double*)coef_i);
+    else if (prec == 3)
+        coef_kernel<DF><<<g, 128, 0, st>>>(M, a, s, m, rstar_min, drs, dth, dt, nr, nth, pitch,
+                                           x_int, x_half, (DF*)coef_h, (DF*)coef_i);
     else
         coef_kernel<float><<<g, 128, 0, st>>>(M, a, s, m, rstar_min, drs, dth, dt, nr, nth, pitch,
                                               x_int, x_half, (float*)coef_h, (float*)coef_i);

@@ -106,7 +106,7 @@ constexpr unsigned long long kRingWaitNs = 1000000000ull;  // a slot wait gives 
 template <class P, int R>
 struct ColumnRing {
     static constexpr int kSlots = R;
-    static constexpr bool kTabs = sizeof(typename P::T) == 4;
+    static constexpr bool kTabs = uses_1d_tables<P>();
     __host__ __device__ static unsigned slot_bytes(int threads) {
         return (unsigned)P::planes * (unsigned)threads * 16u + (kTabs ? (unsigned)sizeof(RTab2) : 0u);
     }
@@ -223,7 +223,7 @@ __device__ __forceinline__ bool strip_step(const InstDev& d, int64_t step, int b
                                            int c1, ColumnRing<P, R>& ring, typename P::T* xbuf) {
     using T = typename P::T;
     using C = Cx<T>;
-    constexpr bool kTabsPath = sizeof(T) == 4;   // FP32 paths: coefficients from 1D tables
+    constexpr bool kTabsPath = uses_1d_tables<P>();   // FP32 paths: coefficients from 1D tables
     const int j = threadIdx.x;
     const int nth = d.nth;
     const bool row_ok = j < nth;
@@ -315,6 +315,8 @@ __device__ __forceinline__ bool strip_step(const InstDev& d, int64_t step, int b
                 cfh[k] = cf2[k].x;
                 cfi[k] = cf2[k].y;
             }
+        } else if constexpr (P::kind == kDF) {
+            coefs_df(d, true, col, j, (DF*)cfh);
         } else {
             coefs64(d, true, col, j, (double*)cfh);
         }
@@ -330,7 +332,10 @@ __device__ __forceinline__ bool strip_step(const InstDev& d, int64_t step, int b
         // Hs = g Hs(0) and DpS = (Dp_R(-1) + Dp_L(-1))/2 = (1 - g) (Fb_R + Fb_L)(0)/2
         T* mine = xb + 4 * (j + 1);
         auto put = [](T* e, C a, C b) {
-            if constexpr (sizeof(T) == 4) {
+            if constexpr (P::kind == kDF) {
+                ((float4*)e)[0] = make_float4(a.re.hi, a.re.lo, a.im.hi, a.im.lo);
+                ((float4*)e)[1] = make_float4(b.re.hi, b.re.lo, b.im.hi, b.im.lo);
+            } else if constexpr (sizeof(T) == 4) {
                 *(float4*)e = make_float4(a.re, a.im, b.re, b.im);
             } else {
                 ((double2*)e)[0] = make_double2(a.re, a.im);
@@ -342,7 +347,13 @@ __device__ __forceinline__ bool strip_step(const InstDev& d, int64_t step, int b
         if (bot) put(xb, g * row.Hs, (T(1) - g) * C::half_sum(Rh.Fb, Lh.Fb));
         __syncthreads();
         C Hs_p, Hs_m, DpS_m;
-        if constexpr (sizeof(T) == 4) {
+        if constexpr (P::kind == kDF) {
+            const float4 a = *(const float4*)(mine + 4);
+            const float4 b0 = ((const float4*)(mine - 4))[0], b1 = ((const float4*)(mine - 4))[1];
+            Hs_p = {DF(a.x, a.y), DF(a.z, a.w)};
+            Hs_m = {DF(b0.x, b0.y), DF(b0.z, b0.w)};
+            DpS_m = {DF(b1.x, b1.y), DF(b1.z, b1.w)};
+        } else if constexpr (sizeof(T) == 4) {
             const float2 a = *(const float2*)(mine + 4);
             const float4 b = *(const float4*)(mine - 4);
             Hs_p = {a.x, a.y};
@@ -361,6 +372,8 @@ __device__ __forceinline__ bool strip_step(const InstDev& d, int64_t step, int b
         if constexpr (kTabsPath) {
 #pragma unroll
             for (int k = 0; k < kNCoef; ++k) cf[k] = cfi[k];
+        } else if constexpr (P::kind == kDF) {
+            coefs_df(d, false, cc, j, (DF*)cf);
         } else {
             coefs64(d, false, cc, j, (double*)cf);
         }
@@ -637,6 +650,7 @@ static int grid_for(int threads) {
 int batched_grid(int prec, int threads) {
     if (prec == 0) return grid_for<P64>(threads);
     if (prec == 1) return grid_for<P32>(threads);
+    if (prec == 3) return grid_for<PD>(threads);
     return grid_for<PK>(threads);
 }
 
@@ -651,6 +665,7 @@ static void launch_batched_p(cudaStream_t st, const BatchDev& b, int grid, int t
 void launch_batched_step(cudaStream_t st, int prec, const BatchDev& b, int grid, int threads) {
     if (prec == 0) launch_batched_p<P64>(st, b, grid, threads);
     else if (prec == 1) launch_batched_p<P32>(st, b, grid, threads);
+    else if (prec == 3) launch_batched_p<PD>(st, b, grid, threads);
     else launch_batched_p<PK>(st, b, grid, threads);
 }
 
@@ -658,6 +673,7 @@ void launch_batched_extract(cudaStream_t st, int prec, const BatchDev& b, int ma
     dim3 g((max_nth + 127) / 128, b.n_inst);
     if (prec == 0) batched_extract_kernel<P64><<<g, 128, 0, st>>>(b);
     else if (prec == 1) batched_extract_kernel<P32><<<g, 128, 0, st>>>(b);
+    else if (prec == 3) batched_extract_kernel<PD><<<g, 128, 0, st>>>(b);
     else batched_extract_kernel<PK><<<g, 128, 0, st>>>(b);
 }
 
@@ -702,6 +718,7 @@ static int resident_p(int threads) {
 int step_resident_blocks(int prec, int threads) {
     if (prec == 0) return resident_p<P64>(threads);
     if (prec == 1) return resident_p<P32>(threads);
+    if (prec == 3) return resident_p<PD>(threads);
     return resident_p<PK>(threads);
 }
 
@@ -709,6 +726,7 @@ void launch_step(cudaStream_t st, const InstDev& d, int64_t step, int bin, int s
                  const int* part) {
     if (d.prec == 0) launch_step_p<P64>(st, d, step, bin, strip, part);
     else if (d.prec == 1) launch_step_p<P32>(st, d, step, bin, strip, part);
+    else if (d.prec == 3) launch_step_p<PD>(st, d, step, bin, strip, part);
     else launch_step_p<PK>(st, d, step, bin, strip, part);
 }
 
@@ -729,6 +747,7 @@ cudaError_t prepare_step_kernels() {
     cudaError_t e = prepare_p<P64>();
     if (e == cudaSuccess) e = prepare_p<P32>();
     if (e == cudaSuccess) e = prepare_p<PK>();
+    if (e == cudaSuccess) e = prepare_p<PD>();
     return e;
 }
 
@@ -736,6 +755,7 @@ void launch_extract(cudaStream_t st, const InstDev& d, int64_t step, int bin) {
     int blocks = (d.nth + 127) / 128;
     if (d.prec == 0) extract_kernel<P64><<<blocks, 128, 0, st>>>(d, step, bin);
     else if (d.prec == 1) extract_kernel<P32><<<blocks, 128, 0, st>>>(d, step, bin);
+    else if (d.prec == 3) extract_kernel<PD><<<blocks, 128, 0, st>>>(d, step, bin);
     else extract_kernel<PK><<<blocks, 128, 0, st>>>(d, step, bin);
 }
 

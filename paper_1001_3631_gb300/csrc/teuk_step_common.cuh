@@ -2,6 +2,7 @@
 // precision policies, node loads/stores, the compensated update, the predictor
 // (Eq. 13) and corrector (Eq. 14) bodies.  See teuk_step.cu for the scheme.
 #pragma once
+#include "teuk_df.cuh"
 #include "teuk_internal.cuh"
 
 namespace teuk {
@@ -64,6 +65,81 @@ template <>
 __device__ __forceinline__ Cx<float> Cx<float>::half_sum(Cx<float> a, Cx<float> b) {
     return up(__fmul2_rn(bc(0.5f), __fadd2_rn(pk(a), pk(b))));
 }
+// Complex double-float values in paired instructions: the high parts (re, im) and the
+// low parts (re, im) each form a register pair, and every step of the scalar
+// double-float operation (teuk_df.cuh) runs on both components at once, with the same
+// roundings, so the results equal the scalar code's.
+struct DF2 { float2 hi, lo; };
+__device__ __forceinline__ DF2 pk2(Cx<DF> a) {
+    return {make_float2(a.re.hi, a.im.hi), make_float2(a.re.lo, a.im.lo)};
+}
+__device__ __forceinline__ Cx<DF> up2(DF2 v) { return {DF(v.hi.x, v.lo.x), DF(v.hi.y, v.lo.y)}; }
+__device__ __forceinline__ float2 p_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 p_sub(float2 a, float2 b) { return __ffma2_rn(bc(-1.0f), b, a); }   // exact product
+__device__ __forceinline__ float2 p_neg(float2 a) { return __fmul2_rn(bc(-1.0f), a); }
+// s + e = a + b exactly (per component)
+__device__ __forceinline__ DF2 p_two_sum(float2 a, float2 b) {
+    const float2 s = p_add(a, b);
+    const float2 bb = p_sub(s, a);
+    return {s, p_add(p_sub(a, p_sub(s, bb)), p_sub(b, bb))};
+}
+// s + e = a - b exactly (two_sum with -b written out)
+__device__ __forceinline__ DF2 p_two_diff(float2 a, float2 b) {
+    const float2 s = p_sub(a, b);
+    const float2 bb = p_sub(s, a);
+    return {s, p_sub(p_sub(a, p_sub(s, bb)), p_add(b, bb))};
+}
+__device__ __forceinline__ DF2 p_fast_two_sum(float2 a, float2 b) {
+    const float2 s = p_add(a, b);
+    return {s, p_sub(b, p_sub(s, a))};
+}
+__device__ __forceinline__ Cx<DF> operator+(Cx<DF> x, Cx<DF> y) {
+    const DF2 X = pk2(x), Y = pk2(y);
+    const DF2 S = p_two_sum(X.hi, Y.hi);
+    return up2(p_fast_two_sum(S.hi, p_add(S.lo, p_add(X.lo, Y.lo))));
+}
+__device__ __forceinline__ Cx<DF> operator-(Cx<DF> x, Cx<DF> y) {
+    const DF2 X = pk2(x), Y = pk2(y);
+    const DF2 S = p_two_diff(X.hi, Y.hi);
+    return up2(p_fast_two_sum(S.hi, p_add(S.lo, p_sub(X.lo, Y.lo))));
+}
+__device__ __forceinline__ Cx<DF> neg(Cx<DF> a) {
+    const DF2 A = pk2(a);
+    return up2({p_neg(A.hi), p_neg(A.lo)});
+}
+// a * b + c per component, a given as pairs (hi, lo): the double-float tfma
+__device__ __forceinline__ DF2 p_tfma(DF2 A, DF2 B, DF2 C) {
+    const float2 p = __fmul2_rn(A.hi, B.hi);
+    float2 e = __ffma2_rn(A.hi, B.hi, p_neg(p));
+    e = __ffma2_rn(A.hi, B.lo, e);
+    e = __ffma2_rn(A.lo, B.hi, e);
+    const DF2 S = p_two_sum(p, C.hi);
+    return p_fast_two_sum(S.hi, p_add(S.lo, p_add(e, C.lo)));
+}
+__device__ __forceinline__ DF2 bc2(DF s) { return {bc(s.hi), bc(s.lo)}; }
+__device__ __forceinline__ Cx<DF> operator*(DF s, Cx<DF> a) {
+    const DF2 S = bc2(s), A = pk2(a);
+    const float2 p = __fmul2_rn(S.hi, A.hi);
+    float2 e = __ffma2_rn(S.hi, A.hi, p_neg(p));
+    e = __ffma2_rn(S.hi, A.lo, e);
+    e = __ffma2_rn(S.lo, A.hi, e);
+    return up2(p_fast_two_sum(p, e));
+}
+__device__ __forceinline__ Cx<DF> rmac(Cx<DF> acc, DF s, Cx<DF> z) {
+    return up2(p_tfma(bc2(s), pk2(z), pk2(acc)));
+}
+// same order as the generic cmac: the ci terms first, then the cr terms
+__device__ __forceinline__ Cx<DF> cmac(Cx<DF> acc, DF cr, DF ci, Cx<DF> z) {
+    const DF2 Z = pk2(z);
+    const DF2 Zs = {make_float2(Z.hi.y, Z.hi.x), make_float2(Z.lo.y, Z.lo.x)};   // (im, re)
+    const DF2 Ci = {make_float2(-ci.hi, ci.hi), make_float2(-ci.lo, ci.lo)};
+    return up2(p_tfma(bc2(cr), Z, p_tfma(Ci, Zs, pk2(acc))));
+}
+template <>
+__device__ __forceinline__ Cx<DF> Cx<DF>::half_sum(Cx<DF> a, Cx<DF> b) {
+    const DF2 s = pk2(a + b);
+    return up2({__fmul2_rn(bc(0.5f), s.hi), __fmul2_rn(bc(0.5f), s.lo)});
+}
 // (a + b)/2 + c (the halving is exact, so one fused operation rounds the same)
 template <typename T>
 __device__ __forceinline__ Cx<T> half_sum_add(Cx<T> a, Cx<T> b, Cx<T> c) {
@@ -77,25 +153,35 @@ __device__ __forceinline__ Cx<float> rmac(Cx<float> acc, float s, Cx<float> z) {
 }
 
 // ---------------------------------------------------------------- precisions
-// planes: 16-byte planes per state buffer (the layout in teuk_internal.cuh);
-// blocks256: resident blocks per SM that the register budget of the step kernel for
-// columns of up to 256 rows aims at (two: at three the FP32 paths fit in 80 registers
-// but run no faster, being issue-bound)
+// kind: the teuk_precision value; planes: 16-byte planes per state buffer (the layout
+// in teuk_internal.cuh); blocks256: resident blocks per SM that the register budget of
+// the step kernel for columns of up to 256 rows aims at (two: at three the FP32 paths
+// fit in 80 registers but run no faster, being issue-bound)
+enum PrecKind { kFP64 = 0, kFP32 = 1, kKahan = 2, kDF = 3 };
 struct P64 {
     using T = double;
     static constexpr bool kahan = false;
-    static constexpr int planes = 2, blocks256 = 2;
+    static constexpr int kind = kFP64, planes = 2, blocks256 = 2;
 };
 struct P32 {
     using T = float;
     static constexpr bool kahan = false;
-    static constexpr int planes = 1, blocks256 = 2;
+    static constexpr int kind = kFP32, planes = 1, blocks256 = 2;
 };
 struct PK {
     using T = float;
     static constexpr bool kahan = true;
-    static constexpr int planes = 2, blocks256 = 2;
+    static constexpr int kind = kKahan, planes = 2, blocks256 = 2;
 };
+// FP64-equivalent: double-float state, coefficients and arithmetic on the FP32 units
+struct PD {
+    using T = DF;
+    static constexpr bool kahan = false;
+    static constexpr int kind = kDF, planes = 2, blocks256 = 2;
+};
+// the FP32 paths that form their coefficients from 1D tables
+template <class P>
+__host__ __device__ constexpr bool uses_1d_tables() { return P::kind == kFP32 || P::kind == kKahan; }
 
 // Compensated add (Kahan 1965) of both components of a complex value: the represented
 // value is hi - c.
@@ -139,9 +225,21 @@ struct NodeV {
         else return Pp - o.Pp;
     }
     __device__ __forceinline__ double2 phi64() const {
-        if constexpr (P::kahan)
-            return make_double2((double)F.re - (double)Fc.re, (double)F.im - (double)Fc.im);
-        else return make_double2((double)F.re, (double)F.im);
+        double v[4];
+        v64(v);
+        return make_double2(v[0], v[1]);
+    }
+    // {Phi_R, Phi_I, Pi_R, Pi_I} as FP64
+    __device__ __forceinline__ void v64(double* v) const {
+        if constexpr (P::kind == kDF) {
+            v[0] = F.re.to_double(); v[1] = F.im.to_double();
+            v[2] = Pp.re.to_double(); v[3] = Pp.im.to_double();
+        } else if constexpr (P::kahan) {
+            v[0] = (double)F.re - (double)Fc.re; v[1] = (double)F.im - (double)Fc.im;
+            v[2] = (double)Pp.re - (double)Pc.re; v[3] = (double)Pp.im - (double)Pc.im;
+        } else {
+            v[0] = (double)F.re; v[1] = (double)F.im; v[2] = (double)Pp.re; v[3] = (double)Pp.im;
+        }
     }
     __device__ __forceinline__ void update(Cx<T> dF, Cx<T> dP) {
         if constexpr (P::kahan) {
@@ -232,6 +330,34 @@ template <> struct Planes<PK> {
     }
 };
 
+template <> struct Planes<PD> {
+    float4* hi; float4* lo;   // {Phi, Pi} high parts, low parts
+    __device__ __forceinline__ static Planes of(const InstDev& d, int b) {
+        return {(float4*)d.buf[b][0], (float4*)d.buf[b][1]};
+    }
+    __device__ __forceinline__ static Planes at(void* base, unsigned stride) {
+        return {(float4*)base, (float4*)base + stride};
+    }
+    __device__ __forceinline__ NodeV<PD> load(size_t o) const {
+        NodeV<PD> n;
+        const float4 a = hi[o], b = lo[o];
+        n.F = {DF(a.x, b.x), DF(a.y, b.y)};
+        n.Pp = {DF(a.z, b.z), DF(a.w, b.w)};
+        n.Fc = n.Pc = Cx<DF>::zero();
+        return n;
+    }
+    __device__ __forceinline__ NodeV<PD> load_phi(size_t o) const {
+        NodeV<PD> n = NodeV<PD>::zero();
+        const float2 a = *(const float2*)(hi + o), b = *(const float2*)(lo + o);
+        n.F = {DF(a.x, b.x), DF(a.y, b.y)};
+        return n;
+    }
+    __device__ __forceinline__ void store(size_t o, const NodeV<PD>& n) const {
+        hi[o] = make_float4(n.F.re.hi, n.F.im.hi, n.Pp.re.hi, n.Pp.im.hi);
+        lo[o] = make_float4(n.F.re.lo, n.F.im.lo, n.Pp.re.lo, n.Pp.im.lo);
+    }
+};
+
 // ---------------------------------------------------------------- half nodes
 template <typename T>
 struct Half { Cx<T> Fb, Pb, dF, dP; };
@@ -246,8 +372,8 @@ __device__ __forceinline__ Half<typename P::T> half_prep(const NodeV<P>& own, co
         h.Fb = T(0.5) * ((own.F + nb.F) - (own.Fc + nb.Fc));
         h.Pb = T(0.5) * ((own.Pp + nb.Pp) - (own.Pc + nb.Pc));
     } else {
-        h.Fb = T(0.5) * (own.F + nb.F);
-        h.Pb = T(0.5) * (own.Pp + nb.Pp);
+        h.Fb = Cx<T>::half_sum(own.F, nb.F);
+        h.Pb = Cx<T>::half_sum(own.Pp, nb.Pp);
     }
     h.dF = nb.dphi(own);
     h.dP = nb.dpi(own);
@@ -293,7 +419,7 @@ template <class P>
 struct RowTab {
     ThPair t;
     __device__ __forceinline__ void load(const ThTab* tab, int j, bool ok) {
-        if constexpr (sizeof(typename P::T) == 4) {
+        if constexpr (uses_1d_tables<P>()) {
             const ThTab h = ok ? tab[j] : ThTab{};
             t = ThPair{bc(h.sin2), bc(h.cs), bc(h.V), bc(h.thp), bc(h.thm)};
         }
@@ -331,6 +457,16 @@ __device__ __forceinline__ void form_coefs2(const RTab2& t, const ThPair& h, flo
 __device__ __forceinline__ void coefs64(const InstDev& d, bool half, int i, int j, double* cf) {
     load_coefs((const double*)(half ? d.coef_h : d.coef_i), plane_elems(d), node_index(d, i, j), cf);
 }
+// Double-float coefficients (FP64-equivalent path), from its 2D tables of (hi, lo) pairs.
+__device__ __forceinline__ void coefs_df(const InstDev& d, bool half, int i, int j, DF* cf) {
+    const float2* tab = (const float2*)(half ? d.coef_h : d.coef_i);
+    const size_t pl = plane_elems(d), o = node_index(d, i, j);
+#pragma unroll
+    for (int k = 0; k < kNCoef; ++k) {
+        const float2 v = __ldg(tab + k * pl + o);
+        cf[k] = DF(v.x, v.y);
+    }
+}
 
 // Eq. (13) at the own half node, as an increment on the averaged state.
 template <typename T>
@@ -367,6 +503,8 @@ __device__ __forceinline__ double2 source_factor(const InstDev& d, int64_t step,
 template <typename T> struct V2T;
 template <> struct V2T<float> { using V = float2; };
 template <> struct V2T<double> { using V = double2; };
+struct DFC { DF x, y; };   // complex double-float as stored: x.hi, x.lo, y.hi, y.lo
+template <> struct V2T<DF> { using V = DFC; };
 
 template <typename T>
 __device__ __forceinline__ Cx<T> source_at(const void* q, int stride, Cx<T> fac, int a, int b) {

@@ -11,10 +11,11 @@ import os
 import numpy as np
 
 from . import _lib
-from ._lib import TEUK_FP32, TEUK_FP32_KAHAN, TEUK_FP64, check, ptr
+from ._lib import TEUK_FP32, TEUK_FP32_KAHAN, TEUK_FP64, TEUK_FP64_DF, check, ptr
 
-PREC = {"fp64": TEUK_FP64, "fp32": TEUK_FP32, "fp32_kahan": TEUK_FP32_KAHAN,
-        TEUK_FP64: TEUK_FP64, TEUK_FP32: TEUK_FP32, TEUK_FP32_KAHAN: TEUK_FP32_KAHAN}
+PREC = {"fp64": TEUK_FP64, "fp32": TEUK_FP32, "fp32_kahan": TEUK_FP32_KAHAN, "fp64_df": TEUK_FP64_DF,
+        TEUK_FP64: TEUK_FP64, TEUK_FP32: TEUK_FP32, TEUK_FP32_KAHAN: TEUK_FP32_KAHAN,
+        TEUK_FP64_DF: TEUK_FP64_DF}
 
 PARAM_DEFAULTS = dict(s=-2, m=2, M=1.0, a=0.9, rstar_min=-50.0, rstar_max=150.0, n_rstar=800,
                       n_theta=64, courant=0.5, dt_rule=1, dt=0.0, rstar_ext=140.0,
