@@ -445,7 +445,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the accuracy, end-to-end and CPU-baseline legs")
-    ap.add_argument("--only", choices=["fp32_kahan", "fp64"], default=None,
+    ap.add_argument("--only", choices=["fp32_kahan", "fp64", "fp64_df"], default=None,
                     help="time one path only (for profiler captures)")
     ap.add_argument("--accuracy-steps", type=int, default=4000)
     ap.add_argument("--precision-sweep", action="store_true",
@@ -482,11 +482,15 @@ def main():
     s_k.close()
     s_d, ms_d, launches_d, _, clocks_d = time_path("fp64", cfg, S, K, W, world, local)
     s_d.close()
+    s_f, ms_f, _, _, clocks_f = time_path("fp64_df", cfg, S, K, W, world, local)
+    s_f.close()
     ms_k_all = reduce_max(ms_k, world)
     ms_d_all = reduce_max(ms_d, world)
+    ms_f_all = reduce_max(ms_f, world)
     units = K * S * npts
     val_k, tk = aggregate(ms_k_all, [units] * world)
     val_d, td = aggregate(ms_d_all, [units] * world)
+    val_f, tf = aggregate(ms_f_all, [units] * world)
 
     if rank != 0:
         if world > 1:
@@ -521,6 +525,13 @@ def main():
                               "hbm_frac": FP64_BYTES_PER_UPDATE * npts / (avg_d * 1e-3) / 1e9 / peak,
                               "kernel": "step_kernel<P64>"},
                  "clocks": clocks_d},
+        "fp64_df": {"value": val_f, "unit": "updates/s", "ms_per_step": tf / K,
+                    "note": "FP64-equivalent double-float path (hi + lo FP32 pairs) on the FP32 units",
+                    "roofline": {"bound": "hbm", "achieved": FP64_BYTES_PER_UPDATE * npts / (tf / step_launches * 1e-3) / 1e9,
+                                 "peak": peak, "unit": "GB/s",
+                                 "frac": FP64_BYTES_PER_UPDATE * npts / (tf / step_launches * 1e-3) / 1e9 / peak,
+                                 "bytes_per_update": FP64_BYTES_PER_UPDATE, "kernel": "step_kernel<PD>"},
+                    "over_fp64": val_f / val_d, "clocks": clocks_f},
         "fp32_kahan_over_fp64": val_k / val_d,
         "gpu_launches": int(launches_k),
         "clocks": clocks,

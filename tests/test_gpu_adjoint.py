@@ -38,6 +38,21 @@ def test_cotangent_mode_matches_oracle_adjoint(orc, m):
     assert gr == pytest.approx(gr_o, rel=1e-11)
 
 
+def test_fp64_df_instance_adjoint_matches_oracle(orc):
+    # double-float instances: FP64 co-state on the double-float coefficient tables
+    params = dict(SMALL, m=2)
+    n, r0 = 30, 8.0
+    amps = inputs.amplitudes(n, seed=5005)
+    gw = np.random.default_rng(12).standard_normal((n, 8, 2))
+    p = oracle_params(orc, params, r0)
+    ga_o, gr_o, _ = orc.adjoint(p, orc.orbit_source(p), gw, amps=amps)
+    with TeukSolver(dict(params, prec="fp64_df", wave_capacity=n + 1)) as s:
+        s.set_source(r0, amps)
+        ga, gr, _ = s.adjoint(n, step0=0, grad_wave=gw)
+    assert rel(ga, ga_o) <= 1e-11
+    assert gr == pytest.approx(gr_o, rel=1e-11)
+
+
 # FP32 instances run the co-state in compensated FP32.  Against the oracle's FP64
 # adjoint (cotangent mode: no forward run, so only the FP32 rounding of the coefficient
 # tables and of the co-state arithmetic separate them) the gradients agree to ~1e-6

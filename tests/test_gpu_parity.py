@@ -77,6 +77,48 @@ def test_fp64_small_grids_random_state_and_source(orc, case):
             assert np.array_equal(ug, ref[0]) and np.array_equal(wg, ref[1])
 
 
+# FP64-equivalent double-float path (hi + lo FP32 pairs, ~48 significant bits): held to
+# the FP64 bound (measured 6e-15 on these grids, 3.9e-14 on the 2000-step run)
+@pytest.mark.parametrize("case", SMALL)
+def test_fp64_df_small_grids_random_state_and_source(orc, case):
+    nr, nth, m, a, (lo, hi), r0, ext = case
+    params = dict(s=-2, m=m, a=a, rstar_min=lo, rstar_max=hi, n_rstar=nr, n_theta=nth,
+                  rstar_ext=ext, dt_rule=1, courant=0.5)
+    u0 = inputs.random_state(nth, nr, seed=nr + nth)
+    amps = inputs.amplitudes(40, seed=nr)
+    uo, wo = oracle_run(orc, params, r0, 37, u0, amps)
+    ref = None
+    for strip, pers in ((0, False), (5, False), (nth, False), (0, True)):
+        ug, wg, first = gpu_run(params, r0, 37, u0, amps, prec="fp64_df", strip=strip,
+                                persistent=pers)
+        assert first == 0 and wg.shape == wo.shape
+        assert rel(ug, uo) <= FP64_TOL, (strip, pers, rel(ug, uo))
+        assert rel(wg, wo) <= FP64_TOL, (strip, pers, rel(wg, wo))
+        if ref is None:
+            ref = (ug, wg)
+        else:
+            assert np.array_equal(ug, ref[0]) and np.array_equal(wg, ref[1])
+
+
+def test_fp64_df_single_mode_800x64_full_run(orc):
+    cfg = inputs.SINGLE_MODE_800x64
+    uo, wo = oracle_run(orc, cfg["params"], cfg["r0"], cfg["steps"])
+    ug, wg, _ = gpu_run(cfg["params"], cfg["r0"], cfg["steps"], prec="fp64_df")
+    print("FP64-DF 800x64x2000: state rel L2 %.3e  waveform rel L2 %.3e" % (rel(ug, uo), rel(wg, wo)))
+    assert rel(ug, uo) <= FP64_TOL
+    assert rel(wg, wo) <= FP64_TOL
+
+
+def test_fp64_df_paper_scale_grid_few_steps(orc):
+    cfg = inputs.PAPER_SCALE_16384x256
+    p = cfg["params"]
+    u0 = inputs.smooth_state(p["n_theta"], p["n_rstar"], seed=2)
+    uo, wo = oracle_run(orc, p, cfg["r0"], 3, u0)
+    ug, wg, _ = gpu_run(p, cfg["r0"], 3, u0, prec="fp64_df")
+    assert rel(ug, uo) <= FP64_TOL
+    assert rel(wg, wo) <= FP64_TOL
+
+
 def test_fp64_single_mode_800x64_full_run(orc):
     cfg = inputs.SINGLE_MODE_800x64
     uo, wo = oracle_run(orc, cfg["params"], cfg["r0"], cfg["steps"])
