@@ -8,8 +8,11 @@
 //             FP32        plane 0 = {Phi_R, Phi_I, Pi_R, Pi_I} (float4)
 //             FP32_KAHAN  plane 0 = hi {Phi, Pi} (float4), plane 1 = c {Phi, Pi} (float4),
 //                         the represented value being hi - c
-//   coef_h  [9][n_rstar][pitch] FP64 path: predictor coefficients at half nodes (i+1/2, j)
-//   coef_i  [9][n_rstar][pitch] FP64 path: corrector coefficients at integer nodes (i, j)
+//             FP64_DF     plane 0 = hi {Phi, Pi} (float4), plane 1 = lo {Phi, Pi} (float4),
+//                         the value being hi + lo (double-float)
+//   coef_h  [9][n_rstar][pitch] FP64 (double) and FP64_DF ((hi, lo) float pairs) paths:
+//           predictor coefficients at half nodes (i+1/2, j)
+//   coef_i  [9][n_rstar][pitch] the same at integer nodes (i, j)
 //   source  FP64 complex profile on a window of nodes around the particle
 //   wave    FP64 ring of waveform records [capacity][n_theta] (double2)
 #pragma once
