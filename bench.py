@@ -530,6 +530,7 @@ def main():
                     "roofline": {"bound": "hbm", "achieved": FP64_BYTES_PER_UPDATE * npts / (tf / step_launches * 1e-3) / 1e9,
                                  "peak": peak, "unit": "GB/s",
                                  "frac": FP64_BYTES_PER_UPDATE * npts / (tf / step_launches * 1e-3) / 1e9 / peak,
+                                 "traffic": ncu_traffic("fp64_df"),
                                  "bytes_per_update": FP64_BYTES_PER_UPDATE, "kernel": "step_kernel<PD>"},
                     "over_fp64": val_f / val_d, "clocks": clocks_f},
         "fp32_kahan_over_fp64": val_k / val_d,
