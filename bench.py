@@ -29,7 +29,8 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = "paper-scale single mode 16384x256 (s=-2, m=2, a=0.9, r*=[-200,800], r0=8M, r*_ext=700)"
 KAHAN_BYTES_PER_UPDATE = 64   # read + write of (hi, c) for Phi and Pi, FP32
-FP64_BYTES_PER_UPDATE = 64    # read + write of Phi and Pi, FP64
+FP64_BYTES_PER_UPDATE = 64    # read + write of Phi and Pi, FP64 (and double-float)
+FP32_BYTES_PER_UPDATE = 32    # read + write of Phi and Pi, plain FP32
 FP64_FLOPS_PER_UPDATE = 156   # FP64 flops of one point update in the kernel's formulation (FMA = 2)
 FP64_PEAK_TFLOPS = 1.25       # GB300 FP64 (non-tensor) nominal: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz
 
@@ -445,7 +446,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the accuracy, end-to-end and CPU-baseline legs")
-    ap.add_argument("--only", choices=["fp32_kahan", "fp64", "fp64_df"], default=None,
+    ap.add_argument("--only", choices=["fp32_kahan", "fp64", "fp64_df", "fp32"], default=None,
                     help="time one path only (for profiler captures)")
     ap.add_argument("--accuracy-steps", type=int, default=4000)
     ap.add_argument("--precision-sweep", action="store_true",
@@ -484,6 +485,9 @@ def main():
     s_d.close()
     s_f, ms_f, _, _, clocks_f = time_path("fp64_df", cfg, S, K, W, world, local)
     s_f.close()
+    s_p, ms_p, _, _, _ = time_path("fp32", cfg, S, K, W, world, local)
+    s_p.close()
+    ms_p_all = reduce_max(ms_p, world)
     ms_k_all = reduce_max(ms_k, world)
     ms_d_all = reduce_max(ms_d, world)
     ms_f_all = reduce_max(ms_f, world)
@@ -491,6 +495,7 @@ def main():
     val_k, tk = aggregate(ms_k_all, [units] * world)
     val_d, td = aggregate(ms_d_all, [units] * world)
     val_f, tf = aggregate(ms_f_all, [units] * world)
+    val_p, tp = aggregate(ms_p_all, [units] * world)
 
     if rank != 0:
         if world > 1:
@@ -533,6 +538,12 @@ def main():
                                  "traffic": ncu_traffic("fp64_df"),
                                  "bytes_per_update": FP64_BYTES_PER_UPDATE, "kernel": "step_kernel<PD>"},
                     "over_fp64": val_f / val_d, "clocks": clocks_f},
+        "fp32": {"value": val_p, "unit": "updates/s", "ms_per_step": tp / K,
+                 "note": "plain FP32 state and arithmetic",
+                 "roofline": {"bound": "hbm", "achieved": FP32_BYTES_PER_UPDATE * npts / (tp / step_launches * 1e-3) / 1e9,
+                              "peak": peak, "unit": "GB/s",
+                              "frac": FP32_BYTES_PER_UPDATE * npts / (tp / step_launches * 1e-3) / 1e9 / peak,
+                              "bytes_per_update": FP32_BYTES_PER_UPDATE, "kernel": "step_kernel<P32>"}},
         "fp32_kahan_over_fp64": val_k / val_d,
         "gpu_launches": int(launches_k),
         "clocks": clocks,
