@@ -301,27 +301,37 @@ __global__ void adj_source_kernel(InstDev d, int64_t n, CoLevel lam, CoMu mu, do
         last = atomicAdd(done, 1u) == gridDim.x - 1;
     }
     __syncthreads();
-    if (!last || threadIdx.x != 0) return;
+    if (!last) return;
     __threadfence();
-    double S[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    for (int b = 0; b < (int)gridDim.x; ++b)
-#pragma unroll
-        for (int v = 0; v < 8; ++v) S[v] += ((volatile double*)part)[b * 8 + v];
+    // the last block: threads 0..7 each add one of the eight sums over the blocks in
+    // index order; threads 32 and 64 form the two phases meanwhile
+    __shared__ double S[8];
+    __shared__ Z<double> ph[4];   // e_p, e_c, de_p, de_c
+    const int t = threadIdx.x;
+    if (t < 8) {
+        double acc_v = 0.0;
+        for (int b = 0; b < (int)gridDim.x; ++b) acc_v += ((volatile double*)part)[b * 8 + t];
+        S[t] = acc_v;
+    }
+    if (t == 32 || t == 64) {
+        const double tt = (double)n * d.dt + (t == 32 ? 0.0 : 0.5 * d.dt);
+        double sn, cs;
+        sincos(s.omega * tt + s.phase0, &sn, &cs);
+        // e = (cos, -sin); de = -i k e with k = d phi / d r0
+        const double k = tt * s.domega + s.dphase0;
+        const Z<double> e = {cs, -sn};
+        ph[t == 32 ? 0 : 1] = e;
+        ph[t == 32 ? 2 : 3] = Z<double>{k * e.y, -k * e.x};
+    }
+    __syncthreads();
+    if (t != 0) return;
     *done = 0;   // ready for the next step's launch (stream-ordered)
-    double A = (s.amps != nullptr && n < s.n_amps) ? s.amps[n] : 1.0;
-    double tp = (double)n * d.dt, tc = tp + 0.5 * d.dt;
-    double sp, cp, sc, cc;
-    sincos(s.omega * tp + s.phase0, &sp, &cp);
-    sincos(s.omega * tc + s.phase0, &sc, &cc);
-    // e = (cos, -sin); de = -i k e with k = d phi / d r0
-    double kp = tp * s.domega + s.dphase0, kc = tc * s.domega + s.dphase0;
-    Z<double> ep = {cp, -sp}, ec = {cc, -sc};
-    Z<double> dep = {kp * ep.y, -kp * ep.x}, dec = {kc * ec.y, -kc * ec.x};
+    const double A = (s.amps != nullptr && n < s.n_amps) ? s.amps[n] : 1.0;
     auto re_mul = [](Z<double> a, double bx, double by) { return a.x * bx - a.y * by; };
     const double hdt = 0.5 * d.dt;
-    *gA = hdt * re_mul(ep, S[0], S[1]) + d.dt * re_mul(ec, S[4], S[5]);
-    *gR = A * (hdt * (re_mul(dep, S[0], S[1]) + re_mul(ep, S[2], S[3])) +
-               d.dt * (re_mul(dec, S[4], S[5]) + re_mul(ec, S[6], S[7])));
+    *gA = hdt * re_mul(ph[0], S[0], S[1]) + d.dt * re_mul(ph[1], S[4], S[5]);
+    *gR = A * (hdt * (re_mul(ph[2], S[0], S[1]) + re_mul(ph[0], S[2], S[3])) +
+               d.dt * (re_mul(ph[3], S[4], S[5]) + re_mul(ph[1], S[6], S[7])));
 }
 
 // Loss of the built-in |r_ext^3 W|^2: per record, lossrec[k] = r^6 sum_j |W_k[j]|^2 (j
