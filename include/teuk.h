@@ -206,6 +206,14 @@ teuk_status teuk_autotune(teuk_ctx* ctx, int trial_steps, int* chosen);
 teuk_status teuk_set_fault_injection(teuk_ctx* ctx, int64_t skip_release_item,
                                      long long spin_limit);
 
+/* Testing aid for the bounded waits of the step kernels' column ring: while column >= 0,
+ * the step kernels of one instance never copy that column of the input level into their
+ * shared-memory ring (no copy is issued, so none is in flight), the blocks waiting for
+ * it give up after about one second, and the next teuk_sync reports TEUK_ETIMEOUT; later
+ * launches of the context return at once until the status has been read, and the state
+ * is undefined until teuk_set_state.  column < 0 clears it. */
+teuk_status teuk_set_fill_fault(teuk_ctx* ctx, int instance, int column);
+
 /* Number of kernels the library launched on this context since creation. */
 int64_t teuk_kernel_launches(const teuk_ctx* ctx);
 

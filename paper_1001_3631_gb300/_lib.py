@@ -58,6 +58,7 @@ _PROTOS = {
     "teuk_set_instance_tiling": (_I, [_P, _I, _I]),
     "teuk_autotune": (_I, [_P, _I, _P]),
     "teuk_set_fault_injection": (_I, [_P, _L, ctypes.c_longlong]),
+    "teuk_set_fill_fault": (_I, [_P, _I, _I]),
     "teuk_kernel_launches": (_L, [_P]),
     "teuk_destroy": (None, [_P]),
     "teuk_last_error": (ctypes.c_char_p, [_P]),

@@ -51,6 +51,7 @@ struct Instance {
     int* d_part = nullptr;
     std::vector<int> h_part;
     int part_strip = 0;
+    int fault_col = -1;         // testing aid (teuk_set_fill_fault)
 };
 
 // Device side of the batched persistent launch of one context: one persistent kernel
@@ -192,6 +193,7 @@ InstDev dev_of(const teuk_ctx* c, const Instance& I) {
     d.wave = I.wave;
     d.wave_cap = I.wave_cap;
     d.status = c->status;
+    d.fault_col = I.fault_col;
     return d;
 }
 
@@ -785,6 +787,14 @@ extern "C" teuk_status teuk_set_fault_injection(teuk_ctx* c, int64_t skip_releas
     if (spin_limit < 0) TK_FAIL(c, TEUK_EINVAL, "spin_limit must be >= 0");
     c->inject_skip_item = skip_release_item;
     c->spin_limit = spin_limit > 0 ? spin_limit : 20000000LL;
+    invalidate_graph(c);
+    return TEUK_OK;
+}
+
+extern "C" teuk_status teuk_set_fill_fault(teuk_ctx* c, int instance, int column) {
+    teuk_status st = check_instance(c, instance);
+    if (st) return st;
+    c->inst[instance].fault_col = column < 0 ? -1 : column;
     invalidate_graph(c);
     return TEUK_OK;
 }

@@ -87,6 +87,8 @@ struct InstDev {
     double2* wave;            // [wave_cap][nth]
     int64_t wave_cap;
     unsigned int* status;     // device status word (bit flags)
+    int fault_col;            // testing aid: this input column is never filled into the
+                              // step kernels' ring (-1: none)
 };
 
 enum StatusBits : unsigned int { ST_NONFINITE = 1u, ST_TIMEOUT = 2u, ST_BOUNDS = 4u };

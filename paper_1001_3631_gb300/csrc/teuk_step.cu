@@ -132,6 +132,7 @@ struct ColumnRing {
     // prefetch the column's slices of the source profile into L2 (read once per step,
     // they would otherwise come from DRAM, evicted by the state streaming through L2).
     __device__ __forceinline__ void fill(const InstDev& d, int bin, int col, int s) const {
+        if (col == d.fault_col) return;   // testing aid: the slot's phase never completes
         if (d.src.on) {
             const SourceDev& w = d.src;
             const unsigned cb = (unsigned)w.q_stride * (unsigned)sizeof(typename V2T<typename P::T>::V);

@@ -156,6 +156,9 @@ class TeukSolver:
     def set_instance_tiling(self, instance, strip):
         check(_lib.load().teuk_set_instance_tiling(self.ctx, instance, strip), self.ctx)
 
+    def set_fill_fault(self, column=-1, instance=0):
+        check(_lib.load().teuk_set_fill_fault(self.ctx, instance, column), self.ctx)
+
     def set_fault_injection(self, skip_release_item=-1, spin_limit=0):
         check(_lib.load().teuk_set_fault_injection(self.ctx, skip_release_item, spin_limit),
               self.ctx)

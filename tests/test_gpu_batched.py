@@ -113,6 +113,33 @@ def test_bounded_wait_gives_up_and_reports_timeout():
         assert np.abs(s.get_state(1)).max() > 0
 
 
+def test_ring_wait_times_out_and_context_recovers():
+    # a column that is never copied into the step kernel's ring: the blocks waiting for
+    # it give up after about a second and the status says so; nothing faults or hangs
+    inst = INST[0]
+    with TeukSolver(dict(inst["params"], prec="fp32_kahan")) as s:
+        s.set_source(inst["r0"])
+        s.step(2)
+        s.sync()
+        s.set_fill_fault(column=7)
+        s.step(3)
+        with pytest.raises(TeukError) as e:
+            s.sync()
+        assert e.value.status == 5  # TEUK_ETIMEOUT
+        # cleared and reset, the context steps normally again (equal to a fresh run)
+        s.set_fill_fault(-1)
+        u0 = inputs.random_state(inst["params"]["n_theta"], inst["params"]["n_rstar"], seed=4)
+        s.set_state(u0, 0)
+        s.step(3)
+        s.sync()
+        u = s.get_state()
+    with TeukSolver(dict(inst["params"], prec="fp32_kahan")) as s2:
+        s2.set_source(inst["r0"])
+        s2.set_state(u0, 0)
+        s2.step(3)
+        assert np.array_equal(s2.get_state(), u)
+
+
 def test_autotune_keeps_results_and_state(tmp_path):
     with TeukSolver([dict(i["params"], prec="fp32_kahan") for i in INST]) as s:
         for k, inst in enumerate(INST):
