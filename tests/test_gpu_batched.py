@@ -165,6 +165,26 @@ def test_autotune_keeps_results_and_state(tmp_path):
                 assert np.array_equal(s3.get_state(k), s.get_state(k))
 
 
+def test_autotune_single_instance_keeps_results_and_state(tmp_path):
+    # one instance stepped per launch: candidates are timed on a scratch copy
+    inst = INST[3]
+    with TeukSolver(dict(inst["params"], prec="fp32_kahan")) as s:
+        s.set_source(inst["r0"])
+        s.step(4)
+        before = s.get_state()
+        wb = s.extract()[0]
+        chosen = s.autotune(trial_steps=3, cache_path=str(tmp_path / "tune.json"))
+        assert len(chosen) == 1 and 1 <= chosen[0] <= inst["params"]["n_rstar"] - 2
+        assert np.array_equal(s.get_state(), before)
+        assert np.array_equal(s.extract()[0], wb)
+        s.step(3)
+        u = s.get_state()
+    with TeukSolver(dict(inst["params"], prec="fp32_kahan")) as s2:
+        s2.set_source(inst["r0"])
+        s2.step(7)
+        assert np.array_equal(s2.get_state(), u)
+
+
 def test_batched_uneven_workload_128_instances(orc):
     # the full 128-instance workload (8 modes x 16 orbits, uneven grids), a few steps in
     # FP32-Kahan; three instances are re-run alone (bitwise) and against the oracle
