@@ -39,13 +39,15 @@
  *   S_Pi  = -c_t Pi + P* Phi_* + w Theta[Phi] + q Phi + tau,   P* = c_t b + p* - b b_{,r*}
  *   b b_{,r*} = a^2 Delta sin^2 (R Delta' - 4 r Delta) / (2 Sigma^4),  Delta' = 2 (r - M).
  *
- * Readings of points the paper leaves open (each is listed in the design doc):
+ * Readings of points the paper leaves open:
  *   grid: r* node-centred with both end points, theta cell-centred
  *         theta_j = (j + 1/2) pi / N_theta, so no node sits on a pole;
  *   S at a half point is evaluated from the averaged state, with the radial
  *         derivative taken as the one-cell difference across the half point;
  *   angular boundary conditions through one ghost row at each pole face;
- *   time step rule (Courant factor) and the synthetic source, see orc_grid().
+ *   time step rule (Courant factor) and the synthetic source, see orc_grid();
+ *   the moving-particle source (orc_run_traj) takes the circular-orbit source with
+ *         the Gaussian centred on sampled particle positions.
  */
 #define _USE_MATH_DEFINES
 #include <complex.h>
@@ -527,6 +529,121 @@ int orc_run(const orc_params* p, double omega, double phase0, const double* P_in
     cplx_to_u(&c, Phi, Pi, u);
 done:
     free(Phi); free(Pi); free(Phi1); free(Pi1); free(hPhi); free(hPi); free(zi); free(zh);
+    ctx_free(&c);
+    return st;
+}
+
+/* ------------------------------------------------------------------ */
+/* Moving particle: a sampled trajectory                                */
+/* ------------------------------------------------------------------ */
+/*
+ * A particle on a general (eccentric or inclined) orbit, known through samples of
+ * its position and amplitude taken every half step:
+ *   traj[k] = {r_p, theta_p, phi_p, A} at t = k dt/2,  k = 0 .. n_samples - 1.
+ * The source at sample k is the circular-orbit source above with the Gaussian
+ * centred on the particle and the phase of its azimuth:
+ *   tau_k(r*, theta) = A_k exp(-i m phi_p,k) pref(r, theta) G(r* - r*(r_p,k), theta - theta_p,k)
+ *   pref = 4 pi Delta (r^2 + a^2 cos^2) / (Sigma^2 r^3),  G as above, zero beyond 8 sigma.
+ * Step n takes sample 2n in Eq. (13) (time t_n, half nodes) and sample 2n + 1 in
+ * Eq. (14) (time t_n + dt/2, integer nodes); a sub-step with no sample has no source.
+ * With r_p = r0, theta_p = pi/2, phi_p = Omega t + phi0 and A_{2n} = A_{2n+1} = A_n it
+ * is the circular-orbit source.
+ */
+
+/* tau of one sample at every node of one kind (integer nodes: half = 0, nodes
+ * r*_min + i dr*; half nodes: half = 1, nodes r*_min + (i + 1/2) dr*), into
+ * out[nth][n_nodes]; xs[i] = r - r_+ at those nodes. */
+static int moving_tau(const orc_params* p, const orc_geom* g, const double* xs, int n_nodes,
+                      int half, const double* smp, double sig_r, double sig_t, cplx* out) {
+    double r_p = smp[0], th_p = smp[1], phi_p = smp[2], A = smp[3];
+    if (!(r_p > g->rp) || !isfinite(th_p) || !isfinite(phi_p) || !isfinite(A)) return ORC_EINVAL;
+    double rs_p = orc_rstar_of_x(p->M, p->a, r_p - g->rp);
+    cplx amp = A * cexp(-I * ((double)p->m * phi_p));
+    const double a = p->a;
+    for (int j = 0; j < g->nth; ++j) {
+        double th = (j + 0.5) * g->dth;
+        double dth_ = th - th_p;
+        for (int i = 0; i < n_nodes; ++i) {
+            double rs = p->rstar_min + (half ? (i + 0.5) : (double)i) * g->drs;
+            double dr = rs - rs_p;
+            cplx* o = &out[(size_t)j * n_nodes + i];
+            if (fabs(dr) > 8.0 * sig_r || fabs(dth_) > 8.0 * sig_t) { *o = 0; continue; }
+            double G = exp(-0.5 * (dr * dr / (sig_r * sig_r) + dth_ * dth_ / (sig_t * sig_t)))
+                       / (2.0 * M_PI * sig_r * sig_t);
+            double x = xs[i];
+            double r = g->rp + x;
+            double Delta = x * (x + g->rp - g->rm);
+            double R = r * r + a * a;
+            double sn = sin(th), cs = cos(th);
+            double Sig2 = R * R - a * a * Delta * sn * sn;
+            double pref = 4.0 * M_PI * (r * r + a * a * cs * cs) * Delta / (Sig2 * r * r * r);
+            *o = amp * (pref * G);
+        }
+    }
+    return ORC_OK;
+}
+
+/*
+ * Evolve nsteps full steps from global step step0 with the sampled-trajectory source
+ * (arrays as in orc_run; traj [n_samples][4] as above; widths from the sigma fields
+ * of p, r0 unused).
+ */
+int orc_run_traj(const orc_params* p, const double* traj, int64_t n_samples, int64_t step0,
+                 int64_t nsteps, double* u, double* wave) {
+    orc_ctx c;
+    int st = ctx_init(&c, p);
+    if (st) return st;
+    const int nr = c.g.nr, nth = c.g.nth;
+    const double sig_r = p->sigma_r_abs > 0 ? p->sigma_r_abs : p->sigma_r_cells * c.g.drs;
+    const double sig_t = p->sigma_th_abs > 0 ? p->sigma_th_abs : p->sigma_th_cells * c.g.dth;
+    size_t np = (size_t)nr * nth, nhp = (size_t)(nr - 1) * nth;
+    cplx* Phi = malloc(sizeof(cplx) * np);
+    cplx* Pi = malloc(sizeof(cplx) * np);
+    cplx* Phi1 = malloc(sizeof(cplx) * np);
+    cplx* Pi1 = malloc(sizeof(cplx) * np);
+    cplx* hPhi = malloc(sizeof(cplx) * nhp);
+    cplx* hPi = malloc(sizeof(cplx) * nhp);
+    cplx* ti = malloc(sizeof(cplx) * np);
+    cplx* th_ = malloc(sizeof(cplx) * nhp);
+    double* xi = malloc(sizeof(double) * nr);
+    double* xh = malloc(sizeof(double) * nr);
+    if (!Phi || !Pi || !Phi1 || !Pi1 || !hPhi || !hPi || !ti || !th_ || !xi || !xh) {
+        st = ORC_ENOMEM;
+        goto done;
+    }
+    if (!(sig_r > 0) || !(sig_t > 0) || n_samples < 0 || (n_samples > 0 && !traj)) {
+        st = ORC_EINVAL;
+        goto done;
+    }
+    for (int i = 0; i < nr; ++i) xi[i] = orc_x_of_rstar(p->M, p->a, p->rstar_min + i * c.g.drs);
+    for (int i = 0; i < nr - 1; ++i)
+        xh[i] = orc_x_of_rstar(p->M, p->a, p->rstar_min + (i + 0.5) * c.g.drs);
+    u_to_cplx(&c, u, Phi, Pi);
+    if (wave) extract(&c, Phi, wave);
+    for (int64_t k = 0; k < nsteps; ++k) {
+        int64_t n = step0 + k;
+        if (2 * n < n_samples) {
+            st = moving_tau(p, &c.g, xh, nr - 1, 1, traj + 4 * (2 * n), sig_r, sig_t, th_);
+            if (st) goto done;
+        } else {
+            memset(th_, 0, sizeof(cplx) * nhp);
+        }
+        if (2 * n + 1 < n_samples) {
+            st = moving_tau(p, &c.g, xi, nr, 0, traj + 4 * (2 * n + 1), sig_r, sig_t, ti);
+            if (st) goto done;
+        } else {
+            memset(ti, 0, sizeof(cplx) * np);
+        }
+        lw_step(&c, Phi, Pi, 1.0, 1.0, ti, th_, hPhi, hPi, Phi1, Pi1);
+        cplx* t;
+        t = Phi; Phi = Phi1; Phi1 = t;
+        t = Pi; Pi = Pi1; Pi1 = t;
+        if (wave) extract(&c, Phi, wave + (size_t)(k + 1) * 2 * nth);
+    }
+    cplx_to_u(&c, Phi, Pi, u);
+done:
+    free(Phi); free(Pi); free(Phi1); free(Pi1); free(hPhi); free(hPi); free(ti); free(th_);
+    free(xi); free(xh);
     ctx_free(&c);
     return st;
 }

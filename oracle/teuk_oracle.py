@@ -71,6 +71,8 @@ def lib():
         _lib.orc_orbit_profile.argtypes = [pp, P, P, P, P]
         _lib.orc_run.restype = I
         _lib.orc_run.argtypes = [pp, D, D, P, P, P, L, L, L, P, P]
+        _lib.orc_run_traj.restype = I
+        _lib.orc_run_traj.argtypes = [pp, P, L, L, L, P, P]
         _lib.orc_apply_K.restype = I
         _lib.orc_apply_K.argtypes = [pp, P, P]
         _lib.orc_apply_KT.restype = I
@@ -183,6 +185,19 @@ def run(p: Params, u0=None, nsteps=1, source: Source | None = None, amps=None, s
     else:
         _check(lib().orc_run(ctypes.byref(p), source.omega, source.phase0, _ptr(source.P_int),
                              _ptr(source.P_half), _ptr(a), na, step0, nsteps, _ptr(u), _ptr(w)))
+    return u, w
+
+
+def run_trajectory(p: Params, traj, u0=None, nsteps=1, step0=0, wave=True):
+    """Evolve with the moving-particle source: traj [n_samples][4] = {r_p, theta_p,
+    phi_p, A} at t = k dt/2 (step n takes samples 2n and 2n + 1).  Returns (u, wave)."""
+    nth, nr = p.n_theta, p.n_rstar
+    u = np.zeros((4, nth, nr)) if u0 is None else np.array(u0, dtype=np.float64, copy=True)
+    assert u.shape == (4, nth, nr)
+    w = np.zeros((nsteps + 1, nth, 2)) if wave else None
+    t = np.ascontiguousarray(traj, dtype=np.float64).reshape(-1, 4)
+    _check(lib().orc_run_traj(ctypes.byref(p), _ptr(t), t.shape[0], step0, nsteps, _ptr(u),
+                              _ptr(w)))
     return u, w
 
 

@@ -44,6 +44,32 @@ def batched_uneven(seed=3003, n_modes=8, n_orbits=16):
     return out
 
 
+def eccentric_trajectory(n_samples, dt, semi_latus=10.0, ecc=0.4, incl=0.3, chi0=0.0,
+                         amp_sigma=0.0, seed=6006):
+    """Samples {r_p, theta_p, phi_p, A} at t = k dt/2, k = 0 .. n_samples - 1, of a
+    synthetic eccentric, inclined particle path: a Keplerian ellipse
+    r = p / (1 + e cos chi) (Kepler's equation for the anomaly, unit mass) on a plane
+    tilted by ``incl`` about the x axis, with A ~ N(1, amp_sigma^2) per sample.  An
+    input shape for the moving-source path, not a Kerr geodesic."""
+    t = 0.5 * dt * np.arange(n_samples, dtype=np.float64)
+    a_sm = semi_latus / (1.0 - ecc * ecc)
+    mean_motion = a_sm ** -1.5
+    E0 = 2.0 * np.arctan(np.sqrt((1.0 - ecc) / (1.0 + ecc)) * np.tan(0.5 * chi0))
+    Mn = E0 - ecc * np.sin(E0) + mean_motion * t
+    E = Mn.copy()
+    for _ in range(50):   # Newton on Kepler's equation E - e sin E = M
+        E = E - (E - ecc * np.sin(E) - Mn) / (1.0 - ecc * np.cos(E))
+    chi = 2.0 * np.arctan2(np.sqrt(1.0 + ecc) * np.sin(0.5 * E), np.sqrt(1.0 - ecc) * np.cos(0.5 * E))
+    r = a_sm * (1.0 - ecc * np.cos(E))
+    x, y, z = np.cos(chi), np.sin(chi) * np.cos(incl), np.sin(chi) * np.sin(incl)
+    theta = np.arccos(np.clip(z, -1.0, 1.0))
+    phi = np.unwrap(np.arctan2(y, x))
+    A = np.ones(n_samples)
+    if amp_sigma > 0:
+        A += amp_sigma * np.random.default_rng(seed).standard_normal(n_samples)
+    return np.stack([r, theta, phi, A], axis=1)
+
+
 def amplitudes(n, seed=5005, sigma=0.1):
     """Per-step source amplitudes A_n ~ N(1, sigma^2)."""
     return 1.0 + sigma * np.random.default_rng(seed).standard_normal(n)

@@ -1,8 +1,9 @@
 """GPU path (through the C ABI) against the FP64 oracle, element by element.
 
 FP64: relative L2 <= 1e-12 on the state and the waveform (the tolerance the
-problem statement fixes).  FP32 / FP32-Kahan: the bounds derived in the design doc
-from the FP32 rounding unit.  Results must not depend on the launch tiling."""
+problem statement fixes).  FP32 / FP32-Kahan: bounds derived from the FP32
+rounding unit u = 2^-24 ~ 6e-8 (a few u per step, growing like the square root of
+the step count for the compensated update).  Results must not depend on the launch tiling."""
 import numpy as np
 import pytest
 

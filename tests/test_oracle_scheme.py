@@ -19,7 +19,9 @@ import derive
 # --------------------------------------------------------------------------
 
 def _brute_force(M, a, s, m, rs_min, rs_max, nr, nth, dt, u0, omega, phase0, P_int, P_half,
-                 amps, nsteps):
+                 amps, nsteps, taus=None):
+    """taus (optional): taus(n, half, j, i) -> the source at step n, half node i+1/2
+    (half = 1, Eq. 13) or node i (half = 0, Eq. 14), replacing A_n e^{-i(omega t + phase0)} P."""
     co = derive.mpmath_coefficients(M, a, s, m)
     drs = (mp.mpf(rs_max) - rs_min) / (nr - 1)
     dth = mp.pi / nth
@@ -62,7 +64,7 @@ def _brute_force(M, a, s, m, rs_min, rs_max, nr, nth, dt, u0, omega, phase0, P_i
         return -k["ct"] * Pb + k["Pst"] * dF + k["w"] * D2 + k["wcot"] * D1 + k["qV"] * Fb + tau
 
     for n in range(nsteps):
-        A = amps[n]
+        A = amps[n] if amps is not None else 1
         t = n * mp.mpf(dt)
         ep = A * mp.expj(-(omega * t + phase0))
         ec = A * mp.expj(-(omega * (t + mp.mpf(dt) / 2) + phase0))
@@ -77,6 +79,7 @@ def _brute_force(M, a, s, m, rs_min, rs_max, nr, nth, dt, u0, omega, phase0, P_i
                 dF = (F0[i + 1] - F0[i]) / drs
                 dP = (Pi[j][i + 1] - Pi[j][i]) / drs
                 sp_ = S_Pi(k, (Fm[i + 1] + Fm[i]) / 2, Fb, (Fp[i + 1] + Fp[i]) / 2, Pb, dF,
+                           taus(n, 1, j, i) if taus else
                            ep * mp.mpc(P_half[j, i].real, P_half[j, i].imag))
                 hF[j][i] = Fb - mp.mpf(dt) / 2 * (k["b"] * dF - Pb)
                 hP[j][i] = Pb - mp.mpf(dt) / 2 * (-k["b"] * dP - sp_)
@@ -91,6 +94,7 @@ def _brute_force(M, a, s, m, rs_min, rs_max, nr, nth, dt, u0, omega, phase0, P_i
                 dF = (H0[i] - H0[i - 1]) / drs
                 dP = (hP[j][i] - hP[j][i - 1]) / drs
                 sp_ = S_Pi(k, (Hm[i] + Hm[i - 1]) / 2, Fb, (Hp[i] + Hp[i - 1]) / 2, Pb, dF,
+                           taus(n, 0, j, i) if taus else
                            ec * mp.mpc(P_int[j, i].real, P_int[j, i].imag))
                 nF[j][i] = Phi[j][i] - mp.mpf(dt) * (k["b"] * dF - Pb)
                 nP[j][i] = Pi[j][i] - mp.mpf(dt) * (-k["b"] * dP - sp_)
