@@ -118,6 +118,32 @@ teuk_status teuk_create(const teuk_params* p, int n_instances, void* cuda_stream
 teuk_status teuk_set_source(teuk_ctx* ctx, int instance, const teuk_orbit* orbit,
                             const double* amps, int64_t n_amps);
 
+/* Moving particle (an eccentric or inclined orbit, the setting of Sec. 1): replace the
+ * source of one instance by the same smeared particle following a sampled path.
+ *   traj   host array [n_samples][4] = {r_p, theta_p, phi_p, A} at t = k dt/2,
+ *          k = 0 .. n_samples-1 (copied; t counts from global step 0).
+ *   widths Gaussian widths as in teuk_orbit (r0 ignored); NULL: 4 cells each.
+ * The source at sample k is
+ *   T_m = A_k exp(-i m phi_p,k) G(r* - r*(r_p,k), theta - theta_p,k)
+ * (G the truncated 2D Gaussian above), entering S_Pi as tau of teuk_set_source.
+ * Step n takes sample 2n in Eq. (13) (time t_n, half nodes) and sample 2n + 1 in
+ * Eq. (14) (time t_n + dt/2, integer nodes); a sub-step with no sample has no
+ * source.  A circular path r_p = r0, theta_p = pi/2, phi_p = Omega t + phi0 gives the
+ * source of teuk_set_source.
+ * Setup: one kernel tabulates, per step, the radial Gaussian factor of every column
+ * and the angular factor of every row of the window that bounds the whole path, and
+ * the complex amplitude of the two samples; the step kernels multiply them into a
+ * static prefactor profile.  Device memory: about (n_samples / 2) x (2 window
+ * columns + 2 window rows) values of the arithmetic type, plus 48 bytes a sample.
+ * Synchronizes.  TEUK_EINVAL (source unchanged) if a sample is not finite, r_p is
+ * not outside the horizon, theta_p is outside (0, pi), the path leaves the radial
+ * grid, or n_samples < 1; TEUK_ENOMEM / TEUK_ECUDA on device failures (the instance
+ * is then left without a source).  teuk_adjoint_n refuses instances with a moving
+ * source (its gradients are those of the circular orbit); teuk_set_source replaces
+ * the moving source. */
+teuk_status teuk_set_trajectory(teuk_ctx* ctx, int instance, const teuk_orbit* widths,
+                                const double* traj, int64_t n_samples);
+
 /* Replace the state of one instance from host memory in u-layout (copied) and
  * set its time level to step0 (t = step0 dt).  Clears that instance's
  * waveform records.  Synchronizes.  The first call of teuk_set_state or

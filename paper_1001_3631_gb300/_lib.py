@@ -46,6 +46,7 @@ _P, _I, _L, _D = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
 _PROTOS = {
     "teuk_create": (_I, [ctypes.POINTER(teuk_params), _I, _P, ctypes.POINTER(_P)]),
     "teuk_set_source": (_I, [_P, _I, ctypes.POINTER(teuk_orbit), _P, _L]),
+    "teuk_set_trajectory": (_I, [_P, _I, ctypes.POINTER(teuk_orbit), _P, _L]),
     "teuk_set_state": (_I, [_P, _I, _P, _L]),
     "teuk_get_state": (_I, [_P, _I, _P]),
     "teuk_step_n": (_I, [_P, _L]),

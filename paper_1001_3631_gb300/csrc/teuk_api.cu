@@ -36,7 +36,9 @@ struct Instance {
     teuk_orbit orbit{};
     double rs0 = 0, sig_r = 0, sig_t = 0, drs0_dr0 = 0;
     double2* P_win = nullptr;   // P_int | P_half | dP_int | dP_half | Q_int | Q_half
+                                // (moving particle: Q_int | Q_half only)
     double* amps = nullptr;
+    void* traj_buf = nullptr;   // moving particle: samples | amp | gr | gt (SourceDev)
     SourceDev sd{};
     // waveform ring: time levels [wave_lo, wave_hi) are held
     double2* wave = nullptr;
@@ -67,6 +69,7 @@ struct BatchClass {
     int64_t items = -1;
     int grid = 0;
     int max_nth = 0;
+    bool moving = false;            // a member has a moving particle
     BatchDev bd{};
 };
 
@@ -303,7 +306,7 @@ void free_instance(cudaStream_t s, Instance& I) {
         for (int k = 0; k < 2; ++k)
             if (I.state[b][k]) cudaFreeAsync(I.state[b][k], s);
     void* ptrs[] = {I.coef_h, I.coef_i, I.x_int, I.x_half, I.P_win, I.amps, I.wave, I.rtab, I.thtab,
-                    I.stage, I.d_part};
+                    I.stage, I.d_part, I.traj_buf};
     for (void* q : ptrs)
         if (q) cudaFreeAsync(q, s);
     I = Instance();
@@ -404,6 +407,49 @@ extern "C" teuk_status teuk_create(const teuk_params* p, int n_instances, void* 
 
 // ------------------------------------------------------------------ source
 
+namespace {
+
+void free_source(teuk_ctx* c, Instance& I) {
+    void* ptrs[] = {I.P_win, I.amps, I.traj_buf};
+    for (void* q : ptrs)
+        if (q) cudaFreeAsync(q, c->stream);
+    I.P_win = nullptr;
+    I.amps = nullptr;
+    I.traj_buf = nullptr;
+    I.src_on = false;
+    I.sd = SourceDev{};
+}
+
+// Gaussian widths of a source (absolute units, else cells; 0 cells means 4)
+void source_widths(const Instance& I, const teuk_orbit* o, double* sr, double* stt) {
+    *sr = o && o->sigma_rstar_abs > 0 ? o->sigma_rstar_abs
+          : (o && o->sigma_rstar_cells > 0 ? o->sigma_rstar_cells : 4.0) * I.drs;
+    *stt = o && o->sigma_theta_abs > 0 ? o->sigma_theta_abs
+           : (o && o->sigma_theta_cells > 0 ? o->sigma_theta_cells : 4.0) * I.dth;
+}
+
+// Window of the nodes that can lie within 8 sigma of a centre in [rs_lo, rs_hi] x
+// [th_lo, th_hi], with one node of margin (the kernels apply the exact cut)
+void source_window(const Instance& I, double rs_lo, double rs_hi, double th_lo, double th_hi,
+                   double sr, double stt, SourceDev& sd) {
+    const teuk_params& q = I.p;
+    const int nr = q.n_rstar, nth = q.n_theta;
+    auto clampi = [](double v, int lo, int hi) {
+        return v < lo ? lo : (v > hi ? hi : (int)v);
+    };
+    int ilo = clampi(std::floor((rs_lo - 8 * sr - q.rstar_min) / I.drs) - 1, 0, nr - 1);
+    int ihi = clampi(std::ceil((rs_hi + 8 * sr - q.rstar_min) / I.drs) + 1, 0, nr - 1);
+    int hlo = clampi(std::floor((rs_lo - 8 * sr - q.rstar_min) / I.drs - 0.5) - 1, 0, nr - 2);
+    int hhi = clampi(std::ceil((rs_hi + 8 * sr - q.rstar_min) / I.drs - 0.5) + 1, 0, nr - 2);
+    int jlo = clampi(std::floor((th_lo - 8 * stt) / I.dth - 0.5) - 1, 0, nth - 1);
+    int jhi = clampi(std::ceil((th_hi + 8 * stt) / I.dth - 0.5) + 1, 0, nth - 1);
+    sd.i_lo = ilo; sd.ni = ihi - ilo + 1;
+    sd.h_lo = hlo; sd.nh = hhi - hlo + 1;
+    sd.j_lo = jlo; sd.nj = jhi - jlo + 1;
+}
+
+}  // namespace
+
 extern "C" teuk_status teuk_set_source(teuk_ctx* c, int instance, const teuk_orbit* orbit,
                                        const double* amps, int64_t n_amps) {
     teuk_status st = check_instance(c, instance);
@@ -417,25 +463,11 @@ extern "C" teuk_status teuk_set_source(teuk_ctx* c, int instance, const teuk_orb
     double rs0 = rstar_of_r(q.M, q.a, r0);
     if (!(rs0 > q.rstar_min && rs0 < q.rstar_max))
         TK_FAIL(c, TEUK_EINVAL, "orbit r*(r0)=%g outside the radial grid", rs0);
-    double sr = orbit->sigma_rstar_abs > 0 ? orbit->sigma_rstar_abs
-                : (orbit->sigma_rstar_cells > 0 ? orbit->sigma_rstar_cells : 4.0) * I.drs;
-    double stt = orbit->sigma_theta_abs > 0 ? orbit->sigma_theta_abs
-                 : (orbit->sigma_theta_cells > 0 ? orbit->sigma_theta_cells : 4.0) * I.dth;
+    double sr, stt;
+    source_widths(I, orbit, &sr, &stt);
     // window of nodes that can be within 8 sigma (the kernel applies the exact cut)
     SourceDev sd{};
-    int nr = q.n_rstar, nth = q.n_theta;
-    auto clampi = [](double v, int lo, int hi) {
-        return v < lo ? lo : (v > hi ? hi : (int)v);
-    };
-    int ilo = clampi(std::floor((rs0 - 8 * sr - q.rstar_min) / I.drs) - 1, 0, nr - 1);
-    int ihi = clampi(std::ceil((rs0 + 8 * sr - q.rstar_min) / I.drs) + 1, 0, nr - 1);
-    int hlo = clampi(std::floor((rs0 - 8 * sr - q.rstar_min) / I.drs - 0.5) - 1, 0, nr - 2);
-    int hhi = clampi(std::ceil((rs0 + 8 * sr - q.rstar_min) / I.drs - 0.5) + 1, 0, nr - 2);
-    int jlo = clampi(std::floor((0.5 * kPi - 8 * stt) / I.dth - 0.5) - 1, 0, nth - 1);
-    int jhi = clampi(std::ceil((0.5 * kPi + 8 * stt) / I.dth - 0.5) + 1, 0, nth - 1);
-    sd.i_lo = ilo; sd.ni = ihi - ilo + 1;
-    sd.h_lo = hlo; sd.nh = hhi - hlo + 1;
-    sd.j_lo = jlo; sd.nj = jhi - jlo + 1;
+    source_window(I, rs0, rs0, 0.5 * kPi, 0.5 * kPi, sr, stt, sd);
     double Omega = std::sqrt(q.M) / (std::pow(r0, 1.5) + q.a * std::sqrt(q.M));
     double phi0 = q.a / (I.rp - I.rm) * std::log((r0 - I.rp) / (r0 - I.rm));
     double Delta0 = r0 * r0 - 2 * q.M * r0 + q.a * q.a;
@@ -446,8 +478,7 @@ extern "C" teuk_status teuk_set_source(teuk_ctx* c, int instance, const teuk_orb
     sd.domega = q.m * dOmega;
     sd.dphase0 = q.m * q.a / Delta0;
     // (re)allocate window and amplitudes
-    if (I.P_win) { cudaFreeAsync(I.P_win, c->stream); I.P_win = nullptr; }
-    if (I.amps) { cudaFreeAsync(I.amps, c->stream); I.amps = nullptr; }
+    free_source(c, I);
     size_t nwi = (size_t)sd.nj * sd.ni, nwh = (size_t)sd.nj * sd.nh;
     // P, P_half, dP, dP_half (double2), then the step kernels' copies Q_int, Q_half
     const bool q16 = q.prec == TEUK_FP64 || q.prec == TEUK_FP64_DF;   // 16-byte profile entries
@@ -483,6 +514,79 @@ extern "C" teuk_status teuk_set_source(teuk_ctx* c, int instance, const teuk_orb
     st = refresh_partition(c, I);
     if (st) return st;
     if (n_amps > 0) TK_CUDA(c, cudaStreamSynchronize(c->stream));  // host amps may be freed
+    return TEUK_OK;
+}
+
+extern "C" teuk_status teuk_set_trajectory(teuk_ctx* c, int instance, const teuk_orbit* widths,
+                                           const double* traj, int64_t n_samples) {
+    teuk_status st = check_instance(c, instance);
+    if (st) return st;
+    Instance& I = c->inst[instance];
+    if (!traj || n_samples < 1) TK_FAIL(c, TEUK_EINVAL, "need a trajectory of at least one sample");
+    if (n_samples > ((int64_t)1 << 31)) TK_FAIL(c, TEUK_EINVAL, "too many trajectory samples");
+    const teuk_params& q = I.p;
+    double r_lo = HUGE_VAL, r_hi = -HUGE_VAL, t_lo = HUGE_VAL, t_hi = -HUGE_VAL;
+    for (int64_t k = 0; k < n_samples; ++k) {
+        const double* smp = traj + 4 * k;
+        if (!std::isfinite(smp[0]) || !std::isfinite(smp[1]) || !std::isfinite(smp[2]) ||
+            !std::isfinite(smp[3]))
+            TK_FAIL(c, TEUK_EINVAL, "trajectory sample %lld is not finite", (long long)k);
+        if (!(smp[0] > I.rp))
+            TK_FAIL(c, TEUK_EINVAL, "trajectory sample %lld: r_p=%g not outside the horizon",
+                    (long long)k, smp[0]);
+        if (!(smp[1] > 0.0 && smp[1] < kPi))
+            TK_FAIL(c, TEUK_EINVAL, "trajectory sample %lld: theta_p=%g outside (0, pi)",
+                    (long long)k, smp[1]);
+        r_lo = std::fmin(r_lo, smp[0]);
+        r_hi = std::fmax(r_hi, smp[0]);
+        t_lo = std::fmin(t_lo, smp[1]);
+        t_hi = std::fmax(t_hi, smp[1]);
+    }
+    const double rs_lo = rstar_of_r(q.M, q.a, r_lo), rs_hi = rstar_of_r(q.M, q.a, r_hi);
+    if (!(rs_lo > q.rstar_min && rs_hi < q.rstar_max))
+        TK_FAIL(c, TEUK_EINVAL, "the path leaves the radial grid (r* from %g to %g)", rs_lo, rs_hi);
+    double sr, stt;
+    source_widths(I, widths, &sr, &stt);
+    SourceDev sd{};
+    source_window(I, rs_lo, rs_hi, t_lo, t_hi, sr, stt, sd);
+    sd.moving = 1;
+    sd.n_traj = (n_samples + 1) / 2;
+    // device memory: the profile Q (as for the circular orbit), then the samples, the
+    // amplitudes and the radial and angular factor tables in the arithmetic type
+    const bool q16 = q.prec == TEUK_FP64 || q.prec == TEUK_FP64_DF;
+    const size_t qe = q16 ? 16 : sizeof(float2);
+    sd.q_stride = q16 ? sd.nj : (sd.nj + 1) / 2 * 2;
+    const size_t qi_bytes = qe * sd.q_stride * sd.ni, qh_bytes = qe * sd.q_stride * sd.nh;
+    const size_t te = q16 ? 8 : 4;
+    auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+    const size_t b_traj = up(sizeof(double) * 4 * (size_t)n_samples);
+    const size_t b_amp = up(sizeof(double2) * 2 * (size_t)sd.n_traj);
+    const size_t b_gr = up(te * (size_t)sd.n_traj * (sd.nh + sd.ni));
+    const size_t b_gt = up(te * (size_t)sd.n_traj * 2 * sd.nj);
+    free_source(c, I);
+    TK_CUDA(c, cudaMallocAsync((void**)&I.P_win, qi_bytes + qh_bytes, c->stream));
+    TK_CUDA(c, cudaMallocAsync(&I.traj_buf, b_traj + b_amp + b_gr + b_gt, c->stream));
+    sd.Q_int = I.P_win;
+    sd.Q_half = (const char*)sd.Q_int + qi_bytes;
+    char* tb = (char*)I.traj_buf;
+    const double* d_traj = (const double*)tb;
+    sd.amp = (const double2*)(tb + b_traj);
+    sd.gr = tb + b_traj + b_amp;
+    sd.gt = tb + b_traj + b_amp + b_gr;
+    TK_CUDA(c, cudaMemcpyAsync((void*)d_traj, traj, sizeof(double) * 4 * (size_t)n_samples,
+                               cudaMemcpyHostToDevice, c->stream));
+    launch_trajectory(c->stream, q.M, q.a, q.m, q.rstar_min, I.drs, I.dth, sr, stt, I.x_int, I.x_half,
+                      d_traj, n_samples, sd, (int)q.prec);
+    c->launches += 2;
+    TK_CUDA(c, cudaGetLastError());
+    I.sd = sd;
+    I.orbit = widths ? *widths : teuk_orbit{};
+    I.sig_r = sr;
+    I.sig_t = stt;
+    I.src_on = true;
+    st = refresh_partition(c, I);
+    if (st) return st;
+    TK_CUDA(c, cudaStreamSynchronize(c->stream));  // the host samples may be freed
     return TEUK_OK;
 }
 
@@ -540,7 +644,7 @@ void enqueue_batched(teuk_ctx* c) {
         cudaMemsetAsync(K.d_counter, 0, sizeof(unsigned long long), c->stream);
         cudaMemsetAsync(K.d_flags, 0, sizeof(int) * K.items, c->stream);
     }
-    for (BatchClass& K : B.cls) launch_batched_step(c->stream, c->prec, K.bd, K.grid, K.pitch);
+    for (BatchClass& K : B.cls) launch_batched_step(c->stream, c->prec, K.bd, K.grid, K.pitch, K.moving);
     for (BatchClass& K : B.cls) launch_batched_extract(c->stream, c->prec, K.bd, K.max_nth);
 }
 
@@ -580,6 +684,7 @@ teuk_status batched_step(teuk_ctx* c, int64_t n) {
         std::vector<int> strip(m), nstrip(m), bb(m);
         std::vector<InstDev> idev(m);
         int max_nth = 0;
+        bool moving = false;
         for (int q = 0; q < m; ++q) {
             Instance& I = c->inst[K.members[q]];
             strip[q] = eff_strip(c, I);
@@ -589,6 +694,7 @@ teuk_status batched_step(teuk_ctx* c, int64_t n) {
             bb[q] = I.cur;
             idev[q] = dev_of(c, I);
             max_nth = std::max(max_nth, I.p.n_theta);
+            moving = moving || (I.src_on && I.sd.moving);
         }
         std::memcpy(blob.data() + o_inst, idev.data(), sizeof(InstDev) * m);
         std::memcpy(blob.data() + o_ib, ib.data(), sizeof(int64_t) * (m + 1));
@@ -597,7 +703,8 @@ teuk_status batched_step(teuk_ctx* c, int64_t n) {
         std::memcpy(blob.data() + o_st, strip.data(), sizeof(int) * m);
         std::memcpy(blob.data() + o_ns, nstrip.data(), sizeof(int) * m);
         std::memcpy(blob.data() + o_bb, bb.data(), sizeof(int) * m);
-        if (ib[m] != K.items || max_nth != K.max_nth) changed = true;
+        if (ib[m] != K.items || max_nth != K.max_nth || moving != K.moving) changed = true;
+        K.moving = moving;
         K.items = ib[m];
         K.max_nth = max_nth;
         K.bd.n_inst = m;
@@ -1107,6 +1214,8 @@ extern "C" teuk_status teuk_adjoint_n(teuk_ctx* c, int instance, int64_t step0, 
     if (st) return st;
     Instance& I = c->inst[instance];
     if (n < 1 || step0 < 0) TK_FAIL(c, TEUK_EINVAL, "need n >= 1 and step0 >= 0");
+    if (I.sd.moving)
+        TK_FAIL(c, TEUK_EINVAL, "source gradients are defined for the circular-orbit source only");
     const bool builtin = grad_wave == nullptr;
     if (builtin && I.step != step0)
         TK_FAIL(c, TEUK_ESTATE, "built-in loss: the state is at step %lld, not step0 = %lld",

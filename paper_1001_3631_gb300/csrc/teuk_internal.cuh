@@ -54,6 +54,16 @@ struct SourceDev {
     double domega, dphase0;  // d omega/d r0, d phase0/d r0
     const double* amps;      // A_n for n < n_amps, else 1
     int64_t n_amps;
+    // Moving particle (a sampled path, teuk_set_trajectory): the window bounds the whole
+    // path, Q holds the static prefactor pref / (2 pi sig_r sig_th) and the source of
+    // step n at node (i, j) is  fac g_r[n](i) g_th[n](j) Q(i, j),  fac = dt_sub A e^{-i m phi_p}
+    // of sample 2n (predictor, half nodes) or 2n + 1 (corrector, integer nodes).
+    int moving;
+    int64_t n_traj;          // steps with tables; later steps have no source
+    const double2* amp;      // [n_traj][2] A e^{-i m phi_p} of samples 2n, 2n + 1 (0: no sample)
+    const void* gr;          // [n_traj][nh + ni] radial factors, half nodes then integer
+                             // nodes, in the arithmetic type (double, float or DF)
+    const void* gt;          // [n_traj][2][nj] angular factors of samples 2n, 2n + 1
 };
 
 // FP32 paths form their coefficients in registers from 1D tables (rounded from FP64 at
@@ -138,6 +148,12 @@ void launch_tables_1d(cudaStream_t st, double M, double a, int s, int m, double 
 void launch_profile(cudaStream_t st, double M, double a, double rstar_min, double drs, double dth,
                     double rs0, double sig_r, double sig_t, double drs0_dr0, const double* x_int,
                     const double* x_half, const SourceDev& src, int prec);
+// moving particle: the prefactor profile Q on the window and the per-step tables of
+// src (traj: device copy of the samples, [n_samples][4])
+void launch_trajectory(cudaStream_t st, double M, double a, int m, double rstar_min, double drs,
+                       double dth, double sig_r, double sig_t, const double* x_int,
+                       const double* x_half, const double* traj, int64_t n_samples,
+                       const SourceDev& src, int prec);
 // teuk_step.cu
 cudaError_t prepare_step_kernels();
 int step_resident_blocks(int prec, int threads);  // blocks of the step kernel the GPU holds at once
@@ -146,7 +162,10 @@ int step_resident_blocks(int prec, int threads);  // blocks of the step kernel t
 void launch_step(cudaStream_t st, const InstDev& d, int64_t step, int bin, int strip,
                  const int* part = nullptr);
 void launch_extract(cudaStream_t st, const InstDev& d, int64_t step, int bin);
-void launch_batched_step(cudaStream_t st, int prec, const BatchDev& b, int grid, int threads);
+// moving: some instance of the class has a moving particle (selects the kernel that
+// carries the per-step Gaussian tables)
+void launch_batched_step(cudaStream_t st, int prec, const BatchDev& b, int grid, int threads,
+                         bool moving);
 int batched_grid(int prec, int threads);
 void launch_batched_extract(cudaStream_t st, int prec, const BatchDev& b, int max_nth);
 // teuk_aux.cu

@@ -152,6 +152,30 @@ __device__ void profile_point(double M, double a, double x, double rs, double th
     *dP = make_double2(pref * G * dr / (sig_r * sig_r) * drs0_dr0, 0.0);
 }
 
+// One complex value into a profile in the arithmetic type of precision prec (double2;
+// double-float re.hi, re.lo, im.hi, im.lo; float2)
+__device__ __forceinline__ void put_cplx(const void* q, size_t idx, double2 v, int prec) {
+    if (prec == 0) {
+        ((double2*)q)[idx] = v;
+    } else if (prec == 3) {
+        const DF x(v.x), y(v.y);
+        ((float4*)q)[idx] = make_float4(x.hi, x.lo, y.hi, y.lo);
+    } else {
+        ((float2*)q)[idx] = make_float2((float)v.x, (float)v.y);
+    }
+}
+// One real value in the arithmetic type (double; double-float hi, lo; float)
+__device__ __forceinline__ void put_real(void* q, size_t idx, double v, int prec) {
+    if (prec == 0) {
+        ((double*)q)[idx] = v;
+    } else if (prec == 3) {
+        const DF x(v);
+        ((float2*)q)[idx] = make_float2(x.hi, x.lo);
+    } else {
+        ((float*)q)[idx] = (float)v;
+    }
+}
+
 __global__ void profile_kernel(double M, double a, double rstar_min, double drs, double dth,
                                double rs0, double sig_r, double sig_t, double drs0_dr0,
                                const double* x_int, const double* x_half, SourceDev src,
@@ -162,16 +186,7 @@ __global__ void profile_kernel(double M, double a, double rstar_min, double drs,
     if (jj >= src.nj) return;
     double th = (src.j_lo + jj + 0.5) * dth;
     // column-major copy for the step kernels, in their arithmetic type
-    auto put_q = [&](const void* q, size_t idx, double2 v) {
-        if (prec == 0) {
-            ((double2*)q)[idx] = v;
-        } else if (prec == 3) {   // double-float: re.hi, re.lo, im.hi, im.lo
-            const DF x(v.x), y(v.y);
-            ((float4*)q)[idx] = make_float4(x.hi, x.lo, y.hi, y.lo);
-        } else {
-            ((float2*)q)[idx] = make_float2((float)v.x, (float)v.y);
-        }
-    };
+    auto put_q = [&](const void* q, size_t idx, double2 v) { put_cplx(q, idx, v, prec); };
     if (k < src.ni) {
         int i = src.i_lo + k;
         double2* p = &P_int[(size_t)jj * src.ni + k];
@@ -185,6 +200,88 @@ __global__ void profile_kernel(double M, double a, double rstar_min, double drs,
         profile_point(M, a, x_half[i], rstar_min + (i + 0.5) * drs, th, rs0, sig_r, sig_t,
                       drs0_dr0, p, &dP_half[(size_t)jj * src.nh + k]);
         put_q(src.Q_half, (size_t)k * src.q_stride + jj, *p);
+    }
+}
+
+// ---------------------------------------------------------------- moving particle
+// A particle on a sampled path: the circular-orbit source with the Gaussian centred on
+// the particle, factored so that the step kernels only multiply tabulated values,
+//   tau_n(i, j) = A e^{-i m phi_p} g_r(r*_i - r*_p) g_th(theta_j - theta_p) Q(i, j)
+//   g_r = exp(-dr^2 / (2 sig_r^2)),  g_th = exp(-dth^2 / (2 sig_t^2)),  each 0 beyond 8 sigma
+//   Q   = 4 pi (r^2 + a^2 cos^2) Delta / (Sigma^2 r^3) / (2 pi sig_r sig_t)   (static)
+// Step n takes sample 2n at the half nodes (Eq. 13) and 2n + 1 at the integer nodes (Eq. 14).
+__global__ void prefactor_kernel(double M, double a, double dth, double norm, const double* x_int,
+                                 const double* x_half, SourceDev src, int prec) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int jj = blockIdx.y;
+    if (jj >= src.nj) return;
+    const double th = (src.j_lo + jj + 0.5) * dth;
+    const double d = sqrt(M * M - a * a);
+    const double rp = M + d, rm = M - d;
+    double sn, cs;
+    sincos(th, &sn, &cs);
+    auto pref = [&](double x) {
+        const double r = rp + x;
+        const double Delta = x * (x + rp - rm);
+        const double R = r * r + a * a;
+        const double Sig2 = R * R - a * a * Delta * sn * sn;
+        return 4.0 * 3.141592653589793238462643 * (r * r + a * a * cs * cs) * Delta /
+               (Sig2 * r * r * r) * norm;
+    };
+    if (k < src.ni)
+        put_cplx(src.Q_int, (size_t)k * src.q_stride + jj, make_double2(pref(x_int[src.i_lo + k]), 0.0), prec);
+    if (k < src.nh)
+        put_cplx(src.Q_half, (size_t)k * src.q_stride + jj, make_double2(pref(x_half[src.h_lo + k]), 0.0), prec);
+}
+
+// Block per step (grid-stride): the amplitudes and the radial and angular factors of
+// the step's two samples.
+__global__ void trajectory_kernel(double M, double a, int m, double rstar_min, double drs,
+                                  double dth, double sig_r, double sig_t, const double* traj,
+                                  int64_t n_samples, SourceDev src, int prec) {
+    const double d = sqrt(M * M - a * a);
+    const double rp = M + d, rm = M - d;
+    const int nrow = src.nh + src.ni;
+    for (int64_t n = blockIdx.x; n < src.n_traj; n += gridDim.x) {
+        for (int q = 0; q < 2; ++q) {   // q = 0: sample 2n, half nodes; q = 1: 2n + 1, integer nodes
+            const int64_t k = 2 * n + q;
+            const bool have = k < n_samples;
+            double rs_p = 0.0, th_p = 0.0;
+            if (have) {
+                const double* smp = traj + 4 * k;
+                rs_p = rstar_of_x(M, rp, rm, smp[0] - rp);
+                th_p = smp[1];
+                if (threadIdx.x == 0) {
+                    double sn, cs;
+                    sincos((double)m * smp[2], &sn, &cs);
+                    ((double2*)src.amp)[2 * n + q] = make_double2(smp[3] * cs, -(smp[3] * sn));
+                }
+            } else if (threadIdx.x == 0) {
+                ((double2*)src.amp)[2 * n + q] = make_double2(0.0, 0.0);
+            }
+            const int nc = q == 0 ? src.nh : src.ni;
+            const int lo = q == 0 ? src.h_lo : src.i_lo;
+            void* gr = (char*)src.gr;
+            const size_t base = (size_t)n * nrow + (q == 0 ? 0 : src.nh);
+            for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+                double g = 0.0;
+                if (have) {
+                    const double rs = rstar_min + (q == 0 ? (lo + c + 0.5) : (double)(lo + c)) * drs;
+                    const double dr = rs - rs_p;
+                    if (!(fabs(dr) > 8.0 * sig_r)) g = exp(-0.5 * (dr * dr / (sig_r * sig_r)));
+                }
+                put_real(gr, base + c, g, prec);
+            }
+            void* gt = (char*)src.gt;
+            for (int jj = threadIdx.x; jj < src.nj; jj += blockDim.x) {
+                double g = 0.0;
+                if (have) {
+                    const double dt_ = (src.j_lo + jj + 0.5) * dth - th_p;
+                    if (!(fabs(dt_) > 8.0 * sig_t)) g = exp(-0.5 * (dt_ * dt_ / (sig_t * sig_t)));
+                }
+                put_real(gt, ((size_t)n * 2 + q) * src.nj + jj, g, prec);
+            }
+        }
     }
 }
 
@@ -297,6 +394,19 @@ void launch_profile(cudaStream_t st, double M, double a, double rstar_min, doubl
                                       x_int, x_half, src, (double2*)src.P_int,
                                       (double2*)src.P_half, (double2*)src.dP_int,
                                       (double2*)src.dP_half, prec);
+}
+
+
+void launch_trajectory(cudaStream_t st, double M, double a, int m, double rstar_min, double drs,
+                       double dth, double sig_r, double sig_t, const double* x_int,
+                       const double* x_half, const double* traj, int64_t n_samples,
+                       const SourceDev& src, int prec) {
+    dim3 g(((src.ni > src.nh ? src.ni : src.nh) + 127) / 128, src.nj);
+    prefactor_kernel<<<g, 128, 0, st>>>(M, a, dth, 1.0 / (2.0 * 3.141592653589793238462643 * sig_r * sig_t),
+                                        x_int, x_half, src, prec);
+    const int64_t blocks = src.n_traj < 4096 ? src.n_traj : 4096;
+    trajectory_kernel<<<(unsigned)(blocks > 0 ? blocks : 1), 128, 0, st>>>(
+        M, a, m, rstar_min, drs, dth, sig_r, sig_t, traj, n_samples, src, prec);
 }
 
 }  // namespace teuk

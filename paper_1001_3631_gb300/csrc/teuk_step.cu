@@ -219,7 +219,9 @@ constexpr int kRingS = 6, kRingL = 4;
 // kPerStep: the block belongs to a per-step launch (programmatic dependent launch: the
 // part before griddepcontrol.wait overlaps the previous step, and the block returns at
 // once when a bounded wait of an earlier launch gave up).  Returns false in that case.
-template <class P, int R, bool kPerStep>
+// kMov: the kernel serves instances whose particle moves (per-step Gaussian tables);
+// the kernels of circular orbits are compiled without that code.
+template <class P, int R, bool kPerStep, bool kMov>
 __device__ __forceinline__ bool strip_step(const InstDev& d, int64_t step, int bin, int c0,
                                            int c1, ColumnRing<P, R>& ring, typename P::T* xbuf) {
     using T = typename P::T;
@@ -253,12 +255,12 @@ __device__ __forceinline__ bool strip_step(const InstDev& d, int64_t step, int b
     if (src_blk) {
         const int w1 = blockDim.x > 32 ? 32 : 0;
         if (threadIdx.x == 0) {
-            const double2 f = source_factor(d, step, 0.0, 0.5 * d.dt);
+            const double2 f = source_factor<kMov>(d, step, 0.0, 0.5 * d.dt);
             sfac[0] = (T)f.x;
             sfac[1] = (T)f.y;
         }
         if (threadIdx.x == w1) {
-            const double2 f = source_factor(d, step, 0.5, d.dt);
+            const double2 f = source_factor<kMov>(d, step, 0.5, d.dt);
             sfac[2] = (T)f.x;
             sfac[3] = (T)f.y;
         }
@@ -280,6 +282,23 @@ __device__ __forceinline__ bool strip_step(const InstDev& d, int64_t step, int b
     if (src_blk) {
         sp_fac = {sfac[0], sfac[1]};
         sc_fac = {sfac[2], sfac[3]};
+    }
+    // moving particle: this row's angular factors join the step's factors; gr points at
+    // the step's radial factors (half nodes, then integer nodes)
+    const T* gr = nullptr;
+    if constexpr (kMov) {
+        if (src_blk && sw.moving && step < sw.n_traj) {
+            const int b = j - sw.j_lo;
+            T gh = T(0), gi = T(0);
+            if ((unsigned)b < (unsigned)sw.nj) {
+                const T* gt = (const T*)sw.gt + (size_t)step * 2 * sw.nj + b;
+                gh = gt[0];
+                gi = gt[sw.nj];
+            }
+            sp_fac = gh * sp_fac;
+            sc_fac = gi * sc_fac;
+            gr = (const T*)sw.gr + (size_t)step * (sw.nh + sw.ni);
+        }
     }
     const bool ex_blk = c0 - 1 <= d.i_e && d.i_e <= c1 - 1;
 
@@ -412,9 +431,27 @@ __device__ __forceinline__ bool strip_step(const InstDev& d, int64_t step, int b
     // source terms at the half node h and the node i (source blocks only)
     auto src_h = [&](int h) { return source_half<T>(sw, sp_fac, h, j); };
     auto src_i = [&](int i) { return source_int<T>(sw, sc_fac, i, j); };
+    // the same for a moving particle: the column's radial factor joins the step's factor
+    auto msrc_h = [&](int h) {
+        const int a = h - sw.h_lo;
+        const T g = (unsigned)a < (unsigned)sw.nh ? gr[a] : T(0);
+        return source_half<T>(sw, g * sp_fac, h, j);
+    };
+    auto msrc_i = [&](int i) {
+        const int a = i - sw.i_lo;
+        const T g = (unsigned)a < (unsigned)sw.ni ? gr[sw.nh + a] : T(0);
+        return source_int<T>(sw, g * sc_fac, i, j);
+    };
     T cfh[kNCoef], cfi[kNCoef];
     coefs(0, c0 - 1, cfh, cfi);
-    HalfRec<T> L = predict(u_prev, u_cur, dl_prev, dl, dlm_prev, dlm, cfh, src_blk ? src_h(c0 - 1) : C::zero());
+    C s_first = C::zero();
+    if constexpr (kMov) {
+        if (gr) s_first = msrc_h(c0 - 1);
+        else if (src_blk) s_first = src_h(c0 - 1);
+    } else {
+        if (src_blk) s_first = src_h(c0 - 1);
+    }
+    HalfRec<T> L = predict(u_prev, u_cur, dl_prev, dl, dlm_prev, dlm, cfh, s_first);
     if (ex_blk && d.i_e == c0 - 1) extract(u_prev, u_cur);
     u_prev = u_cur;
     dl_prev = dl;
@@ -423,24 +460,28 @@ __device__ __forceinline__ bool strip_step(const InstDev& d, int64_t step, int b
 
     // steady state: column c arrives, predictor at c-1/2, corrector at c-1; the slots
     // hold columns c-2 (sf, free once the column's barrier is passed), c-1 (sp) and c (sc).
-    // Two instances of the loop: blocks without source nodes carry no source code; the
-    // source blocks load the next column's source terms one column ahead.
-    auto steady = [&](auto has_src) {
-        constexpr bool kSrc = decltype(has_src)::value;
+    // Three instances of the loop: blocks without source nodes carry no source code; the
+    // source blocks (circular orbit: kSrc = 1, moving particle: 2) load the next
+    // column's source terms one column ahead.
+    auto steady = [&](auto src_kind) {
+        constexpr int kSrc = decltype(src_kind)::value;
+        auto load_src = [&](int c, C& h, C& i) {
+            if constexpr (kSrc == 1) {
+                h = src_h(c);
+                i = src_i(c);
+            } else if constexpr (kSrc == 2 && kMov) {
+                h = msrc_h(c);
+                i = msrc_i(c);
+            }
+        };
         C nxt_h = C::zero(), nxt_i = C::zero();
-        if constexpr (kSrc) {
-            nxt_h = src_h(c0);
-            nxt_i = src_i(c0);
-        }
+        load_src(c0, nxt_h, nxt_i);
         int sf = 0, sp = 1, sc = 2;
 #pragma unroll 2
         for (int c = c0 + 1; c <= c1; ++c) {
             const C s_h = nxt_h, s_i = nxt_i;
-            if constexpr (kSrc) {
-                if (c < c1) {
-                    nxt_h = src_h(c);
-                    nxt_i = src_i(c);
-                }
+            if constexpr (kSrc != 0) {
+                if (c < c1) load_src(c, nxt_h, nxt_i);
             }
             ring.wait(sc);
             u_cur = node(sc);
@@ -460,8 +501,14 @@ __device__ __forceinline__ bool strip_step(const InstDev& d, int64_t step, int b
             sc = sc + 1 == R ? 0 : sc + 1;
         }
     };
-    if (src_blk) steady(std::true_type{});
-    else steady(std::false_type{});
+    if constexpr (kMov) {
+        if (gr) steady(std::integral_constant<int, 2>{});
+        else if (src_blk) steady(std::integral_constant<int, 1>{});
+        else steady(std::integral_constant<int, 0>{});
+    } else {
+        if (src_blk) steady(std::integral_constant<int, 1>{});
+        else steady(std::integral_constant<int, 0>{});
+    }
     if (__syncthreads_or(ring.late)) {
         if (threadIdx.x == 0) {
             ring.drain();
@@ -479,7 +526,7 @@ __device__ __forceinline__ bool strip_step(const InstDev& d, int64_t step, int b
 // part (may be null): the block's columns are [part[b], part[b+1]) instead of the uniform
 // strips; it is written by the host before the launch sequence and never changes while
 // a step runs, so it is read before griddepcontrol.wait.
-template <class P, int R>
+template <class P, int R, bool kMov>
 __device__ __forceinline__ void step_body(const InstDev& d, int64_t step, int bin, int strip,
                                           const int* part) {
     extern __shared__ __align__(128) unsigned char step_smem[];
@@ -498,19 +545,19 @@ __device__ __forceinline__ void step_body(const InstDev& d, int64_t step, int bi
         c0 = 1 + blockIdx.x * strip;
         c1 = min(d.nr - 1, c0 + strip);
     }
-    strip_step<P, R, true>(d, step, bin, c0, c1, ring, StepShared<P, R>::xbuf(step_smem));
+    strip_step<P, R, true, kMov>(d, step, bin, c0, c1, ring, StepShared<P, R>::xbuf(step_smem));
 }
 
-template <class P>
+template <class P, bool kMov>
 __global__ void __launch_bounds__(256, P::blocks256) step_kernel_s(InstDev d, int64_t step, int bin, int strip,
                                                                   const int* part) {
-    step_body<P, kRingS>(d, step, bin, strip, part);
+    step_body<P, kRingS, kMov>(d, step, bin, strip, part);
 }
 
-template <class P>
+template <class P, bool kMov>
 __global__ void __launch_bounds__(1024) step_kernel_l(InstDev d, int64_t step, int bin, int strip,
                                                      const int* part) {
-    step_body<P, kRingL>(d, step, bin, strip, part);
+    step_body<P, kRingL, kMov>(d, step, bin, strip, part);
 }
 
 // Waveform record of the state in buffer bin (time level `step`): one thread per row.
@@ -569,8 +616,8 @@ __device__ bool wait_neighbours(const BatchDev& b, const int* fl, int nstrip, in
 // Persistent kernel of one block-size class: blocks grab (step, instance, strip) items
 // in step order; an item waits for its radial neighbours of the previous step.  Items
 // only wait on items grabbed earlier, so the launch cannot deadlock whatever the
-// number of resident blocks.
-template <class P, int kMaxThreads, int kMinBlocks, int R>
+// number of resident blocks.  kMov: some instance of the class has a moving particle.
+template <class P, int kMaxThreads, int kMinBlocks, int R, bool kMov>
 __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) batched_step_kernel(BatchDev b) {
     extern __shared__ __align__(128) unsigned char step_smem[];
     __shared__ uint64_t mbar[R];
@@ -607,7 +654,7 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) batched_step_kernel(B
         }
         const int c0 = 1 + st * strip;
         const int c1 = min(d.nr - 1, c0 + strip);
-        strip_step<P, R, false>(d, b.base_step[k] + s, (int)((b.base_bin[k] + s) & 1), c0, c1, ring, xbuf);
+        strip_step<P, R, false, kMov>(d, b.base_step[k] + s, (int)((b.base_bin[k] + s) & 1), c0, c1, ring, xbuf);
         __threadfence();
         __syncthreads();
         if (threadIdx.x == 0 && !(s == 0 && r == b.skip_release_item))
@@ -639,12 +686,20 @@ static int grid_for(int threads) {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (threads <= 256)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batched_step_kernel<P, 256, P::blocks256, kRingS>, threads,
-                                                      StepShared<P, kRingS>::bytes(threads));
-    else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batched_step_kernel<P, 1024, 1, kRingL>, threads,
-                                                      StepShared<P, kRingL>::bytes(threads));
+    // the smaller residency of the two variants (with and without moving particles)
+    int per2 = 0;
+    if (threads <= 256) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batched_step_kernel<P, 256, P::blocks256, kRingS, false>,
+                                                      threads, StepShared<P, kRingS>::bytes(threads));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, batched_step_kernel<P, 256, P::blocks256, kRingS, true>,
+                                                      threads, StepShared<P, kRingS>::bytes(threads));
+    } else {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batched_step_kernel<P, 1024, 1, kRingL, false>,
+                                                      threads, StepShared<P, kRingL>::bytes(threads));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, batched_step_kernel<P, 1024, 1, kRingL, true>,
+                                                      threads, StepShared<P, kRingL>::bytes(threads));
+    }
+    per = per < per2 ? per : per2;
     return (per > 0 ? per : 1) * (sms > 0 ? sms : 1);
 }
 
@@ -655,19 +710,25 @@ int batched_grid(int prec, int threads) {
     return grid_for<PK>(threads);
 }
 
-template <class P>
-static void launch_batched_p(cudaStream_t st, const BatchDev& b, int grid, int threads) {
+template <class P, bool kMov>
+static void launch_batched_m(cudaStream_t st, const BatchDev& b, int grid, int threads) {
     if (threads <= 256)
-        batched_step_kernel<P, 256, P::blocks256, kRingS><<<grid, threads, StepShared<P, kRingS>::bytes(threads), st>>>(b);
+        batched_step_kernel<P, 256, P::blocks256, kRingS, kMov><<<grid, threads, StepShared<P, kRingS>::bytes(threads), st>>>(b);
     else
-        batched_step_kernel<P, 1024, 1, kRingL><<<grid, threads, StepShared<P, kRingL>::bytes(threads), st>>>(b);
+        batched_step_kernel<P, 1024, 1, kRingL, kMov><<<grid, threads, StepShared<P, kRingL>::bytes(threads), st>>>(b);
+}
+template <class P>
+static void launch_batched_p(cudaStream_t st, const BatchDev& b, int grid, int threads, bool mov) {
+    if (mov) launch_batched_m<P, true>(st, b, grid, threads);
+    else launch_batched_m<P, false>(st, b, grid, threads);
 }
 
-void launch_batched_step(cudaStream_t st, int prec, const BatchDev& b, int grid, int threads) {
-    if (prec == 0) launch_batched_p<P64>(st, b, grid, threads);
-    else if (prec == 1) launch_batched_p<P32>(st, b, grid, threads);
-    else if (prec == 3) launch_batched_p<PD>(st, b, grid, threads);
-    else launch_batched_p<PK>(st, b, grid, threads);
+void launch_batched_step(cudaStream_t st, int prec, const BatchDev& b, int grid, int threads,
+                         bool moving) {
+    if (prec == 0) launch_batched_p<P64>(st, b, grid, threads, moving);
+    else if (prec == 1) launch_batched_p<P32>(st, b, grid, threads, moving);
+    else if (prec == 3) launch_batched_p<PD>(st, b, grid, threads, moving);
+    else launch_batched_p<PK>(st, b, grid, threads, moving);
 }
 
 void launch_batched_extract(cudaStream_t st, int prec, const BatchDev& b, int max_nth) {
@@ -678,8 +739,8 @@ void launch_batched_extract(cudaStream_t st, int prec, const BatchDev& b, int ma
     else batched_extract_kernel<PK><<<g, 128, 0, st>>>(b);
 }
 
-template <class P>
-static void launch_step_p(cudaStream_t st, const InstDev& d, int64_t step, int bin, int strip,
+template <class P, bool kMov>
+static void launch_step_m(cudaStream_t st, const InstDev& d, int64_t step, int bin, int strip,
                           const int* part) {
     int blocks = (d.nr - 2 + strip - 1) / strip;
     int threads = d.pitch;
@@ -695,11 +756,17 @@ static void launch_step_p(cudaStream_t st, const InstDev& d, int64_t step, int b
     cfg.numAttrs = 1;
     if (threads <= 256) {
         cfg.dynamicSmemBytes = StepShared<P, kRingS>::bytes(threads);
-        cudaLaunchKernelEx(&cfg, step_kernel_s<P>, d, step, bin, strip, part);
+        cudaLaunchKernelEx(&cfg, step_kernel_s<P, kMov>, d, step, bin, strip, part);
     } else {
         cfg.dynamicSmemBytes = StepShared<P, kRingL>::bytes(threads);
-        cudaLaunchKernelEx(&cfg, step_kernel_l<P>, d, step, bin, strip, part);
+        cudaLaunchKernelEx(&cfg, step_kernel_l<P, kMov>, d, step, bin, strip, part);
     }
+}
+template <class P>
+static void launch_step_p(cudaStream_t st, const InstDev& d, int64_t step, int bin, int strip,
+                          const int* part) {
+    if (d.src.on && d.src.moving) launch_step_m<P, true>(st, d, step, bin, strip, part);
+    else launch_step_m<P, false>(st, d, step, bin, strip, part);
 }
 
 template <class P>
@@ -708,10 +775,10 @@ static int resident_p(int threads) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (threads <= 256)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, step_kernel_s<P>, threads,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, step_kernel_s<P, false>, threads,
                                                       StepShared<P, kRingS>::bytes(threads));
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, step_kernel_l<P>, threads,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, step_kernel_l<P, false>, threads,
                                                       StepShared<P, kRingL>::bytes(threads));
     return (per > 0 ? per : 1) * (sms > 0 ? sms : 1);
 }
@@ -733,14 +800,20 @@ void launch_step(cudaStream_t st, const InstDev& d, int64_t step, int bin, int s
 
 // Opt the step kernels in to the dynamic shared memory of their largest blocks (on the
 // current device; called when a context is created).
-template <class P>
-static cudaError_t prepare_p() {
+template <class P, bool kMov>
+static cudaError_t prepare_m() {
     const int s = (int)StepShared<P, kRingS>::bytes(256), l = (int)StepShared<P, kRingL>::bytes(1024);
     const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
-    cudaError_t e = cudaFuncSetAttribute(step_kernel_s<P>, a, s);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(step_kernel_l<P>, a, l);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(batched_step_kernel<P, 256, P::blocks256, kRingS>, a, s);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(batched_step_kernel<P, 1024, 1, kRingL>, a, l);
+    cudaError_t e = cudaFuncSetAttribute(step_kernel_s<P, kMov>, a, s);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(step_kernel_l<P, kMov>, a, l);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(batched_step_kernel<P, 256, P::blocks256, kRingS, kMov>, a, s);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(batched_step_kernel<P, 1024, 1, kRingL, kMov>, a, l);
+    return e;
+}
+template <class P>
+static cudaError_t prepare_p() {
+    cudaError_t e = prepare_m<P, false>();
+    if (e == cudaSuccess) e = prepare_m<P, true>();
     return e;
 }
 

@@ -487,9 +487,18 @@ __device__ __forceinline__ HalfRec<T> predictor(const Half<T>& h, Cx<T> Dp, Cx<T
 
 // ---------------------------------------------------------------- source
 // dt_sub A_n e^{-i (omega t + phase0)} at t = t_n + off * dt: the predictor's factor
-// (off = 0, dt_sub = dt/2) or the corrector's (off = 1/2, dt_sub = dt)
+// (off = 0, dt_sub = dt/2) or the corrector's (off = 1/2, dt_sub = dt); for a moving
+// particle dt_sub A e^{-i m phi_p} of the step's sample (the Gaussian is tabulated)
+template <bool kMov>
 __device__ __forceinline__ double2 source_factor(const InstDev& d, int64_t step, double off,
                                                  double dt_sub) {
+    if constexpr (kMov) {
+        if (d.src.moving) {   // sample 2n (off = 0) or 2n + 1 (off = 1/2) of a sampled path
+            if (step >= d.src.n_traj) return make_double2(0.0, 0.0);
+            const double2 A = d.src.amp[2 * step + (off == 0.0 ? 0 : 1)];
+            return make_double2(dt_sub * A.x, dt_sub * A.y);
+        }
+    }
     double A = (d.src.amps != nullptr && step < d.src.n_amps) ? d.src.amps[step] : 1.0;
     double t = (double)step * d.dt;
     double sn, cs;

@@ -86,6 +86,16 @@ class TeukSolver:
         check(_lib.load().teuk_set_source(self.ctx, instance, ctypes.byref(orb), ptr(a),
                                           0 if a is None else a.size), self.ctx)
 
+    def set_trajectory(self, traj, instance=0, sigma_rstar_cells=4.0, sigma_theta_cells=4.0,
+                       sigma_rstar_abs=0.0, sigma_theta_abs=0.0):
+        """Moving particle: traj [n_samples][4] = {r_p, theta_p, phi_p, A} at t = k dt/2
+        (step n takes samples 2n and 2n + 1)."""
+        orb = _lib.teuk_orbit(0.0, sigma_rstar_cells, sigma_theta_cells, sigma_rstar_abs,
+                              sigma_theta_abs)
+        t = np.ascontiguousarray(traj, dtype=np.float64).reshape(-1, 4)
+        check(_lib.load().teuk_set_trajectory(self.ctx, instance, ctypes.byref(orb), ptr(t),
+                                              t.shape[0]), self.ctx)
+
     def shape(self, instance=0):
         p = self.params[instance]
         return (4, p.n_theta, p.n_rstar)
