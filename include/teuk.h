@@ -168,6 +168,21 @@ teuk_status teuk_step_n(teuk_ctx* ctx, int64_t n);
 teuk_status teuk_extract(teuk_ctx* ctx, int instance, double* out, double* out_scalar,
                          int64_t cap_steps, int64_t* n_written, int64_t* first_step);
 
+/* The waveform summed over modes: the instances of the context are the modes m_i of
+ * one problem (the same s, M, a, n_theta, time step and extraction radius; with
+ * dt_rule 1 the step depends on |m|, so set dt), and the field of Eqs. (3)-(4),
+ * Psi = sum_m e^{i m phi~} r^3 Phi_m, is formed at the extraction radius:
+ *   out[k][j][l] = r_ext^3 sum_i e^{i m_i phi~_l} W_i[first + k][j]
+ *   phi~_l = phi[l] + a/(r_+ - r_-) ln((r_ext - r_+)/(r_ext - r_-))      (Eq. 3)
+ * for the time levels first .. first + n_records - 1 (each held by every instance,
+ * see teuk_extract) and the azimuths phi[0 .. n_phi-1] (host), instances added in
+ * index order, in one kernel.  out: host [n_records][n_theta][n_phi][2] (re, im).
+ * Allocates and frees 16 n_records n_theta n_phi bytes of device memory; synchronizes.
+ * TEUK_EINVAL if the instances are not modes of one problem, a record is not held,
+ * or n_phi < 1. */
+teuk_status teuk_mode_sum(teuk_ctx* ctx, const double* phi, int n_phi, int64_t first,
+                          int64_t n_records, double* out);
+
 /* Reverse-mode derivative of a waveform loss over the steps step0 .. step0+n-1 of
  * one instance (the transposed stencil of Eqs. 13-14, applied in kernels).
  *   grad_wave != NULL: host [n][n_theta][2] holding dL/dW for records step0+1 ..

@@ -18,7 +18,10 @@
  *   Eq. (14)     Lax-Wendroff corrector at the integer points i.
  *   Sec. 2.2 (after Eq. 14): centred second-order angular differences;
  *                Phi = Pi = 0 on both radial boundaries; d_theta Phi = 0 at the
- *                poles for even |m|, Phi = 0 at the poles for odd |m|.
+ *                poles for even |m|, Phi = 0 at the poles for odd |m| (stated for
+ *                the paper's s = -2; read here as the parity of |m + s|, the same for
+ *                even s and the pole behaviour of the spin-weighted harmonics,
+ *                ~ theta^|m+s|, for odd s).
  *
  * The matrices M, L, A of Eq. (8) are not printed in the paper.  The source
  * vector S used here is what Eq. (1) becomes after the substitutions of
@@ -171,7 +174,7 @@ typedef struct {
     int nr, nth;
     double drs, dth, dt;
     double rp, rm;
-    double ghost;            /* +1: even |m| (d_theta Phi = 0), -1: odd |m| (Phi = 0) */
+    double ghost;            /* +1: even |m + s| (d_theta Phi = 0), -1: odd |m + s| (Phi = 0) */
     int i_e;                 /* extraction between i_e and i_e + 1 */
     double f_e;              /* linear weight of node i_e + 1 */
 } orc_geom;
@@ -196,7 +199,7 @@ static int geom_of(const orc_params* p, orc_geom* g) {
         return ORC_EINVAL;
     }
     if (!(g->dt > 0)) return ORC_EINVAL;
-    g->ghost = (abs(p->m) % 2 == 0) ? 1.0 : -1.0;
+    g->ghost = (abs(p->m + p->s) % 2 == 0) ? 1.0 : -1.0;
     double pos = (p->rstar_ext - p->rstar_min) / g->drs;
     if (!(pos >= 0.0) || !(pos <= (double)(g->nr - 1))) return ORC_EINVAL;
     int ie = (int)floor(pos);
@@ -366,8 +369,8 @@ static int ctx_init(orc_ctx* c, const orc_params* p) {
 
 /* Row jj of a field F[nth][ncol] with the angular boundary condition applied
  * through ghost rows: row -1 mirrors row 0 and row nth mirrors row nth-1,
- * with sign +1 for even |m| (d_theta Phi = 0 at the pole face) and -1 for odd
- * |m| (Phi = 0 at the pole face). */
+ * with sign +1 for even |m + s| (d_theta Phi = 0 at the pole face) and -1 for
+ * odd |m + s| (Phi = 0 at the pole face). */
 static cplx row_val(const orc_ctx* c, const cplx* F, int ncol, int jj, int i) {
     int nth = c->g.nth;
     if (jj < 0) return c->g.ghost * F[(size_t)0 * ncol + i];

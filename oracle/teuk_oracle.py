@@ -201,6 +201,24 @@ def run_trajectory(p: Params, traj, u0=None, nsteps=1, step0=0, wave=True):
     return u, w
 
 
+def mode_sum(ps, waves, phi):
+    """The field of Eqs. (3)-(4) at the extraction radius summed over modes:
+    out[k][j][l] = r_ext^3 sum_i e^{i m_i phi~_l} W_i[k][j] with
+    phi~ = phi + a/(r_+ - r_-) ln((r_ext - r_+)/(r_ext - r_-)) (Eq. 3); ps: the modes'
+    parameters (same s, M, a, grid in theta, extraction radius), waves: their records
+    [k][n_theta][2].  Complex [k][n_theta][len(phi)]."""
+    g = grid(ps[0])
+    r_ext = orbit(ps[0])["r_ext"]
+    a, rp, rm = ps[0].a, g["rp"], g["rm"]
+    shift = a / (rp - rm) * np.log((r_ext - rp) / (r_ext - rm))
+    phi = np.atleast_1d(np.asarray(phi, dtype=np.float64))
+    out = np.zeros(waves[0].shape[:2] + (phi.size,), np.complex128)
+    for p, W in zip(ps, waves):
+        Wc = W[..., 0] + 1j * W[..., 1]
+        out += np.exp(1j * p.m * (phi + shift))[None, None, :] * Wc[:, :, None]
+    return r_ext ** 3 * out
+
+
 def apply_K(p: Params, x):
     y = np.zeros_like(x)
     _check(lib().orc_apply_K(ctypes.byref(p), _ptr(np.ascontiguousarray(x)), _ptr(y)))

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "teuk.h"
+#include "teuk_aux.cuh"
 #include "teuk_internal.cuh"
 #include "teuk_step_common.cuh"
 
@@ -181,7 +182,9 @@ InstDev dev_of(const teuk_ctx* c, const Instance& I) {
     d.drs = I.drs;
     d.dth = I.dth;
     d.dt = I.dt;
-    d.ghost = (std::abs(I.p.m) % 2 == 0) ? 1.0 : -1.0;
+    // pole rule of Sec. 2.2 (stated for s = -2) by the parity of |m + s|: the pole
+    // behaviour theta^|m+s| of the spin-weighted harmonics, the paper's rule for even s
+    d.ghost = (std::abs(I.p.m + I.p.s) % 2 == 0) ? 1.0 : -1.0;
     d.ghost_f = (float)d.ghost;
     for (int b = 0; b < 2; ++b)
         for (int k = 0; k < 2; ++k) d.buf[b][k] = I.state[b][k];
@@ -849,6 +852,58 @@ extern "C" teuk_status teuk_extract(teuk_ctx* c, int instance, double* out, doub
     TK_CUDA(c, cudaStreamSynchronize(c->stream));
     if (n_written) *n_written = k;
     if (first_step) *first_step = lvl0;
+    return TEUK_OK;
+}
+
+namespace {
+double r_of_rstar_host(double M, double a, double target);
+}  // namespace
+
+extern "C" teuk_status teuk_mode_sum(teuk_ctx* c, const double* phi, int n_phi, int64_t first,
+                                     int64_t n_records, double* out) {
+    if (!c) return TEUK_EINVAL;
+    if (n_phi < 1 || !phi || n_records < 0 || (n_records > 0 && !out))
+        TK_FAIL(c, TEUK_EINVAL, "need n_phi >= 1, phi, n_records >= 0 and an output buffer");
+    const Instance& I0 = c->inst[0];
+    const int nth = I0.p.n_theta;
+    std::vector<ModeRing> modes(c->inst.size());
+    for (size_t i = 0; i < c->inst.size(); ++i) {
+        const Instance& I = c->inst[i];
+        if (I.p.s != I0.p.s || I.p.M != I0.p.M || I.p.a != I0.p.a || I.p.n_theta != nth ||
+            I.dt != I0.dt || I.p.rstar_ext != I0.p.rstar_ext)
+            TK_FAIL(c, TEUK_EINVAL,
+                    "instance %d is not a mode of instance 0's problem (s, M, a, n_theta, time step "
+                    "and extraction radius must agree; set dt to share the step)", (int)i);
+        if (first < I.wave_lo || first + n_records > I.wave_hi)
+            TK_FAIL(c, TEUK_EINVAL, "instance %d holds records [%lld, %lld), not [%lld, %lld)", (int)i,
+                    (long long)I.wave_lo, (long long)I.wave_hi, (long long)first,
+                    (long long)(first + n_records));
+        modes[i] = ModeRing{I.wave, I.wave_cap, I.p.m, 0};
+    }
+    if (n_records == 0) return TEUK_OK;
+    // Eq. (3): phi~ = phi + a/(r_+ - r_-) ln((r - r_+)/(r - r_-)) at the extraction radius;
+    // Eq. (4): Psi = e^{i m phi~} r^3 Phi
+    const double r_ext = r_of_rstar_host(I0.p.M, I0.p.a, I0.p.rstar_ext);
+    const double shift = I0.p.a / (I0.rp - I0.rm) * std::log((r_ext - I0.rp) / (r_ext - I0.rm));
+    const size_t n_out = (size_t)n_records * nth * n_phi;
+    char* buf = nullptr;
+    const size_t b_modes = (sizeof(ModeRing) * modes.size() + 255) / 256 * 256;
+    const size_t b_phi = (sizeof(double) * n_phi + 255) / 256 * 256;
+    TK_CUDA(c, cudaMallocAsync((void**)&buf, b_modes + b_phi + sizeof(double2) * n_out, c->stream));
+    ModeRing* d_modes = (ModeRing*)buf;
+    double* d_phi = (double*)(buf + b_modes);
+    double2* d_out = (double2*)(buf + b_modes + b_phi);
+    cudaMemcpyAsync(d_modes, modes.data(), sizeof(ModeRing) * modes.size(), cudaMemcpyHostToDevice, c->stream);
+    cudaMemcpyAsync(d_phi, phi, sizeof(double) * n_phi, cudaMemcpyHostToDevice, c->stream);
+    launch_mode_sum(c->stream, d_modes, (int)modes.size(), nth, d_phi, n_phi, first, n_records,
+                    r_ext * r_ext * r_ext, shift, d_out);
+    c->launches++;
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out, d_out, sizeof(double2) * n_out, cudaMemcpyDeviceToHost, c->stream);
+    cudaFreeAsync(buf, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) TK_FAIL(c, TEUK_ECUDA, "mode sum: %s", cudaGetErrorString(e));
     return TEUK_OK;
 }
 

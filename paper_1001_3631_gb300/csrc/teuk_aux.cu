@@ -1,6 +1,7 @@
 // teuk_aux.cu -- small kernels around the time step: conversion between the host
-// u-layout and the internal planes, the finiteness scan, and the sin(theta)-weighted
-// theta sum of the waveform records.
+// u-layout and the internal planes, the finiteness scan, the sin(theta)-weighted
+// theta sum of the waveform records, and the sum of the records over modes.
+#include "teuk_aux.cuh"
 #include "teuk_internal.cuh"
 #include "teuk_step_common.cuh"
 
@@ -114,6 +115,42 @@ void launch_wave_sum(cudaStream_t st, const double2* wave, int64_t cap, int nth,
                      int64_t level0, int64_t k_count, double2* out) {
     wave_sum_kernel<<<(unsigned)((k_count + 127) / 128), 128, 0, st>>>(wave, cap, nth, dth, level0,
                                                                      k_count, out);
+}
+
+// Thread per (record k, row j, azimuth l), grid-stride; the modes are added in order.
+__global__ void mode_sum_kernel(const ModeRing* modes, int n_modes, int nth, const double* phi,
+                                int n_phi, int64_t first, int64_t n_rec, double r3, double shift,
+                                double2* out) {
+    const int64_t total = n_rec * nth * n_phi;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int l = (int)(idx % n_phi);
+        const int64_t t = idx / n_phi;
+        const int j = (int)(t % nth);
+        const int64_t k = t / nth;
+        const double ph = phi[l] + shift;
+        double re = 0.0, im = 0.0;
+        for (int i = 0; i < n_modes; ++i) {
+            const ModeRing q = modes[i];
+            const double2 w = q.wave[(size_t)((first + k) % q.cap) * nth + j];
+            double sn, cs;
+            sincos((double)q.m * ph, &sn, &cs);
+            re += cs * w.x - sn * w.y;
+            im += cs * w.y + sn * w.x;
+        }
+        out[idx] = make_double2(r3 * re, r3 * im);
+    }
+}
+
+void launch_mode_sum(cudaStream_t st, const ModeRing* modes, int n_modes, int nth,
+                     const double* phi, int n_phi, int64_t first, int64_t n_rec, double r3,
+                     double shift, double2* out) {
+    const int64_t total = n_rec * nth * n_phi;
+    int64_t blocks = (total + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks < 1) blocks = 1;
+    mode_sum_kernel<<<(unsigned)blocks, 256, 0, st>>>(modes, n_modes, nth, phi, n_phi, first,
+                                                      n_rec, r3, shift, out);
 }
 
 }  // namespace teuk

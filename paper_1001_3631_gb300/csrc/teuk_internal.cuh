@@ -84,7 +84,7 @@ struct ThTab { float sin2, cs, V, thp, thm, pad0, pad1, pad2; };
 struct InstDev {
     int nr, nth, pitch, prec;
     double drs, dth, dt;
-    float ghost_f;            // +1 even |m|, -1 odd |m|
+    float ghost_f;            // +1 even |m + s|, -1 odd |m + s|
     double ghost;
     void* buf[2][2];          // [ping-pong buffer][plane]
     const void* coef_h;       // [9][nr][pitch] (double or float)

@@ -11,7 +11,7 @@
 // exchange buffer (one barrier per column).  A strip reads two extra columns, so every
 // input is read from HBM about once per step.  The angular ghost
 // rows of the pole condition (Sec. 2.2) mirror row 0 / row n_theta-1 with sign +1
-// (even |m|) or -1 (odd |m|): on the averaged state in the predictor, on the half-node
+// (even |m + s|) or -1 (odd |m + s|): on the averaged state in the predictor, on the half-node
 // results in the corrector.
 //
 // Arithmetic, in differences so that the compensated FP32 state keeps its accuracy (a

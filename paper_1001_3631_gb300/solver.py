@@ -129,6 +129,17 @@ class TeukSolver:
             return out[:k], first.value, sc[:k]
         return out[:k], first.value
 
+    def mode_sum(self, phi, first, n_records):
+        """Psi = sum_m e^{i m phi~} r^3 Phi_m at the extraction radius over the instances
+        (modes of one problem) for time levels first .. first + n_records - 1 and the
+        azimuths phi: complex array [n_records][n_theta][len(phi)]."""
+        ph = np.ascontiguousarray(np.atleast_1d(phi), dtype=np.float64)
+        nth = self.params[0].n_theta
+        out = np.empty((n_records, nth, ph.size, 2))
+        check(_lib.load().teuk_mode_sum(self.ctx, ptr(ph), ph.size, int(first), int(n_records),
+                                        ptr(out)), self.ctx)
+        return out[..., 0] + 1j * out[..., 1]
+
     def adjoint(self, n, step0=0, grad_wave=None, ckpt_every=100, instance=0):
         """Returns (grad_amps [n], grad_r0, loss)."""
         gw = None if grad_wave is None else np.ascontiguousarray(grad_wave, dtype=np.float64)

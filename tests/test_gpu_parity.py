@@ -239,3 +239,30 @@ def test_waveform_ring_keeps_most_recent_records(orc):
         w, first = s.extract()
     assert first == 41 - 16 and w.shape[0] == 16
     assert rel(w, wo[first:]) <= FP64_TOL
+
+
+# ---------------------------------------------------------------- (s, m) sweep
+SWEEP = [(s, m) for s in (-2, -1, 0, 1, 2) for m in (-3, -1, 0, 1, 2, 4)]
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", FP64_TOL), ("fp32_kahan", 2e-6)])
+def test_spin_and_mode_sweep_in_one_batch(orc, prec, tol):
+    # every spin weight of Eq. (1) and positive, zero and negative modes, both pole
+    # parities, as instances of one batched context
+    base = dict(a=0.8, rstar_min=-10.0, rstar_max=30.0, n_rstar=70, n_theta=12,
+                rstar_ext=12.0, dt_rule=1, courant=0.5)
+    insts = [dict(base, s=s, m=m) for s, m in SWEEP]
+    n = 40
+    u0 = inputs.smooth_state(12, 70, seed=21)
+    with TeukSolver([dict(p, prec=prec) for p in insts]) as sv:
+        sv.set_tiling(0, 1)
+        for k in range(len(insts)):
+            sv.set_source(7.0, instance=k)
+            sv.set_state(u0, 0, instance=k)
+        sv.step(n)
+        got = [(sv.get_state(k), sv.extract(instance=k)[0]) for k in range(len(insts))]
+        sv.sync()
+    for k, p in enumerate(insts):
+        uo, wo = oracle_run(orc, p, 7.0, n, u0=u0)
+        assert rel(got[k][0], uo) <= tol, (p["s"], p["m"], rel(got[k][0], uo))
+        assert rel(got[k][1], wo) <= tol, (p["s"], p["m"])

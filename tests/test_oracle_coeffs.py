@@ -77,8 +77,9 @@ def test_first_order_split_terms(orc, a, r, th):
 
 
 # spin-weighted spherical harmonics sY_lm(theta): Theta[S] = -(l - s)(l + s + 1) S.
-# The pole rule of the paper (d_theta Phi = 0 for even |m|, Phi = 0 for odd |m|)
-# matches their behaviour near the poles when s is even, so only even s is used.
+# Near either pole sY_lm ~ theta^|m+s|, so the pole rule d_theta Phi = 0 / Phi = 0 by
+# the parity of |m + s| (the paper's even/odd |m| for its even s) fits every s; the odd
+# s entries fail with the rule by |m| alone.
 _C = sp.cos(derive.th)
 _S = sp.sin(derive.th)
 HARMONICS = [
@@ -88,6 +89,12 @@ HARMONICS = [
     (0, 0, 2, (3 * _C ** 2 - 1) / 2),
     (0, 1, 2, _S * _C),
     (0, 2, 2, _S ** 2),
+    (2, 2, 2, (1 - _C) ** 2),
+    (2, 1, 2, _S * (1 - _C)),
+    (1, 0, 1, _S),
+    (1, 1, 1, 1 - _C),
+    (-1, 1, 1, 1 + _C),
+    (-1, 0, 2, _S * _C),
 ]
 
 

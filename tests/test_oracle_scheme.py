@@ -25,7 +25,7 @@ def _brute_force(M, a, s, m, rs_min, rs_max, nr, nth, dt, u0, omega, phase0, P_i
     co = derive.mpmath_coefficients(M, a, s, m)
     drs = (mp.mpf(rs_max) - rs_min) / (nr - 1)
     dth = mp.pi / nth
-    ghost = 1 if abs(m) % 2 == 0 else -1
+    ghost = 1 if abs(m + s) % 2 == 0 else -1
 
     def r_of(rs):
         y = mp.findroot(lambda yy: derive.tortoise_of_x(M, a, mp.e ** yy) - rs, mp.mpf(0))
