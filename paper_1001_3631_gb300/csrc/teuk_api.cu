@@ -225,16 +225,20 @@ int eff_strip(const teuk_ctx* c, const Instance& I) {
 
 // Column partition of the per-step launch: the same number of blocks as uniform strips
 // of the effective length, cut so that the blocks have about equal cost.  A column costs
-// 1, a column of the source window 1 + alpha (its source terms; alpha = 0.25 on the FP32
-// paths, 0.1 on the FP64 path, measured per column on GB300) and the extraction column
-// 2 more (the FP64 waveform record).  Without it the blocks holding the source window
+// 1, a column of the source window 1 + alpha (its source terms) and the extraction
+// column 2 more (the FP64 waveform record).  alpha, measured on GB300 (16384 x 256 step
+// time against alpha): FP32 paths 0.25, FP64 0.1, double-float 0.4; for a moving
+// particle, whose source terms also carry the per-step Gaussian factors, FP32 0.8 and
+// double-float 0.6 (FP64: no better value than 0.1).  Without it the blocks holding the source window
 // finish last and every step waits for them.  Built on the host whenever the strip
 // length or the source changes, so a step never allocates or copies.
 teuk_status refresh_partition(teuk_ctx* c, Instance& I) {
     const int strip = eff_strip(c, I);
     const int nr = I.p.n_rstar;
     const int nb = (nr - 2 + strip - 1) / strip;
-    const double alpha = (I.p.prec == TEUK_FP64 || I.p.prec == TEUK_FP64_DF) ? 0.1 : 0.25;
+    const double alpha = I.p.prec == TEUK_FP64      ? 0.1
+                         : I.p.prec == TEUK_FP64_DF ? (I.sd.moving ? 0.6 : 0.4)
+                                                    : (I.sd.moving ? 0.8 : 0.25);
     int wlo = nr, whi = 0;
     if (I.src_on) {
         wlo = std::min(I.sd.i_lo, I.sd.h_lo + 1);
