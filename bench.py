@@ -149,13 +149,24 @@ def barrier(world):
         dist.barrier()
 
 
-def time_path(prec, cfg, S, K, W, world, dev_index):
+def moving_path(dt, n_steps):
+    """Samples of the bench's moving particle for n_steps time steps: a Keplerian path
+    (p = 10, e = 0.4, inclination 0.3, from anomaly 1.0)."""
+    from paper_1001_3631_gb300 import inputs
+    return inputs.eccentric_trajectory(2 * n_steps + 2, dt, semi_latus=10.0, ecc=0.4, incl=0.3,
+                                       chi0=1.0)
+
+
+def time_path(prec, cfg, S, K, W, world, dev_index, moving=False):
     import torch
 
     from paper_1001_3631_gb300 import TeukSolver
     p = cfg["params"]
     s = TeukSolver(dict(p, prec=prec))
-    s.set_source(cfg["r0"])
+    if moving:
+        s.set_trajectory(moving_path(s.geometry()["dt"], (W + K) * S))
+    else:
+        s.set_source(cfg["r0"])
     for _ in range(W):
         s.step(S)
     torch.cuda.synchronize()
@@ -179,34 +190,25 @@ def time_path(prec, cfg, S, K, W, world, dev_index):
     return s, ms, launches, npts, clocks
 
 
-def moving_leg(cfg, S, K=4, W=3):
+def moving_leg(cfg, S, world, dev_index, K=4, W=3):
     """The paper-scale grid with the particle on a sampled eccentric, inclined path
     (FP32-Kahan): per-step Gaussian factor tables instead of a fixed profile."""
-    import torch
-
-    from paper_1001_3631_gb300 import TeukSolver, inputs
-    p = cfg["params"]
-    s = TeukSolver(dict(p, prec="fp32_kahan"))
+    s, ms, launches, npts, clocks = time_path("fp32_kahan", cfg, S, K, W, world, dev_index,
+                                              moving=True)
     dt = s.geometry()["dt"]
-    traj = inputs.eccentric_trajectory(2 * (W + K) * S + 2, dt, semi_latus=10.0, ecc=0.4,
-                                       incl=0.3, chi0=1.0)
-    s.set_trajectory(traj)
-    for _ in range(W):
-        s.step(S)
-    stream = torch.cuda.current_stream()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(K):
-        s.step(S)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    s.sync()
     s.close()
-    npts = p["n_rstar"] * p["n_theta"]
+    r = moving_path(dt, (W + K) * S)[:, 0]
+    peak, kind = measured_peaks()
+    ach = KAHAN_BYTES_PER_UPDATE * npts / (ms / (K * S) * 1e-3) / 1e9
     return {"value": K * S * npts / (ms * 1e-3), "unit": "updates/s", "ms_per_step": ms / K,
-            "time_steps": K * S, "path": "Keplerian p = 10, e = 0.4, inclination 0.3 (r 7.1-16.7)"}
+            "time_steps": K * S, "gpu_launches": int(launches),
+            "path": "Keplerian p = 10, e = 0.4, inclination 0.3; r_p %.2f-%.2f over the run"
+                    % (r.min(), r.max()),
+            "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                         "frac": ach / peak, "traffic": ncu_traffic("fp32_kahan_moving"),
+                         "peak_source": kind, "bytes_per_update": KAHAN_BYTES_PER_UPDATE,
+                         "kernel": "step_kernel_s<PK, true>"},
+            "clocks": clocks}
 
 
 def e2e_path(prec, cfg, S, K, W):
@@ -483,7 +485,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the accuracy, end-to-end and CPU-baseline legs")
-    ap.add_argument("--only", choices=["fp32_kahan", "fp64", "fp64_df", "fp32"], default=None,
+    ap.add_argument("--only", choices=["fp32_kahan", "fp64", "fp64_df", "fp32", "moving"], default=None,
                     help="time one path only (for profiler captures)")
     ap.add_argument("--accuracy-steps", type=int, default=4000)
     ap.add_argument("--precision-sweep", action="store_true",
@@ -511,7 +513,10 @@ def main():
     S, K, W = args.chunk_steps, args.steps, args.warmup
 
     if args.only:
-        s_o, ms_o, _, _, _ = time_path(args.only, cfg, S, K, W, world, local)
+        if args.only == "moving":
+            s_o, ms_o, _, _, _ = time_path("fp32_kahan", cfg, S, K, W, world, local, moving=True)
+        else:
+            s_o, ms_o, _, _, _ = time_path(args.only, cfg, S, K, W, world, local)
         s_o.close()
         if rank == 0:
             print(json.dumps({"only": args.only, "ms": ms_o, "time_steps": K * S}))
@@ -587,7 +592,7 @@ def main():
     }
     if not args.no_extras:
         line["batched"] = batched_leg()
-        mv = moving_leg(cfg, S)
+        mv = moving_leg(cfg, S, world, local)
         mv["over_circular_orbit"] = mv["value"] / val_k
         line["moving_particle"] = mv
         line["single_mode_800x64"] = single_mode_leg()
