@@ -266,3 +266,17 @@ def test_spin_and_mode_sweep_in_one_batch(orc, prec, tol):
         uo, wo = oracle_run(orc, p, 7.0, n, u0=u0)
         assert rel(got[k][0], uo) <= tol, (p["s"], p["m"], rel(got[k][0], uo))
         assert rel(got[k][1], wo) <= tol, (p["s"], p["m"])
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", FP64_TOL), ("fp64_df", FP64_TOL),
+                                      ("fp32_kahan", 2e-6), ("fp32", 1e-5)])
+def test_largest_theta_resolution(orc, prec, tol):
+    # 1024 rows, the largest column a block holds (the kernels for columns of more than
+    # 256 rows, per-step and persistent), with a ragged radial size and the source
+    params = dict(s=-2, m=3, a=0.7, rstar_min=-10.0, rstar_max=20.0, n_rstar=23, n_theta=1024,
+                  rstar_ext=5.3, dt_rule=1, courant=0.5)
+    u0 = inputs.smooth_state(1024, 23, seed=13)
+    uo, wo = oracle_run(orc, params, 6.0, 12, u0)
+    for persistent in (False, True):
+        ug, wg, _ = gpu_run(params, 6.0, 12, u0, prec=prec, persistent=persistent)
+        assert rel(ug, uo) <= tol and rel(wg, wo) <= tol, (persistent, rel(ug, uo), rel(wg, wo))
