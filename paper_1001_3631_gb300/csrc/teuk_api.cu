@@ -976,7 +976,7 @@ extern "C" teuk_status teuk_set_instance_tiling(teuk_ctx* c, int instance, int s
 
 // Contexts that step through the persistent kernels (several instances, or one in
 // persistent mode) run one launch per block-size class over all its instances, so a
-// strip length is judged in that setting: trial_steps steps of the whole context are
+// strip length is evaluated in that setting: trial_steps steps of the whole context are
 // timed for each candidate, first with one length for every instance, then class by
 // class with the others held at their best, on the live state; afterwards every
 // instance's state, time level and waveform records are restored from a snapshot.
