@@ -316,13 +316,18 @@ def batched_leg(n_calls=4, steps_per_call=25, warm_calls=2):
 
 def single_mode_leg(steps=2000):
     """The 800 x 64 single mode (51,200 points, L2-resident): one kernel per step on the
-    default stream versus the whole run in one persistent launch from a CUDA graph."""
+    default stream versus the whole run in one persistent launch from a CUDA graph, for
+    FP64, the FP64-equivalent double-float path and FP32-Kahan; hbm_frac is 64 B per
+    update against the measured HBM copy bandwidth (the grid is L2-resident, so this is
+    the fraction of the HBM roofline, not a DRAM measurement)."""
     import torch
 
     from paper_1001_3631_gb300 import TeukSolver, inputs
     cfg = inputs.SINGLE_MODE_800x64
     out = {"workload": "single mode 800x64 (s=-2, m=2, a=0.9), %d steps" % steps}
-    for prec in ("fp64", "fp32_kahan"):
+    peak, _ = measured_peaks()
+    frac = {}
+    for prec in ("fp64", "fp64_df", "fp32_kahan"):
         for mode in ("per_step", "persistent"):
             stream = torch.cuda.Stream()
             with torch.cuda.stream(stream):
@@ -338,8 +343,11 @@ def single_mode_leg(steps=2000):
                 stream.synchronize()
                 ms = e0.elapsed_time(e1)
                 s.close()
-            out["%s_%s" % (prec, mode)] = 51200 * steps / (ms * 1e-3)
+            ups = 51200 * steps / (ms * 1e-3)
+            out["%s_%s" % (prec, mode)] = ups
+            frac["%s_%s" % (prec, mode)] = 64 * ups / 1e9 / peak
     out["unit"] = "updates/s"
+    out["hbm_frac"] = frac
     return out
 
 
