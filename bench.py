@@ -316,7 +316,8 @@ def batched_leg(n_calls=4, steps_per_call=25, warm_calls=2):
 
 def single_mode_leg(steps=2000):
     """The 800 x 64 single mode (51,200 points, L2-resident): one kernel per step on the
-    default stream versus the whole run in one persistent launch from a CUDA graph, for
+    default stream versus the whole run in one persistent launch from a CUDA graph (strip
+    length from the autotuner), for
     FP64, the FP64-equivalent double-float path and FP32-Kahan; hbm_frac is 64 B per
     update against the measured HBM copy bandwidth (the grid is L2-resident, so this is
     the fraction of the HBM roofline, not a DRAM measurement)."""
@@ -334,6 +335,12 @@ def single_mode_leg(steps=2000):
                 s = TeukSolver(dict(cfg["params"], prec=prec), stream=stream)
                 s.set_tiling(0, 1 if mode == "per_step" else 0)
                 s.set_source(cfg["r0"])
+                if mode == "persistent":
+                    # strip length of the persistent kernel from the autotuner (timed on
+                    # this context; a fresh table so that it always measures)
+                    with tempfile.TemporaryDirectory() as td:
+                        out["%s_persistent_strip" % prec] = int(
+                            s.autotune(trial_steps=20, cache_path=os.path.join(td, "t.json"))[0])
                 s.step(steps)
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 stream.synchronize()
