@@ -1052,7 +1052,18 @@ static teuk_status autotune_batched(teuk_ctx* c, int trial_steps, int* chosen) {
         }
         cls[q].push_back(k);
     }
-    const int cand[] = {16, 32, 64, 128, 256, 512};
+    // strips of 16 to 512 columns; shorter ones as well when 16-column strips would leave
+    // fewer than four work items per step for each SM (a grid too small to fill the GPU,
+    // where one-column strips are fastest)
+    std::vector<int> cand = {16, 32, 64, 128, 256, 512};
+    {
+        int64_t items16 = 0;
+        for (int k = 0; k < ni; ++k) items16 += (c->inst[k].p.n_rstar - 2 + 15) / 16;
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (items16 < 4 * (int64_t)(sms > 0 ? sms : 1)) cand.insert(cand.begin(), {1, 2, 4, 8});
+    }
     float best_ms = 1e30f;
     int best_all = 128;
     teuk_status st = TEUK_OK;

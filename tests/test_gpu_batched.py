@@ -148,7 +148,9 @@ def test_autotune_keeps_results_and_state(tmp_path):
         before = [s.get_state(k) for k in range(len(INST))]
         wb = [s.extract(instance=k)[0] for k in range(len(INST))]
         chosen = s.autotune(trial_steps=3, cache_path=str(tmp_path / "tune.json"))
-        assert len(chosen) == len(INST) and all(c >= 4 for c in chosen)
+        # valid strips (grids this small may take one-column strips)
+        assert len(chosen) == len(INST)
+        assert all(1 <= c <= i["params"]["n_rstar"] - 2 for c, i in zip(chosen, INST))
         for k in range(len(INST)):
             assert np.array_equal(s.get_state(k), before[k])
             assert np.array_equal(s.extract(instance=k)[0], wb[k])
