@@ -288,8 +288,11 @@ const char* teuk_last_error(const teuk_ctx* ctx);
  * GPU loading the library holds until the process exits.  n_records above that
  * size, n_theta outside [1, 1024] or NULL pointers are TEUK_EINVAL (message in
  * teuk_last_error(NULL)); CUDA failures are TEUK_ECUDA.
- * The first call on each device looks up the array's device address (once, with
- * that device current); make that first call before any stream capture.
+ * Every call looks up the array's device address on the current device (this
+ * allocates nothing).  With lazy module loading (the CUDA default) the first call on a
+ * device is what loads the library's device code there and places the array, so make
+ * one call with n_records = 0 on each device (it does only that) before the region
+ * that must not allocate, and before any stream capture.
  * All calls share the one array: calls whose GPU work overlaps (different streams
  * or threads at the same time) race on it and must be serialized by the caller.
  */

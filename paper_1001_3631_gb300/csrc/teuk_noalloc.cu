@@ -12,9 +12,9 @@
 // The scratch is one file-scope __device__ array of kNoAllocMaxRecords double2
 // values (1 MiB), present on every GPU that loads the library until the process
 // exits.  Host code never passes the array's name to a kernel (in host code that
-// name is only a stand-in); the first call on each device looks up its device
-// address with cudaGetSymbolAddress, with that device current, and caches it.
-#include <mutex>
+// name is only a stand-in): every call looks up the array's device address on the
+// current device with cudaGetSymbolAddress (which allocates nothing), so the address
+// is never stale, for example after a device reset.
 #include <string>
 
 #include "teuk.h"
@@ -27,27 +27,16 @@ void set_global_error(const std::string& msg);
 namespace {
 
 constexpr int64_t kNoAllocMaxRecords = TEUK_NOALLOC_MAX_RECORDS;
-constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) double2 g_wave_sum_scratch[kNoAllocMaxRecords];
 
-std::mutex g_scratch_mu;
-double2* g_scratch_addr[kMaxDevices] = {};
-
-// Device address of the scratch array on the current device (looked up once per device).
+// Device address of the scratch array on the current device.  Under lazy module
+// loading the first lookup on a device is what loads the module and places the array.
 cudaError_t scratch_address(double2** out) {
-    int dev = -1;
-    cudaError_t e = cudaGetDevice(&dev);
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_wave_sum_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_wave_sum_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_addr[dev] = (double2*)p;
-    }
-    *out = g_scratch_addr[dev];
+    *out = (double2*)p;
     return cudaSuccess;
 }
 
@@ -66,15 +55,21 @@ extern "C" teuk_status teuk_waveform_sum_noalloc(const double* wave_dev, int64_t
         teuk::set_global_error("teuk_waveform_sum_noalloc: n_theta must be in [1, 1024]");
         return TEUK_EINVAL;
     }
+    // the lookup comes first, so that a call with no records places the array on this
+    // device: the warm-up to make before a region that must not allocate
+    double2* scratch = nullptr;
+    cudaError_t e = scratch_address(&scratch);
+    if (e != cudaSuccess) {
+        teuk::set_global_error(std::string("teuk_waveform_sum_noalloc: ") + cudaGetErrorString(e));
+        return TEUK_ECUDA;
+    }
     if (n_records == 0) return TEUK_OK;
     if (!wave_dev || !out_host) {
         teuk::set_global_error("teuk_waveform_sum_noalloc: NULL input or output");
         return TEUK_EINVAL;
     }
     cudaStream_t st = (cudaStream_t)cuda_stream;
-    double2* scratch = nullptr;
-    cudaError_t e = scratch_address(&scratch);
-    if (e == cudaSuccess) {
+    {
         const double dth = 3.141592653589793238462643 / (double)n_theta;
         // every output element is written, so nothing has to be cleared first
         teuk::launch_wave_sum(st, (const double2*)wave_dev, n_records, n_theta, dth, 0, n_records,
