@@ -193,3 +193,58 @@ def test_autograd_function_matches_builtin_adjoint():
     assert float(L.detach()) == pytest.approx(Lb, rel=1e-13)
     assert rel(amps.grad.numpy(), ga) <= 1e-12
     assert float(r0t.grad) == pytest.approx(gr, rel=1e-12)
+
+
+def test_autograd_two_applies_on_one_solver_then_one_backward():
+    """Each apply's backward differentiates its own problem even when a later apply on
+    the same solver has replaced the source: L = f(A1, r1) + f(A2, r2)."""
+    import torch
+
+    from paper_1001_3631_gb300.autograd import TeukWaveformFn, psi_loss
+    params = dict(SMALL, m=2, n_rstar=121, n_theta=8, rstar_min=-20.0, rstar_max=40.0,
+                  rstar_ext=11.0)
+    n = 60
+    a1, a2 = inputs.amplitudes(n, seed=31), inputs.amplitudes(n, seed=32)
+    with TeukSolver(dict(params, prec="fp64", wave_capacity=n + 1)) as s:
+        A1 = torch.tensor(a1, dtype=torch.float64, requires_grad=True)
+        A2 = torch.tensor(a2, dtype=torch.float64, requires_grad=True)
+        r1 = torch.tensor(8.0, dtype=torch.float64, requires_grad=True)
+        r2 = torch.tensor(9.5, dtype=torch.float64, requires_grad=True)
+        L = psi_loss(s, TeukWaveformFn.apply(A1, r1, s, n)) + psi_loss(s, TeukWaveformFn.apply(A2, r2, s, n))
+        L.backward()
+        ref = []
+        for a, r in ((a1, 8.0), (a2, 9.5)):
+            s.set_source(r, a)
+            s.set_state(np.zeros(s.shape()), 0)
+            ref.append(s.adjoint(n, step0=0, ckpt_every=0))
+    assert rel(A1.grad.numpy(), ref[0][0]) <= 1e-12
+    assert rel(A2.grad.numpy(), ref[1][0]) <= 1e-12
+    assert float(r1.grad) == pytest.approx(ref[0][1], rel=1e-12)
+    assert float(r2.grad) == pytest.approx(ref[1][1], rel=1e-12)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_kahan"])
+def test_checkpointed_loss_function_matches_waveform_function(prec):
+    """TeukPsiLossFn (checkpointed forward, segment recomputation in the reverse sweep)
+    gives the loss and gradients of TeukWaveformFn followed by psi_loss, scaled by the
+    incoming gradient."""
+    import torch
+
+    from paper_1001_3631_gb300.autograd import TeukPsiLossFn, TeukWaveformFn, psi_loss
+    params = dict(SMALL, m=2, n_rstar=201, n_theta=16, rstar_min=-20.0, rstar_max=40.0,
+                  rstar_ext=11.0)
+    n, r0 = 230, 8.0
+    amps0 = inputs.amplitudes(n, seed=4)
+    with TeukSolver(dict(params, prec=prec, wave_capacity=n + 1)) as s:
+        A = torch.tensor(amps0, dtype=torch.float64, requires_grad=True)
+        R = torch.tensor(r0, dtype=torch.float64, requires_grad=True)
+        L = TeukPsiLossFn.apply(A, R, s, n, 50)
+        (3.0 * L).backward()
+        A2 = torch.tensor(amps0, dtype=torch.float64, requires_grad=True)
+        R2 = torch.tensor(r0, dtype=torch.float64, requires_grad=True)
+        L2 = psi_loss(s, TeukWaveformFn.apply(A2, R2, s, n))
+        (3.0 * L2).backward()
+    tol = 1e-12 if prec == "fp64" else 1e-6
+    assert float(L.detach()) == pytest.approx(float(L2.detach()), rel=tol)
+    assert rel(A.grad.numpy(), A2.grad.numpy()) <= tol
+    assert float(R.grad) == pytest.approx(float(R2.grad), rel=max(tol, 1e-12))
