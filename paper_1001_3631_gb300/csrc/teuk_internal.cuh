@@ -75,11 +75,12 @@ struct SourceDev {
 //   g  = Rd * rs                                      (Rd = sdt R / dr*)
 //   c_t = (ctr iS, (cti + ctc cos) iS),  E1 = nsdt c_t   (nsdt = -sdt)
 //   E2 = c_t g + ((pr + nbb sin^2 iS) iS, pi iS)       (pr, pi, nbb = -bb scaled by sdt/dr*)
-//   ep, em = Ds iS (1/dth^2 +- cot/(2 dth))           (Ds = sdt Delta)
+//   A, B = Ds iS / dth^2, Ds iS cot / (2 dth)         (Ds = sdt Delta; the split angular
+//                                                       form, ep = A + B, em = A - B)
 //   E3 = ((qr + nDs V) iS, qi iS)                      (qr, qi scaled by sdt; nDs = -Ds)
 struct RTab2 { float2 R2, naD, Rd, ctr, cti, ctc, pr, pi, nbb, Ds, nDs, qr, qi, nsdt, pad0, pad1; };
-// Per theta row: sin^2, cos, V = (m + s cos)^2/sin^2 - s, th_p, th_m = 1/dth^2 +- cot/(2 dth)
-struct ThTab { float sin2, cs, V, thp, thm, pad0, pad1, pad2; };
+// Per theta row: sin^2, cos, V = (m + s cos)^2/sin^2 - s, i2 = 1/dth^2, i1 = cot/(2 dth)
+struct ThTab { float sin2, cs, V, i2, i1, pad0, pad1, pad2; };
 
 struct InstDev {
     int nr, nth, pitch, prec;

@@ -349,8 +349,8 @@ __global__ void tables_1d_kernel(double M, double a, int s, int m, double drs, d
         t.sin2 = (float)(sn * sn);
         t.cs = (float)cs;
         t.V = (float)((mv + sv * cs) * (mv + sv * cs) / (sn * sn) - sv);
-        t.thp = (float)(1.0 / (dth * dth) + cs / sn / (2.0 * dth));
-        t.thm = (float)(1.0 / (dth * dth) - cs / sn / (2.0 * dth));
+        t.i2 = (float)(1.0 / (dth * dth));
+        t.i1 = (float)(cs / sn / (2.0 * dth));
         t.pad0 = t.pad1 = t.pad2 = 0.f;
         thtab[k] = t;
     }

@@ -29,7 +29,9 @@
 // with the scaled coefficients g, E1, E2, ep, em, E3 of teuk_setup.cu (the two
 // sub-steps differ only by the factor 1/2 versus 1 of dt).  This is Eqs. (13)-(14)
 // with S_Pi = -c_t Pi + P* Phi_* + w Theta[Phi] + q Phi + tau, rearranged, not
-// approximated.
+// approximated.  The FP32 paths write the angular part ep D+ - em D- in the split form
+// A (D+ - D-) + B (D+ + D-) (A = (ep + em)/2, B = (ep - em)/2, see split_angular), with
+// the second and two-cell differences formed directly from the state.
 #include <type_traits>
 
 #include "teuk_internal.cuh"
@@ -309,20 +311,26 @@ __device__ __forceinline__ bool strip_step(const InstDev& d, int64_t step, int b
     // own node of the column in slot s (rows past nth read slot padding: their results
     // are never stored or exchanged)
     auto node = [&](int s) { return ring.planes(s).load((size_t)j); };
-    // theta differences of Phi in the column in slot s (own node u)
+    // theta differences of Phi in the column in slot s (own node u): forward and backward
+    // (expanded angular form) or second and two-cell (split form, see split_angular)
+    constexpr bool kSplit = split_angular<P>();
     auto theta_diffs = [&](int s, const NodeV<P>& u, C& dl, C& dlm) {
         const Planes<P> pl = ring.planes(s);
         const NodeV<P> dn = pl.load_phi((size_t)jp), upn = pl.load_phi((size_t)jm);
-        dl = dn.dphi_sl(gp, u);
-        dlm = u.dphi_sr(gm, upn);
+        if constexpr (kSplit) {
+            u.theta_split(gp, dn, gm, upn, dl, dlm);
+        } else {
+            dl = dn.dphi_sl(gp, u);
+            dlm = u.dphi_sr(gm, upn);
+        }
     };
     // predictor at the half node h between columns h (ul) and h+1 (ur)
     auto predict = [&](const NodeV<P>& ul, const NodeV<P>& ur, C dll, C dlr, C dlml, C dlmr,
                        const T* cf, C src) {
         const Half<T> hp = half_prep<P>(ul, ur);
-        const C Dp = C::half_sum(dll, dlr);     // Fb(j+1) - Fb(j)
-        const C Dm = C::half_sum(dlml, dlmr);   // Fb(j) - Fb(j-1)
-        return predictor<T>(hp, Dp, Dm, cf, hdt, src);
+        const C Dp = C::half_sum(dll, dlr);     // Fb(j+1) - Fb(j)    (split: Fb(j+1) - 2 Fb(j) + Fb(j-1))
+        const C Dm = C::half_sum(dlml, dlmr);   // Fb(j) - Fb(j-1)    (split: Fb(j+1) - Fb(j-1))
+        return predictor<T, kSplit>(hp, Dp, Dm, cf, hdt, src);
     };
     // coefficients of column col: the half node col+1/2 into cfh and, on the FP32 paths
     // (formed together in paired instructions), the node col into cfi
@@ -346,10 +354,11 @@ __device__ __forceinline__ bool strip_step(const InstDev& d, int64_t step, int b
     // node's coefficients on the FP32 paths (the FP64 path reads them here)
     auto correct = [&](const HalfRec<T>& Rh, const HalfRec<T>& Lh, const NodeV<P>& uc,
                        const T* cfi, int cc, T* xb, size_t o, C srcc) {
-        const CRow<T> row = combine_lr<T>(Rh, Lh);
+        const CRow<T> row = combine_lr<T, kSplit>(Rh, Lh);
         // publish {Hs, DpS} of this row at entry j + 1; the pole rows also write the
         // ghost entries: row nth (entry nth + 1) Hs = g Hs(nth-1), row -1 (entry 0)
-        // Hs = g Hs(0) and DpS = (Dp_R(-1) + Dp_L(-1))/2 = (1 - g) (Fb_R + Fb_L)(0)/2
+        // Hs = g Hs(0) and DpS = (Dp_R(-1) + Dp_L(-1))/2 = (1 - g) (Fb_R + Fb_L)(0)/2.
+        // The split form needs Hs alone: its averaged differences are the row's own.
         T* mine = xb + 4 * (j + 1);
         auto put = [](T* e, C a, C b) {
             if constexpr (P::kind == kDF) {
@@ -362,12 +371,22 @@ __device__ __forceinline__ bool strip_step(const InstDev& d, int64_t step, int b
                 ((double2*)e)[1] = make_double2(b.re, b.im);
             }
         };
-        if (row_ok) put(mine, row.Hs, row.DpS);
-        if (top) put(mine + 4, g * row.Hs, C::zero());
-        if (bot) put(xb, g * row.Hs, (T(1) - g) * C::half_sum(Rh.Fb, Lh.Fb));
+        if constexpr (kSplit) {
+            if (row_ok) *(float2*)mine = make_float2(row.Hs.re, row.Hs.im);
+            if (top) *(float2*)(mine + 4) = make_float2(g * row.Hs.re, g * row.Hs.im);
+            if (bot) *(float2*)xb = make_float2(g * row.Hs.re, g * row.Hs.im);
+        } else {
+            if (row_ok) put(mine, row.Hs, row.DpS);
+            if (top) put(mine + 4, g * row.Hs, C::zero());
+            if (bot) put(xb, g * row.Hs, (T(1) - g) * C::half_sum(Rh.Fb, Lh.Fb));
+        }
         __syncthreads();
         C Hs_p, Hs_m, DpS_m;
-        if constexpr (P::kind == kDF) {
+        if constexpr (kSplit) {
+            const float2 a = *(const float2*)(mine + 4), b = *(const float2*)(mine - 4);
+            Hs_p = {a.x, a.y};
+            Hs_m = {b.x, b.y};
+        } else if constexpr (P::kind == kDF) {
             const float4 a = *(const float4*)(mine + 4);
             const float4 b0 = ((const float4*)(mine - 4))[0], b1 = ((const float4*)(mine - 4))[1];
             Hs_p = {DF(a.x, a.y), DF(a.z, a.w)};
@@ -386,8 +405,16 @@ __device__ __forceinline__ bool strip_step(const InstDev& d, int64_t step, int b
             Hs_m = {b0.x, b0.y};
             DpS_m = {b1.x, b1.y};
         }
-        const C Dplus = row.DpS + (Hs_p - row.Hs);
-        const C Dminus = DpS_m + (row.Hs - Hs_m);
+        // expanded: Dplus = u~(j+1) - u~(j), Dminus = u~(j) - u~(j-1) of the corrector's
+        // averaged state u~ = (h_R + h_L)/2; split: its second and two-cell differences
+        C Dplus, Dminus;
+        if constexpr (kSplit) {
+            Dplus = row.DpS + ((Hs_p - row.Hs) - (row.Hs - Hs_m));
+            Dminus = row.D1S + (Hs_p - Hs_m);
+        } else {
+            Dplus = row.DpS + (Hs_p - row.Hs);
+            Dminus = DpS_m + (row.Hs - Hs_m);
+        }
         T cf[kNCoef];
         if constexpr (kTabsPath) {
 #pragma unroll
@@ -401,8 +428,13 @@ __device__ __forceinline__ bool strip_step(const InstDev& d, int64_t step, int b
         C dPi = rmac(srcc, cf[C_G], row.dPc);
         dPi = cmac(dPi, cf[C_E1R], cf[C_E1I], row.PC);
         dPi = cmac(dPi, cf[C_E2R], cf[C_E2I], row.dFc);
-        dPi = rmac(dPi, cf[C_EP], Dplus);
-        dPi = rmac(dPi, -cf[C_EM], Dminus);
+        if constexpr (kSplit) {
+            dPi = rmac(dPi, cf[C_EP], Dplus);
+            dPi = rmac(dPi, cf[C_EM], Dminus);
+        } else {
+            dPi = rmac(dPi, cf[C_EP], Dplus);
+            dPi = rmac(dPi, -cf[C_EM], Dminus);
+        }
         dPi = cmac(dPi, cf[C_E3R], cf[C_E3I], row.FC);
         if (row_ok) {
             NodeV<P> u = uc;

@@ -220,6 +220,25 @@ struct NodeV {
         if constexpr (P::kahan) return a - rmac(Fc, -gs, o.Fc);
         else return a;
     }
+    // Split theta differences of Phi at this node from the rows above (a, factor ga)
+    // and below (b, factor gb): d2 = ga a - 2 this + gb b and d1 = ga a - gb b.  For
+    // compensated pairs the hi differences (exact for neighbouring values within a
+    // factor of two) and the c differences are combined first, so d2 and d1 round
+    // relative to their own size, not to that of the first differences.
+    __device__ __forceinline__ void theta_split(T ga, const NodeV& a, T gb, const NodeV& b,
+                                                Cx<T>& d2, Cx<T>& d1) const {
+        const Cx<T> hp = rmac(neg(F), ga, a.F);   // ga a - this
+        const Cx<T> hm = rmac(F, -gb, b.F);       // this - gb b
+        if constexpr (P::kahan) {
+            const Cx<T> cp = rmac(neg(Fc), ga, a.Fc);
+            const Cx<T> cm = rmac(Fc, -gb, b.Fc);
+            d2 = (hp - hm) - (cp - cm);
+            d1 = (hp + hm) - (cp + cm);
+        } else {
+            d2 = hp - hm;
+            d1 = hp + hm;
+        }
+    }
     __device__ __forceinline__ Cx<T> dpi(const NodeV& o) const {
         if constexpr (P::kahan) return (Pp - o.Pp) - (Pc - o.Pc);
         else return Pp - o.Pp;
@@ -380,24 +399,40 @@ __device__ __forceinline__ Half<typename P::T> half_prep(const NodeV<P>& own, co
     return h;
 }
 
+// Angular term of S_Pi, w Theta[F] - w V F (the V part sits in E3), in one of two forms:
+//   expanded (FP64, double-float): ep (F_{j+1} - F_j) - em (F_j - F_{j-1}),
+//   split (FP32 paths):            A (F_{j+1} - 2 F_j + F_{j-1}) + B (F_{j+1} - F_{j-1}),
+//   A = s dt w / dth^2, B = s dt w cot / (2 dth)  (ep = A + B, em = A - B).
+// The two are the same operator.  In FP32 the split form keeps the large coefficient
+// A on the second difference, which is formed from the compensated pairs to its own
+// relative accuracy; the expanded form would round ep and em separately and apply
+// them to first differences, an error of order A times the first difference that the
+// long-run growth of the angular modes then amplifies.
+template <class P>
+__host__ __device__ constexpr bool split_angular() { return P::kind == kFP32 || P::kind == kKahan; }
+
 // Predictor output at one half node, plus the inputs the corrector needs from it.
+// Expanded form: Dp = Fb(j+1) - Fb(j) (D1 unused); split form: Dp = Fb(j+1) - 2 Fb(j) +
+// Fb(j-1), D1 = Fb(j+1) - Fb(j-1).
 template <typename T>
-struct HalfRec { Cx<T> Fb, Pb, dF, dP, Dp, hF, hP; };
+struct HalfRec { Cx<T> Fb, Pb, dF, dP, Dp, D1, hF, hP; };
 
 // Corrector inputs of one row, combined from the half nodes R = i+1/2 and L = i-1/2.
 template <typename T>
 struct CRow {
     Cx<T> Hs;        // (dh_Phi_R + dh_Phi_L)/2
     Cx<T> DpS;       // (Dp_R + Dp_L)/2
+    Cx<T> D1S;       // (D1_R + D1_L)/2 (split form)
     Cx<T> FC, PC;    // u~ = (h_R + h_L)/2 for Phi and Pi
     Cx<T> dFc, dPc;  // h_R - h_L for Phi and Pi
 };
 
-template <typename T>
+template <typename T, bool kSplit>
 __device__ __forceinline__ CRow<T> combine_lr(const HalfRec<T>& R, const HalfRec<T>& L) {
     CRow<T> c;
     c.Hs = Cx<T>::half_sum(R.hF, L.hF);
     c.DpS = Cx<T>::half_sum(R.Dp, L.Dp);
+    if constexpr (kSplit) c.D1S = Cx<T>::half_sum(R.D1, L.D1);
     c.FC = half_sum_add(R.Fb, L.Fb, c.Hs);
     c.PC = half_sum_add(R.Pb, L.Pb, Cx<T>::half_sum(R.hP, L.hP));
     c.dFc = half_sum_add(R.dF, L.dF, R.hF - L.hF);
@@ -414,14 +449,14 @@ __device__ __forceinline__ void load_coefs(const T* tab, size_t pl, size_t o, T*
 
 // The theta table of one row as broadcast pairs (x, x), held in registers by its thread
 // for a whole work item (FP32 paths; empty for FP64, which reads 2D tables).
-struct ThPair { float2 sin2, cs, V, thp, thm; };
+struct ThPair { float2 sin2, cs, V, i2, i1; };
 template <class P>
 struct RowTab {
     ThPair t;
     __device__ __forceinline__ void load(const ThTab* tab, int j, bool ok) {
         if constexpr (uses_1d_tables<P>()) {
             const ThTab h = ok ? tab[j] : ThTab{};
-            t = ThPair{bc(h.sin2), bc(h.cs), bc(h.V), bc(h.thp), bc(h.thm)};
+            t = ThPair{bc(h.sin2), bc(h.cs), bc(h.V), bc(h.i2), bc(h.i1)};
         }
     }
 };
@@ -446,8 +481,8 @@ __device__ __forceinline__ void form_coefs2(const RTab2& t, const ThPair& h, flo
     cf[C_E2R] = __ffma2_rn(ctre, g, __fmul2_rn(pb, iS));
     cf[C_E2I] = __ffma2_rn(ctim, g, __fmul2_rn(t.pi, iS));
     const float2 ws = __fmul2_rn(t.Ds, iS);
-    cf[C_EP] = __fmul2_rn(ws, h.thp);
-    cf[C_EM] = __fmul2_rn(ws, h.thm);
+    cf[C_EP] = __fmul2_rn(ws, h.i2);   // A (split angular form)
+    cf[C_EM] = __fmul2_rn(ws, h.i1);   // B
     cf[C_E3R] = __fmul2_rn(__ffma2_rn(t.nDs, h.V, t.qr), iS);
     cf[C_E3I] = __fmul2_rn(t.qi, iS);
 }
@@ -468,18 +503,25 @@ __device__ __forceinline__ void coefs_df(const InstDev& d, bool half, int i, int
     }
 }
 
-// Eq. (13) at the own half node, as an increment on the averaged state.
-template <typename T>
+// Eq. (13) at the own half node, as an increment on the averaged state.  Dp, Dm: the
+// theta differences of the averaged state in the angular form of kSplit (expanded:
+// forward and backward differences; split: second and two-cell differences).
+template <typename T, bool kSplit>
 __device__ __forceinline__ HalfRec<T> predictor(const Half<T>& h, Cx<T> Dp, Cx<T> Dm, const T* cf,
                                                 T hdt, Cx<T> src) {
     HalfRec<T> r;
-    r.Fb = h.Fb; r.Pb = h.Pb; r.dF = h.dF; r.dP = h.dP; r.Dp = Dp;
+    r.Fb = h.Fb; r.Pb = h.Pb; r.dF = h.dF; r.dP = h.dP; r.Dp = Dp; r.D1 = Dm;
     r.hF = rmac(rmac(Cx<T>::zero(), -cf[C_G], h.dF), hdt, h.Pb);
     Cx<T> a = rmac(src, cf[C_G], h.dP);
     a = cmac(a, cf[C_E1R], cf[C_E1I], h.Pb);
     a = cmac(a, cf[C_E2R], cf[C_E2I], h.dF);
-    a = rmac(a, cf[C_EP], Dp);
-    a = rmac(a, -cf[C_EM], Dm);
+    if constexpr (kSplit) {
+        a = rmac(a, cf[C_EP], Dp);
+        a = rmac(a, cf[C_EM], Dm);
+    } else {
+        a = rmac(a, cf[C_EP], Dp);
+        a = rmac(a, -cf[C_EM], Dm);
+    }
     a = cmac(a, cf[C_E3R], cf[C_E3I], h.Fb);
     r.hP = a;
     return r;
