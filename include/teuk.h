@@ -225,13 +225,29 @@ teuk_status teuk_get_geometry(const teuk_ctx* ctx, int instance, double* out);
  * (the per-point arithmetic is fixed). */
 teuk_status teuk_set_tiling(teuk_ctx* ctx, int strip, int steps_per_launch);
 
+/* Resident launches for a single-instance context whose grid fits the GPU's shared
+ * memory (a not-in-the-paper launch form for small grids, such as 800 x 64): each
+ * teuk_step_n becomes one cooperative launch in which every block keeps a run of r*
+ * columns (with `halo` columns on each side) in shared memory for all n steps and
+ * exchanges `halo` boundary columns with its neighbours through global memory every
+ * `halo` steps, with bounded waits (TEUK_ETIMEOUT after about one second).  The state is
+ * read once at the start and written once at the end; the results equal those of one
+ * launch per step (the per-node arithmetic is the same).  halo = 0 turns it off.
+ * Instances with a moving particle are still stepped one launch per step.
+ * TEUK_EINVAL if the context has several instances or the grid does not fit (every
+ * block must own >= halo columns, hold them in shared memory, and all blocks must be
+ * resident at once).  Allocates the exchange slots (2 x blocks x 2 x halo columns). */
+teuk_status teuk_set_resident(teuk_ctx* ctx, int halo);
+
 /* Strip length (r* columns per block) of one instance (0 = back to the context default). */
 teuk_status teuk_set_instance_tiling(teuk_ctx* ctx, int instance, int strip);
 
 /* Autotuner of the strip length (r* columns per block), written to every instance
  * (chosen, may be NULL, receives them).  A single instance stepped one launch per step:
- * trial_steps steps of each candidate (1 .. 512 columns) on a scratch copy of the
- * instance.  Contexts that run the persistent kernels (several instances, or one with
+ * trial_steps steps of each candidate (1 .. 512 columns) and of resident launches with
+ * halo 1 .. 4 (teuk_set_resident, where the grid fits) on a scratch copy of the
+ * instance; the fastest is applied, and chosen[k] < 0 reports resident launches with
+ * halo -chosen[k].  Contexts that run the persistent kernels (several instances, or one with
  * steps_per_launch = 0): trial_steps steps of the whole context per candidate (16 .. 512),
  * one length for all instances first, then block-size class by class, on the live state,
  * which is restored afterwards from a snapshot (device memory for one copy of every
@@ -243,7 +259,9 @@ teuk_status teuk_autotune(teuk_ctx* ctx, int trial_steps, int* chosen);
  * skip_release_item (numbered within a step, -1 = none) of the first step of each
  * call never publishes its completion, so the items that depend on it give up after
  * spin_limit polls (0 = the default of about one second) and the next teuk_sync
- * reports TEUK_ETIMEOUT; the state is then undefined until teuk_set_state. */
+ * reports TEUK_ETIMEOUT; the state is then undefined until teuk_set_state.  With
+ * resident launches (teuk_set_resident), block skip_release_item never publishes its
+ * exchanged columns, and its neighbours' waits give up after about one second. */
 teuk_status teuk_set_fault_injection(teuk_ctx* ctx, int64_t skip_release_item,
                                      long long spin_limit);
 

@@ -56,6 +56,7 @@ _PROTOS = {
     "teuk_sync": (_I, [_P]),
     "teuk_get_time": (_I, [_P, _I, ctypes.POINTER(_L), ctypes.POINTER(_D)]),
     "teuk_set_tiling": (_I, [_P, _I, _I]),
+    "teuk_set_resident": (_I, [_P, _I]),
     "teuk_get_geometry": (_I, [_P, _I, _P]),
     "teuk_set_instance_tiling": (_I, [_P, _I, _I]),
     "teuk_autotune": (_I, [_P, _I, _P]),

@@ -55,6 +55,12 @@ struct Instance {
     std::vector<int> h_part;
     int part_strip = 0;
     int fault_col = -1;         // testing aid (teuk_set_fill_fault)
+    // resident launches (teuk_set_resident): halo h (0 = off), plan, exchange slots and
+    // flags (nb + 1 ints: the blocks' flags, then the abort flag)
+    int res_h = 0;
+    ResidentPlan res_plan;
+    unsigned char* res_xg = nullptr;
+    int* res_flags = nullptr;
 };
 
 // Device side of the batched persistent launch of one context: one persistent kernel
@@ -313,7 +319,7 @@ void free_instance(cudaStream_t s, Instance& I) {
         for (int k = 0; k < 2; ++k)
             if (I.state[b][k]) cudaFreeAsync(I.state[b][k], s);
     void* ptrs[] = {I.coef_h, I.coef_i, I.x_int, I.x_half, I.P_win, I.amps, I.wave, I.rtab, I.thtab,
-                    I.stage, I.d_part, I.traj_buf};
+                    I.stage, I.d_part, I.traj_buf, I.res_xg, I.res_flags};
     for (void* q : ptrs)
         if (q) cudaFreeAsync(q, s);
     I = Instance();
@@ -801,11 +807,83 @@ teuk_status batched_step(teuk_ctx* c, int64_t n) {
 
 }  // namespace
 
+namespace {
+
+// Plan the resident launch of instance I with halo h and (re)allocate its exchange slots
+// and flags; h = 0 turns resident launches off.
+teuk_status set_resident(teuk_ctx* c, Instance& I, int h) {
+    if (h == 0) {
+        I.res_h = 0;
+        return TEUK_OK;
+    }
+    ResidentPlan plan;
+    if (!resident_plan(I.p.prec, I.p.n_rstar, I.pitch, h, &plan))
+        TK_FAIL(c, TEUK_EINVAL,
+                "the grid does not fit the resident kernel with halo %d (every block must own >= %d "
+                "columns, hold its columns in shared memory and be resident at once)", h, h);
+    const int planes = I.p.prec == TEUK_FP32 ? 1 : 2;
+    const size_t xg_bytes = (size_t)planes * 2 * plan.nb * 2 * h * I.pitch * 16;
+    if (I.res_xg) cudaFreeAsync(I.res_xg, c->stream);
+    if (I.res_flags) cudaFreeAsync(I.res_flags, c->stream);
+    I.res_xg = nullptr;
+    I.res_flags = nullptr;
+    I.res_h = 0;
+    TK_CUDA(c, cudaMallocAsync((void**)&I.res_xg, xg_bytes, c->stream));
+    TK_CUDA(c, cudaMallocAsync((void**)&I.res_flags, sizeof(int) * kResFlagStride * (plan.nb + 1), c->stream));
+    I.res_plan = plan;
+    I.res_h = h;
+    return TEUK_OK;
+}
+
+// n steps of a single instance in one cooperative launch of the resident kernel, then the
+// record of the final level (the kernel records the levels it starts each step from).
+teuk_status resident_step(teuk_ctx* c, Instance& I, int64_t n) {
+    ResidentArgs a{};
+    a.d = dev_of(c, I);
+    a.step0 = I.step;
+    a.bin = I.cur;
+    a.obin = (int)((I.cur + n) & 1);
+    a.n = n;
+    a.h = I.res_plan.h;
+    a.nb = I.res_plan.nb;
+    a.xg = I.res_xg;
+    a.flags = I.res_flags;
+    a.abort = I.res_flags + (size_t)kResFlagStride * I.res_plan.nb;
+    a.skip_publish = (int)c->inject_skip_item;
+    TK_CUDA(c, cudaMemsetAsync(I.res_flags, 0, sizeof(int) * kResFlagStride * (I.res_plan.nb + 1), c->stream));
+    TK_CUDA(c, launch_resident(c->stream, a, I.res_plan));
+    c->launches++;
+    I.step += n;
+    I.cur = a.obin;
+    do_extract(c, I);
+    return TEUK_OK;
+}
+
+}  // namespace
+
+extern "C" teuk_status teuk_set_resident(teuk_ctx* c, int halo) {
+    if (!c) return TEUK_EINVAL;
+    if (halo < 0) TK_FAIL(c, TEUK_EINVAL, "halo must be >= 0");
+    if (c->inst.size() != 1) TK_FAIL(c, TEUK_EINVAL, "resident launches serve single-instance contexts");
+    return set_resident(c, c->inst[0], halo);
+}
+
 extern "C" teuk_status teuk_step_n(teuk_ctx* c, int64_t n) {
     if (!c) return TEUK_EINVAL;
     if (n < 0) TK_FAIL(c, TEUK_EINVAL, "n < 0");
     if (n == 0) return TEUK_OK;
     if (c->inst.size() > 1 || c->steps_per_launch == 0) return batched_step(c, n);
+    Instance& I0 = c->inst[0];
+    if (I0.res_h > 0 && !(I0.src_on && I0.sd.moving)) {   // a moving particle: per-step launches
+        const int64_t s0 = I0.step;
+        teuk_status st = resident_step(c, I0, n);
+        if (st) return st;
+        if (I0.wave_hi != s0 + 1 || I0.wave_lo == I0.wave_hi) I0.wave_lo = s0;
+        I0.wave_hi = I0.step + 1;
+        if (I0.wave_hi - I0.wave_lo > I0.wave_cap) I0.wave_lo = I0.wave_hi - I0.wave_cap;
+        TK_CUDA(c, cudaGetLastError());
+        return TEUK_OK;
+    }
     for (Instance& I : c->inst) {
         int strip = eff_strip(c, I);
         int64_t s0 = I.step;
@@ -1125,7 +1203,7 @@ extern "C" teuk_status teuk_autotune(teuk_ctx* c, int trial_steps, int* chosen) 
     if (trial_steps < 1) TK_FAIL(c, TEUK_EINVAL, "trial_steps must be >= 1");
     if (c->inst.size() > 1 || c->steps_per_launch == 0) return autotune_batched(c, trial_steps, chosen);
     const int ni = (int)c->inst.size();
-    std::vector<int> best(ni, 0);
+    std::vector<int> best(ni, 0), best_res(ni, 0);
     cudaEvent_t e0, e1;
     TK_CUDA(c, cudaEventCreate(&e0));
     TK_CUDA(c, cudaEventCreate(&e1));
@@ -1168,6 +1246,47 @@ extern "C" teuk_status teuk_autotune(teuk_ctx* c, int trial_steps, int* chosen) 
                 c->launches += trial_steps + 2;
                 if (ms < best_ms) { best_ms = ms; best_strip = ch; }
             }
+            // resident launches, halo 1 .. 4 (circular orbits; a moving particle is stepped
+            // one launch per step)
+            for (int hh = 1; hh <= 4 && !(I.src_on && I.sd.moving); ++hh) {
+                ResidentPlan plan;
+                if (!resident_plan(I.p.prec, I.p.n_rstar, I.pitch, hh, &plan)) continue;
+                unsigned char* xg = nullptr;
+                int* fl = nullptr;
+                const size_t xg_bytes = (size_t)nplanes * 2 * plan.nb * 2 * hh * I.pitch * 16;
+                if (cudaMallocAsync((void**)&xg, xg_bytes, c->stream) == cudaSuccess &&
+                    cudaMallocAsync((void**)&fl, sizeof(int) * kResFlagStride * (plan.nb + 1), c->stream) == cudaSuccess) {
+                    ResidentArgs a{};
+                    a.d = d;
+                    a.step0 = I.step;
+                    a.bin = 0;
+                    a.h = hh;
+                    a.nb = plan.nb;
+                    a.xg = xg;
+                    a.flags = fl;
+                    a.abort = fl + (size_t)kResFlagStride * plan.nb;
+                    a.skip_publish = -1;
+                    float ms = 1e30f;
+                    bool ok = true;
+                    for (int w = 0; w < 2 && ok; ++w) {   // warm-up (2 steps), then the timed run
+                        a.n = w == 0 ? 2 : trial_steps;
+                        a.obin = (int)(a.n & 1);
+                        cudaMemsetAsync(fl, 0, sizeof(int) * kResFlagStride * (plan.nb + 1), c->stream);
+                        if (w == 1) cudaEventRecord(e0, c->stream);
+                        ok = launch_resident(c->stream, a, plan) == cudaSuccess;
+                        if (w == 1) cudaEventRecord(e1, c->stream);
+                    }
+                    if (ok && cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+                    c->launches += 2;
+                    if (ok && ms < best_ms) {
+                        best_ms = ms;
+                        best_res[k] = hh;
+                    }
+                }
+                cudaGetLastError();
+                if (xg) cudaFreeAsync(xg, c->stream);
+                if (fl) cudaFreeAsync(fl, c->stream);
+            }
         }
         for (int b = 0; b < 2; ++b)
             for (int q = 0; q < 2; ++q)
@@ -1189,7 +1308,9 @@ extern "C" teuk_status teuk_autotune(teuk_ctx* c, int trial_steps, int* chosen) 
     cudaEventDestroy(e1);
     for (int k = 0; k < ni; ++k) {
         c->inst[k].strip = best[k];
-        if (chosen) chosen[k] = best[k];
+        teuk_status st = set_resident(c, c->inst[k], best_res[k]);
+        if (st) return st;
+        if (chosen) chosen[k] = best_res[k] > 0 ? -best_res[k] : best[k];
     }
     invalidate_graph(c);
     TK_CUDA(c, cudaGetLastError());

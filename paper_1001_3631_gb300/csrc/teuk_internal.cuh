@@ -126,6 +126,27 @@ struct BatchDev {
                                 // releases its flag, so its neighbours' waits run out
 };
 
+// One cooperative launch of the resident kernel (teuk_resident.cu): n steps of one
+// instance held in shared memory, exchanging h boundary columns with the neighbouring
+// blocks every h steps.
+struct ResidentArgs {
+    InstDev d;
+    int64_t step0;        // time level at the start
+    int bin, obin;        // buffer holding it, buffer receiving the final level
+    int64_t n;            // steps
+    int h;                // halo width = steps between exchanges
+    int nb;               // blocks
+    unsigned char* xg;    // exchange slots [planes][2][nb][2][h][pitch] 16-byte nodes
+    int* flags;           // [nb][kResFlagStride] 1 + exchanges published, one 128-byte line
+                          // a block (zeroed before each launch)
+    int* abort;           // set when a wait gives up
+    int skip_publish;     // testing aid (-1: none): this block never publishes its exchanges,
+                          // so its neighbours' waits run out
+};
+constexpr int kResFlagStride = 32;   // ints between two blocks' flags (a 128-byte line each)
+// Launch shape of the resident kernel for one instance.
+struct ResidentPlan { int nb = 0, threads = 0, h = 0; size_t smem = 0; };
+
 __host__ __device__ inline size_t plane_elems(const InstDev& d) {
     return (size_t)d.nr * (size_t)d.pitch;
 }
@@ -169,6 +190,10 @@ void launch_batched_step(cudaStream_t st, int prec, const BatchDev& b, int grid,
                          bool moving);
 int batched_grid(int prec, int threads);
 void launch_batched_extract(cudaStream_t st, int prec, const BatchDev& b, int max_nth);
+// teuk_resident.cu: whether (and how) an instance fits the resident kernel with halo h
+// (all blocks resident at once, one block per run of columns), and its launch
+bool resident_plan(int prec, int nr, int pitch, int h, ResidentPlan* plan);
+cudaError_t launch_resident(cudaStream_t st, const ResidentArgs& a, const ResidentPlan& plan);
 // teuk_aux.cu
 void launch_import_state(cudaStream_t st, const InstDev& d, int bin, const double* u);
 void launch_export_state(cudaStream_t st, const InstDev& d, int bin, double* u);

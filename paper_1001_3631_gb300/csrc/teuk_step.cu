@@ -355,66 +355,13 @@ __device__ __forceinline__ bool strip_step(const InstDev& d, int64_t step, int b
     auto correct = [&](const HalfRec<T>& Rh, const HalfRec<T>& Lh, const NodeV<P>& uc,
                        const T* cfi, int cc, T* xb, size_t o, C srcc) {
         const CRow<T> row = combine_lr<T, kSplit>(Rh, Lh);
-        // publish {Hs, DpS} of this row at entry j + 1; the pole rows also write the
-        // ghost entries: row nth (entry nth + 1) Hs = g Hs(nth-1), row -1 (entry 0)
-        // Hs = g Hs(0) and DpS = (Dp_R(-1) + Dp_L(-1))/2 = (1 - g) (Fb_R + Fb_L)(0)/2.
-        // The split form needs Hs alone: its averaged differences are the row's own.
+        // publish this row's exchange entry (the split form needs Hs alone: its averaged
+        // differences are the row's own), then read the rows above and below
         T* mine = xb + 4 * (j + 1);
-        auto put = [](T* e, C a, C b) {
-            if constexpr (P::kind == kDF) {
-                ((float4*)e)[0] = make_float4(a.re.hi, a.re.lo, a.im.hi, a.im.lo);
-                ((float4*)e)[1] = make_float4(b.re.hi, b.re.lo, b.im.hi, b.im.lo);
-            } else if constexpr (sizeof(T) == 4) {
-                *(float4*)e = make_float4(a.re, a.im, b.re, b.im);
-            } else {
-                ((double2*)e)[0] = make_double2(a.re, a.im);
-                ((double2*)e)[1] = make_double2(b.re, b.im);
-            }
-        };
-        if constexpr (kSplit) {
-            if (row_ok) *(float2*)mine = make_float2(row.Hs.re, row.Hs.im);
-            if (top) *(float2*)(mine + 4) = make_float2(g * row.Hs.re, g * row.Hs.im);
-            if (bot) *(float2*)xb = make_float2(g * row.Hs.re, g * row.Hs.im);
-        } else {
-            if (row_ok) put(mine, row.Hs, row.DpS);
-            if (top) put(mine + 4, g * row.Hs, C::zero());
-            if (bot) put(xb, g * row.Hs, (T(1) - g) * C::half_sum(Rh.Fb, Lh.Fb));
-        }
+        xpublish<P, kSplit>(xb, mine, row, Rh, Lh, g, row_ok, top, bot);
         __syncthreads();
         C Hs_p, Hs_m, DpS_m;
-        if constexpr (kSplit) {
-            const float2 a = *(const float2*)(mine + 4), b = *(const float2*)(mine - 4);
-            Hs_p = {a.x, a.y};
-            Hs_m = {b.x, b.y};
-        } else if constexpr (P::kind == kDF) {
-            const float4 a = *(const float4*)(mine + 4);
-            const float4 b0 = ((const float4*)(mine - 4))[0], b1 = ((const float4*)(mine - 4))[1];
-            Hs_p = {DF(a.x, a.y), DF(a.z, a.w)};
-            Hs_m = {DF(b0.x, b0.y), DF(b0.z, b0.w)};
-            DpS_m = {DF(b1.x, b1.y), DF(b1.z, b1.w)};
-        } else if constexpr (sizeof(T) == 4) {
-            const float2 a = *(const float2*)(mine + 4);
-            const float4 b = *(const float4*)(mine - 4);
-            Hs_p = {a.x, a.y};
-            Hs_m = {b.x, b.y};
-            DpS_m = {b.z, b.w};
-        } else {
-            const double2 a = *(const double2*)(mine + 4);
-            const double2 b0 = ((const double2*)(mine - 4))[0], b1 = ((const double2*)(mine - 4))[1];
-            Hs_p = {a.x, a.y};
-            Hs_m = {b0.x, b0.y};
-            DpS_m = {b1.x, b1.y};
-        }
-        // expanded: Dplus = u~(j+1) - u~(j), Dminus = u~(j) - u~(j-1) of the corrector's
-        // averaged state u~ = (h_R + h_L)/2; split: its second and two-cell differences
-        C Dplus, Dminus;
-        if constexpr (kSplit) {
-            Dplus = row.DpS + ((Hs_p - row.Hs) - (row.Hs - Hs_m));
-            Dminus = row.D1S + (Hs_p - Hs_m);
-        } else {
-            Dplus = row.DpS + (Hs_p - row.Hs);
-            Dminus = DpS_m + (row.Hs - Hs_m);
-        }
+        xread<P, kSplit>(mine, Hs_p, Hs_m, DpS_m);
         T cf[kNCoef];
         if constexpr (kTabsPath) {
 #pragma unroll
@@ -424,18 +371,8 @@ __device__ __forceinline__ bool strip_step(const InstDev& d, int64_t step, int b
         } else {
             coefs64(d, false, cc, j, (double*)cf);
         }
-        C dPhi = rmac(rmac(C::zero(), -cf[C_G], row.dFc), fdt, row.PC);
-        C dPi = rmac(srcc, cf[C_G], row.dPc);
-        dPi = cmac(dPi, cf[C_E1R], cf[C_E1I], row.PC);
-        dPi = cmac(dPi, cf[C_E2R], cf[C_E2I], row.dFc);
-        if constexpr (kSplit) {
-            dPi = rmac(dPi, cf[C_EP], Dplus);
-            dPi = rmac(dPi, cf[C_EM], Dminus);
-        } else {
-            dPi = rmac(dPi, cf[C_EP], Dplus);
-            dPi = rmac(dPi, -cf[C_EM], Dminus);
-        }
-        dPi = cmac(dPi, cf[C_E3R], cf[C_E3I], row.FC);
+        C dPhi, dPi;
+        corrector_incr<P, kSplit>(row, Hs_p, Hs_m, DpS_m, cf, fdt, srcc, dPhi, dPi);
         if (row_ok) {
             NodeV<P> u = uc;
             u.update(dPhi, dPi);
@@ -447,7 +384,7 @@ __device__ __forceinline__ bool strip_step(const InstDev& d, int64_t step, int b
         if (!row_ok) return;
         double2 a = ul.phi64(), b = ur.phi64();
         double f = d.f_e;
-        double2 w = make_double2((1.0 - f) * a.x + f * b.x, (1.0 - f) * a.y + f * b.y);
+        double2 w = wave_lerp(a, b, f);
         d.wave[(size_t)(step % d.wave_cap) * nth + j] = w;
         if (!isfinite(w.x) || !isfinite(w.y)) atomicOr(d.status, (unsigned)ST_NONFINITE);
     };
@@ -601,7 +538,7 @@ __global__ void extract_kernel(InstDev d, int64_t step, int bin) {
     double2 a = in.load(node_index(d, d.i_e, j)).phi64();
     double2 b = in.load(node_index(d, d.i_e + 1, j)).phi64();
     double f = d.f_e;
-    double2 w = make_double2((1.0 - f) * a.x + f * b.x, (1.0 - f) * a.y + f * b.y);
+    double2 w = wave_lerp(a, b, f);
     d.wave[(size_t)(step % d.wave_cap) * d.nth + j] = w;
     if (!isfinite(w.x) || !isfinite(w.y)) atomicOr(d.status, (unsigned)ST_NONFINITE);
 }
@@ -708,7 +645,7 @@ __global__ void batched_extract_kernel(BatchDev b) {
     double2 a = in.load(node_index(d, d.i_e, j)).phi64();
     double2 c = in.load(node_index(d, d.i_e + 1, j)).phi64();
     double f = d.f_e;
-    double2 w = make_double2((1.0 - f) * a.x + f * c.x, (1.0 - f) * a.y + f * c.y);
+    double2 w = wave_lerp(a, c, f);
     d.wave[(size_t)(step % d.wave_cap) * d.nth + j] = w;
     if (!isfinite(w.x) || !isfinite(w.y)) atomicOr(d.status, (unsigned)ST_NONFINITE);
 }

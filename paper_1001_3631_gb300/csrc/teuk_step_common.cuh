@@ -527,6 +527,114 @@ __device__ __forceinline__ HalfRec<T> predictor(const Half<T>& h, Cx<T> Dp, Cx<T
     return r;
 }
 
+// ---------------------------------------------------------------- extraction
+// Waveform record between the nodes i_e (a) and i_e + 1 (b): (1 - f) a + f b, written with
+// explicit roundings so that every kernel that records a level rounds it the same way.
+__device__ __forceinline__ double2 wave_lerp(double2 a, double2 b, double f) {
+    const double g = 1.0 - f;
+    return make_double2(__fma_rn(f, b.x, __dmul_rn(g, a.x)), __fma_rn(f, b.y, __dmul_rn(g, a.y)));
+}
+
+// ---------------------------------------------------------------- corrector
+// Exchange entry of one row for the corrector's theta neighbours: {Hs, DpS} (4 values of
+// T at e; the split form uses Hs alone).  Row j sits at entry j + 1 of its column's
+// buffer; entries 0 and n_theta + 1 hold the ghost rows of the pole rule:
+// row nth Hs = g Hs(nth-1); row -1 Hs = g Hs(0) and DpS = (Dp_R(-1) + Dp_L(-1))/2 =
+// (1 - g) (Fb_R + Fb_L)(0)/2.
+template <class P>
+__device__ __forceinline__ void xput(typename P::T* e, Cx<typename P::T> a, Cx<typename P::T> b) {
+    if constexpr (P::kind == kDF) {
+        ((float4*)e)[0] = make_float4(a.re.hi, a.re.lo, a.im.hi, a.im.lo);
+        ((float4*)e)[1] = make_float4(b.re.hi, b.re.lo, b.im.hi, b.im.lo);
+    } else if constexpr (sizeof(typename P::T) == 4) {
+        *(float4*)e = make_float4(a.re, a.im, b.re, b.im);
+    } else {
+        ((double2*)e)[0] = make_double2(a.re, a.im);
+        ((double2*)e)[1] = make_double2(b.re, b.im);
+    }
+}
+
+// Publish this row's entry (xb: the column's buffer, mine = xb + 4 (j + 1)) and, for the
+// pole rows, the ghost entries.
+template <class P, bool kSplit>
+__device__ __forceinline__ void xpublish(typename P::T* xb, typename P::T* mine, const CRow<typename P::T>& row,
+                                         const HalfRec<typename P::T>& Rh, const HalfRec<typename P::T>& Lh,
+                                         typename P::T g, bool row_ok, bool top, bool bot) {
+    using T = typename P::T;
+    using C = Cx<T>;
+    if constexpr (kSplit) {
+        if (row_ok) *(float2*)mine = make_float2(row.Hs.re, row.Hs.im);
+        if (top) *(float2*)(mine + 4) = make_float2(g * row.Hs.re, g * row.Hs.im);
+        if (bot) *(float2*)xb = make_float2(g * row.Hs.re, g * row.Hs.im);
+    } else {
+        if (row_ok) xput<P>(mine, row.Hs, row.DpS);
+        if (top) xput<P>(mine + 4, g * row.Hs, C::zero());
+        if (bot) xput<P>(xb, g * row.Hs, (T(1) - g) * C::half_sum(Rh.Fb, Lh.Fb));
+    }
+}
+
+// Read the entries of the rows above and below (after the barrier that follows xpublish).
+template <class P, bool kSplit>
+__device__ __forceinline__ void xread(const typename P::T* mine, Cx<typename P::T>& Hs_p,
+                                      Cx<typename P::T>& Hs_m, Cx<typename P::T>& DpS_m) {
+    if constexpr (kSplit) {
+        const float2 a = *(const float2*)(mine + 4), b = *(const float2*)(mine - 4);
+        Hs_p = {a.x, a.y};
+        Hs_m = {b.x, b.y};
+    } else if constexpr (P::kind == kDF) {
+        const float4 a = *(const float4*)(mine + 4);
+        const float4 b0 = ((const float4*)(mine - 4))[0], b1 = ((const float4*)(mine - 4))[1];
+        Hs_p = {DF(a.x, a.y), DF(a.z, a.w)};
+        Hs_m = {DF(b0.x, b0.y), DF(b0.z, b0.w)};
+        DpS_m = {DF(b1.x, b1.y), DF(b1.z, b1.w)};
+    } else if constexpr (sizeof(typename P::T) == 4) {
+        const float2 a = *(const float2*)(mine + 4);
+        const float4 b = *(const float4*)(mine - 4);
+        Hs_p = {a.x, a.y};
+        Hs_m = {b.x, b.y};
+        DpS_m = {b.z, b.w};
+    } else {
+        const double2 a = *(const double2*)(mine + 4);
+        const double2 b0 = ((const double2*)(mine - 4))[0], b1 = ((const double2*)(mine - 4))[1];
+        Hs_p = {a.x, a.y};
+        Hs_m = {b0.x, b0.y};
+        DpS_m = {b1.x, b1.y};
+    }
+}
+
+// Eq. (14) at one node as increments (dPhi, dPi) from the row's combined half-node values,
+// the theta neighbours' exchange entries, the node's coefficients cf and source term.
+template <class P, bool kSplit>
+__device__ __forceinline__ void corrector_incr(const CRow<typename P::T>& row, Cx<typename P::T> Hs_p,
+                                               Cx<typename P::T> Hs_m, Cx<typename P::T> DpS_m,
+                                               const typename P::T* cf, typename P::T fdt,
+                                               Cx<typename P::T> srcc, Cx<typename P::T>& dPhi,
+                                               Cx<typename P::T>& dPi) {
+    using C = Cx<typename P::T>;
+    // expanded: Dplus = u~(j+1) - u~(j), Dminus = u~(j) - u~(j-1) of the corrector's
+    // averaged state u~ = (h_R + h_L)/2; split: its second and two-cell differences
+    C Dplus, Dminus;
+    if constexpr (kSplit) {
+        Dplus = row.DpS + ((Hs_p - row.Hs) - (row.Hs - Hs_m));
+        Dminus = row.D1S + (Hs_p - Hs_m);
+    } else {
+        Dplus = row.DpS + (Hs_p - row.Hs);
+        Dminus = DpS_m + (row.Hs - Hs_m);
+    }
+    dPhi = rmac(rmac(C::zero(), -cf[C_G], row.dFc), fdt, row.PC);
+    dPi = rmac(srcc, cf[C_G], row.dPc);
+    dPi = cmac(dPi, cf[C_E1R], cf[C_E1I], row.PC);
+    dPi = cmac(dPi, cf[C_E2R], cf[C_E2I], row.dFc);
+    if constexpr (kSplit) {
+        dPi = rmac(dPi, cf[C_EP], Dplus);
+        dPi = rmac(dPi, cf[C_EM], Dminus);
+    } else {
+        dPi = rmac(dPi, cf[C_EP], Dplus);
+        dPi = rmac(dPi, -cf[C_EM], Dminus);
+    }
+    dPi = cmac(dPi, cf[C_E3R], cf[C_E3I], row.FC);
+}
+
 // ---------------------------------------------------------------- source
 // dt_sub A_n e^{-i (omega t + phase0)} at t = t_n + off * dt: the predictor's factor
 // (off = 0, dt_sub = dt/2) or the corrector's (off = 1/2, dt_sub = dt); for a moving

@@ -1,0 +1,136 @@
+"""Resident launches (teuk_set_resident): one cooperative launch per step() call, the grid
+held in shared memory, boundary columns exchanged every `halo` steps.  The per-node
+arithmetic is that of the one-launch-per-step kernels, so states and waveform records
+must agree bit for bit with them; the full 800 x 64 run is also checked against the
+oracle, and the bounded halo waits must surface as TEUK_ETIMEOUT."""
+import numpy as np
+import pytest
+
+from paper_1001_3631_gb300 import TeukError, TeukSolver, inputs
+
+pytestmark = pytest.mark.gpu
+
+PRECS = ["fp64", "fp64_df", "fp32_kahan", "fp32"]
+
+
+def rel(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / (nb if nb > 0 else 1.0)
+
+
+def run(params, r0, chunks, halo, u0=None, step0=0, prec="fp64"):
+    with TeukSolver(dict(params, prec=prec)) as s:
+        if halo:
+            s.set_resident(halo)
+        if r0:
+            s.set_source(r0, inputs.amplitudes(400, seed=9))
+        if u0 is not None:
+            s.set_state(u0, step0)
+        for n in chunks:
+            s.step(n)
+        u = s.get_state()
+        w, first = s.extract()
+        s.sync()
+        return u, w, first
+
+
+CASES = [
+    # (params, r0, chunks): the single-mode grid; ragged grids with odd m, the source near
+    # an end and the extraction at the first / last interval; small and tall columns
+    (dict(s=-2, m=2, a=0.9, rstar_min=-50.0, rstar_max=150.0, n_rstar=800, n_theta=64,
+          rstar_ext=140.0, dt_rule=1, courant=0.5), 10.0, [7, 1, 12]),
+    (dict(s=-2, m=3, a=0.7, rstar_min=-10.0, rstar_max=30.0, n_rstar=97, n_theta=33,
+          rstar_ext=-10.0, dt_rule=1, courant=0.5), 5.0, [5, 4]),
+    (dict(s=-1, m=0, a=0.5, rstar_min=-20.0, rstar_max=20.0, n_rstar=71, n_theta=4,
+          rstar_ext=20.0, dt_rule=1, courant=0.5), 6.0, [3, 3, 3]),
+    (dict(s=-2, m=1, a=0.3, rstar_min=-10.0, rstar_max=20.0, n_rstar=60, n_theta=200,
+          rstar_ext=4.1, dt_rule=1, courant=0.5), 7.0, [4]),
+]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("case", range(len(CASES)))
+def test_resident_equals_per_step_launches_bitwise(prec, case):
+    params, r0, chunks = CASES[case]
+    nth, nr = params["n_theta"], params["n_rstar"]
+    u0 = inputs.random_state(nth, nr, seed=5 + case)
+    ref = run(params, r0, chunks, 0, u0, step0=3, prec=prec)
+    tried = 0
+    for halo in (1, 2, 3):
+        try:
+            got = run(params, r0, chunks, halo, u0, step0=3, prec=prec)
+        except TeukError as e:   # wider halos need more threads than some grids allow
+            assert halo > 1 and e.status == 1
+            continue
+        tried += 1
+        assert got[2] == ref[2]
+        assert np.array_equal(got[0], ref[0]), (halo, rel(got[0], ref[0]))
+        assert np.array_equal(got[1], ref[1]), (halo, rel(got[1], ref[1]))
+    assert tried >= 1
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp64_df", 1e-12), ("fp32_kahan", 1e-6)])
+def test_resident_single_mode_800x64_full_run_against_oracle(orc, prec, tol):
+    cfg = inputs.SINGLE_MODE_800x64
+    p = orc.params(**cfg["params"], r0=cfg["r0"])
+    uo, wo = orc.run(p, None, cfg["steps"], orc.orbit_source(p))
+    with TeukSolver(dict(cfg["params"], prec=prec)) as s:
+        s.set_resident(1)
+        s.set_source(cfg["r0"])
+        s.step(cfg["steps"])
+        u = s.get_state()
+        w, first = s.extract(cap=cfg["steps"] + 1)
+        s.sync()
+    assert first == 0
+    assert rel(u, uo) <= tol and rel(w, wo) <= tol, (rel(u, uo), rel(w, wo))
+
+
+def test_resident_halo_wait_times_out_and_context_recovers():
+    params, r0, _ = CASES[0]
+    u0 = inputs.smooth_state(64, 800, seed=4)
+    with TeukSolver(dict(params, prec="fp32_kahan")) as s:
+        s.set_resident(1)
+        s.set_source(r0, inputs.amplitudes(400, seed=9))
+        s.set_fault_injection(skip_release_item=40)   # block 40 never publishes its columns
+        s.step(20)
+        with pytest.raises(TeukError) as e:
+            s.sync()
+        assert e.value.status == 5   # TEUK_ETIMEOUT
+        s.set_fault_injection(-1)
+        s.set_state(u0, 0)
+        s.step(9)
+        u = s.get_state()
+        s.sync()
+    ref = run(params, r0, [9], 0, u0, prec="fp32_kahan")[0]
+    assert np.array_equal(u, ref)
+
+
+def test_resident_refusals():
+    params, r0, _ = CASES[0]
+    with TeukSolver([dict(params), dict(params)]) as s:
+        with pytest.raises(TeukError):
+            s.set_resident(1)
+    big = dict(params, n_rstar=16384, n_theta=256, rstar_min=-200.0, rstar_max=800.0, rstar_ext=700.0)
+    with TeukSolver(dict(big, prec="fp32_kahan")) as s:
+        with pytest.raises(TeukError):
+            s.set_resident(1)
+    with TeukSolver(dict(params)) as s:
+        with pytest.raises(TeukError):
+            s.set_resident(-1)
+
+
+def test_autotune_with_resident_candidates_keeps_results(tmp_path):
+    params, r0, _ = CASES[0]
+    u0 = inputs.smooth_state(64, 800, seed=8)
+    ref = run(params, r0, [30], 0, u0, prec="fp32_kahan")
+    with TeukSolver(dict(params, prec="fp32_kahan")) as s:
+        s.set_source(r0, inputs.amplitudes(400, seed=9))
+        s.set_state(u0, 0)
+        chosen = s.autotune(trial_steps=20, cache_path=str(tmp_path / "t.json"))
+        assert s.time()[0] == 0
+        s.step(30)
+        u = s.get_state()
+        w, _ = s.extract()
+        s.sync()
+    assert chosen[0] != 0
+    assert np.array_equal(u, ref[0]) and np.array_equal(w, ref[1])
