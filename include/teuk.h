@@ -32,6 +32,7 @@
 #ifndef TEUK_H
 #define TEUK_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -102,6 +103,22 @@ typedef struct {
 } teuk_orbit;
 
 typedef struct teuk_ctx teuk_ctx;
+
+/* Device-memory hooks (teuk_set_allocator): alloc returns `bytes` of device memory usable
+ * in stream order on cuda_stream (a cudaStream_t), or NULL on failure; free releases a
+ * block that alloc returned, in stream order on cuda_stream.  user is passed through. */
+typedef void* (*teuk_alloc_fn)(size_t bytes, void* cuda_stream, void* user);
+typedef void (*teuk_free_fn)(void* ptr, void* cuda_stream, void* user);
+
+/* Route the device memory of contexts created from now on through the caller's allocator
+ * (for example a framework's caching allocator, so that the library and the framework
+ * share one pool); alloc = free = NULL restores the default, cudaMallocAsync /
+ * cudaFreeAsync on the context's stream.  A context keeps the allocator it was created
+ * with for all its allocations (state, tables, source, waveform ring, batched and adjoint
+ * buffers) until teuk_destroy.  A NULL return from alloc makes the call that needed the
+ * memory fail with TEUK_ENOMEM (teuk_create then frees what it had taken).  Not thread
+ * safe against concurrent teuk_create.  TEUK_EINVAL if exactly one function is NULL. */
+teuk_status teuk_set_allocator(teuk_alloc_fn alloc, teuk_free_fn free_fn, void* user);
 
 /* Create a context of n_instances independent instances p[0 .. n_instances-1]
  * (uneven grids allowed), on the caller's stream (cudaStream_t passed as void*).

@@ -4,7 +4,7 @@ azimuthal mode, with a smeared particle source (Khanna & McKennon, arXiv 1001.36
 The product path is libteuk.so (include/teuk.h); this package only binds it."""
 from . import _lib, inputs
 from ._lib import (TEUK_FP32, TEUK_FP32_KAHAN, TEUK_FP64, TeukError)
-from .solver import TeukSolver, make_params
+from .solver import TeukSolver, make_params, set_allocator, use_torch_allocator
 
-__all__ = ["TeukSolver", "make_params", "TeukError", "TEUK_FP64", "TEUK_FP32",
+__all__ = ["TeukSolver", "make_params", "set_allocator", "use_torch_allocator", "TeukError", "TEUK_FP64", "TEUK_FP32",
            "TEUK_FP32_KAHAN", "inputs"]

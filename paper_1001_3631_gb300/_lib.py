@@ -57,6 +57,7 @@ _PROTOS = {
     "teuk_get_time": (_I, [_P, _I, ctypes.POINTER(_L), ctypes.POINTER(_D)]),
     "teuk_set_tiling": (_I, [_P, _I, _I]),
     "teuk_set_resident": (_I, [_P, _I]),
+    "teuk_set_allocator": (_I, [_P, _P, _P]),
     "teuk_get_geometry": (_I, [_P, _I, _P]),
     "teuk_set_instance_tiling": (_I, [_P, _I, _I]),
     "teuk_autotune": (_I, [_P, _I, _P]),
@@ -68,6 +69,8 @@ _PROTOS = {
     "teuk_waveform_sum_noalloc": (_I, [_P, _L, _I, _P, _P]),
 }
 TEUK_NOALLOC_MAX_RECORDS = 65536
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
 
 
 def header_functions():

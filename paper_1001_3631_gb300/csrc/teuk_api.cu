@@ -93,7 +93,30 @@ struct Batch {
 
 }  // namespace
 
+namespace {
+// Device memory of a context: stream-ordered cudaMallocAsync / cudaFreeAsync on the
+// context's stream, or the caller's allocator (teuk_set_allocator) in force when the
+// context was created.
+struct DevAlloc {
+    teuk_alloc_fn alloc = nullptr;
+    teuk_free_fn free = nullptr;
+    void* user = nullptr;
+    cudaError_t get(void** p, size_t bytes, cudaStream_t s) const {
+        if (!alloc) return cudaMallocAsync(p, bytes, s);
+        *p = alloc(bytes, (void*)s, user);
+        return *p ? cudaSuccess : cudaErrorMemoryAllocation;
+    }
+    void put(void* p, cudaStream_t s) const {
+        if (!p) return;
+        if (free) free(p, (void*)s, user);
+        else cudaFreeAsync(p, s);
+    }
+};
+DevAlloc g_alloc;   // the allocator new contexts take (teuk_set_allocator)
+}  // namespace
+
 struct teuk_ctx {
+    DevAlloc al;
     cudaStream_t stream = nullptr;
     int prec = 0;
     std::vector<Instance> inst;
@@ -115,6 +138,12 @@ namespace teuk {
 // Error text for calls that have no context (returned by teuk_last_error(NULL)).
 void set_global_error(const std::string& msg) { g_create_err = msg; }
 }  // namespace teuk
+
+template <class T>
+static cudaError_t dmalloc(const teuk_ctx* c, T** p, size_t bytes, cudaStream_t s) {
+    return c->al.get((void**)p, bytes, s);
+}
+static void dfree(const teuk_ctx* c, void* p, cudaStream_t s) { c->al.put(p, s); }
 
 #define TK_FAIL(ctx, code, ...)                                              \
     do {                                                                     \
@@ -268,7 +297,7 @@ teuk_status refresh_partition(teuk_ctx* c, Instance& I) {
         if (col < hi && t - cum[col] > cum[col + 1] - t) ++col;
         I.h_part[k] = col;
     }
-    if (!I.d_part) TK_CUDA(c, cudaMallocAsync((void**)&I.d_part, sizeof(int) * nr, c->stream));
+    if (!I.d_part) TK_CUDA(c, dmalloc(c, (void**)&I.d_part, sizeof(int) * nr, c->stream));
     // (from pageable memory: staged before the call returns, so h_part may change after)
     TK_CUDA(c, cudaMemcpyAsync(I.d_part, I.h_part.data(), sizeof(int) * (nb + 1), cudaMemcpyHostToDevice,
                                c->stream));
@@ -293,8 +322,8 @@ teuk_status coef_tables(teuk_ctx* c, Instance& I) {
     const teuk_params& q = I.p;
     const size_t cs = q.prec == TEUK_FP64 ? sizeof(double) : q.prec == TEUK_FP64_DF ? sizeof(float2) : sizeof(float);
     const size_t cbytes = (size_t)kNCoef * q.n_rstar * I.pitch * cs;
-    TK_CUDA(c, cudaMallocAsync(&I.coef_h, cbytes, c->stream));
-    TK_CUDA(c, cudaMallocAsync(&I.coef_i, cbytes, c->stream));
+    TK_CUDA(c, dmalloc(c, &I.coef_h, cbytes, c->stream));
+    TK_CUDA(c, dmalloc(c, &I.coef_i, cbytes, c->stream));
     launch_coefficients(c->stream, q.prec, q.M, q.a, q.s, q.m, q.rstar_min, I.drs, I.dth, I.dt,
                         q.n_rstar, q.n_theta, I.pitch, I.x_int, I.x_half, I.coef_h, I.coef_i);
     c->launches++;
@@ -314,14 +343,15 @@ void do_extract(teuk_ctx* c, Instance& I) {
     c->launches++;
 }
 
-void free_instance(cudaStream_t s, Instance& I) {
+void free_instance(const teuk_ctx* c, Instance& I) {
+    const cudaStream_t s = c->stream;
     for (int b = 0; b < 2; ++b)
         for (int k = 0; k < 2; ++k)
-            if (I.state[b][k]) cudaFreeAsync(I.state[b][k], s);
+            if (I.state[b][k]) dfree(c, I.state[b][k], s);
     void* ptrs[] = {I.coef_h, I.coef_i, I.x_int, I.x_half, I.P_win, I.amps, I.wave, I.rtab, I.thtab,
                     I.stage, I.d_part, I.traj_buf, I.res_xg, I.res_flags};
     for (void* q : ptrs)
-        if (q) cudaFreeAsync(q, s);
+        if (q) dfree(c, q, s);
     I = Instance();
 }
 
@@ -362,6 +392,7 @@ extern "C" teuk_status teuk_create(const teuk_params* p, int n_instances, void* 
         return TEUK_ECUDA;
     }
     teuk_ctx* c = new teuk_ctx();
+    c->al = g_alloc;
     c->stream = (cudaStream_t)cuda_stream;
     c->prec = p[0].prec;
     c->inst = std::move(inst);
@@ -380,7 +411,7 @@ extern "C" teuk_status teuk_create(const teuk_params* p, int n_instances, void* 
     } while (0)
     TK_CCUDA(prepare_step_kernels());
     for (Instance& I : c->inst) I.resident = step_resident_blocks((int)I.p.prec, I.pitch);
-    TK_CCUDA(cudaMallocAsync((void**)&c->status, sizeof(unsigned), c->stream));
+    TK_CCUDA(dmalloc(c, (void**)&c->status, sizeof(unsigned), c->stream));
     TK_CCUDA(cudaMemsetAsync(c->status, 0, sizeof(unsigned), c->stream));
     for (Instance& I : c->inst) {
         const teuk_params& q = I.p;
@@ -389,12 +420,12 @@ extern "C" teuk_status teuk_create(const teuk_params* p, int n_instances, void* 
         I.plane_bytes = (size_t)q.n_rstar * I.pitch * es;
         for (int b = 0; b < 2; ++b)
             for (int k = 0; k < nplanes; ++k) {
-                TK_CCUDA(cudaMallocAsync(&I.state[b][k], I.plane_bytes, c->stream));
+                TK_CCUDA(dmalloc(c, &I.state[b][k], I.plane_bytes, c->stream));
                 TK_CCUDA(cudaMemsetAsync(I.state[b][k], 0, I.plane_bytes, c->stream));
             }
-        TK_CCUDA(cudaMallocAsync((void**)&I.x_int, sizeof(double) * q.n_rstar, c->stream));
-        TK_CCUDA(cudaMallocAsync((void**)&I.x_half, sizeof(double) * q.n_rstar, c->stream));
-        TK_CCUDA(cudaMallocAsync((void**)&I.wave, sizeof(double2) * I.wave_cap * q.n_theta,
+        TK_CCUDA(dmalloc(c, (void**)&I.x_int, sizeof(double) * q.n_rstar, c->stream));
+        TK_CCUDA(dmalloc(c, (void**)&I.x_half, sizeof(double) * q.n_rstar, c->stream));
+        TK_CCUDA(dmalloc(c, (void**)&I.wave, sizeof(double2) * I.wave_cap * q.n_theta,
                                  c->stream));
         launch_invert_tortoise(c->stream, q.M, q.a, q.rstar_min, I.drs, q.n_rstar, I.x_int,
                                I.x_half);
@@ -403,8 +434,8 @@ extern "C" teuk_status teuk_create(const teuk_params* p, int n_instances, void* 
             const teuk_status e = coef_tables(c, I);
             if (e != TEUK_OK) return fail(e);
         } else {
-            TK_CCUDA(cudaMallocAsync((void**)&I.rtab, sizeof(RTab2) * q.n_rstar, c->stream));
-            TK_CCUDA(cudaMallocAsync((void**)&I.thtab, sizeof(ThTab) * q.n_theta, c->stream));
+            TK_CCUDA(dmalloc(c, (void**)&I.rtab, sizeof(RTab2) * q.n_rstar, c->stream));
+            TK_CCUDA(dmalloc(c, (void**)&I.thtab, sizeof(ThTab) * q.n_theta, c->stream));
             launch_tables_1d(c->stream, q.M, q.a, q.s, q.m, I.drs, I.dth, I.dt, q.n_rstar,
                              q.n_theta, I.x_int, I.x_half, I.rtab, I.thtab);
             c->launches++;
@@ -425,7 +456,7 @@ namespace {
 void free_source(teuk_ctx* c, Instance& I) {
     void* ptrs[] = {I.P_win, I.amps, I.traj_buf};
     for (void* q : ptrs)
-        if (q) cudaFreeAsync(q, c->stream);
+        if (q) dfree(c, q, c->stream);
     I.P_win = nullptr;
     I.amps = nullptr;
     I.traj_buf = nullptr;
@@ -498,7 +529,7 @@ extern "C" teuk_status teuk_set_source(teuk_ctx* c, int instance, const teuk_orb
     const size_t qe = q16 ? 16 : sizeof(float2);
     sd.q_stride = q16 ? sd.nj : (sd.nj + 1) / 2 * 2;
     const size_t qi_bytes = qe * sd.q_stride * sd.ni, qh_bytes = qe * sd.q_stride * sd.nh;
-    TK_CUDA(c, cudaMallocAsync((void**)&I.P_win, sizeof(double2) * 2 * (nwi + nwh) + qi_bytes + qh_bytes,
+    TK_CUDA(c, dmalloc(c, (void**)&I.P_win, sizeof(double2) * 2 * (nwi + nwh) + qi_bytes + qh_bytes,
                                c->stream));
     sd.P_int = I.P_win;
     sd.P_half = I.P_win + nwi;
@@ -507,7 +538,7 @@ extern "C" teuk_status teuk_set_source(teuk_ctx* c, int instance, const teuk_orb
     sd.Q_int = I.P_win + 2 * (nwi + nwh);
     sd.Q_half = (const char*)sd.Q_int + qi_bytes;
     if (n_amps > 0) {
-        TK_CUDA(c, cudaMallocAsync((void**)&I.amps, sizeof(double) * n_amps, c->stream));
+        TK_CUDA(c, dmalloc(c, (void**)&I.amps, sizeof(double) * n_amps, c->stream));
         TK_CUDA(c, cudaMemcpyAsync(I.amps, amps, sizeof(double) * n_amps, cudaMemcpyHostToDevice,
                                    c->stream));
     }
@@ -577,8 +608,8 @@ extern "C" teuk_status teuk_set_trajectory(teuk_ctx* c, int instance, const teuk
     const size_t b_gr = up(te * (size_t)sd.n_traj * (sd.nh + sd.ni));
     const size_t b_gt = up(te * (size_t)sd.n_traj * 2 * sd.nj);
     free_source(c, I);
-    TK_CUDA(c, cudaMallocAsync((void**)&I.P_win, qi_bytes + qh_bytes, c->stream));
-    TK_CUDA(c, cudaMallocAsync(&I.traj_buf, b_traj + b_amp + b_gr + b_gt, c->stream));
+    TK_CUDA(c, dmalloc(c, (void**)&I.P_win, qi_bytes + qh_bytes, c->stream));
+    TK_CUDA(c, dmalloc(c, &I.traj_buf, b_traj + b_amp + b_gr + b_gt, c->stream));
     sd.Q_int = I.P_win;
     sd.Q_half = (const char*)sd.Q_int + qi_bytes;
     char* tb = (char*)I.traj_buf;
@@ -612,7 +643,7 @@ extern "C" teuk_status teuk_set_state(teuk_ctx* c, int instance, const double* h
     if (!host_u || step0 < 0) TK_FAIL(c, TEUK_EINVAL, "host_u is NULL or step0 < 0");
     Instance& I = c->inst[instance];
     size_t bytes = sizeof(double) * 4 * (size_t)I.p.n_rstar * I.p.n_theta;
-    if (!I.stage) TK_CUDA(c, cudaMallocAsync((void**)&I.stage, bytes, c->stream));
+    if (!I.stage) TK_CUDA(c, dmalloc(c, (void**)&I.stage, bytes, c->stream));
     TK_CUDA(c, cudaMemcpyAsync(I.stage, host_u, bytes, cudaMemcpyHostToDevice, c->stream));
     launch_import_state(c->stream, dev_of(c, I), I.cur, I.stage);
     c->launches++;
@@ -629,7 +660,7 @@ extern "C" teuk_status teuk_get_state(teuk_ctx* c, int instance, double* host_u)
     if (!host_u) TK_FAIL(c, TEUK_EINVAL, "host_u is NULL");
     Instance& I = c->inst[instance];
     size_t bytes = sizeof(double) * 4 * (size_t)I.p.n_rstar * I.p.n_theta;
-    if (!I.stage) TK_CUDA(c, cudaMallocAsync((void**)&I.stage, bytes, c->stream));
+    if (!I.stage) TK_CUDA(c, dmalloc(c, (void**)&I.stage, bytes, c->stream));
     launch_export_state(c->stream, dev_of(c, I), I.cur, I.stage);
     c->launches++;
     TK_CUDA(c, cudaGetLastError());
@@ -737,11 +768,11 @@ teuk_status batched_step(teuk_ctx* c, int64_t n) {
         K.bd.base_bin = (const int*)(uintptr_t)o_bb;
     }
     if (!B.alloc) {
-        TK_CUDA(c, cudaMallocAsync((void**)&B.d_blob, blob.size(), c->stream));
-        TK_CUDA(c, cudaMallocAsync((void**)&B.d_abort, sizeof(int), c->stream));
+        TK_CUDA(c, dmalloc(c, (void**)&B.d_blob, blob.size(), c->stream));
+        TK_CUDA(c, dmalloc(c, (void**)&B.d_abort, sizeof(int), c->stream));
         B.blob_bytes = blob.size();
         for (BatchClass& K : B.cls) {
-            TK_CUDA(c, cudaMallocAsync((void**)&K.d_counter, sizeof(unsigned long long), c->stream));
+            TK_CUDA(c, dmalloc(c, (void**)&K.d_counter, sizeof(unsigned long long), c->stream));
             K.grid = batched_grid(c->prec, K.pitch);
         }
         B.alloc = true;
@@ -749,8 +780,8 @@ teuk_status batched_step(teuk_ctx* c, int64_t n) {
     }
     for (BatchClass& K : B.cls) {
         if (K.items > K.flags_cap) {
-            if (K.d_flags) cudaFreeAsync(K.d_flags, c->stream);
-            TK_CUDA(c, cudaMallocAsync((void**)&K.d_flags, sizeof(int) * K.items, c->stream));
+            if (K.d_flags) dfree(c, K.d_flags, c->stream);
+            TK_CUDA(c, dmalloc(c, (void**)&K.d_flags, sizeof(int) * K.items, c->stream));
             K.flags_cap = K.items;
             changed = true;
         }
@@ -823,13 +854,13 @@ teuk_status set_resident(teuk_ctx* c, Instance& I, int h) {
                 "columns, hold its columns in shared memory and be resident at once)", h, h);
     const int planes = I.p.prec == TEUK_FP32 ? 1 : 2;
     const size_t xg_bytes = (size_t)planes * 2 * plan.nb * 2 * h * I.pitch * 16;
-    if (I.res_xg) cudaFreeAsync(I.res_xg, c->stream);
-    if (I.res_flags) cudaFreeAsync(I.res_flags, c->stream);
+    if (I.res_xg) dfree(c, I.res_xg, c->stream);
+    if (I.res_flags) dfree(c, I.res_flags, c->stream);
     I.res_xg = nullptr;
     I.res_flags = nullptr;
     I.res_h = 0;
-    TK_CUDA(c, cudaMallocAsync((void**)&I.res_xg, xg_bytes, c->stream));
-    TK_CUDA(c, cudaMallocAsync((void**)&I.res_flags, sizeof(int) * kResFlagStride * (plan.nb + 1), c->stream));
+    TK_CUDA(c, dmalloc(c, (void**)&I.res_xg, xg_bytes, c->stream));
+    TK_CUDA(c, dmalloc(c, (void**)&I.res_flags, sizeof(int) * kResFlagStride * (plan.nb + 1), c->stream));
     I.res_plan = plan;
     I.res_h = h;
     return TEUK_OK;
@@ -860,6 +891,17 @@ teuk_status resident_step(teuk_ctx* c, Instance& I, int64_t n) {
 }
 
 }  // namespace
+
+extern "C" teuk_status teuk_set_allocator(teuk_alloc_fn alloc, teuk_free_fn free_fn, void* user) {
+    if ((alloc == nullptr) != (free_fn == nullptr)) {
+        g_create_err = "teuk_set_allocator: give both functions, or neither";
+        return TEUK_EINVAL;
+    }
+    g_alloc.alloc = alloc;
+    g_alloc.free = free_fn;
+    g_alloc.user = alloc ? user : nullptr;
+    return TEUK_OK;
+}
 
 extern "C" teuk_status teuk_set_resident(teuk_ctx* c, int halo) {
     if (!c) return TEUK_EINVAL;
@@ -919,10 +961,10 @@ extern "C" teuk_status teuk_extract(teuk_ctx* c, int instance, double* out, doub
     }
     if (out_scalar && k > 0) {
         if (k > c->sum_cap) {
-            if (c->sum_buf) TK_CUDA(c, cudaFreeAsync(c->sum_buf, c->stream));
+            if (c->sum_buf) dfree(c, c->sum_buf, c->stream);
             c->sum_buf = nullptr;
             c->sum_cap = 0;
-            TK_CUDA(c, cudaMallocAsync((void**)&c->sum_buf, sizeof(double2) * k, c->stream));
+            TK_CUDA(c, dmalloc(c, (void**)&c->sum_buf, sizeof(double2) * k, c->stream));
             c->sum_cap = k;
         }
         launch_wave_sum(c->stream, I.wave, I.wave_cap, nth, I.dth, lvl0, k, c->sum_buf);
@@ -971,7 +1013,7 @@ extern "C" teuk_status teuk_mode_sum(teuk_ctx* c, const double* phi, int n_phi, 
     char* buf = nullptr;
     const size_t b_modes = (sizeof(ModeRing) * modes.size() + 255) / 256 * 256;
     const size_t b_phi = (sizeof(double) * n_phi + 255) / 256 * 256;
-    TK_CUDA(c, cudaMallocAsync((void**)&buf, b_modes + b_phi + sizeof(double2) * n_out, c->stream));
+    TK_CUDA(c, dmalloc(c, (void**)&buf, b_modes + b_phi + sizeof(double2) * n_out, c->stream));
     ModeRing* d_modes = (ModeRing*)buf;
     double* d_phi = (double*)(buf + b_modes);
     double2* d_out = (double2*)(buf + b_modes + b_phi);
@@ -983,7 +1025,7 @@ extern "C" teuk_status teuk_mode_sum(teuk_ctx* c, const double* phi, int n_phi, 
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(out, d_out, sizeof(double2) * n_out, cudaMemcpyDeviceToHost, c->stream);
-    cudaFreeAsync(buf, c->stream);
+    dfree(c, buf, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) TK_FAIL(c, TEUK_ECUDA, "mode sum: %s", cudaGetErrorString(e));
     return TEUK_OK;
@@ -1072,8 +1114,8 @@ static teuk_status autotune_batched(teuk_ctx* c, int trial_steps, int* chosen) {
     auto release = [&]() {
         for (Snap& q : snap) {
             for (void* p : q.st)
-                if (p) cudaFreeAsync(p, c->stream);
-            if (q.wave) cudaFreeAsync(q.wave, c->stream);
+                if (p) dfree(c, p, c->stream);
+            if (q.wave) dfree(c, q.wave, c->stream);
         }
     };
     teuk_status err = TEUK_OK;
@@ -1086,12 +1128,12 @@ static teuk_status autotune_batched(teuk_ctx* c, int trial_steps, int* chosen) {
         q.lo = I.wave_lo;
         q.hi = I.wave_hi;
         for (int pl = 0; pl < nplanes && !err; ++pl) {
-            if (cudaMallocAsync(&q.st[pl], I.plane_bytes, c->stream) != cudaSuccess) err = TEUK_ENOMEM;
+            if (dmalloc(c, &q.st[pl], I.plane_bytes, c->stream) != cudaSuccess) err = TEUK_ENOMEM;
             else cudaMemcpyAsync(q.st[pl], I.state[I.cur][pl], I.plane_bytes, cudaMemcpyDeviceToDevice, c->stream);
         }
         const size_t wb = sizeof(double2) * (size_t)I.wave_cap * (size_t)I.p.n_theta;
         if (!err) {
-            if (cudaMallocAsync((void**)&q.wave, wb, c->stream) != cudaSuccess) err = TEUK_ENOMEM;
+            if (dmalloc(c, (void**)&q.wave, wb, c->stream) != cudaSuccess) err = TEUK_ENOMEM;
             else cudaMemcpyAsync(q.wave, I.wave, wb, cudaMemcpyDeviceToDevice, c->stream);
         }
     }
@@ -1217,8 +1259,8 @@ extern "C" teuk_status teuk_autotune(teuk_ctx* c, int trial_steps, int* chosen) 
         teuk_status err = TEUK_OK;
         for (int b = 0; b < 2 && !err; ++b)
             for (int q = 0; q < nplanes && !err; ++q)
-                if (cudaMallocAsync(&scr[b][q], I.plane_bytes, c->stream) != cudaSuccess) err = TEUK_ENOMEM;
-        if (!err && cudaMallocAsync((void**)&scr_wave, sizeof(double2) * I.p.n_theta * (trial_steps + 2),
+                if (dmalloc(c, &scr[b][q], I.plane_bytes, c->stream) != cudaSuccess) err = TEUK_ENOMEM;
+        if (!err && dmalloc(c, (void**)&scr_wave, sizeof(double2) * I.p.n_theta * (trial_steps + 2),
                                     c->stream) != cudaSuccess)
             err = TEUK_ENOMEM;
         float best_ms = 1e30f;
@@ -1254,8 +1296,8 @@ extern "C" teuk_status teuk_autotune(teuk_ctx* c, int trial_steps, int* chosen) 
                 unsigned char* xg = nullptr;
                 int* fl = nullptr;
                 const size_t xg_bytes = (size_t)nplanes * 2 * plan.nb * 2 * hh * I.pitch * 16;
-                if (cudaMallocAsync((void**)&xg, xg_bytes, c->stream) == cudaSuccess &&
-                    cudaMallocAsync((void**)&fl, sizeof(int) * kResFlagStride * (plan.nb + 1), c->stream) == cudaSuccess) {
+                if (dmalloc(c, (void**)&xg, xg_bytes, c->stream) == cudaSuccess &&
+                    dmalloc(c, (void**)&fl, sizeof(int) * kResFlagStride * (plan.nb + 1), c->stream) == cudaSuccess) {
                     ResidentArgs a{};
                     a.d = d;
                     a.step0 = I.step;
@@ -1284,14 +1326,14 @@ extern "C" teuk_status teuk_autotune(teuk_ctx* c, int trial_steps, int* chosen) 
                     }
                 }
                 cudaGetLastError();
-                if (xg) cudaFreeAsync(xg, c->stream);
-                if (fl) cudaFreeAsync(fl, c->stream);
+                if (xg) dfree(c, xg, c->stream);
+                if (fl) dfree(c, fl, c->stream);
             }
         }
         for (int b = 0; b < 2; ++b)
             for (int q = 0; q < 2; ++q)
-                if (scr[b][q]) cudaFreeAsync(scr[b][q], c->stream);
-        if (scr_wave) cudaFreeAsync(scr_wave, c->stream);
+                if (scr[b][q]) dfree(c, scr[b][q], c->stream);
+        if (scr_wave) dfree(c, scr_wave, c->stream);
         if (err) {
             cudaEventDestroy(e0);
             cudaEventDestroy(e1);
@@ -1322,20 +1364,20 @@ extern "C" int64_t teuk_kernel_launches(const teuk_ctx* c) { return c ? c->launc
 extern "C" void teuk_destroy(teuk_ctx* c) {
     if (!c) return;
     {
-        if (c->sum_buf) cudaFreeAsync(c->sum_buf, c->stream);
+        if (c->sum_buf) dfree(c, c->sum_buf, c->stream);
         Batch& B = c->batch;
         if (B.exec) cudaGraphExecDestroy(B.exec);
         if (B.graph) cudaGraphDestroy(B.graph);
         void* ptrs[] = {B.d_blob, B.d_abort};
         for (void* q : ptrs)
-            if (q) cudaFreeAsync(q, c->stream);
+            if (q) dfree(c, q, c->stream);
         for (BatchClass& K : B.cls) {
-            if (K.d_counter) cudaFreeAsync(K.d_counter, c->stream);
-            if (K.d_flags) cudaFreeAsync(K.d_flags, c->stream);
+            if (K.d_counter) dfree(c, K.d_counter, c->stream);
+            if (K.d_flags) dfree(c, K.d_flags, c->stream);
         }
     }
-    for (Instance& I : c->inst) free_instance(c->stream, I);
-    if (c->status) cudaFreeAsync(c->status, c->stream);
+    for (Instance& I : c->inst) free_instance(c, I);
+    if (c->status) dfree(c, c->status, c->stream);
     cudaStreamSynchronize(c->stream);
     delete c;
 }
@@ -1374,16 +1416,17 @@ double r_of_rstar_host(double M, double a, double target) {
 
 // Device buffers of one adjoint call, released in reverse order of allocation.
 struct AdjBuffers {
+    const teuk_ctx* c;
     cudaStream_t st;
     std::vector<void*> ptrs;
-    explicit AdjBuffers(cudaStream_t s) : st(s) {}
+    AdjBuffers(const teuk_ctx* cc, cudaStream_t s) : c(cc), st(s) {}
     cudaError_t get(void** p, size_t bytes) {
-        cudaError_t e = cudaMallocAsync(p, bytes, st);
+        cudaError_t e = dmalloc(c, p, bytes, st);
         if (e == cudaSuccess) ptrs.push_back(*p);
         return e;
     }
     ~AdjBuffers() {
-        for (void* q : ptrs) cudaFreeAsync(q, st);
+        for (void* q : ptrs) dfree(c, q, st);
     }
 };
 
@@ -1419,7 +1462,7 @@ extern "C" teuk_status teuk_adjoint_n(teuk_ctx* c, int instance, int64_t step0, 
     // compensation planes for lam
     const bool co32 = I.p.prec == TEUK_FP32 || I.p.prec == TEUK_FP32_KAHAN;
     const size_t plane = (size_t)I.p.n_rstar * I.pitch * (co32 ? sizeof(float2) : sizeof(double2));
-    AdjBuffers B(s);
+    AdjBuffers B(c, s);
     CoLevel lam[2] = {};
     CoMu mu = {};
     for (int b = 0; b < 2; ++b) {

@@ -32,6 +32,50 @@ def make_params(**kw) -> _lib.teuk_params:
     return _lib.teuk_params(**d)
 
 
+_ALLOC_HOOKS = None   # the ctypes callbacks in force (kept alive while installed)
+
+
+def set_allocator(alloc=None, free=None):
+    """Route the device memory of contexts created from now on through Python callables
+    alloc(bytes, stream_handle) -> device pointer (0 on failure) and free(ptr, stream_handle)
+    (teuk_set_allocator); set_allocator() restores cudaMallocAsync.  Contexts keep the
+    allocator they were created with."""
+    global _ALLOC_HOOKS
+    lib = _lib.load()
+    if alloc is None and free is None:
+        check(lib.teuk_set_allocator(None, None, None), None)
+        _ALLOC_HOOKS = None
+        return
+
+    def _a(nbytes, stream, user):
+        try:
+            return int(alloc(int(nbytes), int(stream or 0))) or None
+        except Exception:
+            return None
+
+    def _f(ptr, stream, user):
+        try:
+            free(int(ptr), int(stream or 0))
+        except Exception:
+            pass
+
+    hooks = (_lib.ALLOC_FN(_a), _lib.FREE_FN(_f), alloc, free)
+    check(lib.teuk_set_allocator(ctypes.cast(hooks[0], ctypes.c_void_p),
+                                 ctypes.cast(hooks[1], ctypes.c_void_p), None), None)
+    _ALLOC_HOOKS = hooks
+
+
+def use_torch_allocator(enable=True):
+    """Device memory of new contexts from torch's caching allocator (one pool with torch)."""
+    if not enable:
+        set_allocator()
+        return
+    import torch
+
+    set_allocator(lambda n, st: torch.cuda.caching_allocator_alloc(n, stream=st),
+                  lambda p, st: torch.cuda.caching_allocator_delete(p))
+
+
 def _stream_handle(stream):
     if stream is None:
         import torch
