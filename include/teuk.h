@@ -71,6 +71,15 @@ typedef enum {
  * prec: arithmetic of this instance (all instances of a context must agree).
  * wave_capacity: number of waveform records kept on the device (a ring); 0 means
  *   4096.
+ * slab_col0, slab_ncols: slab_ncols = 0 for the whole grid.  Otherwise the instance is a
+ *   slab of the grid above (the r* decomposition of the grid over ranks): it owns the
+ *   grid columns [slab_col0, slab_col0 + slab_ncols) (1 <= slab_col0, slab_col0 +
+ *   slab_ncols <= n_rstar - 1, slab_ncols >= 2) and holds one more column on each side,
+ *   the grid's end column or a halo that teuk_slab_import fills from the neighbouring
+ *   slab after every step.  Its local column k is grid column slab_col0 - 1 + k; states
+ *   (teuk_set_state / teuk_get_state) have slab_ncols + 2 columns.  Node positions,
+ *   coefficients, source and time step are those of the whole grid, so slabs stepped one
+ *   step at a time with their halos exchanged reproduce the whole grid bit for bit.
  */
 typedef struct {
     int s, m;
@@ -83,6 +92,7 @@ typedef struct {
     double rstar_ext;
     int prec;
     int64_t wave_capacity;
+    int slab_col0, slab_ncols;
 } teuk_params;
 
 /*
@@ -224,6 +234,23 @@ teuk_status teuk_adjoint_n(teuk_ctx* ctx, int instance, int64_t step0, int64_t n
  * every instance for non-finite values (TEUK_EUNSTABLE); a bounded device wait
  * that gave up is TEUK_ETIMEOUT.  The status word is cleared once reported. */
 teuk_status teuk_sync(teuk_ctx* ctx);
+
+/* Halo exchange of slab instances (teuk_params.slab_ncols > 0), one column of the current
+ * level in the state's own layout, device to device on the context's stream: planes
+ * (1 for TEUK_FP32, else 2) one after the other, each pitch 16-byte nodes (pitch = n_theta
+ * rounded up to a multiple of 32); teuk_slab_halo_bytes gives the size.
+ *   teuk_slab_export: side 0 copies the first owned column, side 1 the last, to dev_buf.
+ *   teuk_slab_import: side 0 fills the left halo, side 1 the right halo, from dev_buf
+ *     (the column the neighbour exported at the same time level), and retakes the
+ *     waveform record of that level if it reads the halo.
+ * After each teuk_step_n(ctx, 1) every slab exports its two end columns and imports its
+ * neighbours'; the caller moves the buffers (a device copy on one GPU, NCCL send / recv
+ * or another transport between ranks).  The grid's own end columns are not imported:
+ * they stay zero (the radial boundary condition).  TEUK_EINVAL for a non-slab instance,
+ * a side other than 0 or 1, or a NULL buffer. */
+teuk_status teuk_slab_halo_bytes(const teuk_ctx* ctx, int instance, int64_t* bytes);
+teuk_status teuk_slab_export(teuk_ctx* ctx, int instance, int side, void* dev_buf);
+teuk_status teuk_slab_import(teuk_ctx* ctx, int instance, int side, const void* dev_buf);
 
 /* Time level (global step index) of one instance, and its time step dt. */
 teuk_status teuk_get_time(const teuk_ctx* ctx, int instance, int64_t* step, double* dt);

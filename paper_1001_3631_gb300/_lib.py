@@ -25,7 +25,8 @@ class teuk_params(ctypes.Structure):
                 ("n_rstar", ctypes.c_int), ("n_theta", ctypes.c_int),
                 ("courant", ctypes.c_double), ("dt_rule", ctypes.c_int), ("dt", ctypes.c_double),
                 ("rstar_ext", ctypes.c_double), ("prec", ctypes.c_int),
-                ("wave_capacity", ctypes.c_int64)]
+                ("wave_capacity", ctypes.c_int64),
+                ("slab_col0", ctypes.c_int), ("slab_ncols", ctypes.c_int)]
 
 
 class teuk_orbit(ctypes.Structure):
@@ -58,6 +59,9 @@ _PROTOS = {
     "teuk_set_tiling": (_I, [_P, _I, _I]),
     "teuk_set_resident": (_I, [_P, _I]),
     "teuk_set_allocator": (_I, [_P, _P, _P]),
+    "teuk_slab_halo_bytes": (_I, [_P, _I, ctypes.POINTER(_L)]),
+    "teuk_slab_export": (_I, [_P, _I, _I, _P]),
+    "teuk_slab_import": (_I, [_P, _I, _I, _P]),
     "teuk_get_geometry": (_I, [_P, _I, _P]),
     "teuk_set_instance_tiling": (_I, [_P, _I, _I]),
     "teuk_autotune": (_I, [_P, _I, _P]),

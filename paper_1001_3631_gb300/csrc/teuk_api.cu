@@ -55,6 +55,11 @@ struct Instance {
     std::vector<int> h_part;
     int part_strip = 0;
     int fault_col = -1;         // testing aid (teuk_set_fill_fault)
+    // slab of a larger grid (teuk_params.slab_ncols > 0): local column k is grid column
+    // k + off; local columns 0 and n_rstar - 1 are halos (or the grid's own ends)
+    int off = 0;
+    bool slab = false;
+    bool ext_here = true;       // the extraction radius lies between two local columns
     // resident launches (teuk_set_resident): halo h (0 = off), plan, exchange slots and
     // flags (nb + 1 ints: the blocks' flags, then the abort flag)
     int res_h = 0;
@@ -203,6 +208,21 @@ std::string derive(const teuk_params& p, Instance& I) {
     if (ie > p.n_rstar - 2) ie = p.n_rstar - 2;
     I.i_e = ie;
     I.f_e = (p.rstar_ext - (p.rstar_min + ie * I.drs)) / I.drs;
+    if (p.slab_ncols < 0) return "slab_ncols must be >= 0";
+    if (p.slab_ncols > 0) {
+        // the owned grid columns [col0, col0 + ncols), all interior, plus one halo per side
+        if (p.slab_col0 < 1 || p.slab_ncols < 2 || p.slab_col0 + p.slab_ncols > p.n_rstar - 1)
+            return "a slab must own >= 2 interior columns: 1 <= slab_col0, slab_col0 + slab_ncols <= n_rstar - 1";
+        I.slab = true;
+        I.off = p.slab_col0 - 1;
+        I.p.n_rstar = p.slab_ncols + 2;
+        I.i_e = ie - I.off;
+        I.ext_here = I.i_e >= 0 && I.i_e <= I.p.n_rstar - 2;
+        if (!I.ext_here) {
+            I.i_e = 0;
+            I.f_e = 0.0;
+        }
+    }
     I.pitch = (p.n_theta + kPitchAlign - 1) / kPitchAlign * kPitchAlign;
     I.wave_cap = p.wave_capacity > 0 ? p.wave_capacity : 4096;
     return "";
@@ -427,7 +447,7 @@ extern "C" teuk_status teuk_create(const teuk_params* p, int n_instances, void* 
         TK_CCUDA(dmalloc(c, (void**)&I.x_half, sizeof(double) * q.n_rstar, c->stream));
         TK_CCUDA(dmalloc(c, (void**)&I.wave, sizeof(double2) * I.wave_cap * q.n_theta,
                                  c->stream));
-        launch_invert_tortoise(c->stream, q.M, q.a, q.rstar_min, I.drs, q.n_rstar, I.x_int,
+        launch_invert_tortoise(c->stream, q.M, q.a, q.rstar_min, I.drs, q.n_rstar, I.off, I.x_int,
                                I.x_half);
         c->launches++;
         if (q.prec == TEUK_FP64 || q.prec == TEUK_FP64_DF) {  // the FP32 paths build theirs on the first adjoint call
@@ -481,10 +501,11 @@ void source_window(const Instance& I, double rs_lo, double rs_hi, double th_lo, 
     auto clampi = [](double v, int lo, int hi) {
         return v < lo ? lo : (v > hi ? hi : (int)v);
     };
-    int ilo = clampi(std::floor((rs_lo - 8 * sr - q.rstar_min) / I.drs) - 1, 0, nr - 1);
-    int ihi = clampi(std::ceil((rs_hi + 8 * sr - q.rstar_min) / I.drs) + 1, 0, nr - 1);
-    int hlo = clampi(std::floor((rs_lo - 8 * sr - q.rstar_min) / I.drs - 0.5) - 1, 0, nr - 2);
-    int hhi = clampi(std::ceil((rs_hi + 8 * sr - q.rstar_min) / I.drs - 0.5) + 1, 0, nr - 2);
+    // (local indices: grid index - off)
+    int ilo = clampi(std::floor((rs_lo - 8 * sr - q.rstar_min) / I.drs) - 1 - I.off, 0, nr - 1);
+    int ihi = clampi(std::ceil((rs_hi + 8 * sr - q.rstar_min) / I.drs) + 1 - I.off, 0, nr - 1);
+    int hlo = clampi(std::floor((rs_lo - 8 * sr - q.rstar_min) / I.drs - 0.5) - 1 - I.off, 0, nr - 2);
+    int hhi = clampi(std::ceil((rs_hi + 8 * sr - q.rstar_min) / I.drs - 0.5) + 1 - I.off, 0, nr - 2);
     int jlo = clampi(std::floor((th_lo - 8 * stt) / I.dth - 0.5) - 1, 0, nth - 1);
     int jhi = clampi(std::ceil((th_hi + 8 * stt) / I.dth - 0.5) + 1, 0, nth - 1);
     sd.i_lo = ilo; sd.ni = ihi - ilo + 1;
@@ -548,7 +569,7 @@ extern "C" teuk_status teuk_set_source(teuk_ctx* c, int instance, const teuk_orb
     I.sig_r = sr;
     I.sig_t = stt;
     I.drs0_dr0 = (r0 * r0 + q.a * q.a) / Delta0;
-    launch_profile(c->stream, q.M, q.a, q.rstar_min, I.drs, I.dth, rs0, sr, stt, I.drs0_dr0,
+    launch_profile(c->stream, q.M, q.a, q.rstar_min, I.drs, I.off, I.dth, rs0, sr, stt, I.drs0_dr0,
                    I.x_int, I.x_half, sd, (int)q.prec);
     c->launches++;
     TK_CUDA(c, cudaGetLastError());
@@ -619,7 +640,7 @@ extern "C" teuk_status teuk_set_trajectory(teuk_ctx* c, int instance, const teuk
     sd.gt = tb + b_traj + b_amp + b_gr;
     TK_CUDA(c, cudaMemcpyAsync((void*)d_traj, traj, sizeof(double) * 4 * (size_t)n_samples,
                                cudaMemcpyHostToDevice, c->stream));
-    launch_trajectory(c->stream, q.M, q.a, q.m, q.rstar_min, I.drs, I.dth, sr, stt, I.x_int, I.x_half,
+    launch_trajectory(c->stream, q.M, q.a, q.m, q.rstar_min, I.drs, I.off, I.dth, sr, stt, I.x_int, I.x_half,
                       d_traj, n_samples, sd, (int)q.prec);
     c->launches += 2;
     TK_CUDA(c, cudaGetLastError());
@@ -907,6 +928,8 @@ extern "C" teuk_status teuk_set_resident(teuk_ctx* c, int halo) {
     if (!c) return TEUK_EINVAL;
     if (halo < 0) TK_FAIL(c, TEUK_EINVAL, "halo must be >= 0");
     if (c->inst.size() != 1) TK_FAIL(c, TEUK_EINVAL, "resident launches serve single-instance contexts");
+    if (halo > 0 && c->inst[0].slab)
+        TK_FAIL(c, TEUK_EINVAL, "a slab takes its halo columns between steps: no resident launches");
     return set_resident(c, c->inst[0], halo);
 }
 
@@ -945,6 +968,8 @@ extern "C" teuk_status teuk_extract(teuk_ctx* c, int instance, double* out, doub
     if (st) return st;
     if (cap_steps < 0 || (cap_steps > 0 && !out)) TK_FAIL(c, TEUK_EINVAL, "bad output buffer");
     Instance& I = c->inst[instance];
+    if (!I.ext_here)
+        TK_FAIL(c, TEUK_EINVAL, "instance %d is a slab that does not hold the extraction radius", instance);
     int64_t held = I.wave_hi - I.wave_lo;
     int64_t k = std::min(cap_steps, held);
     int64_t lvl0 = I.wave_hi - k;
@@ -998,6 +1023,8 @@ extern "C" teuk_status teuk_mode_sum(teuk_ctx* c, const double* phi, int n_phi, 
             TK_FAIL(c, TEUK_EINVAL,
                     "instance %d is not a mode of instance 0's problem (s, M, a, n_theta, time step "
                     "and extraction radius must agree; set dt to share the step)", (int)i);
+        if (!I.ext_here)
+            TK_FAIL(c, TEUK_EINVAL, "instance %d is a slab that does not hold the extraction radius", (int)i);
         if (first < I.wave_lo || first + n_records > I.wave_hi)
             TK_FAIL(c, TEUK_EINVAL, "instance %d holds records [%lld, %lld), not [%lld, %lld)", (int)i,
                     (long long)I.wave_lo, (long long)I.wave_hi, (long long)first,
@@ -1441,6 +1468,56 @@ extern "C" teuk_status teuk_get_geometry(const teuk_ctx* c, int instance, double
     return TEUK_OK;
 }
 
+extern "C" teuk_status teuk_slab_halo_bytes(const teuk_ctx* c, int instance, int64_t* bytes) {
+    if (!c || !bytes || instance < 0 || instance >= (int)c->inst.size()) return TEUK_EINVAL;
+    const Instance& I = c->inst[instance];
+    const int planes = I.p.prec == TEUK_FP32 ? 1 : 2;
+    *bytes = (int64_t)planes * I.pitch * 16;
+    return TEUK_OK;
+}
+
+namespace {
+// Device copy of local column col of the current level to / from dev (planes one after
+// the other, pitch 16-byte nodes each), on the context's stream.
+teuk_status column_copy(teuk_ctx* c, Instance& I, int col, void* dev, bool out) {
+    const int planes = I.p.prec == TEUK_FP32 ? 1 : 2;
+    const size_t cb = (size_t)I.pitch * 16;
+    for (int k = 0; k < planes; ++k) {
+        char* st = (char*)I.state[I.cur][k] + (size_t)col * cb;
+        char* ex = (char*)dev + k * cb;
+        TK_CUDA(c, cudaMemcpyAsync(out ? ex : st, out ? st : ex, cb, cudaMemcpyDeviceToDevice, c->stream));
+    }
+    return TEUK_OK;
+}
+}  // namespace
+
+extern "C" teuk_status teuk_slab_export(teuk_ctx* c, int instance, int side, void* dev_buf) {
+    teuk_status st = check_instance(c, instance);
+    if (st) return st;
+    Instance& I = c->inst[instance];
+    if (!I.slab || (side != 0 && side != 1) || !dev_buf)
+        TK_FAIL(c, TEUK_EINVAL, "need a slab instance, side 0 or 1 and a device buffer");
+    return column_copy(c, I, side == 0 ? 1 : I.p.n_rstar - 2, dev_buf, true);
+}
+
+extern "C" teuk_status teuk_slab_import(teuk_ctx* c, int instance, int side, const void* dev_buf) {
+    teuk_status st = check_instance(c, instance);
+    if (st) return st;
+    Instance& I = c->inst[instance];
+    if (!I.slab || (side != 0 && side != 1) || !dev_buf)
+        TK_FAIL(c, TEUK_EINVAL, "need a slab instance, side 0 or 1 and a device buffer");
+    st = column_copy(c, I, side == 0 ? 0 : I.p.n_rstar - 1, (void*)dev_buf, false);
+    if (st) return st;
+    // the record of the current level, if it reads the column just replaced
+    const int col = side == 0 ? 0 : I.p.n_rstar - 1;
+    if (I.ext_here && (I.i_e == col || I.i_e + 1 == col) && I.wave_hi > I.wave_lo) {
+        launch_extract(c->stream, dev_of(c, I), I.step, I.cur);
+        c->launches++;
+        TK_CUDA(c, cudaGetLastError());
+    }
+    return TEUK_OK;
+}
+
 extern "C" teuk_status teuk_adjoint_n(teuk_ctx* c, int instance, int64_t step0, int64_t n,
                                       int64_t ckpt_every, const double* grad_wave,
                                       double* grad_amps, double* grad_r0, double* loss) {
@@ -1450,6 +1527,7 @@ extern "C" teuk_status teuk_adjoint_n(teuk_ctx* c, int instance, int64_t step0, 
     if (n < 1 || step0 < 0) TK_FAIL(c, TEUK_EINVAL, "need n >= 1 and step0 >= 0");
     if (I.sd.moving)
         TK_FAIL(c, TEUK_EINVAL, "source gradients are defined for the circular-orbit source only");
+    if (I.slab) TK_FAIL(c, TEUK_EINVAL, "the adjoint is not available for slab instances");
     const bool builtin = grad_wave == nullptr;
     if (builtin && I.step != step0)
         TK_FAIL(c, TEUK_ESTATE, "built-in loss: the state is at step %lld, not step0 = %lld",

@@ -158,8 +158,9 @@ __host__ __device__ inline size_t node_index(const InstDev& d, int i, int j) {
 
 // ---- host launchers (each defined next to its kernels) ----
 // teuk_setup.cu
+// (off: node k of the instance is node k + off of its grid, > 0 for a slab)
 void launch_invert_tortoise(cudaStream_t st, double M, double a, double rstar_min, double drs,
-                            int nr, double* x_int, double* x_half);
+                            int nr, int off, double* x_int, double* x_half);
 void launch_coefficients(cudaStream_t st, int prec, double M, double a, int s, int m,
                          double rstar_min, double drs, double dth, double dt, int nr, int nth,
                          int pitch, const double* x_int, const double* x_half, void* coef_h,
@@ -167,13 +168,13 @@ void launch_coefficients(cudaStream_t st, int prec, double M, double a, int s, i
 void launch_tables_1d(cudaStream_t st, double M, double a, int s, int m, double drs, double dth,
                       double dt, int nr, int nth, const double* x_int, const double* x_half,
                       RTab2* rtab, ThTab* thtab);
-void launch_profile(cudaStream_t st, double M, double a, double rstar_min, double drs, double dth,
-                    double rs0, double sig_r, double sig_t, double drs0_dr0, const double* x_int,
-                    const double* x_half, const SourceDev& src, int prec);
+void launch_profile(cudaStream_t st, double M, double a, double rstar_min, double drs, int off,
+                    double dth, double rs0, double sig_r, double sig_t, double drs0_dr0,
+                    const double* x_int, const double* x_half, const SourceDev& src, int prec);
 // moving particle: the prefactor profile Q on the window and the per-step tables of
 // src (traj: device copy of the samples, [n_samples][4])
 void launch_trajectory(cudaStream_t st, double M, double a, int m, double rstar_min, double drs,
-                       double dth, double sig_r, double sig_t, const double* x_int,
+                       int off, double dth, double sig_r, double sig_t, const double* x_int,
                        const double* x_half, const double* traj, int64_t n_samples,
                        const SourceDev& src, int prec);
 // teuk_step.cu

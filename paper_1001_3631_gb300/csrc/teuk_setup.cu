@@ -50,11 +50,12 @@ __device__ double x_of_rstar(double M, double a, double target) {
     return exp(y);
 }
 
+// Node k of the instance is node k + off of its grid (off > 0 for a slab of a larger grid).
 __global__ void invert_tortoise_kernel(double M, double a, double rstar_min, double drs, int nr,
-                                       double* x_int, double* x_half) {
+                                       int off, double* x_int, double* x_half) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < nr) x_int[k] = x_of_rstar(M, a, rstar_min + k * drs);
-    if (k < nr - 1) x_half[k] = x_of_rstar(M, a, rstar_min + (k + 0.5) * drs);
+    if (k < nr) x_int[k] = x_of_rstar(M, a, rstar_min + (k + off) * drs);
+    if (k < nr - 1) x_half[k] = x_of_rstar(M, a, rstar_min + ((k + off) + 0.5) * drs);
 }
 
 struct Cplx { double re, im; };
@@ -176,7 +177,7 @@ __device__ __forceinline__ void put_real(void* q, size_t idx, double v, int prec
     }
 }
 
-__global__ void profile_kernel(double M, double a, double rstar_min, double drs, double dth,
+__global__ void profile_kernel(double M, double a, double rstar_min, double drs, int off, double dth,
                                double rs0, double sig_r, double sig_t, double drs0_dr0,
                                const double* x_int, const double* x_half, SourceDev src,
                                double2* P_int, double2* P_half, double2* dP_int,
@@ -190,14 +191,14 @@ __global__ void profile_kernel(double M, double a, double rstar_min, double drs,
     if (k < src.ni) {
         int i = src.i_lo + k;
         double2* p = &P_int[(size_t)jj * src.ni + k];
-        profile_point(M, a, x_int[i], rstar_min + i * drs, th, rs0, sig_r, sig_t, drs0_dr0,
+        profile_point(M, a, x_int[i], rstar_min + (i + off) * drs, th, rs0, sig_r, sig_t, drs0_dr0,
                       p, &dP_int[(size_t)jj * src.ni + k]);
         put_q(src.Q_int, (size_t)k * src.q_stride + jj, *p);
     }
     if (k < src.nh) {
         int i = src.h_lo + k;
         double2* p = &P_half[(size_t)jj * src.nh + k];
-        profile_point(M, a, x_half[i], rstar_min + (i + 0.5) * drs, th, rs0, sig_r, sig_t,
+        profile_point(M, a, x_half[i], rstar_min + ((i + off) + 0.5) * drs, th, rs0, sig_r, sig_t,
                       drs0_dr0, p, &dP_half[(size_t)jj * src.nh + k]);
         put_q(src.Q_half, (size_t)k * src.q_stride + jj, *p);
     }
@@ -236,7 +237,7 @@ __global__ void prefactor_kernel(double M, double a, double dth, double norm, co
 
 // Block per step (grid-stride): the amplitudes and the radial and angular factors of
 // the step's two samples.
-__global__ void trajectory_kernel(double M, double a, int m, double rstar_min, double drs,
+__global__ void trajectory_kernel(double M, double a, int m, double rstar_min, double drs, int off,
                                   double dth, double sig_r, double sig_t, const double* traj,
                                   int64_t n_samples, SourceDev src, int prec) {
     const double d = sqrt(M * M - a * a);
@@ -266,7 +267,7 @@ __global__ void trajectory_kernel(double M, double a, int m, double rstar_min, d
             for (int c = threadIdx.x; c < nc; c += blockDim.x) {
                 double g = 0.0;
                 if (have) {
-                    const double rs = rstar_min + (q == 0 ? (lo + c + 0.5) : (double)(lo + c)) * drs;
+                    const double rs = rstar_min + (q == 0 ? ((lo + c + off) + 0.5) : (double)(lo + c + off)) * drs;
                     const double dr = rs - rs_p;
                     if (!(fabs(dr) > 8.0 * sig_r)) g = exp(-0.5 * (dr * dr / (sig_r * sig_r)));
                 }
@@ -365,8 +366,8 @@ void launch_tables_1d(cudaStream_t st, double M, double a, int s, int m, double 
 }
 
 void launch_invert_tortoise(cudaStream_t st, double M, double a, double rstar_min, double drs,
-                            int nr, double* x_int, double* x_half) {
-    invert_tortoise_kernel<<<(nr + 127) / 128, 128, 0, st>>>(M, a, rstar_min, drs, nr, x_int,
+                            int nr, int off, double* x_int, double* x_half) {
+    invert_tortoise_kernel<<<(nr + 127) / 128, 128, 0, st>>>(M, a, rstar_min, drs, nr, off, x_int,
                                                               x_half);
 }
 
@@ -386,11 +387,11 @@ void launch_coefficients(cudaStream_t st, int prec, double M, double a, int s, i
                                               x_int, x_half, (float*)coef_h, (float*)coef_i);
 }
 
-void launch_profile(cudaStream_t st, double M, double a, double rstar_min, double drs, double dth,
-                    double rs0, double sig_r, double sig_t, double drs0_dr0, const double* x_int,
-                    const double* x_half, const SourceDev& src, int prec) {
+void launch_profile(cudaStream_t st, double M, double a, double rstar_min, double drs, int off,
+                    double dth, double rs0, double sig_r, double sig_t, double drs0_dr0,
+                    const double* x_int, const double* x_half, const SourceDev& src, int prec) {
     dim3 g(((src.ni > src.nh ? src.ni : src.nh) + 127) / 128, src.nj);
-    profile_kernel<<<g, 128, 0, st>>>(M, a, rstar_min, drs, dth, rs0, sig_r, sig_t, drs0_dr0,
+    profile_kernel<<<g, 128, 0, st>>>(M, a, rstar_min, drs, off, dth, rs0, sig_r, sig_t, drs0_dr0,
                                       x_int, x_half, src, (double2*)src.P_int,
                                       (double2*)src.P_half, (double2*)src.dP_int,
                                       (double2*)src.dP_half, prec);
@@ -398,7 +399,7 @@ void launch_profile(cudaStream_t st, double M, double a, double rstar_min, doubl
 
 
 void launch_trajectory(cudaStream_t st, double M, double a, int m, double rstar_min, double drs,
-                       double dth, double sig_r, double sig_t, const double* x_int,
+                       int off, double dth, double sig_r, double sig_t, const double* x_int,
                        const double* x_half, const double* traj, int64_t n_samples,
                        const SourceDev& src, int prec) {
     dim3 g(((src.ni > src.nh ? src.ni : src.nh) + 127) / 128, src.nj);
@@ -406,7 +407,7 @@ void launch_trajectory(cudaStream_t st, double M, double a, int m, double rstar_
                                         x_int, x_half, src, prec);
     const int64_t blocks = src.n_traj < 4096 ? src.n_traj : 4096;
     trajectory_kernel<<<(unsigned)(blocks > 0 ? blocks : 1), 128, 0, st>>>(
-        M, a, m, rstar_min, drs, dth, sig_r, sig_t, traj, n_samples, src, prec);
+        M, a, m, rstar_min, drs, off, dth, sig_r, sig_t, traj, n_samples, src, prec);
 }
 
 }  // namespace teuk

@@ -19,7 +19,7 @@ PREC = {"fp64": TEUK_FP64, "fp32": TEUK_FP32, "fp32_kahan": TEUK_FP32_KAHAN, "fp
 
 PARAM_DEFAULTS = dict(s=-2, m=2, M=1.0, a=0.9, rstar_min=-50.0, rstar_max=150.0, n_rstar=800,
                       n_theta=64, courant=0.5, dt_rule=1, dt=0.0, rstar_ext=140.0,
-                      prec="fp64", wave_capacity=0)
+                      prec="fp64", wave_capacity=0, slab_col0=0, slab_ncols=0)
 
 
 def make_params(**kw) -> _lib.teuk_params:
@@ -142,7 +142,19 @@ class TeukSolver:
 
     def shape(self, instance=0):
         p = self.params[instance]
-        return (4, p.n_theta, p.n_rstar)
+        return (4, p.n_theta, p.slab_ncols + 2 if p.slab_ncols > 0 else p.n_rstar)
+
+    # -- slabs (teuk_params.slab_ncols > 0): halo columns, device to device
+    def halo_bytes(self, instance=0):
+        b = ctypes.c_int64(0)
+        check(_lib.load().teuk_slab_halo_bytes(self.ctx, instance, ctypes.byref(b)), self.ctx)
+        return b.value
+
+    def slab_export(self, side, dev_ptr, instance=0):
+        check(_lib.load().teuk_slab_export(self.ctx, instance, side, ctypes.c_void_p(dev_ptr)), self.ctx)
+
+    def slab_import(self, side, dev_ptr, instance=0):
+        check(_lib.load().teuk_slab_import(self.ctx, instance, side, ctypes.c_void_p(dev_ptr)), self.ctx)
 
     def set_state(self, u, step0=0, instance=0):
         u = np.ascontiguousarray(u, dtype=np.float64)
