@@ -386,34 +386,61 @@ def single_mode_leg(steps=2000):
     return out
 
 
-def adjoint_leg():
-    """The adjoint workload (4096 x 128, 10000 steps, A_n ~ N(1, 0.1) seed 5005, checkpoint
-    every 100 steps, loss at a near-zone probe r* = 12.5): the forward run alone and the
-    full gradient call (checkpointed forward, recomputation, backward sweep with the FP64
-    co-state, FP64 gradient sums), each timed on the host around a synchronising call."""
+def adjoint_leg(peaks=None):
+    """The adjoint workload (4096 x 128, 10000 steps, A_n ~ N(1, 0.1) seed 5005, loss at a
+    near-zone probe r* = 12.5): the forward run alone; the built-in-loss gradient call
+    without checkpoints (forward sweep keeping every record's cotangent, then the reverse
+    sweep) and with a checkpoint every 100 steps (each segment's records recomputed from
+    its checkpoint in the reverse sweep), each timed on the host around a synchronising
+    call; and the reverse sweep alone (cotangent mode) timed with CUDA events, with its
+    bytes per update: the co-state read and written once a step (FP32 instances: value
+    and compensation planes of lam_Phi and lam_Pi, 4 x 8 B each way; FP64: 2 x 16 B each
+    way) = 64 B.  The 4096 x 128 co-state (2 x 16.8 MB) stays in L2, so the fraction of
+    the measured HBM copy rate can exceed what DRAM alone would allow."""
     import numpy as np
+    import torch
 
     from paper_1001_3631_gb300 import TeukSolver, inputs
     cfg = inputs.ADJOINT_4096x128
     p = dict(cfg["params"], rstar_ext=12.5)
     n, npts = cfg["steps"], cfg["params"]["n_rstar"] * cfg["params"]["n_theta"]
+    nth = cfg["params"]["n_theta"]
     amps = inputs.amplitudes(n, seed=cfg["amp_seed"])
-    out = {"workload": "adjoint 4096x128, %d steps, checkpoint every %d" % (n, cfg["ckpt_every"])}
+    out = {"workload": "adjoint 4096x128, %d steps; checkpointed mode: every %d steps" % (n, cfg["ckpt_every"])}
+    gw = np.random.default_rng(cfg["amp_seed"]).standard_normal((n, nth, 2))
+    hbm = (peaks or {}).get("hbm_gbs")
     for prec in ("fp64", "fp32_kahan"):
         with TeukSolver(dict(p, prec=prec)) as s:
             s.set_source(cfg["r0"], amps)
+            s.adjoint(10, step0=0, grad_wave=gw[:10])   # warm-up (tables, buffers)
             s.set_state(np.zeros(s.shape()), 0)
             t0 = time.perf_counter()
             s.step(n)
             s.sync()
             tf = time.perf_counter() - t0
-            s.set_state(np.zeros(s.shape()), 0)
-            t0 = time.perf_counter()
-            s.adjoint(n, step0=0, ckpt_every=cfg["ckpt_every"])
-            ta = time.perf_counter() - t0
-        out[prec] = {"forward_s": tf, "gradient_s": ta, "gradient_over_forward": ta / tf,
-                     "gradient_updates_per_s": npts * n / ta}
-    out["unit_note"] = "gradient_updates_per_s = forward point-updates covered per second of the gradient call"
+            res = {"forward_s": tf}
+            for ck, key in ((0, "gradient"), (cfg["ckpt_every"], "gradient_ckpt")):
+                s.set_state(np.zeros(s.shape()), 0)
+                t0 = time.perf_counter()
+                s.adjoint(n, step0=0, ckpt_every=ck)
+                ta = time.perf_counter() - t0
+                res[key + "_s"] = ta
+                res[key + "_over_forward"] = ta / tf
+            st = torch.cuda.current_stream()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            s.adjoint(n, step0=0, grad_wave=gw)
+            e1.record(st)
+            torch.cuda.synchronize()
+            us = e0.elapsed_time(e1) * 1e3 / n
+            gbs = 64.0 * npts / (us * 1e-6) / 1e9
+            res.update({"reverse_us_per_step": us, "reverse_bytes_per_update": 64,
+                        "reverse_gbs": gbs, "reverse_frac_of_measured_hbm": (gbs / hbm) if hbm else None,
+                        "gradient_updates_per_s": npts * n / res["gradient_s"]})
+        out[prec] = res
+    out["unit_note"] = ("gradient_updates_per_s = forward point-updates covered per second of the "
+                        "gradient call; reverse_us_per_step includes the cotangent upload (pageable host "
+                        "memory) of the timed call")
     return out
 
 
@@ -632,6 +659,9 @@ def summary(line):
                                            for p in ("fp32_kahan", "fp32", "fp64_df")},
         "long_run_final_err": {p: g("precision_sweep", p, "final") for p in ("fp32_kahan", "fp32", "fp64_df", "fp64")},
         "adjoint_gradient_over_forward": {p: g("adjoint", p, "gradient_over_forward") for p in ("fp64", "fp32_kahan")},
+        "adjoint_ckpt_gradient_over_forward": {p: g("adjoint", p, "gradient_ckpt_over_forward")
+                                               for p in ("fp64", "fp32_kahan")},
+        "adjoint_reverse_us_per_step": {p: g("adjoint", p, "reverse_us_per_step") for p in ("fp64", "fp32_kahan")},
         "cpu_baseline": g("cpu_baseline", "value"),
     }
 
@@ -761,7 +791,7 @@ def main():
         line["single_mode_800x64"] = single_mode_leg()
         line["accuracy"] = accuracy(cfg, n_steps=args.accuracy_steps)
         line["e2e"] = e2e_path("fp32_kahan", cfg, S, max(2, K // 2), 1)
-        line["adjoint"] = adjoint_leg()
+        line["adjoint"] = adjoint_leg({"hbm_gbs": measured_peaks()[0]})
         if not args.no_sweep:
             line["precision_sweep"] = precision_sweep()
         if not args.no_cpu_baseline:

@@ -217,10 +217,15 @@ teuk_status teuk_mode_sum(teuk_ctx* ctx, const double* phi, int n_phi, int64_t f
  *     step is linear; the context's state is not touched; *loss is not written.
  *   grad_wave == NULL: the built-in loss L = sum_{k=1..n} sum_j |r_ext^3 W_{step0+k}[j]|^2
  *     (psi = r^3 Phi, Eq. 4).  The instance's time level must be step0
- *     (else TEUK_ESTATE).  The forward sweep runs from the current state with a
- *     checkpoint every ckpt_every steps (ckpt_every <= 0: no checkpoints, the
- *     forward waveform is kept instead); the reverse sweep recomputes each
- *     segment's waveform from its checkpoint.  The state ends at step0 + n.
+ *     (else TEUK_ESTATE).  The forward sweep runs from the current state.
+ *     ckpt_every <= 0: it keeps the cotangent of every record (16 n n_theta bytes)
+ *     and the reverse sweep follows; ckpt_every = K > 0: it keeps a state
+ *     checkpoint every K steps instead and the reverse sweep recomputes each
+ *     segment's records from its checkpoint (one more forward sweep of work; the
+ *     cotangent array is still n records long).  The state ends at step0 + n.
+ * With a source, the reverse step stores the co-state over the source window into a
+ * ring of at most 256 steps (32 MB at most), turned into gradients every ring's worth of
+ * steps by one launch with a block per step.
  * Out (host): grad_amps[k] = dL/dA_{step0+k} (n values, may be NULL),
  *   *grad_r0 = dL/dr0 (may be NULL), *loss (built-in loss only, may be NULL).
  * The co-state is FP64 for TEUK_FP64 instances and compensated FP32 (the Kahan

@@ -7,13 +7,12 @@
 // <x, y> = sum Re(conj(x) y), the transpose of y += c x is x += conj(c) y.  So one
 // reverse step is
 //   lam'  = P lam^{n+1}
-//   mu    = C^T lam'                       (adj_corrector_kernel, one thread per half node)
-//   lam^n = lam' + H^T mu + E^T gbar_n     (adj_predictor_kernel, one thread per node)
+//   mu    = C^T lam'                       (half nodes)
+//   lam^n = lam' + H^T mu + E^T gbar_n     (integer nodes), both in adj_step_kernel
 // and the source enters the gradients as
 //   dL/dA_n  = <mu_Pi, (dt/2) e_p P_half> + <lam'_Pi, dt e_c P_int>
 //   dL/dr0  += A_n (<mu_Pi, (dt/2) d(e_p P_half)/dr0> + <lam'_Pi, dt d(e_c P_int)/dr0>)
-// with e_p = e^{-i(omega t_n + phase0)}, e_c the same at t_n + dt/2
-// (adj_source_kernel, one block per step, fixed reduction order).
+// with e_p = e^{-i(omega t_n + phase0)}, e_c the same at t_n + dt/2.
 // Coefficients are the scaled tables of teuk_setup.cu (g, E1, E2, ep, em, E3); in
 // the corrector's angular term  ep Phi~(j+1) + em Phi~(j-1) + (E3 - ep - em) Phi~(j)
 // the ghost rows fold back onto rows 0 and n_theta-1 with the sign of the pole
@@ -24,6 +23,7 @@
 
 #include "teuk_df.cuh"
 #include "teuk_internal.cuh"
+#include "teuk_step_common.cuh"
 
 namespace teuk {
 
@@ -83,66 +83,6 @@ __device__ __forceinline__ R cget(const T* tab, size_t pl, int k, size_t o) {
     else return (R)tab[(size_t)k * pl + o];
 }
 
-// Cotangent of the averaged Phi~ at (col, j) produced by the angular term of the
-// sub-step whose coefficients are `tab` and whose Pi cotangents are LP (col fixed).
-template <typename T, typename R, class LD>
-__device__ __forceinline__ Z<R> theta_cotangent(const T* tab, size_t pl, const LD& LP,
-                                                const InstDev& d, int col, int j, R g) {
-    const int nth = d.nth;
-    size_t o = node_index(d, col, j);
-    Z<R> l0 = LP(o);
-    R ep0 = cget<T, R>(tab, pl, C_EP, o), em0 = cget<T, R>(tab, pl, C_EM, o);
-    Z<R> r = zconjmul(cget<T, R>(tab, pl, C_E3R, o) - ep0 - em0, cget<T, R>(tab, pl, C_E3I, o), l0);
-    if (j >= 1) {
-        size_t om = o - 1;   // row j-1
-        r = zadd(r, zscale(cget<T, R>(tab, pl, C_EP, om), LP(om)));
-    } else {
-        r = zadd(r, zscale(g * em0, l0));   // ghost row -1 = g * row 0
-    }
-    if (j + 1 < nth) {
-        size_t op = o + 1;   // row j+1
-        r = zadd(r, zscale(cget<T, R>(tab, pl, C_EM, op), LP(op)));
-    } else {
-        r = zadd(r, zscale(g * ep0, l0));   // ghost row nth = g * row nth-1
-    }
-    return r;
-}
-
-// mu = C^T P lam  at half node (h, j), h in [0, nr-2].
-template <typename T, typename R>
-__global__ void adj_corrector_kernel(InstDev d, CoLevel lam, CoMu mu) {
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
-    int h = blockIdx.y;
-    if (h > d.nr - 2 || j >= d.nth) return;
-    const T* ci = (const T*)d.coef_i;
-    const size_t pl = plane_elems(d);
-    const CoPlane<R> lF = coplane<R>(lam, 0), lP = coplane<R>(lam, 1);
-    auto LPf = [&](size_t o) { return lP.ld(o); };
-    Z<R> muF = {0, 0}, muP = {0, 0};
-    // integer node h (this half node is its right neighbour R, sign +1) and
-    // integer node h+1 (this half node is its left neighbour L, sign -1)
-    for (int side = 0; side < 2; ++side) {
-        int col = h + side;
-        if (col < 1 || col > d.nr - 2) continue;   // P: boundary columns carry no cotangent
-        R sR = side == 0 ? R(1) : R(-1);
-        size_t o = node_index(d, col, j);
-        Z<R> LF = lF.ld(o), LPi = lP.ld(o);
-        R G = cget<T, R>(ci, pl, C_G, o);
-        Z<R> tc = theta_cotangent<T, R>(ci, pl, LPf, d, col, j, (R)d.ghost);
-        // Delta Phi = -G (hF_R - hF_L) + dt (hP_R + hP_L)/2
-        // Delta Pi  =  G (hP_R - hP_L) + E1 (hP_R + hP_L)/2 + E2 (hF_R - hF_L) + angular(Phi~)
-        muF = zadd(muF, zscale(-sR * G, LF));
-        muF = zadd(muF, zscale(sR, zconjmul(cget<T, R>(ci, pl, C_E2R, o), cget<T, R>(ci, pl, C_E2I, o), LPi)));
-        muF = zadd(muF, zscale(R(0.5), tc));
-        muP = zadd(muP, zscale((R)(0.5 * d.dt), LF));
-        muP = zadd(muP, zscale(sR * G, LPi));
-        muP = zadd(muP, zscale(R(0.5), zconjmul(cget<T, R>(ci, pl, C_E1R, o), cget<T, R>(ci, pl, C_E1I, o), LPi)));
-    }
-    size_t oh = node_index(d, h, j);
-    stv<R>(mu.F, oh, muF);
-    stv<R>(mu.P, oh, muP);
-}
-
 // Compensated add of an increment to one co-state node (FP32): value = v - c.
 __device__ __forceinline__ void kahan_node(float2& v, float2& c, Z<float> dlt) {
     float yx = __fsub_rn(dlt.x, c.x), yy = __fsub_rn(dlt.y, c.y);
@@ -151,72 +91,6 @@ __device__ __forceinline__ void kahan_node(float2& v, float2& c, Z<float> dlt) {
     c.y = __fsub_rn(__fsub_rn(ty, v.y), yy);
     v.x = tx;
     v.y = ty;
-}
-
-// lam^n = P lam^{n+1} + H^T mu (+ E^T gbar) at node (i, j).
-template <typename T, typename R>
-__global__ void adj_predictor_kernel(InstDev d, CoLevel lin, CoMu mu, const double2* gbar,
-                                     CoLevel lout) {
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
-    int i = blockIdx.y;
-    if (i >= d.nr || j >= d.nth) return;
-    const T* ch = (const T*)d.coef_h;
-    const size_t pl = plane_elems(d);
-    const size_t o = node_index(d, i, j);
-    const bool interior = i >= 1 && i <= d.nr - 2;
-    constexpr bool kComp = sizeof(R) == 4;
-    // FP64: the sum starts from P lam^{n+1}; FP32: the increment alone, added to the
-    // compensated lam^{n+1} at the end
-    Z<R> aF = {0, 0}, aP = {0, 0};
-    if constexpr (!kComp) {
-        if (interior) {
-            aF = ldv<R>(lin.F, o);
-            aP = ldv<R>(lin.P, o);
-        }
-    }
-    const R hdt = (R)(0.5 * d.dt);
-    auto MPf = [&](size_t q) { return ldv<R>(mu.P, q); };
-    // half node i-1/2 (index i-1, this column is its right input R, sign +1) and
-    // half node i+1/2 (index i, this column is its left input L, sign -1)
-    for (int side = 0; side < 2; ++side) {
-        int h = i - 1 + side;
-        if (h < 0 || h > d.nr - 2) continue;
-        R sR = side == 0 ? R(1) : R(-1);
-        size_t oh = node_index(d, h, j);
-        Z<R> MF = ldv<R>(mu.F, oh), MP = ldv<R>(mu.P, oh);
-        R G = cget<T, R>(ch, pl, C_G, oh);
-        Z<R> tc = theta_cotangent<T, R>(ch, pl, MPf, d, h, j, (R)d.ghost);
-        // hF = (F_L + F_R)/2 - G (F_R - F_L) + hdt (P_L + P_R)/2
-        // hP = (P_L + P_R)/2 + G (P_R - P_L) + E1 (P_L + P_R)/2 + E2 (F_R - F_L) + angular(Fbar)
-        aF = zadd(aF, zscale(R(0.5) - sR * G, MF));
-        aF = zadd(aF, zscale(sR, zconjmul(cget<T, R>(ch, pl, C_E2R, oh), cget<T, R>(ch, pl, C_E2I, oh), MP)));
-        aF = zadd(aF, zscale(R(0.5), tc));
-        aP = zadd(aP, zscale(R(0.5) * hdt, MF));
-        aP = zadd(aP, zscale(R(0.5) + sR * G, MP));
-        aP = zadd(aP, zscale(R(0.5), zconjmul(cget<T, R>(ch, pl, C_E1R, oh), cget<T, R>(ch, pl, C_E1I, oh), MP)));
-    }
-    if (gbar) {  // transpose of the linear extraction between i_e and i_e + 1
-        if (i == d.i_e) aF = zadd(aF, zscale((R)(1.0 - d.f_e), gld<R>(gbar, j)));
-        if (i == d.i_e + 1) aF = zadd(aF, zscale((R)d.f_e, gld<R>(gbar, j)));
-    }
-    if constexpr (kComp) {
-        float2 vF = {0.f, 0.f}, cF = {0.f, 0.f}, vP = {0.f, 0.f}, cP = {0.f, 0.f};
-        if (interior) {
-            vF = ((const float2*)lin.F)[o];
-            cF = ((const float2*)lin.Fc)[o];
-            vP = ((const float2*)lin.P)[o];
-            cP = ((const float2*)lin.Pc)[o];
-        }
-        kahan_node(vF, cF, aF);
-        kahan_node(vP, cP, aP);
-        ((float2*)lout.F)[o] = vF;
-        ((float2*)lout.Fc)[o] = cF;
-        ((float2*)lout.P)[o] = vP;
-        ((float2*)lout.Pc)[o] = cP;
-    } else {
-        stv<R>(lout.F, o, aF);
-        stv<R>(lout.P, o, aP);
-    }
 }
 
 // lam = E^T gbar (the start of the reverse sweep).
@@ -237,115 +111,452 @@ __global__ void adj_init_kernel(InstDev d, const double2* gbar, CoLevel out) {
     }
 }
 
+// ------------------------------------------------------------------ fused reverse step
+// One reverse step in one pass over the grid: lam^n = P lam^{n+1} + H^T (C^T P lam^{n+1})
+// + E^T gbar.  A block holds one theta column (one thread a row) and streams along r*
+// over a strip of output columns [c0, c1): at half node h it forms mu(h) = C^T lam' from
+// the integer columns h and h+1 (the angular neighbours of lam'_Pi through shared
+// memory), then lam^n(h) = H^T mu from the half nodes h-1 and h (the angular neighbours
+// of mu_Pi through shared memory), so neither mu nor lam' is written to memory.  The
+// arithmetic of each node is that of the two gather passes in the same order
+// (corrector: integer node h, then h+1; predictor: half node h-1, then h).  Over the
+// source window the step also stores mu_Pi (half nodes) and lam'_Pi (integer nodes) into
+// one slot of a ring, from which adj_src_grad_kernel forms the source gradients of many
+// steps at once, off the step's critical path.
+
+// theta_cotangent with the angular neighbours given: lm, l0, lp the Pi cotangents of
+// rows j-1, j, j+1 of column node o.
+template <typename T, typename R>
+__device__ __forceinline__ Z<R> theta_cot3(const T* tab, size_t pl, size_t o, int j, int nth, Z<R> lm,
+                                           Z<R> l0, Z<R> lp, R g) {
+    R ep0 = cget<T, R>(tab, pl, C_EP, o), em0 = cget<T, R>(tab, pl, C_EM, o);
+    Z<R> r = zconjmul(cget<T, R>(tab, pl, C_E3R, o) - ep0 - em0, cget<T, R>(tab, pl, C_E3I, o), l0);
+    if (j >= 1) r = zadd(r, zscale(cget<T, R>(tab, pl, C_EP, o - 1), lm));
+    else r = zadd(r, zscale(g * em0, l0));
+    if (j + 1 < nth) r = zadd(r, zscale(cget<T, R>(tab, pl, C_EM, o + 1), lp));
+    else r = zadd(r, zscale(g * ep0, l0));
+    return r;
+}
+
+// The co-state of one node as stored: FP64 value, or FP32 (v, c) pairs with value v - c.
+template <typename R>
+struct CoNode {
+    Z<R> F, P;          // values
+    float2 vF, cF, vP, cP;   // FP32: the stored pairs
+};
+template <typename R>
+__device__ __forceinline__ CoNode<R> co_load(const CoLevel& L, size_t o) {
+    CoNode<R> n{};
+    if constexpr (sizeof(R) == 4) {
+        n.vF = ((const float2*)L.F)[o];
+        n.cF = ((const float2*)L.Fc)[o];
+        n.vP = ((const float2*)L.P)[o];
+        n.cP = ((const float2*)L.Pc)[o];
+        n.F = {n.vF.x - n.cF.x, n.vF.y - n.cF.y};
+        n.P = {n.vP.x - n.cP.x, n.vP.y - n.cP.y};
+    } else {
+        n.F = ldv<R>(L.F, o);
+        n.P = ldv<R>(L.P, o);
+    }
+    return n;
+}
+
 // Source gradients of step n.  With e = e^{-i phi} the phase of a sub-step and
 // de = d e / d r0,
 //   dL/dA_n  = Re( (dt/2) e_p S_h + dt e_c S_i ),
 //   dL/dr0  += A_n Re( (dt/2) (de_p S_h + e_p S'_h) + dt (de_c S_i + e_c S'_i) ),
 // where S_h = sum conj(mu_Pi) P_half and S'_h = sum conj(mu_Pi) dP_half over the
 // half-node window, S_i and S'_i the same with lam'_Pi over the integer-node window
-// (interior columns only).  The four complex sums are FP64: each block reduces a fixed
-// slice of the window in a fixed order, and the last block to finish adds the blocks'
-// partial sums in index order and applies the phases, so the result does not depend
-// on the scheduling.
-constexpr int kSrcThreads = 256;
+// (zero off the interior columns).  One block a step: the steps k0 .. k0 + count - 1 of
+// a sweep (absolute step step0 + k); ring slot k % slots holds the step's half-node
+// window ([nj][nh]) followed by its integer-node window ([nj][ni]).  Each
+// thread sums its nodes (t, t + blockDim, ...) in FP64, the threads are added in a fixed
+// tree, so the result does not depend on the scheduling.
+constexpr int kSrcGradThreads = 256;
+
 template <typename R>
-__global__ void adj_source_kernel(InstDev d, int64_t n, CoLevel lam, CoMu mu, double* part,
-                                  unsigned* done, double* gA, double* gR) {
-    __shared__ double red[8][kSrcThreads];
-    __shared__ bool last;
+__global__ void __launch_bounds__(kSrcGradThreads) adj_src_grad_kernel(InstDev d, int64_t step0, int64_t k0,
+                                                                       int slots, const void* ring,
+                                                                       double* gA, double* gR) {
+    using V = typename R2T<R>::V;
     const SourceDev& s = d.src;
-    const CoPlane<R> lP = coplane<R>(lam, 1);
+    const int64_t k = k0 + blockIdx.x, n = step0 + k;
+    const size_t nhw = (size_t)s.nh * s.nj, niw = (size_t)s.ni * s.nj;
+    const V* Hw = (const V*)ring + (size_t)(k % slots) * (nhw + niw);
+    const V* Iw = Hw + nhw;
     double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // S_h, S'_h, S_i, S'_i (re, im)
-    const int nh_tot = s.nj * s.nh, ni_tot = s.nj * s.ni;
-    const int stride = gridDim.x * kSrcThreads;
-    for (int k = blockIdx.x * kSrcThreads + threadIdx.x; k < nh_tot + ni_tot; k += stride) {
-        Z<double> l, P, dP;
-        int q;
-        if (k < nh_tot) {
-            int jj = k / s.nh, hh = k % s.nh;
-            const Z<R> m = ldv<R>(mu.P, node_index(d, s.h_lo + hh, s.j_lo + jj));
-            l = {(double)m.x, (double)m.y};
-            P = {s.P_half[k].x, s.P_half[k].y};
-            dP = {s.dP_half[k].x, s.dP_half[k].y};
-            q = 0;
-        } else {
-            int kk = k - nh_tot;
-            int jj = kk / s.ni, ii = kk % s.ni;
-            int col = s.i_lo + ii;
-            if (col < 1 || col > d.nr - 2) continue;
-            const Z<R> v = lP.ld(node_index(d, col, s.j_lo + jj));
-            l = {(double)v.x, (double)v.y};
-            P = {s.P_int[kk].x, s.P_int[kk].y};
-            dP = {s.dP_int[kk].x, s.dP_int[kk].y};
-            q = 4;
-        }
-        // conj(l) P and conj(l) dP
-        acc[q + 0] += l.x * P.x + l.y * P.y;
-        acc[q + 1] += l.x * P.y - l.y * P.x;
-        acc[q + 2] += l.x * dP.x + l.y * dP.y;
-        acc[q + 3] += l.x * dP.y - l.y * dP.x;
+    for (size_t q = threadIdx.x; q < nhw; q += blockDim.x) {
+        const V m = Hw[q];
+        const double lx = (double)m.x, ly = (double)m.y;
+        const double2 P = s.P_half[q], dP = s.dP_half[q];
+        acc[0] += lx * P.x + ly * P.y;
+        acc[1] += lx * P.y - ly * P.x;
+        acc[2] += lx * dP.x + ly * dP.y;
+        acc[3] += lx * dP.y - ly * dP.x;
     }
-#pragma unroll
-    for (int v = 0; v < 8; ++v) red[v][threadIdx.x] = acc[v];
-    __syncthreads();
-    for (int st = kSrcThreads / 2; st > 0; st >>= 1) {
-        if (threadIdx.x < st)
-#pragma unroll
-            for (int v = 0; v < 8; ++v) red[v][threadIdx.x] += red[v][threadIdx.x + st];
-        __syncthreads();
+    for (size_t q = threadIdx.x; q < niw; q += blockDim.x) {
+        const V m = Iw[q];
+        const double lx = (double)m.x, ly = (double)m.y;
+        const double2 P = s.P_int[q], dP = s.dP_int[q];
+        acc[4] += lx * P.x + ly * P.y;
+        acc[5] += lx * P.y - ly * P.x;
+        acc[6] += lx * dP.x + ly * dP.y;
+        acc[7] += lx * dP.y - ly * dP.x;
     }
-    if (threadIdx.x == 0) {
-#pragma unroll
-        for (int v = 0; v < 8; ++v) part[blockIdx.x * 8 + v] = red[v][0];
-        __threadfence();
-        last = atomicAdd(done, 1u) == gridDim.x - 1;
-    }
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    // the last block: threads 0..7 each add one of the eight sums over the blocks in
-    // index order; threads 32 and 64 form the two phases meanwhile
+    __shared__ double wred[kSrcGradThreads / 32][8];
     __shared__ double S[8];
     __shared__ Z<double> ph[4];   // e_p, e_c, de_p, de_c
-    const int t = threadIdx.x;
-    if (t < 8) {
-        double acc_v = 0.0;
-        for (int b = 0; b < (int)gridDim.x; ++b) acc_v += ((volatile double*)part)[b * 8 + t];
-        S[t] = acc_v;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+        double x = acc[v];
+        for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
+        if (lane == 0) wred[warp][v] = x;
     }
-    if (t == 32 || t == 64) {
-        const double tt = (double)n * d.dt + (t == 32 ? 0.0 : 0.5 * d.dt);
+    __syncthreads();
+    if (t < 8) {
+        double x = 0.0;
+        for (int w = 0; w < kSrcGradThreads / 32; ++w) x += wred[w][t];
+        S[t] = x;
+    }
+    if (t == 64 || t == 96) {   // the two sub-step phases, on two other warps
+        const double tt = (double)n * d.dt + (t == 64 ? 0.0 : 0.5 * d.dt);
         double sn, cs;
         sincos(s.omega * tt + s.phase0, &sn, &cs);
-        // e = (cos, -sin); de = -i k e with k = d phi / d r0
-        const double k = tt * s.domega + s.dphase0;
+        const double kk = tt * s.domega + s.dphase0;   // e = (cos, -sin); de = -i k e
         const Z<double> e = {cs, -sn};
-        ph[t == 32 ? 0 : 1] = e;
-        ph[t == 32 ? 2 : 3] = Z<double>{k * e.y, -k * e.x};
+        ph[t == 64 ? 0 : 1] = e;
+        ph[t == 64 ? 2 : 3] = Z<double>{kk * e.y, -kk * e.x};
     }
     __syncthreads();
     if (t != 0) return;
-    *done = 0;   // ready for the next step's launch (stream-ordered)
     const double A = (s.amps != nullptr && n < s.n_amps) ? s.amps[n] : 1.0;
     auto re_mul = [](Z<double> a, double bx, double by) { return a.x * bx - a.y * by; };
-    const double hdt = 0.5 * d.dt;
-    *gA = hdt * re_mul(ph[0], S[0], S[1]) + d.dt * re_mul(ph[1], S[4], S[5]);
-    *gR = A * (hdt * (re_mul(ph[2], S[0], S[1]) + re_mul(ph[0], S[2], S[3])) +
-               d.dt * (re_mul(ph[3], S[4], S[5]) + re_mul(ph[1], S[6], S[7])));
+    const double hd = 0.5 * d.dt;
+    gA[k] = hd * re_mul(ph[0], S[0], S[1]) + d.dt * re_mul(ph[1], S[4], S[5]);
+    gR[k] = A * (hd * (re_mul(ph[2], S[0], S[1]) + re_mul(ph[0], S[2], S[3])) +
+                 d.dt * (re_mul(ph[3], S[4], S[5]) + re_mul(ph[1], S[6], S[7])));
+}
+
+// kMaxT: the largest block this instance serves (256: columns of up to 256 rows, with
+// the register budget of several blocks per SM; 1024: taller columns)
+template <typename T, typename R, int kMaxT>
+__global__ void __launch_bounds__(kMaxT) adj_step_kernel(InstDev d, CoLevel lin, const double2* gbar,
+                                                         CoLevel lout, int strip, void* wh, void* wi) {
+    extern __shared__ __align__(16) unsigned char adj_smem[];
+    Z<R>* LB = (Z<R>*)adj_smem;                 // [2][pitch] lam'_Pi of a column
+    Z<R>* MB = LB + 2 * (size_t)d.pitch;        // [2][pitch] mu_Pi of a half node
+    const int j = threadIdx.x, nth = d.nth, nr = d.nr, pitch = d.pitch;
+    const bool row_ok = j < nth;
+    const int c0 = blockIdx.x * strip, c1 = min(nr, c0 + strip);   // output columns [c0, c1)
+    const T* ci = (const T*)d.coef_i;
+    const T* ch = (const T*)d.coef_h;
+    const size_t pl = plane_elems(d);
+    const R g = (R)d.ghost, hdt = (R)(0.5 * d.dt);
+    constexpr bool kComp = sizeof(R) == 4;
+    const SourceDev& s = d.src;
+    // wh, wi: this step's ring slot of the window co-states (null: no source)
+    // lam' = P lam^{n+1} at column col (zero at the boundary columns and outside)
+    auto lam_at = [&](int col) {
+        CoNode<R> z{};
+        if (row_ok && col >= 1 && col <= nr - 2) z = co_load<R>(lin, node_index(d, col, j));
+        return z;
+    };
+    auto nb3 = [&](const Z<R>* buf, int sl, Z<R>& lm, Z<R>& lp) {
+        const Z<R>* b = buf + (size_t)sl * pitch;
+        lm = j >= 1 ? b[j - 1] : Z<R>{0, 0};
+        lp = j + 1 < nth ? b[j + 1] : Z<R>{0, 0};
+    };
+    CoNode<R> l_cur = lam_at(c0 - 1), l_next;
+    LB[(size_t)((c0 - 1) & 1) * pitch + j] = l_cur.P;
+    Z<R> mu_prevF = {0, 0}, mu_prevP = {0, 0};
+    for (int h = c0 - 1; h <= c1 - 1; ++h) {
+        // A: lam' of column h+1
+        l_next = lam_at(h + 1);
+        LB[(size_t)((h + 1) & 1) * pitch + j] = l_next.P;
+        __syncthreads();
+        // C: mu at half node h = C^T lam' from the integer columns h (right neighbour of
+        // this half node, sign +1) and h+1 (left neighbour, sign -1)
+        Z<R> muF = {0, 0}, muP = {0, 0};
+        if (row_ok && h >= 0 && h <= nr - 2) {
+            for (int side = 0; side < 2; ++side) {
+                const int col = h + side;
+                if (col < 1 || col > nr - 2) continue;
+                const R sR = side == 0 ? R(1) : R(-1);
+                const size_t o = node_index(d, col, j);
+                const CoNode<R>& L = side == 0 ? l_cur : l_next;
+                Z<R> lm, lp;
+                nb3(LB, col & 1, lm, lp);
+                const R G = cget<T, R>(ci, pl, C_G, o);
+                const Z<R> tc = theta_cot3<T, R>(ci, pl, o, j, nth, lm, L.P, lp, g);
+                muF = zadd(muF, zscale(-sR * G, L.F));
+                muF = zadd(muF, zscale(sR, zconjmul(cget<T, R>(ci, pl, C_E2R, o), cget<T, R>(ci, pl, C_E2I, o), L.P)));
+                muF = zadd(muF, zscale(R(0.5), tc));
+                muP = zadd(muP, zscale((R)(0.5 * d.dt), L.F));
+                muP = zadd(muP, zscale(sR * G, L.P));
+                muP = zadd(muP, zscale(R(0.5), zconjmul(cget<T, R>(ci, pl, C_E1R, o), cget<T, R>(ci, pl, C_E1I, o), L.P)));
+            }
+            if (wh && h >= c0) {   // half-node window: mu_Pi (half node c0 - 1 is the
+                                   // previous block's)
+                const int a = h - s.h_lo, bb = j - s.j_lo;
+                if ((unsigned)a < (unsigned)s.nh && (unsigned)bb < (unsigned)s.nj)
+                    stv<R>(wh, (size_t)bb * s.nh + a, muP);
+            }
+        }
+        MB[(size_t)(h & 1) * pitch + j] = muP;
+        __syncthreads();
+        // F: lam^n at integer column h from the half nodes h-1 (this column is their right
+        // input, sign +1) and h (left input, sign -1)
+        if (h >= c0 && row_ok) {
+            const int i = h;
+            const size_t o = node_index(d, i, j);
+            const bool interior = i >= 1 && i <= nr - 2;
+            Z<R> aF = {0, 0}, aP = {0, 0};
+            if constexpr (!kComp) {
+                if (interior) {
+                    aF = l_cur.F;
+                    aP = l_cur.P;
+                }
+            }
+            for (int side = 0; side < 2; ++side) {
+                const int hh = i - 1 + side;
+                if (hh < 0 || hh > nr - 2) continue;
+                const R sR = side == 0 ? R(1) : R(-1);
+                const size_t oh = node_index(d, hh, j);
+                const Z<R> MF = side == 0 ? mu_prevF : muF, MP = side == 0 ? mu_prevP : muP;
+                Z<R> mm, mp;
+                nb3(MB, hh & 1, mm, mp);
+                const R G = cget<T, R>(ch, pl, C_G, oh);
+                const Z<R> tc = theta_cot3<T, R>(ch, pl, oh, j, nth, mm, MP, mp, g);
+                aF = zadd(aF, zscale(R(0.5) - sR * G, MF));
+                aF = zadd(aF, zscale(sR, zconjmul(cget<T, R>(ch, pl, C_E2R, oh), cget<T, R>(ch, pl, C_E2I, oh), MP)));
+                aF = zadd(aF, zscale(R(0.5), tc));
+                aP = zadd(aP, zscale(R(0.5) * hdt, MF));
+                aP = zadd(aP, zscale(R(0.5) + sR * G, MP));
+                aP = zadd(aP, zscale(R(0.5), zconjmul(cget<T, R>(ch, pl, C_E1R, oh), cget<T, R>(ch, pl, C_E1I, oh), MP)));
+            }
+            if (gbar) {   // transpose of the linear extraction between i_e and i_e + 1
+                if (i == d.i_e) aF = zadd(aF, zscale((R)(1.0 - d.f_e), gld<R>(gbar, j)));
+                if (i == d.i_e + 1) aF = zadd(aF, zscale((R)d.f_e, gld<R>(gbar, j)));
+            }
+            if constexpr (kComp) {
+                float2 vF = {0.f, 0.f}, cF = {0.f, 0.f}, vP = {0.f, 0.f}, cP = {0.f, 0.f};
+                if (interior) {
+                    vF = l_cur.vF;
+                    cF = l_cur.cF;
+                    vP = l_cur.vP;
+                    cP = l_cur.cP;
+                }
+                kahan_node(vF, cF, aF);
+                kahan_node(vP, cP, aP);
+                ((float2*)lout.F)[o] = vF;
+                ((float2*)lout.Fc)[o] = cF;
+                ((float2*)lout.P)[o] = vP;
+                ((float2*)lout.Pc)[o] = cP;
+            } else {
+                stv<R>(lout.F, o, aF);
+                stv<R>(lout.P, o, aP);
+            }
+            if (wi) {   // integer-node window: lam'_Pi (zero off the interior columns)
+                const int a = i - s.i_lo, bb = j - s.j_lo;
+                if ((unsigned)a < (unsigned)s.ni && (unsigned)bb < (unsigned)s.nj)
+                    stv<R>(wi, (size_t)bb * s.ni + a, interior ? l_cur.P : Z<R>{0, 0});
+            }
+        }
+        l_cur = l_next;
+        mu_prevF = muF;
+        mu_prevP = muP;
+    }
+}
+
+// The FP32 co-state (FP32 and FP32-Kahan instances): the same reverse step with the
+// coefficients formed in registers from the 1D tables (form_coefs2, the split angular
+// form turned back into ep = A + B, em = A - B), i.e. the coefficients the forward FP32
+// kernels compute, instead of 2D tables: the reverse step is then the transpose of the
+// forward operator as it is evaluated, and it reads no coefficient tables.  Each column's
+// coefficients are formed once per step and used at once for both nodes they enter: the
+// corrector coefficients of column c enter mu(c-1) (as its right node) and mu(c) (as its
+// left node), those of half node c enter lam(c) and lam(c+1); the partial sums are
+// carried to the next column, so every sum is formed in the order of the gather form
+// (left neighbour first).
+struct CfF { float g, e1r, e1i, e2r, e2i, ep, em, e3r, e3i; };
+
+__device__ __forceinline__ Z<float> theta_cot_v(const CfF& c, float ep_m, float em_p, Z<float> lm,
+                                                Z<float> l0, Z<float> lp, int j, int nth, float g) {
+    Z<float> r = zconjmul(c.e3r - c.ep - c.em, c.e3i, l0);
+    if (j >= 1) r = zadd(r, zscale(ep_m, lm));
+    else r = zadd(r, zscale(g * c.em, l0));
+    if (j + 1 < nth) r = zadd(r, zscale(em_p, lp));
+    else r = zadd(r, zscale(g * c.ep, l0));
+    return r;
+}
+
+template <int kMaxT>
+__global__ void __launch_bounds__(kMaxT) adj_step_kernel_f32(InstDev d, CoLevel lin, const double2* gbar,
+                                                             CoLevel lout, int strip, void* wh, void* wi) {
+    using R = float;
+    extern __shared__ __align__(16) unsigned char adj_smem[];
+    const int j = threadIdx.x, nth = d.nth, nr = d.nr, pitch = d.pitch;
+    Z<R>* LB = (Z<R>*)adj_smem;                   // [2][pitch] lam'_Pi of a column
+    Z<R>* MB = LB + 2 * (size_t)pitch;            // [2][pitch] mu_Pi of a half node
+    float4* EB = (float4*)(MB + 2 * (size_t)pitch);   // [3][pitch] {ep, em} of node, half node
+    const bool row_ok = j < nth;
+    const int c0 = blockIdx.x * strip, c1 = min(nr, c0 + strip);   // output columns [c0, c1)
+    const R g = (R)d.ghost, hdt = (R)(0.5 * d.dt), qdt = (R)(0.5 * d.dt);
+    const SourceDev& s = d.src;
+    // wh, wi: this step's ring slot of the window co-states (null: no source)
+    RowTab<PK> rt;
+    rt.load(d.thtab, j, row_ok);
+    auto lam_at = [&](int col) {
+        CoNode<R> z{};
+        if (row_ok && col >= 1 && col <= nr - 2) z = co_load<R>(lin, node_index(d, col, j));
+        return z;
+    };
+    // coefficients of column col: node col (ci) and half node col+1/2 (ch)
+    auto form = [&](int col, CfF& ci, CfF& ch) {
+        float2 cf2[kNCoef];
+        if (col >= 0 && col <= nr - 1) {
+            form_coefs2(d.rtab[col], rt.t, cf2);
+        } else {
+#pragma unroll
+            for (int q = 0; q < kNCoef; ++q) cf2[q] = make_float2(0.f, 0.f);
+        }
+        auto pick = [&](bool half) {
+            auto v = [&](int q) { return half ? cf2[q].x : cf2[q].y; };
+            return CfF{v(C_G), v(C_E1R), v(C_E1I), v(C_E2R), v(C_E2I), __fadd_rn(v(C_EP), v(C_EM)),
+                       __fsub_rn(v(C_EP), v(C_EM)), v(C_E3R), v(C_E3I)};
+        };
+        ci = pick(false);
+        ch = pick(true);
+    };
+    auto nb3 = [&](const Z<R>* buf, int sl, Z<R>& lm, Z<R>& lp) {
+        const Z<R>* b = buf + (size_t)sl * pitch;
+        lm = j >= 1 ? b[j - 1] : Z<R>{0, 0};
+        lp = j + 1 < nth ? b[j + 1] : Z<R>{0, 0};
+    };
+    // corrector contribution of node col (coefficients c, co-state L) to a half node on
+    // its right (sR = +1) or left (sR = -1)
+    auto e3 = [](int col) { return (col + 3) % 3; };   // EB slot of column col >= -1
+    auto corr = [&](const CfF& c, const CoNode<R>& L, int col, R sR, Z<R>& muF, Z<R>& muP) {
+        const int sl = col & 1;
+        Z<R> lm, lp;
+        nb3(LB, sl, lm, lp);
+        const float4 em = EB[(size_t)e3(col) * pitch + (j >= 1 ? j - 1 : j)];   // row j-1
+        const float4 ep = EB[(size_t)e3(col) * pitch + (j + 1 < nth ? j + 1 : j)];   // row j+1
+        const Z<R> tc = theta_cot_v(c, em.x, ep.y, lm, L.P, lp, j, nth, g);
+        muF = zadd(muF, zscale(-sR * c.g, L.F));
+        muF = zadd(muF, zscale(sR, zconjmul(c.e2r, c.e2i, L.P)));
+        muF = zadd(muF, zscale(R(0.5), tc));
+        muP = zadd(muP, zscale(hdt, L.F));
+        muP = zadd(muP, zscale(sR * c.g, L.P));
+        muP = zadd(muP, zscale(R(0.5), zconjmul(c.e1r, c.e1i, L.P)));
+    };
+    // predictor contribution of half node hh (coefficients c, cotangent MF, MP) to the node
+    // on its right (sR = +1) or left (sR = -1)
+    auto pred = [&](const CfF& c, Z<R> MF, Z<R> MP, int hh, R sR, Z<R>& aF, Z<R>& aP) {
+        const int sl = hh & 1;
+        Z<R> mm, mp;
+        nb3(MB, sl, mm, mp);
+        const float4 em = EB[(size_t)e3(hh) * pitch + (j >= 1 ? j - 1 : j)];   // row j-1
+        const float4 ep = EB[(size_t)e3(hh) * pitch + (j + 1 < nth ? j + 1 : j)];   // row j+1
+        const Z<R> tc = theta_cot_v(c, em.z, ep.w, mm, MP, mp, j, nth, g);
+        aF = zadd(aF, zscale(R(0.5) - sR * c.g, MF));
+        aF = zadd(aF, zscale(sR, zconjmul(c.e2r, c.e2i, MP)));
+        aF = zadd(aF, zscale(R(0.5), tc));
+        aP = zadd(aP, zscale(R(0.5) * qdt, MF));
+        aP = zadd(aP, zscale(R(0.5) + sR * c.g, MP));
+        aP = zadd(aP, zscale(R(0.5), zconjmul(c.e1r, c.e1i, MP)));
+    };
+    // prologue: column c0 - 1
+    CoNode<R> l_cur = lam_at(c0 - 1);
+    CfF ci_cur, ch_cur;
+    form(c0 - 1, ci_cur, ch_cur);
+    LB[(size_t)((c0 - 1) & 1) * pitch + j] = l_cur.P;
+    EB[(size_t)e3(c0 - 1) * pitch + j] = make_float4(ci_cur.ep, ci_cur.em, ch_cur.ep, ch_cur.em);
+    __syncthreads();
+    Z<R> muF_part = {0, 0}, muP_part = {0, 0};      // mu(h): the left node's share
+    if (row_ok && c0 - 1 >= 1 && c0 - 1 <= nr - 2) corr(ci_cur, l_cur, c0 - 1, R(1), muF_part, muP_part);
+    Z<R> aF_part = {0, 0}, aP_part = {0, 0};        // lam(h): the left half node's share
+    for (int h = c0 - 1; h <= c1 - 1; ++h) {
+        // A: column h+1: its co-state and coefficients
+        const CoNode<R> l_next = lam_at(h + 1);
+        CfF ci_n, ch_n;
+        form(h + 1, ci_n, ch_n);
+        LB[(size_t)((h + 1) & 1) * pitch + j] = l_next.P;
+        EB[(size_t)e3(h + 1) * pitch + j] = make_float4(ci_n.ep, ci_n.em, ch_n.ep, ch_n.em);
+        __syncthreads();
+        // C: mu(h) = its left node's share + the right node h+1; the left share of mu(h+1)
+        Z<R> muF = muF_part, muP = muP_part, mfn = {0, 0}, mpn = {0, 0};
+        const bool half_ok = h >= 0 && h <= nr - 2;
+        if (row_ok && h + 1 >= 1 && h + 1 <= nr - 2) {
+            if (half_ok) corr(ci_n, l_next, h + 1, R(-1), muF, muP);
+            if (h + 1 <= nr - 2) corr(ci_n, l_next, h + 1, R(1), mfn, mpn);
+        }
+        if (!half_ok || !row_ok) muF = muP = Z<R>{0, 0};
+        if (wh && half_ok && row_ok && h >= c0) {
+            const int a = h - s.h_lo, bb = j - s.j_lo;
+            if ((unsigned)a < (unsigned)s.nh && (unsigned)bb < (unsigned)s.nj)
+                stv<R>(wh, (size_t)bb * s.nh + a, muP);
+        }
+        MB[(size_t)(h & 1) * pitch + j] = muP;
+        __syncthreads();
+        // F: half node h's shares of lam(h) (completing it) and lam(h+1)
+        Z<R> aF = aF_part, aP = aP_part, afn = {0, 0}, apn = {0, 0};
+        if (row_ok && half_ok) {
+            pred(ch_cur, muF, muP, h, R(-1), aF, aP);
+            pred(ch_cur, muF, muP, h, R(1), afn, apn);
+        }
+        if (h >= c0 && row_ok) {
+            const int i = h;
+            const size_t o = node_index(d, i, j);
+            const bool interior = i >= 1 && i <= nr - 2;
+            if (gbar) {
+                if (i == d.i_e) aF = zadd(aF, zscale((R)(1.0 - d.f_e), gld<R>(gbar, j)));
+                if (i == d.i_e + 1) aF = zadd(aF, zscale((R)d.f_e, gld<R>(gbar, j)));
+            }
+            float2 vF = {0.f, 0.f}, cF = {0.f, 0.f}, vP = {0.f, 0.f}, cP = {0.f, 0.f};
+            if (interior) {
+                vF = l_cur.vF;
+                cF = l_cur.cF;
+                vP = l_cur.vP;
+                cP = l_cur.cP;
+            }
+            kahan_node(vF, cF, aF);
+            kahan_node(vP, cP, aP);
+            ((float2*)lout.F)[o] = vF;
+            ((float2*)lout.Fc)[o] = cF;
+            ((float2*)lout.P)[o] = vP;
+            ((float2*)lout.Pc)[o] = cP;
+            if (wi) {
+                const int a = i - s.i_lo, bb = j - s.j_lo;
+                if ((unsigned)a < (unsigned)s.ni && (unsigned)bb < (unsigned)s.nj)
+                    stv<R>(wi, (size_t)bb * s.ni + a, interior ? l_cur.P : Z<R>{0, 0});
+            }
+        }
+        l_cur = l_next;
+        ch_cur = ch_n;
+        muF_part = mfn;
+        muP_part = mpn;
+        aF_part = afn;
+        aP_part = apn;
+    }
 }
 
 // Loss of the built-in |r_ext^3 W|^2: per record, lossrec[k] = r^6 sum_j |W_k[j]|^2 (j
-// ascending) and gbar_k = 2 r^6 W_k.  Records are read from a ring (slot level % cap).
+// ascending) and gbar_k = 2 r^6 W_k.  Records are read from a ring (slot level % cap),
+// gbar_k is written to slot (g0 + k) % gcap of another.
 __global__ void loss_records_kernel(const double2* wave, int64_t cap, int nth, int64_t level0,
-                                    int64_t count, double r6, double* lossrec, double2* gbar) {
+                                    int64_t count, double r6, double* lossrec, double2* gbar,
+                                    int64_t gcap, int64_t g0) {
     int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (k >= count) return;
     const double2* w = wave + (size_t)((level0 + k) % cap) * nth;
+    double2* g = gbar + (size_t)((g0 + k) % gcap) * nth;
     double acc = 0.0;
     for (int j = 0; j < nth; ++j) {
         double2 v = w[j];
         acc += v.x * v.x + v.y * v.y;
-        gbar[(size_t)k * nth + j] = make_double2(2.0 * r6 * v.x, 2.0 * r6 * v.y);
+        g[j] = make_double2(2.0 * r6 * v.x, 2.0 * r6 * v.y);
     }
     lossrec[k] = r6 * acc;
 }
@@ -360,46 +571,84 @@ __global__ void ordered_sum_kernel(const double* v, int64_t n, double* out) {
 
 // ------------------------------------------------------------------ launchers
 
-void launch_adj_corrector(cudaStream_t st, const InstDev& d, const CoLevel& lam, const CoMu& mu) {
-    dim3 g((d.nth + 127) / 128, d.nr - 1);
-    if (d.prec == 0) adj_corrector_kernel<double, double><<<g, 128, 0, st>>>(d, lam, mu);
-    else if (d.prec == 3) adj_corrector_kernel<DF, double><<<g, 128, 0, st>>>(d, lam, mu);
-    else adj_corrector_kernel<float, float><<<g, 128, 0, st>>>(d, lam, mu);
-}
-
-void launch_adj_predictor(cudaStream_t st, const InstDev& d, const CoLevel& lin, const CoMu& mu,
-                          const double2* gbar, const CoLevel& lout) {
-    dim3 g((d.nth + 127) / 128, d.nr);
-    if (d.prec == 0) adj_predictor_kernel<double, double><<<g, 128, 0, st>>>(d, lin, mu, gbar, lout);
-    else if (d.prec == 3) adj_predictor_kernel<DF, double><<<g, 128, 0, st>>>(d, lin, mu, gbar, lout);
-    else adj_predictor_kernel<float, float><<<g, 128, 0, st>>>(d, lin, mu, gbar, lout);
-}
-
 void launch_adj_init(cudaStream_t st, const InstDev& d, const double2* gbar, const CoLevel& out) {
     dim3 g((d.pitch + 127) / 128, d.nr);
     if (d.prec == 0 || d.prec == 3) adj_init_kernel<double><<<g, 128, 0, st>>>(d, gbar, out);
     else adj_init_kernel<float><<<g, 128, 0, st>>>(d, gbar, out);
 }
 
-int adj_source_blocks(const InstDev& d) {
-    const int tot = d.src.nj * (d.src.nh + d.src.ni);
-    const int b = (tot + kSrcThreads - 1) / kSrcThreads;
-    return b < 1 ? 1 : (b > kAdjSourceMaxBlocks ? kAdjSourceMaxBlocks : b);
+// dynamic shared memory of the reverse-step kernels for blocks of `threads` rows
+template <typename R>
+static size_t adj_smem(int threads, bool f32) {
+    return 4 * (size_t)threads * sizeof(Z<R>) + (f32 ? 3 * (size_t)threads * sizeof(float4) : 0);
 }
 
-void launch_adj_source(cudaStream_t st, const InstDev& d, int64_t n, const CoLevel& lam,
-                       const CoMu& mu, double* part, unsigned* done, double* gA, double* gR) {
-    const int nb = adj_source_blocks(d);
+template <class K>
+static int adj_resident(K kernel, int threads, size_t smem) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, smem);
+    return (per > 0 ? per : 1) * (sms > 0 ? sms : 1);
+}
+
+int adj_step_plan(const InstDev& d, int* strip) {
+    const int t = d.pitch;
+    int res;
+    if (d.prec == 0)
+        res = t <= 256 ? adj_resident(adj_step_kernel<double, double, 256>, t, adj_smem<double>(t, false))
+                       : adj_resident(adj_step_kernel<double, double, 1024>, t, adj_smem<double>(t, false));
+    else if (d.prec == 3)
+        res = t <= 256 ? adj_resident(adj_step_kernel<DF, double, 256>, t, adj_smem<double>(t, false))
+                       : adj_resident(adj_step_kernel<DF, double, 1024>, t, adj_smem<double>(t, false));
+    else
+        res = t <= 256 ? adj_resident(adj_step_kernel_f32<256>, t, adj_smem<float>(t, true))
+                       : adj_resident(adj_step_kernel_f32<1024>, t, adj_smem<float>(t, true));
+    int L = (d.nr + res - 1) / res;   // one wave of resident blocks, >= 4 columns each
+    if (L < 4) L = 4;
+    *strip = L;
+    return (d.nr + L - 1) / L;
+}
+
+void launch_adj_step(cudaStream_t st, const InstDev& d, const CoLevel& lin, const double2* gbar,
+                     const CoLevel& lout, int strip, void* wh, void* wi) {
+    const int nb = (d.nr + strip - 1) / strip;
+    const int t = d.pitch;
+    if (d.prec == 0 || d.prec == 3) {
+        const size_t sm = adj_smem<double>(t, false);
+        if (d.prec == 0) {
+            if (t <= 256) adj_step_kernel<double, double, 256><<<nb, t, sm, st>>>(d, lin, gbar, lout, strip, wh, wi);
+            else adj_step_kernel<double, double, 1024><<<nb, t, sm, st>>>(d, lin, gbar, lout, strip, wh, wi);
+        } else {
+            if (t <= 256) adj_step_kernel<DF, double, 256><<<nb, t, sm, st>>>(d, lin, gbar, lout, strip, wh, wi);
+            else adj_step_kernel<DF, double, 1024><<<nb, t, sm, st>>>(d, lin, gbar, lout, strip, wh, wi);
+        }
+    } else {
+        const size_t sm = adj_smem<float>(t, true);
+        if (t <= 256) adj_step_kernel_f32<256><<<nb, t, sm, st>>>(d, lin, gbar, lout, strip, wh, wi);
+        else adj_step_kernel_f32<1024><<<nb, t, sm, st>>>(d, lin, gbar, lout, strip, wh, wi);
+    }
+}
+
+size_t adj_window_bytes(const InstDev& d) {
+    const size_t es = (d.prec == 0 || d.prec == 3) ? sizeof(double2) : sizeof(float2);
+    return ((size_t)d.src.nh + d.src.ni) * d.src.nj * es;
+}
+
+void launch_adj_src_grad(cudaStream_t st, const InstDev& d, int64_t step0, int64_t k0, int64_t count,
+                         int slots, const void* ring, double* gA, double* gR) {
+    if (count <= 0) return;
     if (d.prec == 0 || d.prec == 3)
-        adj_source_kernel<double><<<nb, kSrcThreads, 0, st>>>(d, n, lam, mu, part, done, gA, gR);
-    else adj_source_kernel<float><<<nb, kSrcThreads, 0, st>>>(d, n, lam, mu, part, done, gA, gR);
+        adj_src_grad_kernel<double><<<(unsigned)count, kSrcGradThreads, 0, st>>>(d, step0, k0, slots, ring, gA, gR);
+    else
+        adj_src_grad_kernel<float><<<(unsigned)count, kSrcGradThreads, 0, st>>>(d, step0, k0, slots, ring, gA, gR);
 }
 
 void launch_loss_records(cudaStream_t st, const double2* wave, int64_t cap, int nth,
                          int64_t level0, int64_t count, double r6, double* lossrec,
-                         double2* gbar) {
-    loss_records_kernel<<<(unsigned)((count + 127) / 128), 128, 0, st>>>(wave, cap, nth, level0,
-                                                                        count, r6, lossrec, gbar);
+                         double2* gbar, int64_t gcap, int64_t g0) {
+    loss_records_kernel<<<(unsigned)((count + 127) / 128), 128, 0, st>>>(wave, cap, nth, level0, count, r6,
+                                                                        lossrec, gbar, gcap, g0);
 }
 
 void launch_ordered_sum(cudaStream_t st, const double* v, int64_t n, double* out) {

@@ -334,9 +334,9 @@ teuk_status refresh_partitions(teuk_ctx* c) {
 }
 
 // The 2D coefficient tables [9][n_rstar][pitch] at half and integer nodes, in the
-// instance's precision: read by the FP64 step kernel and by the adjoint.  FP64 instances
-// build them at creation, FP32 instances (whose step kernels form their coefficients
-// from 1D tables) on the first adjoint call.
+// instance's precision: read by the FP64 and double-float step kernels and their adjoint,
+// built at creation.  FP32 instances form their coefficients from 1D tables, forward and
+// adjoint, and have none.
 teuk_status coef_tables(teuk_ctx* c, Instance& I) {
     if (I.coef_h) return TEUK_OK;
     const teuk_params& q = I.p;
@@ -450,7 +450,7 @@ extern "C" teuk_status teuk_create(const teuk_params* p, int n_instances, void* 
         launch_invert_tortoise(c->stream, q.M, q.a, q.rstar_min, I.drs, q.n_rstar, I.off, I.x_int,
                                I.x_half);
         c->launches++;
-        if (q.prec == TEUK_FP64 || q.prec == TEUK_FP64_DF) {  // the FP32 paths build theirs on the first adjoint call
+        if (q.prec == TEUK_FP64 || q.prec == TEUK_FP64_DF) {  // the FP32 paths form theirs from 1D tables
             const teuk_status e = coef_tables(c, I);
             if (e != TEUK_OK) return fail(e);
         } else {
@@ -1534,15 +1534,16 @@ extern "C" teuk_status teuk_adjoint_n(teuk_ctx* c, int instance, int64_t step0, 
                 (long long)I.step, (long long)step0);
     cudaStream_t s = c->stream;
     const int nth = I.p.n_theta;
-    st = coef_tables(c, I);
-    if (st) return st;
+    if (I.p.prec == TEUK_FP64 || I.p.prec == TEUK_FP64_DF) {   // (FP32 instances form theirs)
+        st = coef_tables(c, I);
+        if (st) return st;
+    }
     // co-state planes ([nr][pitch] complex): FP64 for FP64 instances, else FP32 with
     // compensation planes for lam
     const bool co32 = I.p.prec == TEUK_FP32 || I.p.prec == TEUK_FP32_KAHAN;
     const size_t plane = (size_t)I.p.n_rstar * I.pitch * (co32 ? sizeof(float2) : sizeof(double2));
     AdjBuffers B(c, s);
     CoLevel lam[2] = {};
-    CoMu mu = {};
     for (int b = 0; b < 2; ++b) {
         TK_CUDA(c, B.get(&lam[b].F, plane));
         TK_CUDA(c, B.get(&lam[b].P, plane));
@@ -1551,19 +1552,28 @@ extern "C" teuk_status teuk_adjoint_n(teuk_ctx* c, int instance, int64_t step0, 
             TK_CUDA(c, B.get(&lam[b].Pc, plane));
         }
     }
-    TK_CUDA(c, B.get(&mu.F, plane));
-    TK_CUDA(c, B.get(&mu.P, plane));
-    double* src_part = nullptr;
-    unsigned* src_done = nullptr;
-    TK_CUDA(c, B.get((void**)&src_part, sizeof(double) * 8 * kAdjSourceMaxBlocks));
-    TK_CUDA(c, B.get((void**)&src_done, sizeof(unsigned)));
-    TK_CUDA(c, cudaMemsetAsync(src_done, 0, sizeof(unsigned), s));
+    // the fused reverse step's strip; with a source, a ring of window co-states that
+    // adj_src_grad_kernel turns into gradients every `slots` steps (32 MB at most)
+    int adj_strip = 0;
+    adj_step_plan(dev_of(c, I), &adj_strip);
+    const bool src_on = I.src_on;
+    const size_t wbytes = src_on ? adj_window_bytes(dev_of(c, I)) : 0;
+    const int64_t slots = src_on ? std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(n, 256),
+                                                                          (int64_t)((32u << 20) / wbytes)))
+                                 : 0;
+    char* wring = nullptr;
+    if (src_on) TK_CUDA(c, B.get((void**)&wring, wbytes * (size_t)slots));
+    const size_t wh_bytes = (size_t)I.sd.nh * I.sd.nj * (co32 ? sizeof(float2) : sizeof(double2));
     double *gA = nullptr, *gR = nullptr, *lossrec = nullptr, *scal = nullptr;
     double2* gbar = nullptr;
     TK_CUDA(c, B.get((void**)&gA, sizeof(double) * n));
     TK_CUDA(c, B.get((void**)&gR, sizeof(double) * n));
     TK_CUDA(c, B.get((void**)&scal, sizeof(double) * 3));
-    TK_CUDA(c, B.get((void**)&gbar, sizeof(double2) * nth * (size_t)n));
+    // record cotangents: all n, or (checkpointed built-in loss) a ring of one segment's
+    const int64_t Kc = (builtin && ckpt_every > 0) ? std::min<int64_t>(ckpt_every, n) : n;
+    const int64_t gcap = (builtin && ckpt_every > 0) ? Kc + 1 : n;
+    TK_CUDA(c, B.get((void**)&gbar, sizeof(double2) * nth * (size_t)gcap));
+    auto gslot = [&](int64_t idx) { return gbar + (size_t)(idx % gcap) * nth; };
     TK_CUDA(c, cudaMemsetAsync(gA, 0, sizeof(double) * n, s));
     TK_CUDA(c, cudaMemsetAsync(gR, 0, sizeof(double) * n, s));
     TK_CUDA(c, cudaMemsetAsync(scal, 0, sizeof(double) * 3, s));
@@ -1585,7 +1595,7 @@ extern "C" teuk_status teuk_adjoint_n(teuk_ctx* c, int instance, int64_t step0, 
     };
     const int strip = eff_strip(c, I);
     // the segment plan: segments [a_k, a_k + len_k) of the steps step0 .. step0+n-1
-    int64_t K = (builtin && ckpt_every > 0) ? ckpt_every : n;
+    const int64_t K = Kc;
     int64_t nseg = (n + K - 1) / K;
     void* ckpt = nullptr;
     void* scratch_state[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
@@ -1619,7 +1629,7 @@ extern "C" teuk_status teuk_adjoint_n(teuk_ctx* c, int instance, int64_t step0, 
             I.step = a + len;
             if (!ckpt) {  // one segment holds everything: take the loss now
                 launch_loss_records(s, segrec, K + 1, nth, a + 1, len, r6, lossrec + (a - step0),
-                                    gbar + (size_t)(a - step0) * nth);
+                                    gbar, gcap, a - step0);
                 c->launches++;
             }
         }
@@ -1651,24 +1661,24 @@ extern "C" teuk_status teuk_adjoint_n(teuk_ctx* c, int instance, int64_t step0, 
             // previous segment is recomputed; writing it twice stores the same value
             int64_t lo = a > step0 ? a : a + 1;
             launch_loss_records(s, segrec, K + 1, nth, lo, a + len - lo + 1, r6,
-                                lossrec + (lo - step0 - 1), gbar + (size_t)(lo - step0 - 1) * nth);
+                                lossrec + (lo - step0 - 1), gbar, gcap, lo - step0 - 1);
             c->launches++;
         }
         for (int64_t m = a + len - 1; m >= a; --m) {
             const int64_t k = m - step0;  // step index within the call
             if (!started) {
-                launch_adj_init(s, d, gbar + (size_t)(n - 1) * nth, lam[cur]);
+                launch_adj_init(s, d, gslot(n - 1), lam[cur]);
                 c->launches++;
                 started = true;
             }
-            launch_adj_corrector(s, d, lam[cur], mu);
-            c->launches++;
-            if (I.src_on) {
-                launch_adj_source(s, d, m, lam[cur], mu, src_part, src_done, gA + k, gR + k);
+            const double2* gb = k >= 1 ? gslot(k - 1) : nullptr;
+            char* slot = src_on ? wring + (size_t)(k % slots) * wbytes : nullptr;
+            launch_adj_step(s, d, lam[cur], gb, lam[1 - cur], adj_strip, slot, slot ? slot + wh_bytes : nullptr);
+            if (src_on && k % slots == 0) {   // the steps k .. k + slots - 1 are all stored
+                launch_adj_src_grad(s, d, step0, k, std::min<int64_t>(n - 1, k + slots - 1) - k + 1,
+                                    (int)slots, wring, gA, gR);
                 c->launches++;
             }
-            const double2* gb = k >= 1 ? gbar + (size_t)(k - 1) * nth : nullptr;
-            launch_adj_predictor(s, d, lam[cur], mu, gb, lam[1 - cur]);
             c->launches++;
             cur = 1 - cur;
         }

@@ -204,23 +204,28 @@ void launch_wave_sum(cudaStream_t st, const double2* wave, int64_t cap, int nth,
 // teuk_adjoint.cu
 // Co-state of one time level (teuk_adjoint.cu): F and P planes ([nr][pitch] complex,
 // double2 for FP64 instances, float2 otherwise) and, for FP32, their compensation
-// planes (float2; the value is v - c).  mu: the half-node cotangents (same type, no
-// compensation).
+// planes (float2; the value is v - c).
 struct CoLevel { void* F; void* P; void* Fc; void* Pc; };
-struct CoMu { void* F; void* P; };
-void launch_adj_corrector(cudaStream_t st, const InstDev& d, const CoLevel& lam, const CoMu& mu);
-void launch_adj_predictor(cudaStream_t st, const InstDev& d, const CoLevel& lin, const CoMu& mu,
-                          const double2* gbar, const CoLevel& lout);
+// lam = E^T gbar: the co-state that starts the reverse sweep
 void launch_adj_init(cudaStream_t st, const InstDev& d, const double2* gbar, const CoLevel& out);
-// source gradients of one step: part holds 8 doubles per block (at most
-// kAdjSourceMaxBlocks blocks), done one zero-initialised counter (left zero)
-constexpr int kAdjSourceMaxBlocks = 64;
-int adj_source_blocks(const InstDev& d);
-void launch_adj_source(cudaStream_t st, const InstDev& d, int64_t n, const CoLevel& lam,
-                       const CoMu& mu, double* part, unsigned* done, double* gA, double* gR);
+// the fused reverse step (lam^n from lam^{n+1}): strip length and block count from
+// adj_step_plan; wh, wi (null without a source): the step's ring slot of the window
+// co-states, mu_Pi at the half-node window ([nj][nh]) and lam'_Pi at the integer-node
+// window ([nj][ni]), complex in the co-state's type
+int adj_step_plan(const InstDev& d, int* strip);
+void launch_adj_step(cudaStream_t st, const InstDev& d, const CoLevel& lin, const double2* gbar,
+                     const CoLevel& lout, int strip, void* wh, void* wi);
+// bytes of one ring slot (the half-node window, then the integer-node window)
+size_t adj_window_bytes(const InstDev& d);
+// source gradients gA[k], gR[k] of the steps k0 .. k0 + count - 1 of a sweep starting at
+// step0, from ring slots k % slots
+void launch_adj_src_grad(cudaStream_t st, const InstDev& d, int64_t step0, int64_t k0, int64_t count,
+                         int slots, const void* ring, double* gA, double* gR);
+// built-in loss of records level0 .. level0 + count - 1 (ring wave of cap slots):
+// lossrec[0 .. count), their cotangents into slots (g0 + k) % gcap of gbar
 void launch_loss_records(cudaStream_t st, const double2* wave, int64_t cap, int nth,
                          int64_t level0, int64_t count, double r6, double* lossrec,
-                         double2* gbar);
+                         double2* gbar, int64_t gcap, int64_t g0);
 void launch_ordered_sum(cudaStream_t st, const double* v, int64_t n, double* out);
 
 }  // namespace teuk
