@@ -46,7 +46,8 @@ typedef enum {
     TEUK_ECUDA = 3,     /* CUDA runtime error (no device, launch failure, ...) */
     TEUK_EUNSTABLE = 4, /* non-finite values found in the state or waveform */
     TEUK_ETIMEOUT = 5,  /* a bounded device-side wait gave up */
-    TEUK_ESTATE = 6     /* call not valid in the context's current state */
+    TEUK_ESTATE = 6,    /* call not valid in the context's current state */
+    TEUK_EBOUNDS = 7    /* checked builds: a device-side index check failed */
 } teuk_status;
 
 typedef enum {
@@ -237,7 +238,8 @@ teuk_status teuk_adjoint_n(teuk_ctx* ctx, int instance, int64_t step0, int64_t n
 
 /* Wait for queued work, read the device status word and check the state of
  * every instance for non-finite values (TEUK_EUNSTABLE); a bounded device wait
- * that gave up is TEUK_ETIMEOUT.  The status word is cleared once reported. */
+ * that gave up is TEUK_ETIMEOUT; in a checked build, an index that failed its bounds
+ * check is TEUK_EBOUNDS.  The status word is cleared once reported. */
 teuk_status teuk_sync(teuk_ctx* ctx);
 
 /* Halo exchange of slab instances (teuk_params.slab_ncols > 0), one column of the current
@@ -321,6 +323,21 @@ teuk_status teuk_set_fault_injection(teuk_ctx* ctx, int64_t skip_release_item,
  * launches of the context return at once until the status has been read, and the state
  * is undefined until teuk_set_state.  column < 0 clears it. */
 teuk_status teuk_set_fill_fault(teuk_ctx* ctx, int instance, int column);
+
+/* Checked builds.  The library also builds as libteuk_check.so with TEUK_CHECK defined:
+ * before each global-memory access of the time loop's kernels (state planes, TMA column
+ * fills, coefficient tables, exchange buffers, co-state planes, waveform ring) the index
+ * is tested against the extent of its buffer; a failure sets a bit of the device status
+ * word and the access is skipped (a load gives zero), so nothing traps, and the next
+ * teuk_sync returns TEUK_EBOUNDS.  (A skipped ring fill leaves its waiters to give up
+ * after their bounded wait.)  No counterpart in the paper: a debugging aid standing in
+ * for a device sanitizer.
+ * teuk_checked_build: 1 in a checked build, 0 otherwise.
+ * teuk_check_selftest: checked builds only (else TEUK_EINVAL): queues one kernel that
+ * submits the index one past the end of instance 0's state plane to the bounds check,
+ * without addressing it, so that the next teuk_sync returns TEUK_EBOUNDS. */
+int teuk_checked_build(void);
+teuk_status teuk_check_selftest(teuk_ctx* ctx);
 
 /* Number of kernels the library launched on this context since creation. */
 int64_t teuk_kernel_launches(const teuk_ctx* ctx);

@@ -9,13 +9,15 @@ import re
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
-LIB_PATH = os.path.join(HERE, "libteuk.so")
+# TEUK_LIB_VARIANT=check loads the checked build (device-side index checks, TEUK_EBOUNDS)
+LIB_PATH = os.path.join(HERE, "libteuk_check.so" if os.environ.get("TEUK_LIB_VARIANT") == "check"
+                        else "libteuk.so")
 HEADER = os.path.join(ROOT, "include", "teuk.h")
 
-TEUK_OK, TEUK_EINVAL, TEUK_ENOMEM, TEUK_ECUDA, TEUK_EUNSTABLE, TEUK_ETIMEOUT, TEUK_ESTATE = range(7)
+TEUK_OK, TEUK_EINVAL, TEUK_ENOMEM, TEUK_ECUDA, TEUK_EUNSTABLE, TEUK_ETIMEOUT, TEUK_ESTATE, TEUK_EBOUNDS = range(8)
 TEUK_FP64, TEUK_FP32, TEUK_FP32_KAHAN, TEUK_FP64_DF = 0, 1, 2, 3
 STATUS_NAMES = {0: "TEUK_OK", 1: "TEUK_EINVAL", 2: "TEUK_ENOMEM", 3: "TEUK_ECUDA",
-                4: "TEUK_EUNSTABLE", 5: "TEUK_ETIMEOUT", 6: "TEUK_ESTATE"}
+                4: "TEUK_EUNSTABLE", 5: "TEUK_ETIMEOUT", 6: "TEUK_ESTATE", 7: "TEUK_EBOUNDS"}
 
 
 class teuk_params(ctypes.Structure):
@@ -55,6 +57,8 @@ _PROTOS = {
     "teuk_extract": (_I, [_P, _I, _P, _P, _L, ctypes.POINTER(_L), ctypes.POINTER(_L)]),
     "teuk_adjoint_n": (_I, [_P, _I, _L, _L, _L, _P, _P, _P, _P]),
     "teuk_sync": (_I, [_P]),
+    "teuk_checked_build": (_I, []),
+    "teuk_check_selftest": (_I, [_P]),
     "teuk_get_time": (_I, [_P, _I, ctypes.POINTER(_L), ctypes.POINTER(_D)]),
     "teuk_set_tiling": (_I, [_P, _I, _I]),
     "teuk_set_resident": (_I, [_P, _I]),
@@ -89,7 +93,8 @@ def load():
     global _lib
     if _lib is None:
         if not os.path.exists(LIB_PATH):
-            raise ImportError("libteuk.so not built; run paper_1001_3631_gb300.build.build()")
+            raise ImportError("%s not built; run paper_1001_3631_gb300.build.build()"
+                              % os.path.basename(LIB_PATH))
         lib = ctypes.CDLL(LIB_PATH)
         for name, (res, args) in _PROTOS.items():
             if not hasattr(lib, name):

@@ -349,11 +349,13 @@ __global__ void __launch_bounds__(kMaxT) adj_step_kernel(InstDev d, CoLevel lin,
                 }
                 kahan_node(vF, cF, aF);
                 kahan_node(vP, cP, aP);
-                ((float2*)lout.F)[o] = vF;
-                ((float2*)lout.Fc)[o] = cF;
-                ((float2*)lout.P)[o] = vP;
-                ((float2*)lout.Pc)[o] = cP;
-            } else {
+                if (TK_IN(d.status, o, pl)) {
+                    ((float2*)lout.F)[o] = vF;
+                    ((float2*)lout.Fc)[o] = cF;
+                    ((float2*)lout.P)[o] = vP;
+                    ((float2*)lout.Pc)[o] = cP;
+                }
+            } else if (TK_IN(d.status, o, pl)) {
                 stv<R>(lout.F, o, aF);
                 stv<R>(lout.P, o, aP);
             }
@@ -523,10 +525,12 @@ __global__ void __launch_bounds__(kMaxT) adj_step_kernel_f32(InstDev d, CoLevel 
             }
             kahan_node(vF, cF, aF);
             kahan_node(vP, cP, aP);
-            ((float2*)lout.F)[o] = vF;
-            ((float2*)lout.Fc)[o] = cF;
-            ((float2*)lout.P)[o] = vP;
-            ((float2*)lout.Pc)[o] = cP;
+            if (TK_IN(d.status, o, plane_elems(d))) {
+                ((float2*)lout.F)[o] = vF;
+                ((float2*)lout.Fc)[o] = cF;
+                ((float2*)lout.P)[o] = vP;
+                ((float2*)lout.Pc)[o] = cP;
+            }
             if (wi) {
                 const int a = i - s.i_lo, bb = j - s.j_lo;
                 if ((unsigned)a < (unsigned)s.ni && (unsigned)bb < (unsigned)s.nj)

@@ -1058,6 +1058,23 @@ extern "C" teuk_status teuk_mode_sum(teuk_ctx* c, const double* phi, int n_phi, 
     return TEUK_OK;
 }
 
+extern "C" int teuk_checked_build(void) {
+#ifdef TEUK_CHECK
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+extern "C" teuk_status teuk_check_selftest(teuk_ctx* c) {
+    if (!c) return TEUK_EINVAL;
+    if (!teuk_checked_build()) TK_FAIL(c, TEUK_EINVAL, "not a checked build (libteuk_check.so)");
+    launch_check_selftest(c->stream, dev_of(c, c->inst[0]));
+    c->launches++;
+    TK_CUDA(c, cudaGetLastError());
+    return TEUK_OK;
+}
+
 extern "C" teuk_status teuk_sync(teuk_ctx* c) {
     if (!c) return TEUK_EINVAL;
     for (Instance& I : c->inst) {
@@ -1071,7 +1088,7 @@ extern "C" teuk_status teuk_sync(teuk_ctx* c) {
     TK_CUDA(c, cudaStreamSynchronize(c->stream));
     if (h & ST_TIMEOUT) TK_FAIL(c, TEUK_ETIMEOUT, "a bounded device wait gave up");
     if (h & ST_NONFINITE) TK_FAIL(c, TEUK_EUNSTABLE, "non-finite values in the state or waveform");
-    if (h & ST_BOUNDS) TK_FAIL(c, TEUK_ECUDA, "device-side bounds check failed");
+    if (h & ST_BOUNDS) TK_FAIL(c, TEUK_EBOUNDS, "a device-side index check failed (checked build)");
     return TEUK_OK;
 }
 

@@ -153,4 +153,17 @@ void launch_mode_sum(cudaStream_t st, const ModeRing* modes, int n_modes, int nt
                                                       n_rec, r3, shift, out);
 }
 
+// (checked builds) the bounds check of an index one past the end of the state plane; the
+// index is only tested, never addressed
+__global__ void check_selftest_kernel(InstDev d) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        const bool in = TK_IN(d.status, plane_elems(d), plane_elems(d));
+        (void)in;
+    }
+}
+
+void launch_check_selftest(cudaStream_t st, const InstDev& d) {
+    check_selftest_kernel<<<1, 32, 0, st>>>(d);
+}
+
 }  // namespace teuk

@@ -22,4 +22,9 @@ void launch_mode_sum(cudaStream_t st, const ModeRing* modes, int n_modes, int nt
                      const double* phi, int n_phi, int64_t first, int64_t n_rec, double r3,
                      double shift, double2* out);
 
+struct InstDev;
+// Checked builds: submit the index one past the end of d's state plane to the bounds
+// check (no access), setting the status word's bounds bit.
+void launch_check_selftest(cudaStream_t st, const InstDev& d);
+
 }  // namespace teuk

@@ -104,6 +104,21 @@ struct InstDev {
 
 enum StatusBits : unsigned int { ST_NONFINITE = 1u, ST_TIMEOUT = 2u, ST_BOUNDS = 4u };
 
+// Checked builds (-DTEUK_CHECK, libteuk_check.so): TK_IN(status, i, n) tests an index
+// against the extent of the buffer it is about to address; a failure sets ST_BOUNDS in
+// the status word and the caller skips the access (a load gives zero), so nothing traps
+// and teuk_sync reports TEUK_EBOUNDS.  Release builds compile every check to `true`.
+#ifdef TEUK_CHECK
+__device__ __forceinline__ bool check_index(unsigned int* status, long long i, long long n) {
+    if (i >= 0 && i < n) return true;
+    atomicOr(status, (unsigned)ST_BOUNDS);
+    return false;
+}
+#define TK_IN(status, i, n) ::teuk::check_index((status), (long long)(i), (long long)(n))
+#else
+#define TK_IN(status, i, n) true
+#endif
+
 // Batched persistent launch over many instances of one block-size class (teuk_step.cu).
 // Work items are (relative step s, instance k, r* strip) in that order of priority;
 // items of one step are numbered instance by instance from item_base[k].

@@ -122,8 +122,11 @@ __global__ void __launch_bounds__(kResMaxThreads, 1) resident_kernel(ResidentArg
     T* X = (T*)(sm + L::s_bytes(ncol, pitch) + L::hr_bytes(ncol, pitch));
     T* CF = (T*)(sm + L::s_bytes(ncol, pitch) + L::hr_bytes(ncol, pitch) + L::x_bytes(ncol, pitch));
     auto sidx = [&](int q, int jj) { return (size_t)q * pitch + jj; };
-    // raw 16-byte node copies between global planes and the shared planes
-    auto copy_in = [&](const unsigned char* const* src_planes, size_t src_node, size_t dst_node, bool bypass) {
+    // raw 16-byte node copies between global planes (glim nodes a plane) and the shared
+    // planes
+    auto copy_in = [&](const unsigned char* const* src_planes, size_t src_node, size_t dst_node, bool bypass,
+                       size_t glim) {
+        if (!TK_IN(d.status, src_node, glim) || !TK_IN(d.status, dst_node, (size_t)ncol * pitch)) return;
 #pragma unroll
         for (int p = 0; p < P::planes; ++p) {
             const float4* s = (const float4*)src_planes[p] + src_node;
@@ -131,7 +134,8 @@ __global__ void __launch_bounds__(kResMaxThreads, 1) resident_kernel(ResidentArg
             *dd = bypass ? __ldcg(s) : *s;
         }
     };
-    auto copy_out = [&](unsigned char* const* dst_planes, size_t src_node, size_t dst_node) {
+    auto copy_out = [&](unsigned char* const* dst_planes, size_t src_node, size_t dst_node, size_t glim) {
+        if (!TK_IN(d.status, dst_node, glim) || !TK_IN(d.status, src_node, (size_t)ncol * pitch)) return;
 #pragma unroll
         for (int p = 0; p < P::planes; ++p) {
             const float4* s = (const float4*)(sm + (size_t)p * ncol * pitch * 16) + src_node;
@@ -146,7 +150,7 @@ __global__ void __launch_bounds__(kResMaxThreads, 1) resident_kernel(ResidentArg
                                       (const unsigned char*)d.buf[r.bin][P::planes - 1]};
         for (int idx = t; idx < ncol * pitch; idx += blockDim.x) {
             const int q = idx / pitch, jj = idx % pitch, cc = c0 - h + q;
-            if (cc >= 0 && cc <= nr - 1) copy_in(in, (size_t)cc * pitch + jj, sidx(q, jj), false);
+            if (cc >= 0 && cc <= nr - 1) copy_in(in, (size_t)cc * pitch + jj, sidx(q, jj), false, plane_elems(d));
         }
     }
     RowTab<P> rt;
@@ -193,7 +197,8 @@ __global__ void __launch_bounds__(kResMaxThreads, 1) resident_kernel(ResidentArg
         if (!ex_blk || !row_ok || t >= pitch) return;
         const double2 a = S.load(sidx(qe, j)).phi64(), c = S.load(sidx(qe + 1, j)).phi64();
         const double2 w = wave_lerp(a, c, d.f_e);
-        d.wave[(size_t)(level % d.wave_cap) * nth + j] = w;
+        const size_t wi = (size_t)(level % d.wave_cap) * nth + j;
+        if (TK_IN(d.status, wi, d.wave_cap * nth)) d.wave[wi] = w;
         if (!isfinite(w.x) || !isfinite(w.y)) atomicOr(d.status, (unsigned)ST_NONFINITE);
     };
     // exchange slots: plane p, slot, block, side (0: first h owned, 1: last h owned)
@@ -335,7 +340,7 @@ __global__ void __launch_bounds__(kResMaxThreads, 1) resident_kernel(ResidentArg
         for (int idx = t; idx < 2 * h * pitch; idx += blockDim.x) {
             const int side = idx / (h * pitch), rem = idx % (h * pitch), qq = rem / pitch, jj = rem % pitch;
             const int q = side == 0 ? h + qq : ncol - 2 * h + qq;
-            copy_out(xp, sidx(q, jj), xnode(slot, b, side, qq, jj));
+            copy_out(xp, sidx(q, jj), xnode(slot, b, side, qq, jj), xplane);
         }
         __syncthreads();
         if (t == 0 && b != r.skip_publish) res_st_release(r.flags + (size_t)b * kResFlagStride, exch + 1);
@@ -350,7 +355,7 @@ __global__ void __launch_bounds__(kResMaxThreads, 1) resident_kernel(ResidentArg
             const int nbk = side == 0 ? b - 1 : b + 1;
             const int q = side == 0 ? qq : ncol - h + qq;
             const unsigned char* src[2] = {xp[0], xp[1]};
-            copy_in(src, xnode(slot, nbk, 1 - side, qq, jj), sidx(q, jj), true);
+            copy_in(src, xnode(slot, nbk, 1 - side, qq, jj), sidx(q, jj), true, xplane);
         }
         __syncthreads();
     }
@@ -362,7 +367,7 @@ __global__ void __launch_bounds__(kResMaxThreads, 1) resident_kernel(ResidentArg
     const int qlo = b == 0 ? h - 1 : h, qhi = (b == r.nb - 1) ? ncol - h + 1 : ncol - h;
     for (int idx = t; idx < (qhi - qlo) * pitch; idx += blockDim.x) {
         const int q = qlo + idx / pitch, jj = idx % pitch, cc = c0 - h + q;
-        copy_out(out, sidx(q, jj), (size_t)cc * pitch + jj);
+        copy_out(out, sidx(q, jj), (size_t)cc * pitch + jj, plane_elems(d));
     }
 }
 

@@ -135,6 +135,7 @@ struct ColumnRing {
     // they would otherwise come from DRAM, evicted by the state streaming through L2).
     __device__ __forceinline__ void fill(const InstDev& d, int bin, int col, int s) const {
         if (col == d.fault_col) return;   // testing aid: the slot's phase never completes
+        if (!TK_IN(d.status, col, d.nr)) return;   // (checked builds; the waiters time out)
         if (d.src.on) {
             const SourceDev& w = d.src;
             const unsigned cb = (unsigned)w.q_stride * (unsigned)sizeof(typename V2T<typename P::T>::V);
@@ -344,9 +345,9 @@ __device__ __forceinline__ bool strip_step(const InstDev& d, int64_t step, int b
                 cfi[k] = cf2[k].y;
             }
         } else if constexpr (P::kind == kDF) {
-            coefs_df(d, true, col, j, (DF*)cfh);
+            if (TK_IN(d.status, col, d.nr)) coefs_df(d, true, col, j, (DF*)cfh);
         } else {
-            coefs64(d, true, col, j, (double*)cfh);
+            if (TK_IN(d.status, col, d.nr)) coefs64(d, true, col, j, (double*)cfh);
         }
     };
     // corrector at column cc from the half nodes L = cc-1/2 and R = cc+1/2; xb is the
@@ -367,13 +368,13 @@ __device__ __forceinline__ bool strip_step(const InstDev& d, int64_t step, int b
 #pragma unroll
             for (int k = 0; k < kNCoef; ++k) cf[k] = cfi[k];
         } else if constexpr (P::kind == kDF) {
-            coefs_df(d, false, cc, j, (DF*)cf);
+            if (TK_IN(d.status, cc, d.nr)) coefs_df(d, false, cc, j, (DF*)cf);
         } else {
-            coefs64(d, false, cc, j, (double*)cf);
+            if (TK_IN(d.status, cc, d.nr)) coefs64(d, false, cc, j, (double*)cf);
         }
         C dPhi, dPi;
         corrector_incr<P, kSplit>(row, Hs_p, Hs_m, DpS_m, cf, fdt, srcc, dPhi, dPi);
-        if (row_ok) {
+        if (row_ok && TK_IN(d.status, o, plane_elems(d))) {
             NodeV<P> u = uc;
             u.update(dPhi, dPi);
             out.store(o, u);
@@ -385,7 +386,8 @@ __device__ __forceinline__ bool strip_step(const InstDev& d, int64_t step, int b
         double2 a = ul.phi64(), b = ur.phi64();
         double f = d.f_e;
         double2 w = wave_lerp(a, b, f);
-        d.wave[(size_t)(step % d.wave_cap) * nth + j] = w;
+        const size_t wi = (size_t)(step % d.wave_cap) * nth + j;
+        if (TK_IN(d.status, wi, d.wave_cap * nth)) d.wave[wi] = w;
         if (!isfinite(w.x) || !isfinite(w.y)) atomicOr(d.status, (unsigned)ST_NONFINITE);
     };
 
@@ -534,12 +536,14 @@ template <class P>
 __global__ void extract_kernel(InstDev d, int64_t step, int bin) {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= d.nth) return;
+    if (!TK_IN(d.status, d.i_e + 1, d.nr) || !TK_IN(d.status, d.i_e, d.nr)) return;
     const Planes<P> in = Planes<P>::of(d, bin);
     double2 a = in.load(node_index(d, d.i_e, j)).phi64();
     double2 b = in.load(node_index(d, d.i_e + 1, j)).phi64();
     double f = d.f_e;
     double2 w = wave_lerp(a, b, f);
-    d.wave[(size_t)(step % d.wave_cap) * d.nth + j] = w;
+    const size_t wi = (size_t)(step % d.wave_cap) * d.nth + j;
+    if (TK_IN(d.status, wi, d.wave_cap * d.nth)) d.wave[wi] = w;
     if (!isfinite(w.x) || !isfinite(w.y)) atomicOr(d.status, (unsigned)ST_NONFINITE);
 }
 
@@ -611,8 +615,10 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) batched_step_kernel(B
         }
         const int k = lo;
         const int st = (int)(r - b.item_base[k]);
+        if (!TK_IN(b.status, k, b.n_inst) || !TK_IN(b.status, r, b.items_per_step)) return;
         const InstDev& d = b.inst[k];
         const int strip = b.strip[k], nstrip = b.nstrip[k];
+        if (!TK_IN(b.status, st, nstrip)) return;
         int* fl = b.flags + b.item_base[k];
         if (s > 0 && !wait_neighbours(b, fl, nstrip, st, s, &flag)) {
             if (threadIdx.x == 0) {
@@ -635,9 +641,11 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) batched_step_kernel(B
 template <class P>
 __global__ void batched_extract_kernel(BatchDev b) {
     const int k = blockIdx.y;
+    if (!TK_IN(b.status, k, b.n_inst)) return;
     const InstDev& d = b.inst[k];
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= d.nth) return;
+    if (!TK_IN(d.status, d.i_e + 1, d.nr) || !TK_IN(d.status, d.i_e, d.nr)) return;
     const int64_t n = *b.n_steps;
     const int bin = (int)((b.base_bin[k] + n) & 1);
     const int64_t step = b.base_step[k] + n;
@@ -646,7 +654,8 @@ __global__ void batched_extract_kernel(BatchDev b) {
     double2 c = in.load(node_index(d, d.i_e + 1, j)).phi64();
     double f = d.f_e;
     double2 w = wave_lerp(a, c, f);
-    d.wave[(size_t)(step % d.wave_cap) * d.nth + j] = w;
+    const size_t wi = (size_t)(step % d.wave_cap) * d.nth + j;
+    if (TK_IN(d.status, wi, d.wave_cap * d.nth)) d.wave[wi] = w;
     if (!isfinite(w.x) || !isfinite(w.y)) atomicOr(d.status, (unsigned)ST_NONFINITE);
 }
 

@@ -210,6 +210,10 @@ class TeukSolver:
     def sync(self):
         check(_lib.load().teuk_sync(self.ctx), self.ctx)
 
+    def check_selftest(self):
+        """Checked builds: make the next sync report TEUK_EBOUNDS (no memory is addressed)."""
+        check(_lib.load().teuk_check_selftest(self.ctx), self.ctx)
+
     def time(self, instance=0):
         s, dt = ctypes.c_int64(0), ctypes.c_double(0.0)
         check(_lib.load().teuk_get_time(self.ctx, instance, ctypes.byref(s), ctypes.byref(dt)),

@@ -29,6 +29,12 @@ def test_exports_every_declared_function(lib):
                          text=True).stdout
     for n in names:
         assert (" T " + n) in out, n
+    # the checked build exports the same functions
+    chk = os.path.join(os.path.dirname(_lib.LIB_PATH), "libteuk_check.so")
+    out = subprocess.run(["nm", "-D", "--defined-only", chk], capture_output=True, text=True).stdout
+    for n in names:
+        assert (" T " + n) in out, n
+    assert lib.teuk_checked_build() == 0 and ctypes.CDLL(chk).teuk_checked_build() == 1
 
 
 def test_struct_layout_matches_header(tmp_path):
