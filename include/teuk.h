@@ -183,6 +183,20 @@ teuk_status teuk_set_state(teuk_ctx* ctx, int instance, const double* host_u, in
  * buffer described at teuk_set_state).  Synchronizes. */
 teuk_status teuk_get_state(teuk_ctx* ctx, int instance, double* host_u);
 
+/* Checkpoint and resume of one instance (no counterpart in the paper: long runs are
+ * stopped and resumed).  The file holds the instance's parameters, its time level and
+ * the planes of its current level in the library's own layout (the Kahan compensation
+ * and the double-float low parts as stored), in one file.
+ * teuk_save_state: writes path (created or truncated); synchronizes.
+ * teuk_load_state: reads path into the instance.  The saved parameters must equal the
+ * instance's (all of teuk_params but wave_capacity), else TEUK_EINVAL and nothing is
+ * changed.  Sets the time level to the saved one and clears the waveform records, as
+ * teuk_set_state does; with the same source and launch form the steps that follow are
+ * bit for bit those that follow the save.  Synchronizes.
+ * File errors (cannot open, short read or write, not a saved state): TEUK_EINVAL. */
+teuk_status teuk_save_state(teuk_ctx* ctx, int instance, const char* path);
+teuk_status teuk_load_state(teuk_ctx* ctx, int instance, const char* path);
+
 /* Advance every instance by n full Lax-Wendroff steps (Eqs. 13-14), recording the
  * waveform at every time level.  Asynchronous on the context's stream. */
 teuk_status teuk_step_n(teuk_ctx* ctx, int64_t n);

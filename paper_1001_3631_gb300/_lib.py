@@ -58,6 +58,8 @@ _PROTOS = {
     "teuk_adjoint_n": (_I, [_P, _I, _L, _L, _L, _P, _P, _P, _P]),
     "teuk_sync": (_I, [_P]),
     "teuk_checked_build": (_I, []),
+    "teuk_save_state": (_I, [_P, _I, ctypes.c_char_p]),
+    "teuk_load_state": (_I, [_P, _I, ctypes.c_char_p]),
     "teuk_check_selftest": (_I, [_P]),
     "teuk_get_time": (_I, [_P, _I, ctypes.POINTER(_L), ctypes.POINTER(_D)]),
     "teuk_set_tiling": (_I, [_P, _I, _I]),

@@ -690,6 +690,95 @@ extern "C" teuk_status teuk_get_state(teuk_ctx* c, int instance, double* host_u)
     return TEUK_OK;
 }
 
+// ------------------------------------------------------------------ checkpoint / resume
+// File: 8-byte magic, then the fields below (host byte order), then the planes of the
+// current level, each plane_bytes long, in the library's own layout.
+
+namespace {
+
+constexpr char kStateMagic[8] = {'T', 'E', 'U', 'K', 'S', 'T', '0', '1'};
+
+struct StateFileHeader {
+    int32_t s, m, n_rstar, n_theta, dt_rule, prec, slab_col0, slab_ncols;
+    double M, a, rstar_min, rstar_max, courant, dt, rstar_ext;
+    int64_t step;
+    uint64_t plane_bytes;
+    int32_t nplanes, pad;
+};
+
+StateFileHeader header_of(const Instance& I) {
+    const teuk_params& q = I.p;
+    StateFileHeader h{};
+    h.s = q.s; h.m = q.m; h.n_rstar = q.n_rstar; h.n_theta = q.n_theta; h.dt_rule = q.dt_rule;
+    h.prec = q.prec; h.slab_col0 = q.slab_col0; h.slab_ncols = q.slab_ncols;
+    h.M = q.M; h.a = q.a; h.rstar_min = q.rstar_min; h.rstar_max = q.rstar_max;
+    h.courant = q.courant; h.dt = q.dt; h.rstar_ext = q.rstar_ext;
+    h.step = I.step;
+    h.plane_bytes = I.plane_bytes;
+    h.nplanes = I.p.prec == TEUK_FP32 ? 1 : 2;
+    return h;
+}
+
+// the saved problem is this instance's: every parameter but the waveform capacity
+bool same_problem(const StateFileHeader& a, const StateFileHeader& b) {
+    return a.s == b.s && a.m == b.m && a.n_rstar == b.n_rstar && a.n_theta == b.n_theta &&
+           a.dt_rule == b.dt_rule && a.prec == b.prec && a.slab_col0 == b.slab_col0 &&
+           a.slab_ncols == b.slab_ncols && a.M == b.M && a.a == b.a && a.rstar_min == b.rstar_min &&
+           a.rstar_max == b.rstar_max && a.courant == b.courant && a.dt == b.dt &&
+           a.rstar_ext == b.rstar_ext && a.plane_bytes == b.plane_bytes && a.nplanes == b.nplanes;
+}
+
+}  // namespace
+
+extern "C" teuk_status teuk_save_state(teuk_ctx* c, int instance, const char* path) {
+    teuk_status st = check_instance(c, instance);
+    if (st) return st;
+    if (!path) TK_FAIL(c, TEUK_EINVAL, "path is NULL");
+    Instance& I = c->inst[instance];
+    const StateFileHeader h = header_of(I);
+    std::vector<char> buf((size_t)h.nplanes * I.plane_bytes);
+    for (int k = 0; k < h.nplanes; ++k)
+        TK_CUDA(c, cudaMemcpyAsync(buf.data() + (size_t)k * I.plane_bytes, I.state[I.cur][k], I.plane_bytes,
+                                   cudaMemcpyDeviceToHost, c->stream));
+    TK_CUDA(c, cudaStreamSynchronize(c->stream));
+    FILE* f = std::fopen(path, "wb");
+    if (!f) TK_FAIL(c, TEUK_EINVAL, "cannot open %s for writing", path);
+    const bool ok = std::fwrite(kStateMagic, 1, 8, f) == 8 && std::fwrite(&h, sizeof h, 1, f) == 1 &&
+                    std::fwrite(buf.data(), 1, buf.size(), f) == buf.size();
+    const bool closed = std::fclose(f) == 0;
+    if (!ok || !closed) TK_FAIL(c, TEUK_EINVAL, "writing %s failed", path);
+    return TEUK_OK;
+}
+
+extern "C" teuk_status teuk_load_state(teuk_ctx* c, int instance, const char* path) {
+    teuk_status st = check_instance(c, instance);
+    if (st) return st;
+    if (!path) TK_FAIL(c, TEUK_EINVAL, "path is NULL");
+    Instance& I = c->inst[instance];
+    const StateFileHeader want = header_of(I);
+    FILE* f = std::fopen(path, "rb");
+    if (!f) TK_FAIL(c, TEUK_EINVAL, "cannot open %s", path);
+    char magic[8] = {};
+    StateFileHeader h{};
+    bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kStateMagic, 8) == 0 &&
+              std::fread(&h, sizeof h, 1, f) == 1;
+    if (!ok || !same_problem(h, want) || h.step < 0) {
+        std::fclose(f);
+        TK_FAIL(c, TEUK_EINVAL, "%s is not a saved state of this instance's problem", path);
+    }
+    std::vector<char> buf((size_t)h.nplanes * I.plane_bytes);
+    ok = std::fread(buf.data(), 1, buf.size(), f) == buf.size();
+    std::fclose(f);
+    if (!ok) TK_FAIL(c, TEUK_EINVAL, "%s is truncated", path);
+    for (int k = 0; k < h.nplanes; ++k)
+        TK_CUDA(c, cudaMemcpyAsync(I.state[I.cur][k], buf.data() + (size_t)k * I.plane_bytes, I.plane_bytes,
+                                   cudaMemcpyHostToDevice, c->stream));
+    TK_CUDA(c, cudaStreamSynchronize(c->stream));   // the host buffer goes away on return
+    I.step = h.step;
+    I.wave_lo = I.wave_hi = h.step;
+    return TEUK_OK;
+}
+
 // ------------------------------------------------------------------ step
 
 namespace {

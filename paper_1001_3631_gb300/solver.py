@@ -210,6 +210,14 @@ class TeukSolver:
     def sync(self):
         check(_lib.load().teuk_sync(self.ctx), self.ctx)
 
+    def save_state(self, path, instance=0):
+        """Checkpoint: parameters, time level and the current level's planes, bit for bit."""
+        check(_lib.load().teuk_save_state(self.ctx, instance, os.fsencode(path)), self.ctx)
+
+    def load_state(self, path, instance=0):
+        """Resume from save_state's file (the same problem; clears the waveform records)."""
+        check(_lib.load().teuk_load_state(self.ctx, instance, os.fsencode(path)), self.ctx)
+
     def check_selftest(self):
         """Checked builds: make the next sync report TEUK_EBOUNDS (no memory is addressed)."""
         check(_lib.load().teuk_check_selftest(self.ctx), self.ctx)
