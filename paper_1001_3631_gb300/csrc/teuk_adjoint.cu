@@ -238,12 +238,20 @@ __global__ void __launch_bounds__(kSrcGradThreads) adj_src_grad_kernel(InstDev d
                  d.dt * (re_mul(ph[3], S[4], S[5]) + re_mul(ph[1], S[6], S[7])));
 }
 
+// Programmatic dependent launch of consecutive reverse steps: a block releases the next
+// step's launch on entry; the next step's blocks set up what depends only on constant
+// data and wait (griddepcontrol.wait: the previous grid has completed and its writes are
+// visible) before they read the co-state or write anything to global memory.
+__device__ __forceinline__ void adj_release_next() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void adj_wait_prev() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // kMaxT: the largest block this instance serves (256: columns of up to 256 rows, with
 // the register budget of several blocks per SM; 1024: taller columns)
 template <typename T, typename R, int kMaxT>
 __global__ void __launch_bounds__(kMaxT) adj_step_kernel(InstDev d, CoLevel lin, const double2* gbar,
                                                          CoLevel lout, int strip, void* wh, void* wi) {
     extern __shared__ __align__(16) unsigned char adj_smem[];
+    adj_release_next();
     Z<R>* LB = (Z<R>*)adj_smem;                 // [2][pitch] lam'_Pi of a column
     Z<R>* MB = LB + 2 * (size_t)d.pitch;        // [2][pitch] mu_Pi of a half node
     const int j = threadIdx.x, nth = d.nth, nr = d.nr, pitch = d.pitch;
@@ -267,6 +275,7 @@ __global__ void __launch_bounds__(kMaxT) adj_step_kernel(InstDev d, CoLevel lin,
         lm = j >= 1 ? b[j - 1] : Z<R>{0, 0};
         lp = j + 1 < nth ? b[j + 1] : Z<R>{0, 0};
     };
+    adj_wait_prev();
     CoNode<R> l_cur = lam_at(c0 - 1), l_next;
     LB[(size_t)((c0 - 1) & 1) * pitch + j] = l_cur.P;
     Z<R> mu_prevF = {0, 0}, mu_prevP = {0, 0};
@@ -393,17 +402,24 @@ __device__ __forceinline__ Z<float> theta_cot_v(const CfF& c, float ep_m, float 
     return r;
 }
 
+// columns of radial tables the FP32 reverse step stages in shared memory (strips of up
+// to kAdjRtCols - 2 columns; longer strips read the tables from global memory)
+constexpr int kAdjRtCols = 64;
+
 template <int kMaxT>
 __global__ void __launch_bounds__(kMaxT) adj_step_kernel_f32(InstDev d, CoLevel lin, const double2* gbar,
                                                              CoLevel lout, int strip, void* wh, void* wi) {
     using R = float;
     extern __shared__ __align__(16) unsigned char adj_smem[];
+    adj_release_next();
     const int j = threadIdx.x, nth = d.nth, nr = d.nr, pitch = d.pitch;
     Z<R>* LB = (Z<R>*)adj_smem;                   // [2][pitch] lam'_Pi of a column
     Z<R>* MB = LB + 2 * (size_t)pitch;            // [2][pitch] mu_Pi of a half node
     float4* EB = (float4*)(MB + 2 * (size_t)pitch);   // [3][pitch] {ep, em} of node, half node
+    RTab2* RT = (RTab2*)(EB + 3 * (size_t)pitch);      // radial tables of columns c0-1 .. c1
     const bool row_ok = j < nth;
     const int c0 = blockIdx.x * strip, c1 = min(nr, c0 + strip);   // output columns [c0, c1)
+    const bool rt_smem = strip + 2 <= kAdjRtCols;   // else the tables are read from global
     const R g = (R)d.ghost, hdt = (R)(0.5 * d.dt), qdt = (R)(0.5 * d.dt);
     const SourceDev& s = d.src;
     // wh, wi: this step's ring slot of the window co-states (null: no source)
@@ -414,11 +430,35 @@ __global__ void __launch_bounds__(kMaxT) adj_step_kernel_f32(InstDev d, CoLevel 
         if (row_ok && col >= 1 && col <= nr - 2) z = co_load<R>(lin, node_index(d, col, j));
         return z;
     };
+    // the stored pairs of a column, loaded one column ahead of use (zero outside the
+    // interior columns, as lam_at); as_node forms the values when the column is used
+    struct CoRaw { float2 vF, cF, vP, cP; };
+    auto raw_at = [&](int col) {
+        CoRaw z{};
+        if (row_ok && col >= 1 && col <= nr - 2) {
+            const size_t o = node_index(d, col, j);
+            z.vF = __ldg((const float2*)lin.F + o);
+            z.cF = __ldg((const float2*)lin.Fc + o);
+            z.vP = __ldg((const float2*)lin.P + o);
+            z.cP = __ldg((const float2*)lin.Pc + o);
+        }
+        return z;
+    };
+    auto as_node = [](const CoRaw& r) {
+        CoNode<R> n;
+        n.vF = r.vF;
+        n.cF = r.cF;
+        n.vP = r.vP;
+        n.cP = r.cP;
+        n.F = {r.vF.x - r.cF.x, r.vF.y - r.cF.y};
+        n.P = {r.vP.x - r.cP.x, r.vP.y - r.cP.y};
+        return n;
+    };
     // coefficients of column col: node col (ci) and half node col+1/2 (ch)
     auto form = [&](int col, CfF& ci, CfF& ch) {
         float2 cf2[kNCoef];
         if (col >= 0 && col <= nr - 1) {
-            form_coefs2(d.rtab[col], rt.t, cf2);
+            form_coefs2(rt_smem ? RT[col - (c0 - 1)] : d.rtab[col], rt.t, cf2);
         } else {
 #pragma unroll
             for (int q = 0; q < kNCoef; ++q) cf2[q] = make_float2(0.f, 0.f);
@@ -469,6 +509,16 @@ __global__ void __launch_bounds__(kMaxT) adj_step_kernel_f32(InstDev d, CoLevel 
         aP = zadd(aP, zscale(R(0.5) + sR * c.g, MP));
         aP = zadd(aP, zscale(R(0.5), zconjmul(c.e1r, c.e1i, MP)));
     };
+    // the strip's radial tables into shared memory (one broadcast read per column later)
+    if (rt_smem) {
+        const int ncols = c1 - c0 + 2;
+        for (int q = threadIdx.x; q < ncols * 8; q += blockDim.x) {
+            const int k = q >> 3, col = c0 - 1 + k;
+            if (col >= 0 && col <= nr - 1) ((float4*)(RT + k))[q & 7] = __ldg((const float4*)(d.rtab + col) + (q & 7));
+        }
+        __syncthreads();
+    }
+    adj_wait_prev();
     // prologue: column c0 - 1
     CoNode<R> l_cur = lam_at(c0 - 1);
     CfF ci_cur, ch_cur;
@@ -479,9 +529,11 @@ __global__ void __launch_bounds__(kMaxT) adj_step_kernel_f32(InstDev d, CoLevel 
     Z<R> muF_part = {0, 0}, muP_part = {0, 0};      // mu(h): the left node's share
     if (row_ok && c0 - 1 >= 1 && c0 - 1 <= nr - 2) corr(ci_cur, l_cur, c0 - 1, R(1), muF_part, muP_part);
     Z<R> aF_part = {0, 0}, aP_part = {0, 0};        // lam(h): the left half node's share
+    CoRaw r_next = raw_at(c0);
     for (int h = c0 - 1; h <= c1 - 1; ++h) {
-        // A: column h+1: its co-state and coefficients
-        const CoNode<R> l_next = lam_at(h + 1);
+        // A: column h+1: its co-state (loaded one column ahead) and coefficients
+        const CoNode<R> l_next = as_node(r_next);
+        r_next = raw_at(h + 2);
         CfF ci_n, ch_n;
         form(h + 1, ci_n, ch_n);
         LB[(size_t)((h + 1) & 1) * pitch + j] = l_next.P;
@@ -584,7 +636,8 @@ void launch_adj_init(cudaStream_t st, const InstDev& d, const double2* gbar, con
 // dynamic shared memory of the reverse-step kernels for blocks of `threads` rows
 template <typename R>
 static size_t adj_smem(int threads, bool f32) {
-    return 4 * (size_t)threads * sizeof(Z<R>) + (f32 ? 3 * (size_t)threads * sizeof(float4) : 0);
+    return 4 * (size_t)threads * sizeof(Z<R>) +
+           (f32 ? 3 * (size_t)threads * sizeof(float4) + kAdjRtCols * sizeof(RTab2) : 0);
 }
 
 template <class K>
@@ -596,8 +649,17 @@ static int adj_resident(K kernel, int threads, size_t smem) {
     return (per > 0 ? per : 1) * (sms > 0 ? sms : 1);
 }
 
+// the largest dynamic shared memory a reverse-step kernel takes (columns of 1024 rows)
+template <class K>
+static void adj_allow_smem(K kernel, size_t bytes) {
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
 int adj_step_plan(const InstDev& d, int* strip) {
     const int t = d.pitch;
+    if (d.prec == 0) adj_allow_smem(adj_step_kernel<double, double, 1024>, adj_smem<double>(1024, false));
+    else if (d.prec == 3) adj_allow_smem(adj_step_kernel<DF, double, 1024>, adj_smem<double>(1024, false));
+    else adj_allow_smem(adj_step_kernel_f32<1024>, adj_smem<float>(1024, true));
     int res;
     if (d.prec == 0)
         res = t <= 256 ? adj_resident(adj_step_kernel<double, double, 256>, t, adj_smem<double>(t, false))
@@ -614,6 +676,22 @@ int adj_step_plan(const InstDev& d, int* strip) {
     return (d.nr + L - 1) / L;
 }
 
+template <class K>
+static void adj_launch(cudaStream_t st, K kernel, int nb, int t, size_t sm, const InstDev& d, const CoLevel& lin,
+                       const double2* gbar, const CoLevel& lout, int strip, void* wh, void* wi) {
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nb);
+    cfg.blockDim = dim3(t);
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = st;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, d, lin, gbar, lout, strip, wh, wi);
+}
+
 void launch_adj_step(cudaStream_t st, const InstDev& d, const CoLevel& lin, const double2* gbar,
                      const CoLevel& lout, int strip, void* wh, void* wi) {
     const int nb = (d.nr + strip - 1) / strip;
@@ -621,16 +699,16 @@ void launch_adj_step(cudaStream_t st, const InstDev& d, const CoLevel& lin, cons
     if (d.prec == 0 || d.prec == 3) {
         const size_t sm = adj_smem<double>(t, false);
         if (d.prec == 0) {
-            if (t <= 256) adj_step_kernel<double, double, 256><<<nb, t, sm, st>>>(d, lin, gbar, lout, strip, wh, wi);
-            else adj_step_kernel<double, double, 1024><<<nb, t, sm, st>>>(d, lin, gbar, lout, strip, wh, wi);
+            if (t <= 256) adj_launch(st, adj_step_kernel<double, double, 256>, nb, t, sm, d, lin, gbar, lout, strip, wh, wi);
+            else adj_launch(st, adj_step_kernel<double, double, 1024>, nb, t, sm, d, lin, gbar, lout, strip, wh, wi);
         } else {
-            if (t <= 256) adj_step_kernel<DF, double, 256><<<nb, t, sm, st>>>(d, lin, gbar, lout, strip, wh, wi);
-            else adj_step_kernel<DF, double, 1024><<<nb, t, sm, st>>>(d, lin, gbar, lout, strip, wh, wi);
+            if (t <= 256) adj_launch(st, adj_step_kernel<DF, double, 256>, nb, t, sm, d, lin, gbar, lout, strip, wh, wi);
+            else adj_launch(st, adj_step_kernel<DF, double, 1024>, nb, t, sm, d, lin, gbar, lout, strip, wh, wi);
         }
     } else {
         const size_t sm = adj_smem<float>(t, true);
-        if (t <= 256) adj_step_kernel_f32<256><<<nb, t, sm, st>>>(d, lin, gbar, lout, strip, wh, wi);
-        else adj_step_kernel_f32<1024><<<nb, t, sm, st>>>(d, lin, gbar, lout, strip, wh, wi);
+        if (t <= 256) adj_launch(st, adj_step_kernel_f32<256>, nb, t, sm, d, lin, gbar, lout, strip, wh, wi);
+        else adj_launch(st, adj_step_kernel_f32<1024>, nb, t, sm, d, lin, gbar, lout, strip, wh, wi);
     }
 }
 
