@@ -198,7 +198,12 @@ teuk_status teuk_save_state(teuk_ctx* ctx, int instance, const char* path);
 teuk_status teuk_load_state(teuk_ctx* ctx, int instance, const char* path);
 
 /* Advance every instance by n full Lax-Wendroff steps (Eqs. 13-14), recording the
- * waveform at every time level.  Asynchronous on the context's stream. */
+ * waveform at every time level.  Asynchronous on the context's stream.  A single
+ * instance stepped one launch per step replays a CUDA graph of 64 launches (captured on
+ * first use and again when the launch configuration changes; one per parity of the
+ * buffer holding the state) for each whole 64 steps and launches the rest directly; on
+ * a stream that cannot be captured (the legacy default stream, or one the caller is
+ * capturing) every step is launched directly.  The results are the same either way. */
 teuk_status teuk_step_n(teuk_ctx* ctx, int64_t n);
 
 /* Copy the waveform records of one instance to host memory: out [k][n_theta][2]

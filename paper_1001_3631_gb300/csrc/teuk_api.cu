@@ -18,6 +18,14 @@ namespace {
 
 constexpr double kPi = 3.141592653589793238462643;
 
+// The launch configuration a per-step graph captured (compared byte for byte).
+struct StepGraphKey {
+    InstDev d;
+    const int* part;
+    int strip;
+    int pad;
+};
+
 struct Instance {
     teuk_params p{};
     double drs = 0, dth = 0, dt = 0, rp = 0, rm = 0;
@@ -66,6 +74,14 @@ struct Instance {
     ResidentPlan res_plan;
     unsigned char* res_xg = nullptr;
     int* res_flags = nullptr;
+    // per-step launches replayed from CUDA graphs of kStepGraph steps (one graph per parity
+    // of the buffer holding the state); sg_key is the launch configuration each captured
+    int64_t* d_step = nullptr;      // the graphs' step base (device)
+    int64_t graph_base = -1;        // the step *d_step holds (-1: unknown)
+    int64_t h_step = 0;             // host source of the base's copy
+    cudaGraphExec_t sg_exec[2] = {nullptr, nullptr};
+    StepGraphKey sg_key[2] = {};
+    bool sg_failed = false;         // capture refused (legacy stream): launch directly
 };
 
 // Device side of the batched persistent launch of one context: one persistent kernel
@@ -363,8 +379,63 @@ void do_extract(teuk_ctx* c, Instance& I) {
     c->launches++;
 }
 
+// Steps per replayed graph (even, so that the state returns to the buffer it started in).
+constexpr int64_t kStepGraph = 64;
+
+// The graph of kStepGraph per-step launches for the instance's current buffer parity and
+// configuration, captured on first use and again whenever the configuration changed.
+// Returns nullptr where capture is not possible (the legacy default stream, or a stream
+// that the caller is capturing); the steps are then launched directly.
+cudaGraphExec_t step_graph(teuk_ctx* c, Instance& I, int strip) {
+    if (I.sg_failed) return nullptr;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(c->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (!I.d_step && dmalloc(c, (void**)&I.d_step, sizeof(int64_t), c->stream) != cudaSuccess) {
+        cudaGetLastError();
+        I.sg_failed = true;
+        return nullptr;
+    }
+    StepGraphKey key;
+    std::memset(&key, 0, sizeof key);
+    key.d = dev_of(c, I);
+    key.d.step_base = I.d_step;
+    key.part = I.part_strip == strip ? I.d_part : nullptr;
+    key.strip = strip;
+    const int p = I.cur;
+    if (I.sg_exec[p] && std::memcmp(&key, &I.sg_key[p], sizeof key) == 0) return I.sg_exec[p];
+    if (I.sg_exec[p]) cudaGraphExecDestroy(I.sg_exec[p]);
+    I.sg_exec[p] = nullptr;
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        I.sg_failed = true;
+        return nullptr;
+    }
+    for (int64_t k = 0; k < kStepGraph; ++k)
+        launch_step(c->stream, key.d, k, (int)((p + k) & 1), strip, key.part);
+    launch_advance_step(c->stream, I.d_step, kStepGraph);
+    cudaGraphExec_t e = nullptr;
+    if (cudaStreamEndCapture(c->stream, &g) != cudaSuccess || !g ||
+        cudaGraphInstantiate(&e, g, 0) != cudaSuccess) {
+        cudaGetLastError();
+        if (g) cudaGraphDestroy(g);
+        I.sg_failed = true;
+        return nullptr;
+    }
+    cudaGraphDestroy(g);
+    I.sg_exec[p] = e;
+    I.sg_key[p] = key;
+    return e;
+}
+
 void free_instance(const teuk_ctx* c, Instance& I) {
     const cudaStream_t s = c->stream;
+    for (int p = 0; p < 2; ++p)
+        if (I.sg_exec[p]) cudaGraphExecDestroy(I.sg_exec[p]);
+    if (I.d_step) dfree(c, I.d_step, s);
     for (int b = 0; b < 2; ++b)
         for (int k = 0; k < 2; ++k)
             if (I.state[b][k]) dfree(c, I.state[b][k], s);
@@ -1041,7 +1112,24 @@ extern "C" teuk_status teuk_step_n(teuk_ctx* c, int64_t n) {
     for (Instance& I : c->inst) {
         int strip = eff_strip(c, I);
         int64_t s0 = I.step;
-        for (int64_t k = 0; k < n; ++k) do_step(c, I, strip);
+        int64_t k = 0;
+        // whole graphs of kStepGraph steps, then the rest one launch at a time
+        cudaGraphExec_t e = n >= kStepGraph ? step_graph(c, I, strip) : nullptr;
+        if (e) {
+            if (I.graph_base != I.step) {   // the base the graph's steps are offsets from
+                I.h_step = I.step;
+                TK_CUDA(c, cudaMemcpyAsync(I.d_step, &I.h_step, sizeof(int64_t), cudaMemcpyHostToDevice,
+                                           c->stream));
+                I.graph_base = I.step;
+            }
+            for (; k + kStepGraph <= n; k += kStepGraph) {
+                TK_CUDA(c, cudaGraphLaunch(e, c->stream));
+                c->launches += kStepGraph + 1;
+                I.step += kStepGraph;
+                I.graph_base += kStepGraph;   // advanced by the graph's last node
+            }
+        }
+        for (; k < n; ++k) do_step(c, I, strip);
         do_extract(c, I);
         if (I.wave_hi != s0 + 1 || I.wave_lo == I.wave_hi) I.wave_lo = s0;
         I.wave_hi = I.step + 1;

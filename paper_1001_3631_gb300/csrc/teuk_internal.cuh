@@ -100,6 +100,8 @@ struct InstDev {
     unsigned int* status;     // device status word (bit flags)
     int fault_col;            // testing aid: this input column is never filled into the
                               // step kernels' ring (-1: none)
+    const int64_t* step_base; // per-step kernels replayed from a graph: their step argument
+                              // is an offset from *step_base (null: the argument is the step)
 };
 
 enum StatusBits : unsigned int { ST_NONFINITE = 1u, ST_TIMEOUT = 2u, ST_BOUNDS = 4u };
@@ -200,6 +202,8 @@ int step_resident_blocks(int prec, int threads);  // blocks of the step kernel t
 void launch_step(cudaStream_t st, const InstDev& d, int64_t step, int bin, int strip,
                  const int* part = nullptr);
 void launch_extract(cudaStream_t st, const InstDev& d, int64_t step, int bin);
+// *base += k (one thread): closes a replayed graph of k per-step launches
+void launch_advance_step(cudaStream_t st, int64_t* base, int64_t k);
 // moving: some instance of the class has a moving particle (selects the kernel that
 // carries the per-step Gaussian tables)
 void launch_batched_step(cudaStream_t st, int prec, const BatchDev& b, int grid, int threads,

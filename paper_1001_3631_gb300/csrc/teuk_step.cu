@@ -505,6 +505,10 @@ __device__ __forceinline__ void step_body(const InstDev& d, int64_t step, int bi
     // the next step's launch may begin now: its blocks become resident as ours retire and
     // run their set-up while this step drains
     griddep_launch_dependents();
+    // replayed from a graph: the step is an offset from a base that the host (before the
+    // first replay) or the graph's last node (after each replay) sets; it does not change
+    // while the graph's steps run
+    if (d.step_base) step += *d.step_base;
     ColumnRing<P, R> ring(step_smem, mbar);
     if (threadIdx.x == 0) ring.init();
     __syncthreads();
@@ -529,6 +533,14 @@ template <class P, bool kMov>
 __global__ void __launch_bounds__(1024) step_kernel_l(InstDev d, int64_t step, int bin, int strip,
                                                      const int* part) {
     step_body<P, kRingL, kMov>(d, step, bin, strip, part);
+}
+
+__global__ void advance_step_kernel(int64_t* base, int64_t k) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) *base += k;
+}
+
+void launch_advance_step(cudaStream_t st, int64_t* base, int64_t k) {
+    advance_step_kernel<<<1, 32, 0, st>>>(base, k);
 }
 
 // Waveform record of the state in buffer bin (time level `step`): one thread per row.
