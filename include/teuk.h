@@ -20,9 +20,9 @@
  *     keeps no host pointer past the call.  Device memory is owned by the
  *     context and released by teuk_destroy.
  *   - Work is queued on the caller's CUDA stream (the cuda_stream of
- *     teuk_create; NULL is the legacy default stream, on which the batched launch
- *     cannot be captured in a CUDA graph and is issued directly).  Calls that return
- *     host data synchronize that stream.
+ *     teuk_create; NULL is the legacy default stream).  The context's CUDA graphs
+ *     are captured on a private stream of its own and replayed on that stream.
+ *     Calls that return host data synchronize that stream.
  *   - Every call returns a teuk_status; teuk_last_error() gives the message of
  *     the last failing call on that context.  Nothing aborts the process and
  *     no kernel traps: device-side failures are reported through a status
@@ -201,9 +201,10 @@ teuk_status teuk_load_state(teuk_ctx* ctx, int instance, const char* path);
  * waveform at every time level.  Asynchronous on the context's stream.  A single
  * instance stepped one launch per step replays a CUDA graph of 64 launches (captured on
  * first use and again when the launch configuration changes; one per parity of the
- * buffer holding the state) for each whole 64 steps and launches the rest directly; on
- * a stream that cannot be captured (the legacy default stream, or one the caller is
- * capturing) every step is launched directly.  The results are the same either way. */
+ * buffer holding the state) for each whole 64 steps and launches the rest directly.  The
+ * graphs are captured on a private stream of the context and replayed on its stream;
+ * while the caller is capturing that stream every step is launched directly.  The
+ * results are the same either way. */
 teuk_status teuk_step_n(teuk_ctx* ctx, int64_t n);
 
 /* Copy the waveform records of one instance to host memory: out [k][n_theta][2]

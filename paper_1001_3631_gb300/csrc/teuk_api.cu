@@ -151,6 +151,9 @@ struct teuk_ctx {
     long long spin_limit = 20000000LL;
     double2* sum_buf = nullptr;      // teuk_extract's summed records, grown on demand
     int64_t sum_cap = 0;
+    cudaStream_t cap = nullptr;      // private stream on which the context's CUDA graphs are
+                                     // captured (any stream, the legacy one included, can
+                                     // then replay them)
 };
 
 static std::string g_create_err = "no error";
@@ -379,17 +382,28 @@ void do_extract(teuk_ctx* c, Instance& I) {
     c->launches++;
 }
 
+// The private capture stream (created on first use; nullptr if that fails).
+cudaStream_t capture_stream(teuk_ctx* c) {
+    if (!c->cap && cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        c->cap = nullptr;
+    }
+    return c->cap;
+}
+
 // Steps per replayed graph (even, so that the state returns to the buffer it started in).
 constexpr int64_t kStepGraph = 64;
 
 // The graph of kStepGraph per-step launches for the instance's current buffer parity and
 // configuration, captured on first use and again whenever the configuration changed.
-// Returns nullptr where capture is not possible (the legacy default stream, or a stream
-// that the caller is capturing); the steps are then launched directly.
+// The graph is captured on the context's private stream and replayed on its stream (any
+// stream, the legacy default one included).  Returns nullptr while the caller is
+// capturing the context's stream, or if capture failed; the steps are then launched
+// directly.
 cudaGraphExec_t step_graph(teuk_ctx* c, Instance& I, int strip) {
     if (I.sg_failed) return nullptr;
-    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    if (cudaStreamIsCapturing(c->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+    cudaStreamCaptureStatus ucs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(c->stream, &ucs) != cudaSuccess || ucs != cudaStreamCaptureStatusNone) {
         cudaGetLastError();
         return nullptr;
     }
@@ -409,16 +423,17 @@ cudaGraphExec_t step_graph(teuk_ctx* c, Instance& I, int strip) {
     if (I.sg_exec[p]) cudaGraphExecDestroy(I.sg_exec[p]);
     I.sg_exec[p] = nullptr;
     cudaGraph_t g = nullptr;
-    if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaStream_t cs = capture_stream(c);
+    if (!cs || cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
         cudaGetLastError();
         I.sg_failed = true;
         return nullptr;
     }
     for (int64_t k = 0; k < kStepGraph; ++k)
-        launch_step(c->stream, key.d, k, (int)((p + k) & 1), strip, key.part);
-    launch_advance_step(c->stream, I.d_step, kStepGraph);
+        launch_step(cs, key.d, k, (int)((p + k) & 1), strip, key.part);
+    launch_advance_step(cs, I.d_step, kStepGraph);
     cudaGraphExec_t e = nullptr;
-    if (cudaStreamEndCapture(c->stream, &g) != cudaSuccess || !g ||
+    if (cudaStreamEndCapture(cs, &g) != cudaSuccess || !g ||
         cudaGraphInstantiate(&e, g, 0) != cudaSuccess) {
         cudaGetLastError();
         if (g) cudaGraphDestroy(g);
@@ -862,15 +877,15 @@ void invalidate_graph(teuk_ctx* c) {
     B.graph = nullptr;
 }
 
-void enqueue_batched(teuk_ctx* c) {
+void enqueue_batched(teuk_ctx* c, cudaStream_t st) {
     Batch& B = c->batch;
-    cudaMemsetAsync(B.d_abort, 0, sizeof(int), c->stream);
+    cudaMemsetAsync(B.d_abort, 0, sizeof(int), st);
     for (BatchClass& K : B.cls) {
-        cudaMemsetAsync(K.d_counter, 0, sizeof(unsigned long long), c->stream);
-        cudaMemsetAsync(K.d_flags, 0, sizeof(int) * K.items, c->stream);
+        cudaMemsetAsync(K.d_counter, 0, sizeof(unsigned long long), st);
+        cudaMemsetAsync(K.d_flags, 0, sizeof(int) * K.items, st);
     }
-    for (BatchClass& K : B.cls) launch_batched_step(c->stream, c->prec, K.bd, K.grid, K.pitch, K.moving);
-    for (BatchClass& K : B.cls) launch_batched_extract(c->stream, c->prec, K.bd, K.max_nth);
+    for (BatchClass& K : B.cls) launch_batched_step(st, c->prec, K.bd, K.grid, K.pitch, K.moving);
+    for (BatchClass& K : B.cls) launch_batched_extract(st, c->prec, K.bd, K.max_nth);
 }
 
 // All instances advance n steps: one persistent launch per block-size class, captured
@@ -982,11 +997,16 @@ teuk_status batched_step(teuk_ctx* c, int64_t n) {
     // pageable source: the call returns once the host bytes are staged
     TK_CUDA(c, cudaMemcpyAsync(B.d_blob, blob.data(), blob.size(), cudaMemcpyHostToDevice,
                                c->stream));
-    if (!B.exec && !B.graph_failed) {
+    cudaStreamCaptureStatus ucs = cudaStreamCaptureStatusNone;
+    const bool user_capturing = cudaStreamIsCapturing(c->stream, &ucs) != cudaSuccess ||
+                                ucs != cudaStreamCaptureStatusNone;
+    cudaGetLastError();
+    cudaStream_t cs = user_capturing ? nullptr : capture_stream(c);
+    if (!B.exec && !B.graph_failed && cs) {
         cudaGraph_t g = nullptr;
-        if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-            enqueue_batched(c);
-            if (cudaStreamEndCapture(c->stream, &g) == cudaSuccess && g &&
+        if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+            enqueue_batched(c, cs);
+            if (cudaStreamEndCapture(cs, &g) == cudaSuccess && g &&
                 cudaGraphInstantiate(&B.exec, g, 0) == cudaSuccess) {
                 B.graph = g;
             } else {
@@ -997,12 +1017,12 @@ teuk_status batched_step(teuk_ctx* c, int64_t n) {
         } else {
             B.graph_failed = true;
         }
-        cudaGetLastError();  // a refused capture (legacy stream) is not an error here
+        cudaGetLastError();  // a refused capture is not an error here
     }
-    if (B.exec) {
+    if (B.exec && !user_capturing) {
         TK_CUDA(c, cudaGraphLaunch(B.exec, c->stream));
     } else {
-        enqueue_batched(c);
+        enqueue_batched(c, c->stream);
     }
     c->launches += 2 * (int64_t)B.cls.size();
     for (Instance& I : c->inst) {
@@ -1600,6 +1620,7 @@ extern "C" void teuk_destroy(teuk_ctx* c) {
     for (Instance& I : c->inst) free_instance(c, I);
     if (c->status) dfree(c, c->status, c->stream);
     cudaStreamSynchronize(c->stream);
+    if (c->cap) cudaStreamDestroy(c->cap);
     delete c;
 }
 

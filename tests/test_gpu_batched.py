@@ -60,8 +60,8 @@ def run_batched(prec, steps, strip, stream=None):
 
 @pytest.mark.parametrize("prec,graph", [("fp64", True), ("fp32_kahan", True), ("fp64", False)])
 def test_batched_equals_per_step_launches_bitwise(prec, graph):
-    # on a side stream the persistent launch is captured in a CUDA graph and replayed;
-    # the legacy default stream cannot be captured, so there it is launched directly
+    # the persistent launch is captured in a CUDA graph (on the context's private stream)
+    # and replayed on the caller's stream: a side stream or the legacy default stream
     import torch
     stream = torch.cuda.Stream() if graph else None
     steps = [37, 5, 1]
