@@ -11,12 +11,13 @@ L = sum_{k=1..n} sum_j |r_ext^3 W_k[j]|^2 (psi = r^3 Phi, Eq. 4) of the same run
 forward is one teuk_adjoint_n call in built-in-loss mode; the gradients it returns are
 kept for backward, which scales them by the incoming gradient of L.  The step is linear
 in the state, so the reverse sweep needs only the loss's cotangent on the records, never
-a forward state: with ckpt_every = 0 (the default) the forward sweep keeps every
+a forward state: with ckpt_every = 0 the forward sweep keeps every
 record's cotangent (n_steps x n_theta x 16 B) and the reverse sweep follows at once;
-with ckpt_every = K > 0 the forward sweep keeps a state checkpoint every K steps and the
-reverse sweep recomputes each segment's records from its checkpoint (one more forward
-sweep of work).  A checkpoint is a whole state, so this saves memory only where a
-segment's records outweigh a state, i.e. for K above about 4 n_rstar (FP32-Kahan)."""
+with ckpt_every = K > 0 (the default, K = 100) the forward sweep keeps a state
+checkpoint every K steps and the reverse sweep recomputes each segment's records from
+its checkpoint (one more forward sweep of work).  A checkpoint is a whole state, so
+this saves memory only where a segment's records outweigh a state, i.e. for K above
+about 4 n_rstar (FP32-Kahan)."""
 from __future__ import annotations
 
 import numpy as np
@@ -59,7 +60,7 @@ class TeukWaveformFn(torch.autograd.Function):
 
 class TeukPsiLossFn(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, amps, r0, solver, n_steps, ckpt_every=0):
+    def forward(ctx, amps, r0, solver, n_steps, ckpt_every=100):
         a, r, dev_r = _source_args(amps, r0)
         solver.set_source(r, a)
         solver.set_state(np.zeros(solver.shape()), 0)

@@ -412,9 +412,12 @@ cudaGraphExec_t step_graph(teuk_ctx* c, Instance& I, int strip) {
         I.sg_failed = true;
         return nullptr;
     }
+    // (object representations copied byte for byte, so that the comparison below sees
+    // only the members)
     StepGraphKey key;
     std::memset(&key, 0, sizeof key);
-    key.d = dev_of(c, I);
+    const InstDev cur_d = dev_of(c, I);
+    std::memcpy(&key.d, &cur_d, sizeof cur_d);
     key.d.step_base = I.d_step;
     key.part = I.part_strip == strip ? I.d_part : nullptr;
     key.strip = strip;
@@ -442,7 +445,7 @@ cudaGraphExec_t step_graph(teuk_ctx* c, Instance& I, int strip) {
     }
     cudaGraphDestroy(g);
     I.sg_exec[p] = e;
-    I.sg_key[p] = key;
+    std::memcpy(&I.sg_key[p], &key, sizeof key);
     return e;
 }
 

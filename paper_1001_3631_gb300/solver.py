@@ -196,10 +196,10 @@ class TeukSolver:
                                         ptr(out)), self.ctx)
         return out[..., 0] + 1j * out[..., 1]
 
-    def adjoint(self, n, step0=0, grad_wave=None, ckpt_every=0, instance=0):
-        """Returns (grad_amps [n], grad_r0, loss).  ckpt_every (built-in loss only): 0 keeps
-        every record's cotangent; K > 0 recomputes each K-step segment's records from a
-        state checkpoint in the reverse sweep."""
+    def adjoint(self, n, step0=0, grad_wave=None, ckpt_every=100, instance=0):
+        """Returns (grad_amps [n], grad_r0, loss).  ckpt_every (built-in loss only): K > 0
+        recomputes each K-step segment's records from a state checkpoint in the reverse
+        sweep; 0 keeps every record's cotangent instead (no recomputation)."""
         gw = None if grad_wave is None else np.ascontiguousarray(grad_wave, dtype=np.float64)
         ga = np.zeros(n)
         gr, loss = ctypes.c_double(0.0), ctypes.c_double(0.0)
