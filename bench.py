@@ -277,10 +277,10 @@ def accuracy(cfg, n_steps=4000, probe=12.0):
     return res
 
 
-def batched_leg(n_calls=4, steps_per_call=25, warm_calls=2):
+def batched_leg(n_calls=2, steps_per_call=100, warm_calls=1):
     """The 128-instance uneven workload (8 modes x 16 orbits) in FP32-Kahan: one
-    persistent launch per call, replayed from a CUDA graph on a side stream, tiles from
-    the autotuner's cached table."""
+    persistent launch per block-size class and call (100 steps), replayed from a CUDA
+    graph on a side stream, tiles from the autotuner's cached table."""
     import torch
 
     from paper_1001_3631_gb300 import TeukSolver, inputs

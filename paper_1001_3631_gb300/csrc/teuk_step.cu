@@ -608,6 +608,8 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) batched_step_kernel(B
     __shared__ uint64_t mbar[R];
     __shared__ unsigned long long item;
     __shared__ int flag;
+    __shared__ InstDev inst_sm;
+    static_assert(sizeof(InstDev) % sizeof(int) == 0, "descriptor copied as ints");
     ColumnRing<P, R> ring(step_smem, mbar);
     typename P::T* xbuf = StepShared<P, R>::xbuf(step_smem);
     if (threadIdx.x == 0) ring.init();
@@ -628,7 +630,13 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) batched_step_kernel(B
         const int k = lo;
         const int st = (int)(r - b.item_base[k]);
         if (!TK_IN(b.status, k, b.n_inst) || !TK_IN(b.status, r, b.items_per_step)) return;
-        const InstDev& d = b.inst[k];
+        // the item's instance descriptor in shared memory: its fields are then cheap
+        // shared loads instead of global loads held in registers (the previous item's
+        // readers are past the barrier that ends strip_step)
+        for (int q = threadIdx.x; q < (int)(sizeof(InstDev) / sizeof(int)); q += blockDim.x)
+            ((int*)&inst_sm)[q] = ((const int*)(b.inst + k))[q];
+        __syncthreads();
+        const InstDev& d = inst_sm;
         const int strip = b.strip[k], nstrip = b.nstrip[k];
         if (!TK_IN(b.status, st, nstrip)) return;
         int* fl = b.flags + b.item_base[k];
