@@ -318,7 +318,8 @@ def single_mode_leg(steps=2000):
     """The 800 x 64 single mode (51,200 points, L2-resident): one kernel per step, the
     persistent batched kernel replayed from a CUDA graph (strip length from the
     autotuner), and resident launches (the grid in shared memory, one cooperative launch
-    per call, halo from the autotuner's candidates 1 .. 4), for FP64, the FP64-equivalent
+    per call; halo 1 .. 4 and 1 .. 3 blocks per SM timed, the fastest reported), for FP64,
+    the FP64-equivalent
     double-float path, FP32-Kahan and FP32.  hbm_frac is the algorithmic bytes per update
     against the measured HBM copy bandwidth (the grid is L2-resident, so this is the
     fraction of the HBM roofline, not a DRAM measurement); native FP64 is also stated
@@ -346,9 +347,9 @@ def single_mode_leg(steps=2000):
                             s.autotune(trial_steps=20, cache_path=os.path.join(td, "t.json"))[0])
                 elif mode == "resident":
                     best = None
-                    for h in (1, 2, 3, 4):
+                    for h, bps in [(h, b) for b in (1, 2, 3) for h in (1, 2, 3, 4)]:
                         try:
-                            s.set_resident(h)
+                            s.set_resident(h, bps)
                         except Exception:
                             continue
                         s.step(200)
@@ -360,9 +361,10 @@ def single_mode_leg(steps=2000):
                         stream.synchronize()
                         ms = e0.elapsed_time(e1)
                         if best is None or ms < best[0]:
-                            best = (ms, h)
-                    s.set_resident(best[1])
+                            best = (ms, h, bps)
+                    s.set_resident(best[1], best[2])
                     out["%s_resident_halo" % prec] = best[1]
+                    out["%s_resident_blocks_per_sm" % prec] = best[2]
                 s.step(steps)
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 stream.synchronize()

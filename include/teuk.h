@@ -307,8 +307,13 @@ teuk_status teuk_set_tiling(teuk_ctx* ctx, int strip, int steps_per_launch);
  * Instances with a moving particle are still stepped one launch per step.
  * TEUK_EINVAL if the context has several instances or the grid does not fit (every
  * block must own >= halo columns, hold them in shared memory, and all blocks must be
- * resident at once).  Allocates the exchange slots (2 x blocks x 2 x halo columns). */
+ * resident at once).  Allocates the exchange slots (2 x blocks x 2 x halo columns).
+ * teuk_set_resident_shape also sets the number of blocks per SM the column runs are cut
+ * for (blocks_per_sm >= 1; teuk_set_resident takes 1): with several, the runs are
+ * shorter and one block's halo wait overlaps another block's arithmetic on the same SM.
+ * A shape that does not fit is TEUK_EINVAL. */
 teuk_status teuk_set_resident(teuk_ctx* ctx, int halo);
+teuk_status teuk_set_resident_shape(teuk_ctx* ctx, int halo, int blocks_per_sm);
 
 /* Strip length (r* columns per block) of one instance (0 = back to the context default). */
 teuk_status teuk_set_instance_tiling(teuk_ctx* ctx, int instance, int strip);
@@ -316,9 +321,9 @@ teuk_status teuk_set_instance_tiling(teuk_ctx* ctx, int instance, int strip);
 /* Autotuner of the strip length (r* columns per block), written to every instance
  * (chosen, may be NULL, receives them).  A single instance stepped one launch per step:
  * trial_steps steps of each candidate (1 .. 512 columns) and of resident launches with
- * halo 1 .. 4 (teuk_set_resident, where the grid fits) on a scratch copy of the
- * instance; the fastest is applied, and chosen[k] < 0 reports resident launches with
- * halo -chosen[k].  Contexts that run the persistent kernels (several instances, or one with
+ * halo 1 .. 4 and 1 .. 3 blocks per SM (teuk_set_resident_shape, where the grid fits) on
+ * a scratch copy of the instance; the fastest is applied, and chosen[k] < 0 reports
+ * resident launches with halo (-chosen[k]) % 16 and (-chosen[k]) / 16 + 1 blocks per SM.  Contexts that run the persistent kernels (several instances, or one with
  * steps_per_launch = 0): trial_steps steps of the whole context per candidate (16 .. 512),
  * one length for all instances first, then block-size class by class, on the live state,
  * which is restored afterwards from a snapshot (device memory for one copy of every

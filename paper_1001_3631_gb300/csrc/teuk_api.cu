@@ -71,6 +71,7 @@ struct Instance {
     // resident launches (teuk_set_resident): halo h (0 = off), plan, exchange slots and
     // flags (nb + 1 ints: the blocks' flags, then the abort flag)
     int res_h = 0;
+    int res_bps = 1;
     ResidentPlan res_plan;
     unsigned char* res_xg = nullptr;
     int* res_flags = nullptr;
@@ -1044,18 +1045,19 @@ teuk_status batched_step(teuk_ctx* c, int64_t n) {
 
 namespace {
 
-// Plan the resident launch of instance I with halo h and (re)allocate its exchange slots
-// and flags; h = 0 turns resident launches off.
-teuk_status set_resident(teuk_ctx* c, Instance& I, int h) {
+// Plan the resident launch of instance I with halo h, aiming at bps blocks per SM, and
+// (re)allocate its exchange slots and flags; h = 0 turns resident launches off.
+teuk_status set_resident(teuk_ctx* c, Instance& I, int h, int bps) {
     if (h == 0) {
         I.res_h = 0;
         return TEUK_OK;
     }
     ResidentPlan plan;
-    if (!resident_plan(I.p.prec, I.p.n_rstar, I.pitch, h, &plan))
+    if (!resident_plan(I.p.prec, I.p.n_rstar, I.pitch, h, bps, &plan))
         TK_FAIL(c, TEUK_EINVAL,
-                "the grid does not fit the resident kernel with halo %d (every block must own >= %d "
-                "columns, hold its columns in shared memory and be resident at once)", h, h);
+                "the grid does not fit the resident kernel with halo %d and %d blocks per SM (every "
+                "block must own >= %d columns, hold its columns in shared memory and be resident "
+                "at once)", h, bps, h);
     const int planes = I.p.prec == TEUK_FP32 ? 1 : 2;
     const size_t xg_bytes = (size_t)planes * 2 * plan.nb * 2 * h * I.pitch * 16;
     if (I.res_xg) dfree(c, I.res_xg, c->stream);
@@ -1067,6 +1069,7 @@ teuk_status set_resident(teuk_ctx* c, Instance& I, int h) {
     TK_CUDA(c, dmalloc(c, (void**)&I.res_flags, sizeof(int) * kResFlagStride * (plan.nb + 1), c->stream));
     I.res_plan = plan;
     I.res_h = h;
+    I.res_bps = bps;
     return TEUK_OK;
 }
 
@@ -1107,13 +1110,18 @@ extern "C" teuk_status teuk_set_allocator(teuk_alloc_fn alloc, teuk_free_fn free
     return TEUK_OK;
 }
 
-extern "C" teuk_status teuk_set_resident(teuk_ctx* c, int halo) {
+extern "C" teuk_status teuk_set_resident_shape(teuk_ctx* c, int halo, int blocks_per_sm) {
     if (!c) return TEUK_EINVAL;
     if (halo < 0) TK_FAIL(c, TEUK_EINVAL, "halo must be >= 0");
+    if (blocks_per_sm < 1) TK_FAIL(c, TEUK_EINVAL, "blocks_per_sm must be >= 1");
     if (c->inst.size() != 1) TK_FAIL(c, TEUK_EINVAL, "resident launches serve single-instance contexts");
     if (halo > 0 && c->inst[0].slab)
         TK_FAIL(c, TEUK_EINVAL, "a slab takes its halo columns between steps: no resident launches");
-    return set_resident(c, c->inst[0], halo);
+    return set_resident(c, c->inst[0], halo, blocks_per_sm);
+}
+
+extern "C" teuk_status teuk_set_resident(teuk_ctx* c, int halo) {
+    return teuk_set_resident_shape(c, halo, 1);
 }
 
 extern "C" teuk_status teuk_step_n(teuk_ctx* c, int64_t n) {
@@ -1534,9 +1542,18 @@ extern "C" teuk_status teuk_autotune(teuk_ctx* c, int trial_steps, int* chosen) 
             }
             // resident launches, halo 1 .. 4 (circular orbits; a moving particle is stepped
             // one launch per step)
-            for (int hh = 1; hh <= 4 && !(I.src_on && I.sd.moving); ++hh) {
+            // (halo 1 .. 4, aiming at 1 .. 3 blocks per SM; a plan equal to one already
+            // timed is skipped; best_res holds halo + 16 (blocks per SM - 1))
+            for (int code = 1; code <= 4 + 16 * 2 && !(I.src_on && I.sd.moving); ++code) {
+                const int hh = code % 16, bps = code / 16 + 1;
+                if (hh < 1 || hh > 4) continue;
                 ResidentPlan plan;
-                if (!resident_plan(I.p.prec, I.p.n_rstar, I.pitch, hh, &plan)) continue;
+                if (!resident_plan(I.p.prec, I.p.n_rstar, I.pitch, hh, bps, &plan)) continue;
+                if (bps > 1) {
+                    ResidentPlan fewer;
+                    if (resident_plan(I.p.prec, I.p.n_rstar, I.pitch, hh, bps - 1, &fewer) && fewer.nb == plan.nb)
+                        continue;
+                }
                 unsigned char* xg = nullptr;
                 int* fl = nullptr;
                 const size_t xg_bytes = (size_t)nplanes * 2 * plan.nb * 2 * hh * I.pitch * 16;
@@ -1566,7 +1583,7 @@ extern "C" teuk_status teuk_autotune(teuk_ctx* c, int trial_steps, int* chosen) 
                     c->launches += 2;
                     if (ok && ms < best_ms) {
                         best_ms = ms;
-                        best_res[k] = hh;
+                        best_res[k] = code;
                     }
                 }
                 cudaGetLastError();
@@ -1594,7 +1611,7 @@ extern "C" teuk_status teuk_autotune(teuk_ctx* c, int trial_steps, int* chosen) 
     cudaEventDestroy(e1);
     for (int k = 0; k < ni; ++k) {
         c->inst[k].strip = best[k];
-        teuk_status st = set_resident(c, c->inst[k], best_res[k]);
+        teuk_status st = set_resident(c, c->inst[k], best_res[k] % 16, best_res[k] / 16 + 1);
         if (st) return st;
         if (chosen) chosen[k] = best_res[k] > 0 ? -best_res[k] : best[k];
     }

@@ -162,7 +162,7 @@ struct ResidentArgs {
 };
 constexpr int kResFlagStride = 32;   // ints between two blocks' flags (a 128-byte line each)
 // Launch shape of the resident kernel for one instance.
-struct ResidentPlan { int nb = 0, threads = 0, h = 0; size_t smem = 0; };
+struct ResidentPlan { int nb = 0, threads = 0, h = 0, bps = 1; size_t smem = 0; };
 
 __host__ __device__ inline size_t plane_elems(const InstDev& d) {
     return (size_t)d.nr * (size_t)d.pitch;
@@ -211,8 +211,9 @@ void launch_batched_step(cudaStream_t st, int prec, const BatchDev& b, int grid,
 int batched_grid(int prec, int threads);
 void launch_batched_extract(cudaStream_t st, int prec, const BatchDev& b, int max_nth);
 // teuk_resident.cu: whether (and how) an instance fits the resident kernel with halo h
-// (all blocks resident at once, one block per run of columns), and its launch
-bool resident_plan(int prec, int nr, int pitch, int h, ResidentPlan* plan);
+// (all blocks resident at once, one block per run of columns, aiming at bps blocks per
+// SM: with several, one block's halo wait overlaps another's arithmetic), and its launch
+bool resident_plan(int prec, int nr, int pitch, int h, int bps, ResidentPlan* plan);
 cudaError_t launch_resident(cudaStream_t st, const ResidentArgs& a, const ResidentPlan& plan);
 // teuk_aux.cu
 void launch_import_state(cudaStream_t st, const InstDev& d, int bin, const double* u);

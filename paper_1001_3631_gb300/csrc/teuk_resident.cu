@@ -33,6 +33,7 @@ namespace {
 
 constexpr int kResMaxThreads = 512;
 constexpr int kResMaxHalo = 4;             // steps between exchanges, at most
+constexpr int kResMaxBps = 4;              // blocks per SM a plan may aim at
 constexpr unsigned long long kResWaitNs = 1000000000ull;   // a halo wait gives up after 1 s
 
 __device__ __forceinline__ unsigned long long res_ns() {
@@ -382,13 +383,15 @@ static cudaError_t res_occupancy(int threads, size_t smem, int* per_sm) {
 }
 
 template <class P>
-static bool res_plan_p(int nr, int pitch, int h, ResidentPlan* plan) {
+static bool res_plan_p(int nr, int pitch, int h, int bps, ResidentPlan* plan) {
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return false;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int cols = nr - 2;
-    // the fewest columns per block such that all blocks are resident at once
-    for (int W = (cols + sms - 1) / (sms > 0 ? sms : 1); W <= cols; ++W) {
+    const int slots = (sms > 0 ? sms : 1) * bps;
+    // the fewest columns per block (from cols / (SMs x bps) up) such that all blocks are
+    // resident at once
+    for (int W = (cols + slots - 1) / slots; W <= cols; ++W) {
         const int nb = (cols + W - 1) / W;
         if (cols / nb < h) continue;                     // every block owns >= h columns
         const int ncol = W + 2 * h;
@@ -407,18 +410,19 @@ static bool res_plan_p(int nr, int pitch, int h, ResidentPlan* plan) {
             plan->threads = threads;
             plan->smem = smem;
             plan->h = h;
+            plan->bps = bps;
             return true;
         }
     }
     return false;
 }
 
-bool resident_plan(int prec, int nr, int pitch, int h, ResidentPlan* plan) {
-    if (h < 1 || h > kResMaxHalo || nr < 4) return false;
-    if (prec == 0) return res_plan_p<P64>(nr, pitch, h, plan);
-    if (prec == 1) return res_plan_p<P32>(nr, pitch, h, plan);
-    if (prec == 3) return res_plan_p<PD>(nr, pitch, h, plan);
-    return res_plan_p<PK>(nr, pitch, h, plan);
+bool resident_plan(int prec, int nr, int pitch, int h, int bps, ResidentPlan* plan) {
+    if (h < 1 || h > kResMaxHalo || nr < 4 || bps < 1 || bps > kResMaxBps) return false;
+    if (prec == 0) return res_plan_p<P64>(nr, pitch, h, bps, plan);
+    if (prec == 1) return res_plan_p<P32>(nr, pitch, h, bps, plan);
+    if (prec == 3) return res_plan_p<PD>(nr, pitch, h, bps, plan);
+    return res_plan_p<PK>(nr, pitch, h, bps, plan);
 }
 
 template <class P>

@@ -241,10 +241,11 @@ class TeukSolver:
         check(_lib.load().teuk_set_tiling(self.ctx, strip, steps_per_launch), self.ctx)
         self._steps_per_launch = steps_per_launch
 
-    def set_resident(self, halo=1):
+    def set_resident(self, halo=1, blocks_per_sm=1):
         """Resident launches (one cooperative launch per step() call, the grid held in
-        shared memory, boundary columns exchanged every ``halo`` steps); 0 turns them off."""
-        check(_lib.load().teuk_set_resident(self.ctx, int(halo)), self.ctx)
+        shared memory, boundary columns exchanged every ``halo`` steps, the column runs cut
+        for ``blocks_per_sm`` blocks per SM); halo 0 turns them off."""
+        check(_lib.load().teuk_set_resident_shape(self.ctx, int(halo), int(blocks_per_sm)), self.ctx)
 
     def kernel_launches(self):
         return _lib.load().teuk_kernel_launches(self.ctx)
@@ -262,8 +263,8 @@ class TeukSolver:
     def autotune(self, trial_steps=10, cache_path=None):
         """Strip length per instance from a cached table keyed by (GPU, launch mode, n_theta,
         precision, n_rstar bucket); entries missing from the table are timed by
-        teuk_autotune.  A negative entry (single instance stepped per call) selects resident
-        launches with that halo.  The launch mode is "step" for one instance stepped one launch per
+        teuk_autotune.  A negative entry -v (single instance stepped per call) selects
+        resident launches with halo v % 16 and v // 16 + 1 blocks per SM.  The launch mode is "step" for one instance stepped one launch per
         step, and for contexts that run the persistent kernels a signature of the whole
         set of instances (their best strips depend on one another)."""
         import hashlib
@@ -289,8 +290,8 @@ class TeukSolver:
         if all(k in table for k in keys):
             for i, k in enumerate(keys):
                 v = int(table[k])
-                if v < 0:   # resident launches with halo -v
-                    self.set_resident(-v)
+                if v < 0:   # resident launches: halo (-v) % 16, (-v) // 16 + 1 blocks per SM
+                    self.set_resident((-v) % 16, (-v) // 16 + 1)
                 else:
                     self.set_instance_tiling(i, v)
                     if self.n == 1 and self._steps_per_launch != 0:

@@ -134,3 +134,30 @@ def test_autotune_with_resident_candidates_keeps_results(tmp_path):
         s.sync()
     assert chosen[0] != 0
     assert np.array_equal(u, ref[0]) and np.array_equal(w, ref[1])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_kahan"])
+def test_resident_shapes_with_several_blocks_per_sm_are_bitwise(prec):
+    # shorter column runs (2 or 3 blocks per SM) change only the decomposition
+    params, r0, chunks = CASES[0]
+    u0 = inputs.random_state(64, 800, seed=21)
+    ref = run(params, r0, chunks, 0, u0, step0=3, prec=prec)
+    tried = 0
+    for halo, bps in ((1, 2), (2, 2), (1, 3)):
+        with TeukSolver(dict(params, prec=prec)) as s:
+            try:
+                s.set_resident(halo, bps)
+            except TeukError as e:
+                assert e.status == 1
+                continue
+            s.set_source(r0, inputs.amplitudes(400, seed=9))
+            s.set_state(u0, 3)
+            for n in chunks:
+                s.step(n)
+            u = s.get_state()
+            w, first = s.extract()
+            s.sync()
+        tried += 1
+        assert first == ref[2]
+        assert np.array_equal(u, ref[0]) and np.array_equal(w, ref[1]), (halo, bps)
+    assert tried >= 2
