@@ -1624,6 +1624,7 @@ extern "C" int64_t teuk_kernel_launches(const teuk_ctx* c) { return c ? c->launc
 
 extern "C" void teuk_destroy(teuk_ctx* c) {
     if (!c) return;
+    cudaStreamSynchronize(c->stream);   // no replay of the context's graphs is in flight
     {
         if (c->sum_buf) dfree(c, c->sum_buf, c->stream);
         Batch& B = c->batch;
