@@ -8,12 +8,15 @@
 // reverse step is
 //   lam'  = P lam^{n+1}
 //   mu    = C^T lam'                       (half nodes)
-//   lam^n = lam' + H^T mu + E^T gbar_n     (integer nodes), both in adj_step_kernel
+//   lam^n = lam' + H^T mu + E^T gbar_n     (integer nodes), all in one reverse-step kernel
 // and the source enters the gradients as
 //   dL/dA_n  = <mu_Pi, (dt/2) e_p P_half> + <lam'_Pi, dt e_c P_int>
 //   dL/dr0  += A_n (<mu_Pi, (dt/2) d(e_p P_half)/dr0> + <lam'_Pi, dt d(e_c P_int)/dr0>)
-// with e_p = e^{-i(omega t_n + phase0)}, e_c the same at t_n + dt/2.
-// Coefficients are the scaled tables of teuk_setup.cu (g, E1, E2, ep, em, E3); in
+// with e_p = e^{-i(omega t_n + phase0)}, e_c the same at t_n + dt/2 (the step stores
+// mu_Pi and lam'_Pi over the source window; adj_src_grad_kernel forms the sums).
+// Coefficients (g, E1, E2, ep, em, E3, scaled as in teuk_setup.cu) are read from the 2D
+// tables for FP64 and double-float instances and formed from the 1D tables, as the
+// forward kernels form them, for FP32 instances; in
 // the corrector's angular term  ep Phi~(j+1) + em Phi~(j-1) + (E3 - ep - em) Phi~(j)
 // the ghost rows fold back onto rows 0 and n_theta-1 with the sign of the pole
 // condition.  The co-state lam and mu are FP64 for FP64 instances; for FP32 instances
