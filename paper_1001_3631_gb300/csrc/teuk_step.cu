@@ -207,8 +207,8 @@ struct StepShared {
     }
 };
 
-// Slots of the ring: six for blocks of up to 256 rows, four for larger blocks (whose
-// slots are four times bigger).
+// Slots of the ring: six for blocks of up to 512 rows, four for larger blocks (whose
+// slots are up to four times bigger than those of 256 rows).
 constexpr int kRingS = 6, kRingL = 4;
 
 // One work item: the columns [c0, c1) of one instance for one step, one thread per row.
@@ -491,8 +491,9 @@ __device__ __forceinline__ bool strip_step(const InstDev& d, int64_t step, int b
     return true;
 }
 
-// Two register budgets: columns of up to 256 rows (the common case, P::blocks256
-// blocks per SM) and of up to 1024 rows.  Dynamic shared memory:
+// Three register budgets: columns of up to 256 rows (the common case, P::blocks256
+// blocks per SM), of up to 512 rows (one block per SM, 128 registers a thread) and of up
+// to 1024 rows.  Dynamic shared memory:
 // StepShared<P, R>::bytes(blockDim.x).
 // part (may be null): the block's columns are [part[b], part[b+1]) instead of the uniform
 // strips; it is written by the host before the launch sequence and never changes while
@@ -526,6 +527,12 @@ __device__ __forceinline__ void step_body(const InstDev& d, int64_t step, int bi
 template <class P, bool kMov>
 __global__ void __launch_bounds__(256, P::blocks256) step_kernel_s(InstDev d, int64_t step, int bin, int strip,
                                                                   const int* part) {
+    step_body<P, kRingS, kMov>(d, step, bin, strip, part);
+}
+
+template <class P, bool kMov>
+__global__ void __launch_bounds__(512, 1) step_kernel_m(InstDev d, int64_t step, int bin, int strip,
+                                                       const int* part) {
     step_body<P, kRingS, kMov>(d, step, bin, strip, part);
 }
 
@@ -691,6 +698,11 @@ static int grid_for(int threads) {
                                                       threads, StepShared<P, kRingS>::bytes(threads));
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, batched_step_kernel<P, 256, P::blocks256, kRingS, true>,
                                                       threads, StepShared<P, kRingS>::bytes(threads));
+    } else if (threads <= 512) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batched_step_kernel<P, 512, 1, kRingS, false>,
+                                                      threads, StepShared<P, kRingS>::bytes(threads));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, batched_step_kernel<P, 512, 1, kRingS, true>,
+                                                      threads, StepShared<P, kRingS>::bytes(threads));
     } else {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batched_step_kernel<P, 1024, 1, kRingL, false>,
                                                       threads, StepShared<P, kRingL>::bytes(threads));
@@ -712,6 +724,8 @@ template <class P, bool kMov>
 static void launch_batched_m(cudaStream_t st, const BatchDev& b, int grid, int threads) {
     if (threads <= 256)
         batched_step_kernel<P, 256, P::blocks256, kRingS, kMov><<<grid, threads, StepShared<P, kRingS>::bytes(threads), st>>>(b);
+    else if (threads <= 512)
+        batched_step_kernel<P, 512, 1, kRingS, kMov><<<grid, threads, StepShared<P, kRingS>::bytes(threads), st>>>(b);
     else
         batched_step_kernel<P, 1024, 1, kRingL, kMov><<<grid, threads, StepShared<P, kRingL>::bytes(threads), st>>>(b);
 }
@@ -755,6 +769,9 @@ static void launch_step_m(cudaStream_t st, const InstDev& d, int64_t step, int b
     if (threads <= 256) {
         cfg.dynamicSmemBytes = StepShared<P, kRingS>::bytes(threads);
         cudaLaunchKernelEx(&cfg, step_kernel_s<P, kMov>, d, step, bin, strip, part);
+    } else if (threads <= 512) {
+        cfg.dynamicSmemBytes = StepShared<P, kRingS>::bytes(threads);
+        cudaLaunchKernelEx(&cfg, step_kernel_m<P, kMov>, d, step, bin, strip, part);
     } else {
         cfg.dynamicSmemBytes = StepShared<P, kRingL>::bytes(threads);
         cudaLaunchKernelEx(&cfg, step_kernel_l<P, kMov>, d, step, bin, strip, part);
@@ -774,6 +791,9 @@ static int resident_p(int threads) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (threads <= 256)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, step_kernel_s<P, false>, threads,
+                                                      StepShared<P, kRingS>::bytes(threads));
+    else if (threads <= 512)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, step_kernel_m<P, false>, threads,
                                                       StepShared<P, kRingS>::bytes(threads));
     else
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, step_kernel_l<P, false>, threads,
@@ -800,11 +820,14 @@ void launch_step(cudaStream_t st, const InstDev& d, int64_t step, int bin, int s
 // current device; called when a context is created).
 template <class P, bool kMov>
 static cudaError_t prepare_m() {
-    const int s = (int)StepShared<P, kRingS>::bytes(256), l = (int)StepShared<P, kRingL>::bytes(1024);
+    const int s = (int)StepShared<P, kRingS>::bytes(256), m = (int)StepShared<P, kRingS>::bytes(512),
+              l = (int)StepShared<P, kRingL>::bytes(1024);
     const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
     cudaError_t e = cudaFuncSetAttribute(step_kernel_s<P, kMov>, a, s);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(step_kernel_m<P, kMov>, a, m);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(step_kernel_l<P, kMov>, a, l);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(batched_step_kernel<P, 256, P::blocks256, kRingS, kMov>, a, s);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(batched_step_kernel<P, 512, 1, kRingS, kMov>, a, m);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(batched_step_kernel<P, 1024, 1, kRingL, kMov>, a, l);
     return e;
 }
