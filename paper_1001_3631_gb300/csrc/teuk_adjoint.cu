@@ -249,7 +249,8 @@ __device__ __forceinline__ void adj_release_next() { asm volatile("griddepcontro
 __device__ __forceinline__ void adj_wait_prev() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 // kMaxT: the largest block this instance serves (256: columns of up to 256 rows, with
-// the register budget of several blocks per SM; 1024: taller columns)
+// the register budget of several blocks per SM; 512: up to 512 rows, one block per SM;
+// 1024: taller columns)
 template <typename T, typename R, int kMaxT>
 __global__ void __launch_bounds__(kMaxT) adj_step_kernel(InstDev d, CoLevel lin, const double2* gbar,
                                                          CoLevel lout, int strip, void* wh, void* wi) {
@@ -652,27 +653,36 @@ static int adj_resident(K kernel, int threads, size_t smem) {
     return (per > 0 ? per : 1) * (sms > 0 ? sms : 1);
 }
 
-// the largest dynamic shared memory a reverse-step kernel takes (columns of 1024 rows)
-template <class K>
-static void adj_allow_smem(K kernel, size_t bytes) {
-    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+// f(kernel, dynamic shared memory) with the reverse-step kernel built for blocks of t rows
+// (up to 256, 512 or 1024)
+template <class F>
+static void adj_dispatch(int prec, int t, F f) {
+    if (prec == 0 || prec == 3) {
+        const size_t sm = adj_smem<double>(t, false);
+        if (prec == 0) {
+            if (t <= 256) f(adj_step_kernel<double, double, 256>, sm);
+            else if (t <= 512) f(adj_step_kernel<double, double, 512>, sm);
+            else f(adj_step_kernel<double, double, 1024>, sm);
+        } else {
+            if (t <= 256) f(adj_step_kernel<DF, double, 256>, sm);
+            else if (t <= 512) f(adj_step_kernel<DF, double, 512>, sm);
+            else f(adj_step_kernel<DF, double, 1024>, sm);
+        }
+    } else {
+        const size_t sm = adj_smem<float>(t, true);
+        if (t <= 256) f(adj_step_kernel_f32<256>, sm);
+        else if (t <= 512) f(adj_step_kernel_f32<512>, sm);
+        else f(adj_step_kernel_f32<1024>, sm);
+    }
 }
 
 int adj_step_plan(const InstDev& d, int* strip) {
-    const int t = d.pitch;
-    if (d.prec == 0) adj_allow_smem(adj_step_kernel<double, double, 1024>, adj_smem<double>(1024, false));
-    else if (d.prec == 3) adj_allow_smem(adj_step_kernel<DF, double, 1024>, adj_smem<double>(1024, false));
-    else adj_allow_smem(adj_step_kernel_f32<1024>, adj_smem<float>(1024, true));
-    int res;
-    if (d.prec == 0)
-        res = t <= 256 ? adj_resident(adj_step_kernel<double, double, 256>, t, adj_smem<double>(t, false))
-                       : adj_resident(adj_step_kernel<double, double, 1024>, t, adj_smem<double>(t, false));
-    else if (d.prec == 3)
-        res = t <= 256 ? adj_resident(adj_step_kernel<DF, double, 256>, t, adj_smem<double>(t, false))
-                       : adj_resident(adj_step_kernel<DF, double, 1024>, t, adj_smem<double>(t, false));
-    else
-        res = t <= 256 ? adj_resident(adj_step_kernel_f32<256>, t, adj_smem<float>(t, true))
-                       : adj_resident(adj_step_kernel_f32<1024>, t, adj_smem<float>(t, true));
+    int res = 1;
+    adj_dispatch(d.prec, d.pitch, [&](auto kernel, size_t sm) {
+        // (blocks of more than 256 rows take more than the default 48 KB)
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        res = adj_resident(kernel, d.pitch, sm);
+    });
     int L = (d.nr + res - 1) / res;   // one wave of resident blocks, >= 4 columns each
     if (L < 4) L = 4;
     *strip = L;
@@ -698,21 +708,9 @@ static void adj_launch(cudaStream_t st, K kernel, int nb, int t, size_t sm, cons
 void launch_adj_step(cudaStream_t st, const InstDev& d, const CoLevel& lin, const double2* gbar,
                      const CoLevel& lout, int strip, void* wh, void* wi) {
     const int nb = (d.nr + strip - 1) / strip;
-    const int t = d.pitch;
-    if (d.prec == 0 || d.prec == 3) {
-        const size_t sm = adj_smem<double>(t, false);
-        if (d.prec == 0) {
-            if (t <= 256) adj_launch(st, adj_step_kernel<double, double, 256>, nb, t, sm, d, lin, gbar, lout, strip, wh, wi);
-            else adj_launch(st, adj_step_kernel<double, double, 1024>, nb, t, sm, d, lin, gbar, lout, strip, wh, wi);
-        } else {
-            if (t <= 256) adj_launch(st, adj_step_kernel<DF, double, 256>, nb, t, sm, d, lin, gbar, lout, strip, wh, wi);
-            else adj_launch(st, adj_step_kernel<DF, double, 1024>, nb, t, sm, d, lin, gbar, lout, strip, wh, wi);
-        }
-    } else {
-        const size_t sm = adj_smem<float>(t, true);
-        if (t <= 256) adj_launch(st, adj_step_kernel_f32<256>, nb, t, sm, d, lin, gbar, lout, strip, wh, wi);
-        else adj_launch(st, adj_step_kernel_f32<1024>, nb, t, sm, d, lin, gbar, lout, strip, wh, wi);
-    }
+    adj_dispatch(d.prec, d.pitch, [&](auto kernel, size_t sm) {
+        adj_launch(st, kernel, nb, d.pitch, sm, d, lin, gbar, lout, strip, wh, wi);
+    });
 }
 
 size_t adj_window_bytes(const InstDev& d) {

@@ -250,15 +250,16 @@ def test_checkpointed_loss_function_matches_waveform_function(prec):
     assert float(R.grad) == pytest.approx(float(R2.grad), rel=max(tol, 1e-12))
 
 
+@pytest.mark.parametrize("nth", [400, 600])
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("fp32_kahan", 1e-5)])
-def test_tall_columns_use_the_large_block_kernels(orc, prec, tol):
-    # n_theta = 600: blocks of 608 threads, the reverse-step kernels built for columns of
-    # up to 1024 rows (their shared memory exceeds the default 48 KB)
-    params = dict(SMALL, m=2, n_rstar=24, n_theta=600, rstar_min=-10.0, rstar_max=20.0,
+def test_tall_columns_use_the_large_block_kernels(orc, prec, tol, nth):
+    # n_theta = 400 / 600: blocks of 416 / 608 threads, the reverse-step kernels built for
+    # columns of up to 512 / 1024 rows (their shared memory exceeds the default 48 KB)
+    params = dict(SMALL, m=2, n_rstar=24, n_theta=nth, rstar_min=-10.0, rstar_max=20.0,
                   rstar_ext=12.0)
     n, r0 = 6, 6.0
     amps = inputs.amplitudes(n, seed=5)
-    gw = np.random.default_rng(3).standard_normal((n, 600, 2))
+    gw = np.random.default_rng(3).standard_normal((n, nth, 2))
     p = oracle_params(orc, params, r0)
     ga_o, gr_o, _ = orc.adjoint(p, orc.orbit_source(p), gw, amps=amps)
     with TeukSolver(dict(params, prec=prec, wave_capacity=n + 1)) as s:
