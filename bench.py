@@ -344,7 +344,9 @@ def single_mode_leg(steps=2000):
     """The 800 x 64 single mode (51,200 points, L2-resident): one kernel per step, the
     persistent batched kernel replayed from a CUDA graph (strip length from the
     autotuner), and resident launches (the grid in shared memory, one cooperative launch
-    per call; halo 1 .. 4 and 1 .. 3 blocks per SM timed, the fastest reported), for FP64,
+    per call; halo 1 .. 4 and 1 .. 3 blocks per SM timed, the fastest reported), blocked
+    launches (1 .. 4 steps a launch of the grid held in shared memory, no exchange; shapes
+    timed the same way), for FP64,
     the FP64-equivalent
     double-float path, FP32-Kahan and FP32.  hbm_frac is the algorithmic bytes per update
     against the measured HBM copy bandwidth (the grid is L2-resident, so this is the
@@ -359,7 +361,7 @@ def single_mode_leg(steps=2000):
     frac = {}
     for prec in ("fp64", "fp64_df", "fp32_kahan", "fp32"):
         bpu = FP32_BYTES_PER_UPDATE if prec == "fp32" else 64
-        for mode in ("per_step", "persistent", "resident"):
+        for mode in ("per_step", "persistent", "resident", "blocked"):
             stream = torch.cuda.Stream()
             with torch.cuda.stream(stream):
                 s = TeukSolver(dict(cfg["params"], prec=prec), stream=stream)
@@ -371,11 +373,14 @@ def single_mode_leg(steps=2000):
                     with tempfile.TemporaryDirectory() as td:
                         out["%s_persistent_strip" % prec] = int(
                             s.autotune(trial_steps=20, cache_path=os.path.join(td, "t.json"))[0])
-                elif mode == "resident":
+                elif mode in ("resident", "blocked"):
                     best = None
                     for h, bps in [(h, b) for b in (1, 2, 3) for h in (1, 2, 3, 4)]:
                         try:
-                            s.set_resident(h, bps)
+                            if mode == "resident":
+                                s.set_resident(h, bps)
+                            else:
+                                s.set_blocked(h, bps)
                         except Exception:
                             continue
                         s.step(200)
@@ -388,9 +393,12 @@ def single_mode_leg(steps=2000):
                         ms = e0.elapsed_time(e1)
                         if best is None or ms < best[0]:
                             best = (ms, h, bps)
-                    s.set_resident(best[1], best[2])
-                    out["%s_resident_halo" % prec] = best[1]
-                    out["%s_resident_blocks_per_sm" % prec] = best[2]
+                    if mode == "resident":
+                        s.set_resident(best[1], best[2])
+                    else:
+                        s.set_blocked(best[1], best[2])
+                    out["%s_%s_halo" % (prec, mode)] = best[1]
+                    out["%s_%s_blocks_per_sm" % (prec, mode)] = best[2]
                 s.step(steps)
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 stream.synchronize()
@@ -408,8 +416,8 @@ def single_mode_leg(steps=2000):
     out["hbm_frac"] = frac
     alu_cap = FP64_PEAK_TFLOPS * 1e12 / FP64_FLOPS_PER_UPDATE
     out["fp64_alu_cap"] = alu_cap
-    out["fp64_alu_frac"] = {m: out["fp64_" + m] / alu_cap for m in ("per_step", "persistent", "resident")}
-    out["best"] = {p: max(("per_step", "persistent", "resident"), key=lambda m: out["%s_%s" % (p, m)])
+    out["fp64_alu_frac"] = {m: out["fp64_" + m] / alu_cap for m in ("per_step", "persistent", "resident", "blocked")}
+    out["best"] = {p: max(("per_step", "persistent", "resident", "blocked"), key=lambda m: out["%s_%s" % (p, m)])
                    for p in ("fp64", "fp64_df", "fp32_kahan", "fp32")}
     return out
 

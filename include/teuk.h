@@ -315,6 +315,18 @@ teuk_status teuk_set_tiling(teuk_ctx* ctx, int strip, int steps_per_launch);
 teuk_status teuk_set_resident(teuk_ctx* ctx, int halo);
 teuk_status teuk_set_resident_shape(teuk_ctx* ctx, int halo, int blocks_per_sm);
 
+/* Blocked launches for a single-instance context whose grid fits the GPU's shared memory
+ * (a not-in-the-paper launch form for small grids): each launch advances `steps` steps
+ * (the last one of a teuk_step_n the rest), every block holding its run of r* columns with
+ * `steps` halo columns on each side in shared memory and computing the steps on the
+ * shrinking region, the halos read from the previous launch's output; there is no
+ * exchange and no wait between blocks (the launch boundary, with programmatic dependent
+ * launch, is the synchronisation), and each launch writes the other state buffer.  The
+ * results equal those of one launch per step.  Runs cut for blocks_per_sm blocks per SM
+ * as in teuk_set_resident_shape.  steps = 0 turns it off; steps is at most 4; a shape that
+ * does not fit is TEUK_EINVAL.  Allocates as teuk_set_resident does. */
+teuk_status teuk_set_blocked(teuk_ctx* ctx, int steps, int blocks_per_sm);
+
 /* Strip length (r* columns per block) of one instance (0 = back to the context default). */
 teuk_status teuk_set_instance_tiling(teuk_ctx* ctx, int instance, int strip);
 

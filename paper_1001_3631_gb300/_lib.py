@@ -65,6 +65,7 @@ _PROTOS = {
     "teuk_set_tiling": (_I, [_P, _I, _I]),
     "teuk_set_resident": (_I, [_P, _I]),
     "teuk_set_resident_shape": (_I, [_P, _I, _I]),
+    "teuk_set_blocked": (_I, [_P, _I, _I]),
     "teuk_set_allocator": (_I, [_P, _P, _P]),
     "teuk_slab_halo_bytes": (_I, [_P, _I, ctypes.POINTER(_L)]),
     "teuk_slab_export": (_I, [_P, _I, _I, _P]),

@@ -72,6 +72,7 @@ struct Instance {
     // flags (nb + 1 ints: the blocks' flags, then the abort flag)
     int res_h = 0;
     int res_bps = 1;
+    bool res_blocked = false;   // blocked launches: h steps a launch, no exchange (teuk_set_blocked)
     ResidentPlan res_plan;
     unsigned char* res_xg = nullptr;
     int* res_flags = nullptr;
@@ -1047,9 +1048,10 @@ namespace {
 
 // Plan the resident launch of instance I with halo h, aiming at bps blocks per SM, and
 // (re)allocate its exchange slots and flags; h = 0 turns resident launches off.
-teuk_status set_resident(teuk_ctx* c, Instance& I, int h, int bps) {
+teuk_status set_resident(teuk_ctx* c, Instance& I, int h, int bps, bool blocked = false) {
     if (h == 0) {
         I.res_h = 0;
+        I.res_blocked = false;
         return TEUK_OK;
     }
     ResidentPlan plan;
@@ -1070,6 +1072,7 @@ teuk_status set_resident(teuk_ctx* c, Instance& I, int h, int bps) {
     I.res_plan = plan;
     I.res_h = h;
     I.res_bps = bps;
+    I.res_blocked = blocked;
     return TEUK_OK;
 }
 
@@ -1088,11 +1091,42 @@ teuk_status resident_step(teuk_ctx* c, Instance& I, int64_t n) {
     a.flags = I.res_flags;
     a.abort = I.res_flags + (size_t)kResFlagStride * I.res_plan.nb;
     a.skip_publish = (int)c->inject_skip_item;
+    a.no_wait = 0;
     TK_CUDA(c, cudaMemsetAsync(I.res_flags, 0, sizeof(int) * kResFlagStride * (I.res_plan.nb + 1), c->stream));
     TK_CUDA(c, launch_resident(c->stream, a, I.res_plan));
     c->launches++;
     I.step += n;
     I.cur = a.obin;
+    do_extract(c, I);
+    return TEUK_OK;
+}
+
+// n steps of a single instance in blocked launches: each takes at most h steps of the grid
+// held in shared memory, reading its halo columns from the previous launch's output, and
+// writes the other buffer (the launch boundary is the synchronisation: no flag waits);
+// then the record of the final level.
+teuk_status blocked_step(teuk_ctx* c, Instance& I, int64_t n) {
+    for (int64_t done = 0; done < n;) {
+        const int64_t k = std::min<int64_t>(n - done, I.res_plan.h);
+        ResidentArgs a{};
+        a.d = dev_of(c, I);
+        a.step0 = I.step;
+        a.bin = I.cur;
+        a.obin = 1 - I.cur;
+        a.n = k;
+        a.h = I.res_plan.h;
+        a.nb = I.res_plan.nb;
+        a.xg = I.res_xg;
+        a.flags = I.res_flags;
+        a.abort = I.res_flags + (size_t)kResFlagStride * I.res_plan.nb;
+        a.skip_publish = -1;
+        a.no_wait = 1;
+        TK_CUDA(c, launch_resident(c->stream, a, I.res_plan, false));
+        c->launches++;
+        I.step += k;
+        I.cur = a.obin;
+        done += k;
+    }
     do_extract(c, I);
     return TEUK_OK;
 }
@@ -1124,6 +1158,16 @@ extern "C" teuk_status teuk_set_resident(teuk_ctx* c, int halo) {
     return teuk_set_resident_shape(c, halo, 1);
 }
 
+extern "C" teuk_status teuk_set_blocked(teuk_ctx* c, int steps, int blocks_per_sm) {
+    if (!c) return TEUK_EINVAL;
+    if (steps < 0) TK_FAIL(c, TEUK_EINVAL, "steps must be >= 0");
+    if (blocks_per_sm < 1) TK_FAIL(c, TEUK_EINVAL, "blocks_per_sm must be >= 1");
+    if (c->inst.size() != 1) TK_FAIL(c, TEUK_EINVAL, "blocked launches serve single-instance contexts");
+    if (steps > 0 && c->inst[0].slab)
+        TK_FAIL(c, TEUK_EINVAL, "a slab takes its halo columns between steps: no blocked launches");
+    return set_resident(c, c->inst[0], steps, blocks_per_sm, true);
+}
+
 extern "C" teuk_status teuk_step_n(teuk_ctx* c, int64_t n) {
     if (!c) return TEUK_EINVAL;
     if (n < 0) TK_FAIL(c, TEUK_EINVAL, "n < 0");
@@ -1132,7 +1176,7 @@ extern "C" teuk_status teuk_step_n(teuk_ctx* c, int64_t n) {
     Instance& I0 = c->inst[0];
     if (I0.res_h > 0 && !(I0.src_on && I0.sd.moving)) {   // a moving particle: per-step launches
         const int64_t s0 = I0.step;
-        teuk_status st = resident_step(c, I0, n);
+        teuk_status st = I0.res_blocked ? blocked_step(c, I0, n) : resident_step(c, I0, n);
         if (st) return st;
         if (I0.wave_hi != s0 + 1 || I0.wave_lo == I0.wave_hi) I0.wave_lo = s0;
         I0.wave_hi = I0.step + 1;

@@ -159,6 +159,8 @@ struct ResidentArgs {
     int* abort;           // set when a wait gives up
     int skip_publish;     // testing aid (-1: none): this block never publishes its exchanges,
                           // so its neighbours' waits run out
+    int no_wait;          // blocked launches (n <= h, obin != bin): no exchange and no wait
+                          // before the final level is written (no block reads buffer obin)
 };
 constexpr int kResFlagStride = 32;   // ints between two blocks' flags (a 128-byte line each)
 // Launch shape of the resident kernel for one instance.
@@ -214,7 +216,10 @@ void launch_batched_extract(cudaStream_t st, int prec, const BatchDev& b, int ma
 // (all blocks resident at once, one block per run of columns, aiming at bps blocks per
 // SM: with several, one block's halo wait overlaps another's arithmetic), and its launch
 bool resident_plan(int prec, int nr, int pitch, int h, int bps, ResidentPlan* plan);
-cudaError_t launch_resident(cudaStream_t st, const ResidentArgs& a, const ResidentPlan& plan);
+// cooperative: one launch for a whole teuk_step_n (blocks wait on one another); otherwise a
+// blocked launch of at most h steps (a.no_wait), issued with programmatic dependent launch
+cudaError_t launch_resident(cudaStream_t st, const ResidentArgs& a, const ResidentPlan& plan,
+                            bool cooperative = true);
 // teuk_aux.cu
 void launch_import_state(cudaStream_t st, const InstDev& d, int bin, const double* u);
 void launch_export_state(cudaStream_t st, const InstDev& d, int bin, double* u);

@@ -144,16 +144,12 @@ __global__ void __launch_bounds__(kResMaxThreads, 1) resident_kernel(ResidentArg
         }
     };
 
-    // ---- start: the state of local columns [0, ncol) that exist, from buffer bin, and the
-    // coefficients of every thread-column's half node col+1/2 and node col
-    {
-        const unsigned char* in[2] = {(const unsigned char*)d.buf[r.bin][0],
-                                      (const unsigned char*)d.buf[r.bin][P::planes - 1]};
-        for (int idx = t; idx < ncol * pitch; idx += blockDim.x) {
-            const int q = idx / pitch, jj = idx % pitch, cc = c0 - h + q;
-            if (cc >= 0 && cc <= nr - 1) copy_in(in, (size_t)cc * pitch + jj, sidx(q, jj), false, plane_elems(d));
-        }
-    }
+    // ---- start: the coefficients of every thread-column's half node col+1/2 and node col
+    // (constant data), then the state of the local columns [0, ncol) that exist, from
+    // buffer bin.  A blocked launch releases the next one at once and waits for the
+    // previous one (griddepcontrol; no-ops for a launch without programmatic dependence)
+    // only before it touches the state.
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     RowTab<P> rt;
     rt.load(d.thtab, j, row_ok);
     for (int k = k0; k < nk; k += KT) {
@@ -174,6 +170,15 @@ __global__ void __launch_bounds__(kResMaxThreads, 1) resident_kernel(ResidentArg
         } else {
             coefs64(d, true, col, j, (double*)mine);
             coefs64(d, false, col, j, (double*)(mine + kNCoef));
+        }
+    }
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    {
+        const unsigned char* in[2] = {(const unsigned char*)d.buf[r.bin][0],
+                                      (const unsigned char*)d.buf[r.bin][P::planes - 1]};
+        for (int idx = t; idx < ncol * pitch; idx += blockDim.x) {
+            const int q = idx / pitch, jj = idx % pitch, cc = c0 - h + q;
+            if (cc >= 0 && cc <= nr - 1) copy_in(in, (size_t)cc * pitch + jj, sidx(q, jj), false, plane_elems(d));
         }
     }
     // source: does this block meet the window (its local columns, halos included)?
@@ -363,7 +368,7 @@ __global__ void __launch_bounds__(kResMaxThreads, 1) resident_kernel(ResidentArg
     // (the record of the final level is taken by the extraction kernel after the launch)
     // ---- end: the owned columns (and the grid's boundary columns at the two ends) into
     // buffer obin, once the neighbours have read their initial halos from buffer bin
-    if (!wait_neighbours(1)) return;
+    if (!r.no_wait && !wait_neighbours(1)) return;
     unsigned char* out[2] = {(unsigned char*)d.buf[r.obin][0], (unsigned char*)d.buf[r.obin][P::planes - 1]};
     const int qlo = b == 0 ? h - 1 : h, qhi = (b == r.nb - 1) ? ncol - h + 1 : ncol - h;
     for (int idx = t; idx < (qhi - qlo) * pitch; idx += blockDim.x) {
@@ -426,19 +431,33 @@ bool resident_plan(int prec, int nr, int pitch, int h, int bps, ResidentPlan* pl
 }
 
 template <class P>
-static cudaError_t launch_res_p(cudaStream_t st, const ResidentArgs& a, const ResidentPlan& plan) {
+static cudaError_t launch_res_p(cudaStream_t st, const ResidentArgs& a, const ResidentPlan& plan,
+                                bool cooperative) {
     ResidentArgs arg = a;
-    void* params[] = {&arg};
-    return cudaLaunchCooperativeKernel((const void*)resident_kernel<P>, dim3(plan.nb), dim3(plan.threads),
-                                       params, plan.smem, st);
+    if (cooperative) {
+        void* params[] = {&arg};
+        return cudaLaunchCooperativeKernel((const void*)resident_kernel<P>, dim3(plan.nb), dim3(plan.threads),
+                                           params, plan.smem, st);
+    }
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(plan.nb);
+    cfg.blockDim = dim3(plan.threads);
+    cfg.dynamicSmemBytes = plan.smem;
+    cfg.stream = st;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, resident_kernel<P>, arg);
 }
 
-cudaError_t launch_resident(cudaStream_t st, const ResidentArgs& a, const ResidentPlan& plan) {
+cudaError_t launch_resident(cudaStream_t st, const ResidentArgs& a, const ResidentPlan& plan, bool cooperative) {
     switch (a.d.prec) {
-        case 0: return launch_res_p<P64>(st, a, plan);
-        case 1: return launch_res_p<P32>(st, a, plan);
-        case 3: return launch_res_p<PD>(st, a, plan);
-        default: return launch_res_p<PK>(st, a, plan);
+        case 0: return launch_res_p<P64>(st, a, plan, cooperative);
+        case 1: return launch_res_p<P32>(st, a, plan, cooperative);
+        case 3: return launch_res_p<PD>(st, a, plan, cooperative);
+        default: return launch_res_p<PK>(st, a, plan, cooperative);
     }
 }
 

@@ -247,6 +247,11 @@ class TeukSolver:
         for ``blocks_per_sm`` blocks per SM); halo 0 turns them off."""
         check(_lib.load().teuk_set_resident_shape(self.ctx, int(halo), int(blocks_per_sm)), self.ctx)
 
+    def set_blocked(self, steps=2, blocks_per_sm=1):
+        """Blocked launches (each launch advances ``steps`` steps of the grid held in shared
+        memory, halos from the previous launch's output, no exchange); 0 turns them off."""
+        check(_lib.load().teuk_set_blocked(self.ctx, int(steps), int(blocks_per_sm)), self.ctx)
+
     def kernel_launches(self):
         return _lib.load().teuk_kernel_launches(self.ctx)
 

@@ -161,3 +161,33 @@ def test_resident_shapes_with_several_blocks_per_sm_are_bitwise(prec):
         assert first == ref[2]
         assert np.array_equal(u, ref[0]) and np.array_equal(w, ref[1]), (halo, bps)
     assert tried >= 2
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("case", [0, 1, 3])
+def test_blocked_launches_equal_per_step_launches_bitwise(prec, case):
+    # teuk_set_blocked: each launch advances up to k steps of the grid held in shared
+    # memory, the halos read from the previous launch's output; chunks leave remainders
+    params, r0, chunks = CASES[case]
+    nth, nr = params["n_theta"], params["n_rstar"]
+    u0 = inputs.random_state(nth, nr, seed=31 + case)
+    ref = run(params, r0, chunks, 0, u0, step0=3, prec=prec)
+    tried = 0
+    for k, bps in ((1, 1), (2, 1), (3, 2), (4, 1)):
+        with TeukSolver(dict(params, prec=prec)) as s:
+            try:
+                s.set_blocked(k, bps)
+            except TeukError as e:
+                assert e.status == 1
+                continue
+            s.set_source(r0, inputs.amplitudes(400, seed=9))
+            s.set_state(u0, 3)
+            for n in chunks:
+                s.step(n)
+            u = s.get_state()
+            w, first = s.extract()
+            s.sync()
+        tried += 1
+        assert first == ref[2]
+        assert np.array_equal(u, ref[0]) and np.array_equal(w, ref[1]), (k, bps)
+    assert tried >= 1
