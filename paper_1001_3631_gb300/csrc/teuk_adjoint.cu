@@ -99,8 +99,8 @@ __device__ __forceinline__ void kahan_node(float2& v, float2& c, Z<float> dlt) {
 // lam = E^T gbar (the start of the reverse sweep).
 template <typename R>
 __global__ void adj_init_kernel(InstDev d, const double2* gbar, CoLevel out) {
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
-    int i = blockIdx.y;
+    int j = blockIdx.y * blockDim.x + threadIdx.x;   // theta row
+    int i = blockIdx.x;                              // r* column
     if (j >= d.pitch || i >= d.nr) return;
     size_t o = node_index(d, i, j);
     Z<double> a = {0, 0};
@@ -632,7 +632,7 @@ __global__ void ordered_sum_kernel(const double* v, int64_t n, double* out) {
 // ------------------------------------------------------------------ launchers
 
 void launch_adj_init(cudaStream_t st, const InstDev& d, const double2* gbar, const CoLevel& out) {
-    dim3 g((d.pitch + 127) / 128, d.nr);
+    dim3 g(d.nr, (d.pitch + 127) / 128);
     if (d.prec == 0 || d.prec == 3) adj_init_kernel<double><<<g, 128, 0, st>>>(d, gbar, out);
     else adj_init_kernel<float><<<g, 128, 0, st>>>(d, gbar, out);
 }

@@ -12,8 +12,8 @@ namespace teuk {
 // about 2^-48 relative; the double-float state as hi = fl32(v), lo = fl32(v - hi).
 template <class P>
 __global__ void import_state_kernel(InstDev d, int b, const double* u) {
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
-    int i = blockIdx.y;
+    int j = blockIdx.y * blockDim.x + threadIdx.x;   // theta row
+    int i = blockIdx.x;                              // r* column
     if (i >= d.nr || j >= d.nth) return;
     size_t np = (size_t)d.nr * d.nth, q = (size_t)j * d.nr + i, o = node_index(d, i, j);
     double v[4] = {u[q], u[np + q], u[2 * np + q], u[3 * np + q]};
@@ -40,8 +40,8 @@ __global__ void import_state_kernel(InstDev d, int b, const double* u) {
 
 template <class P>
 __global__ void export_state_kernel(InstDev d, int b, double* u) {
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
-    int i = blockIdx.y;
+    int j = blockIdx.y * blockDim.x + threadIdx.x;   // theta row
+    int i = blockIdx.x;                              // r* column
     if (i >= d.nr || j >= d.nth) return;
     size_t np = (size_t)d.nr * d.nth, q = (size_t)j * d.nr + i, o = node_index(d, i, j);
     NodeV<P> n = Planes<P>::of(d, b).load(o);
@@ -53,8 +53,8 @@ __global__ void export_state_kernel(InstDev d, int b, double* u) {
 // Sets ST_NONFINITE if any state value of buffer b is NaN or infinite.
 template <class P>
 __global__ void scan_finite_kernel(InstDev d, int b) {
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
-    int i = blockIdx.y;
+    int j = blockIdx.y * blockDim.x + threadIdx.x;   // theta row
+    int i = blockIdx.x;                              // r* column
     if (i >= d.nr || j >= d.nth) return;
     NodeV<P> n = Planes<P>::of(d, b).load(node_index(d, i, j));
     double v[4];
@@ -88,7 +88,7 @@ __global__ void zero_kernel(double* p, size_t n) {
 }
 
 void launch_import_state(cudaStream_t st, const InstDev& d, int bin, const double* u) {
-    dim3 g((d.nth + 127) / 128, d.nr);
+    dim3 g(d.nr, (d.nth + 127) / 128);
     if (d.prec == 0) import_state_kernel<P64><<<g, 128, 0, st>>>(d, bin, u);
     else if (d.prec == 1) import_state_kernel<P32><<<g, 128, 0, st>>>(d, bin, u);
     else if (d.prec == 3) import_state_kernel<PD><<<g, 128, 0, st>>>(d, bin, u);
@@ -96,7 +96,7 @@ void launch_import_state(cudaStream_t st, const InstDev& d, int bin, const doubl
 }
 
 void launch_export_state(cudaStream_t st, const InstDev& d, int bin, double* u) {
-    dim3 g((d.nth + 127) / 128, d.nr);
+    dim3 g(d.nr, (d.nth + 127) / 128);
     if (d.prec == 0) export_state_kernel<P64><<<g, 128, 0, st>>>(d, bin, u);
     else if (d.prec == 1) export_state_kernel<P32><<<g, 128, 0, st>>>(d, bin, u);
     else if (d.prec == 3) export_state_kernel<PD><<<g, 128, 0, st>>>(d, bin, u);
@@ -104,7 +104,7 @@ void launch_export_state(cudaStream_t st, const InstDev& d, int bin, double* u) 
 }
 
 void launch_scan_finite(cudaStream_t st, const InstDev& d, int bin) {
-    dim3 g((d.nth + 127) / 128, d.nr);
+    dim3 g(d.nr, (d.nth + 127) / 128);
     if (d.prec == 0) scan_finite_kernel<P64><<<g, 128, 0, st>>>(d, bin);
     else if (d.prec == 1) scan_finite_kernel<P32><<<g, 128, 0, st>>>(d, bin);
     else if (d.prec == 3) scan_finite_kernel<PD><<<g, 128, 0, st>>>(d, bin);

@@ -104,8 +104,8 @@ template <typename T>
 __global__ void coef_kernel(double M, double a, int s, int m, double rstar_min, double drs,
                             double dth, double dt, int nr, int nth, int pitch,
                             const double* x_int, const double* x_half, T* coef_h, T* coef_i) {
-    int j = blockIdx.x * blockDim.x + threadIdx.x;   // theta row (fastest in memory)
-    int i = blockIdx.y;                              // r* column
+    int j = blockIdx.y * blockDim.x + threadIdx.x;   // theta row (fastest in memory)
+    int i = blockIdx.x;                              // r* column (grid x: up to 2^31 - 1)
     if (j >= pitch || i >= nr) return;
     size_t pl = (size_t)nr * pitch;
     size_t o = (size_t)i * pitch + j;
@@ -375,7 +375,7 @@ void launch_coefficients(cudaStream_t st, int prec, double M, double a, int s, i
                          double rstar_min, double drs, double dth, double dt, int nr, int nth,
                          int pitch, const double* x_int, const double* x_half, void* coef_h,
                          void* coef_i) {
-    dim3 g((pitch + 127) / 128, nr);
+    dim3 g(nr, (pitch + 127) / 128);
     if (prec == 0)
         coef_kernel<double><<<g, 128, 0, st>>>(M, a, s, m, rstar_min, drs, dth, dt, nr, nth, pitch,
                                                x_int, x_half, (double*)coef_h, (double*)coef_i);

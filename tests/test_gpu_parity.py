@@ -280,3 +280,16 @@ def test_largest_theta_resolution(orc, prec, tol):
     for persistent in (False, True):
         ug, wg, _ = gpu_run(params, 6.0, 12, u0, prec=prec, persistent=persistent)
         assert rel(ug, uo) <= tol and rel(wg, wo) <= tol, (persistent, rel(ug, uo), rel(wg, wo))
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", FP64_TOL), ("fp32_kahan", 1e-6)])
+@pytest.mark.parametrize("persistent", [False, True])
+def test_long_radial_grid(orc, prec, tol, persistent):
+    # a long, thin grid (65536 columns of 8 rows, a = 0.99): many blocks and work items,
+    # the source window deep inside, the extraction near the far end
+    params = dict(s=-2, m=2, a=0.99, rstar_min=-300.0, rstar_max=2000.0, n_rstar=65536, n_theta=8,
+                  rstar_ext=1990.0, dt_rule=1, courant=0.5)
+    u0 = inputs.smooth_state(8, 65536, seed=17)
+    uo, wo = oracle_run(orc, params, 12.0, 25, u0)
+    ug, wg, _ = gpu_run(params, 12.0, 25, u0, prec=prec, persistent=persistent)
+    assert rel(ug, uo) <= tol and rel(wg, wo) <= tol, (rel(ug, uo), rel(wg, wo))
