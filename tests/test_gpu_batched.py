@@ -209,3 +209,36 @@ def test_batched_uneven_workload_128_instances(orc):
         p = orc.params(**inst["params"], r0=inst["r0"])
         uo, wo = orc.run(p, None, 3, orc.orbit_source(p))
         assert rel(got[k], uo) <= 1e-6
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_kahan"])
+def test_batched_block_size_classes_up_to_1024_rows(prec):
+    # one context with columns of 8, 300, 600 and 1024 rows: the persistent kernels built
+    # for blocks of up to 256, 512 and 1024 rows in one replayed graph, each instance
+    # bitwise equal to its own run
+    tall = [dict(params=dict(s=-2, m=m, a=0.6, rstar_min=-10.0, rstar_max=20.0, n_rstar=nr, n_theta=nth,
+                             rstar_ext=15.0, dt_rule=1, courant=0.5), r0=6.0, step0=k)
+            for k, (m, nr, nth) in enumerate(((2, 90, 8), (1, 40, 300), (3, 30, 600), (2, 24, 1024)))]
+    steps = [9, 4]
+    with TeukSolver([dict(i["params"], prec=prec) for i in tall]) as s:
+        for k, inst in enumerate(tall):
+            s.set_source(inst["r0"], inputs.amplitudes(100, seed=k + 1), instance=k)
+            u0 = inputs.random_state(inst["params"]["n_theta"], inst["params"]["n_rstar"], seed=5 + k)
+            s.set_state(u0, inst["step0"], instance=k)
+        for n in steps:
+            s.step(n)
+        got = [(s.get_state(k), s.extract(instance=k)) for k in range(len(tall))]
+        s.sync()
+    for k, inst in enumerate(tall):
+        with TeukSolver(dict(inst["params"], prec=prec)) as s:
+            s.set_source(inst["r0"], inputs.amplitudes(100, seed=k + 1))
+            u0 = inputs.random_state(inst["params"]["n_theta"], inst["params"]["n_rstar"], seed=5 + k)
+            s.set_state(u0, inst["step0"])
+            for n in steps:
+                s.step(n)
+            u = s.get_state()
+            w, first = s.extract()
+            s.sync()
+        assert got[k][1][1] == first
+        assert np.array_equal(got[k][0], u), k
+        assert np.array_equal(got[k][1][0], w), k
