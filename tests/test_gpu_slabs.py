@@ -25,9 +25,17 @@ GRIDS = [
 STEPS = 30
 
 
-def unsplit(params, prec, u0):
-    with TeukSolver(dict(params, prec=prec, wave_capacity=STEPS + 1)) as s:
+def set_src(s, moving):
+    if moving:   # an eccentric, inclined path (per-step source tables in local columns)
+        traj = inputs.eccentric_trajectory(2 * STEPS + 2, s.time()[1], semi_latus=7.0, ecc=0.5, incl=0.5)
+        s.set_trajectory(traj)
+    else:
         s.set_source(8.0, inputs.amplitudes(STEPS, seed=4))
+
+
+def unsplit(params, prec, u0, moving=False):
+    with TeukSolver(dict(params, prec=prec, wave_capacity=STEPS + 1)) as s:
+        set_src(s, moving)
         s.set_state(u0, 0)
         s.step(STEPS)
         u = s.get_state()
@@ -36,19 +44,20 @@ def unsplit(params, prec, u0):
     return u, w
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32_kahan", "fp64_df"])
-@pytest.mark.parametrize("g", range(len(GRIDS)))
-def test_three_slabs_on_one_gpu_equal_the_unsplit_run(prec, g):
+@pytest.mark.parametrize("prec,g,moving", [(p, g, False) for p in ("fp64", "fp32_kahan", "fp64_df")
+                                           for g in range(len(GRIDS))] +
+                         [("fp64", 0, True), ("fp32_kahan", 0, True)])
+def test_three_slabs_on_one_gpu_equal_the_unsplit_run(prec, g, moving):
     import torch
     params = GRIDS[g]
     nr, nth = params["n_rstar"], params["n_theta"]
     u0 = inputs.smooth_state(nth, nr, seed=23)
-    ref_u, ref_w = unsplit(params, prec, u0)
+    ref_u, ref_w = unsplit(params, prec, u0, moving)
     parts = slabs.partition(nr, 3)
     sv = []
     for c0, n in parts:
         s = TeukSolver(dict(params, prec=prec, wave_capacity=STEPS + 1, slab_col0=c0, slab_ncols=n))
-        s.set_source(8.0, inputs.amplitudes(STEPS, seed=4))
+        set_src(s, moving)
         s.set_state(np.ascontiguousarray(u0[:, :, c0 - 1:c0 + n + 1]), 0)
         sv.append(s)
     nb = sv[0].halo_bytes()
