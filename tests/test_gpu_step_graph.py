@@ -49,3 +49,14 @@ def test_graph_follows_state_time_and_source_changes():
     got = run("fp32_kahan", [70, 130, 65], u0, changes)
     assert got[2] == ref[2]
     assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1])
+
+
+def test_graph_follows_tiling_changes():
+    # a new strip length, then the default again, between graph replays: each change
+    # captures a new graph, and the results stay those of direct launches
+    u0 = inputs.smooth_state(32, 300, seed=5)
+    ref = run("fp32_kahan", [-70, -70, -70], u0)
+    changes = {1: lambda s: s.set_instance_tiling(0, 9), 2: lambda s: s.set_instance_tiling(0, 0)}
+    got = run("fp32_kahan", [70, 70, 70], u0, changes)
+    assert got[2] == ref[2]
+    assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1])
