@@ -17,6 +17,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import re
 import statistics
@@ -480,6 +481,55 @@ def adjoint_leg(peaks=None):
     return out
 
 
+def radiated_flux_leg(peaks=None, n_modes=8, n_steps=4000):
+    """The recoil diagnostic (teuk_radiated_flux): the modes m = 1..8 of one particle on a
+    circular orbit at r0 = 10 (2048 x 256 grid, a = 0.9, FP32-Kahan, the time step of
+    the m = 8 mode's rule shared by all) stepped 4000 steps in one batched context, then
+    the energy, momentum and Jz fluxes of all 4001 records at r* = 14, next to the
+    particle (r* = 12.8).  Timed with CUDA events on the context's stream around the call (it
+    allocates its scratch, runs the kernels, copies the [R][10] result back and
+    synchronizes), and on the host.  Bytes: the records read once (16 B per mode, row
+    and record) are the algorithmic minimum; the kernels read them twice (the chunk
+    totals, then the sums).  The sums are FP64 arithmetic (about 30 flops per mode, row
+    and record), which bounds the call on GB300 before its bytes do."""
+    import torch
+
+    from paper_1001_3631_gb300 import TeukSolver
+    ms = list(range(1, n_modes + 1))
+    dt = 0.5 * (math.pi / 256) / (n_modes + 2 + 2)    # dt_rule 1 of the largest |m|
+    p = dict(s=-2, a=0.9, rstar_min=-60.0, rstar_max=140.0, n_rstar=2048, n_theta=256,
+             rstar_ext=14.0, dt=dt, prec="fp32_kahan")
+    with TeukSolver([dict(p, m=m) for m in ms]) as s:
+        for k in range(len(ms)):
+            s.set_source(10.0, instance=k)
+        s.step(n_steps)
+        s.radiated_flux(0, 64)                     # warm-up (module load, allocator)
+        st = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        R = n_steps + 1
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e0.record(st)
+        out = s.radiated_flux(0, R)
+        e1.record(st)
+        torch.cuda.synchronize()
+        th = time.perf_counter() - t0
+        ms_ev = e0.elapsed_time(e1)
+        s.sync()
+    ent = len(ms) * p["n_theta"] * R
+    alg = 16.0 * ent / (ms_ev * 1e-3) / 1e9
+    hbm = (peaks or {}).get("hbm_gbs")
+    return {"workload": "%d modes x %d rows x %d records (2048x256 grid, FP32-Kahan records)"
+                        % (len(ms), p["n_theta"], R),
+            "ms": ms_ev, "host_ms": th * 1e3, "records_per_s": R / (ms_ev * 1e-3),
+            "entry_records_per_s": ent / (ms_ev * 1e-3),
+            "roofline": {"bound": "hbm", "achieved": alg, "peak": hbm, "unit": "GB/s",
+                         "frac": (alg / hbm) if hbm else None, "bytes_per_entry_record": 16,
+                         "kernel": "the whole call"},
+            "E_total": float(out[-1, 5]), "P_total": [float(x) for x in out[-1, 6:9]],
+            "Jz_total": float(out[-1, 9])}
+
+
 def cpu_baseline(cfg, budget_s=12.0):
     """The oracle (single-threaded FP64 C) on the same grid, per-step time from the
     difference of two run lengths (so its setup is excluded)."""
@@ -700,6 +750,7 @@ def summary(line):
         "adjoint_ckpt_gradient_over_forward": {p: g("adjoint", p, "gradient_ckpt_over_forward")
                                                for p in ("fp64", "fp32_kahan")},
         "adjoint_reverse_us_per_step": {p: g("adjoint", p, "reverse_us_per_step") for p in ("fp64", "fp32_kahan")},
+        "radiated_flux_ms": g("radiated_flux", "ms"),
         "cpu_baseline": g("cpu_baseline", "value"),
     }
 
@@ -830,6 +881,7 @@ def main():
         line["accuracy"] = accuracy(cfg, n_steps=args.accuracy_steps)
         line["e2e"] = e2e_path("fp32_kahan", cfg, S, max(2, K // 2), 1)
         line["adjoint"] = adjoint_leg({"hbm_gbs": measured_peaks()[0]})
+        line["radiated_flux"] = radiated_flux_leg({"hbm_gbs": measured_peaks()[0]})
         if not args.no_sweep:
             line["precision_sweep"] = precision_sweep()
         if not args.no_cpu_baseline:

@@ -231,6 +231,28 @@ teuk_status teuk_extract(teuk_ctx* ctx, int instance, double* out, double* out_s
 teuk_status teuk_mode_sum(teuk_ctx* ctx, const double* phi, int n_phi, int64_t first,
                           int64_t n_records, double* out);
 
+/* Energy, linear momentum and angular momentum about the spin axis carried off by the
+ * field of the context's instances, the modes m_i of one problem (as teuk_mode_sum, and
+ * no two with the same m): the recoil of Sec. 2.2 (the system's kick velocity is
+ * -P / M_total).  The paper prints no flux formula; these are Teukolsky and Press's
+ * (1974, Kinnersley tetrad), from the records at the extraction radius r, taken far
+ * from the source:
+ *   r psi_4 = sum_i W_i e^{i m_i phi~} (r / (r - i a cos theta))^4   (psi_4 = rho^4 Psi,
+ *             Psi = e^{i m phi~} r^3 Phi of Eq. 4; phi~ of Eq. 3 at r)
+ *   N = int r psi_4 dt,  H = int N dt  (trapezoid rule from the record `first`)
+ *   dE/dt = 1/(4 pi) oint |N|^2 dOmega,   dP/dt = 1/(4 pi) oint n |N|^2 dOmega,
+ *   dJz/dt = -1/(4 pi) Re oint conj(N) d_phi H dOmega,
+ * n = (sin th cos phi, sin th sin phi, cos th) in Boyer-Lindquist phi; theta by the
+ * midpoint rule of the waveform sum (weights sin theta_j dtheta), the azimuth exactly.
+ * Out (host): [n_records][10] FP64: dE/dt, dPx/dt, dPy/dt, dPz/dt, dJz/dt, E, Px, Py,
+ * Pz, Jz at the time levels first .. first + n_records - 1 (totals from `first`).
+ * In kernels: chunked time scans, each record's sums over modes and rows in a fixed
+ * order, a block per quantity for the totals.  Allocates and frees at most 128 MB of
+ * scan scratch plus 40 n_records ceil(n_theta / max(1, 256 / K)) + 80 n_records bytes
+ * of device memory (K instances, at most 256); synchronizes.  TEUK_EINVAL if the
+ * instances are not distinct modes of one problem or a record is not held. */
+teuk_status teuk_radiated_flux(teuk_ctx* ctx, int64_t first, int64_t n_records, double* out);
+
 /* Reverse-mode derivative of a waveform loss over the steps step0 .. step0+n-1 of
  * one instance (the transposed stencil of Eqs. 13-14, applied in kernels).
  *   grad_wave != NULL: host [n][n_theta][2] holding dL/dW for records step0+1 ..

@@ -265,23 +265,24 @@ def radiated_flux(ps, waves):
     # azimuth grid: |N|^2 times e^{+-i phi} holds harmonics up to (m_max - m_min + 1)
     L = 2 * (max(ms) - min(ms)) + 4
     ph = 2.0 * np.pi * np.arange(L) / L
-    Nf = np.zeros((nrec, nth, L), np.complex128)
-    dHf = np.zeros((nrec, nth, L), np.complex128)
-    for m, Ni, Hi in zip(ms, N, H):
-        e = np.exp(1j * m * (ph + shift))[None, None, :]
-        Nf += Ni[:, :, None] * e
-        dHf += 1j * m * Hi[:, :, None] * e
-    dA = (np.sin(th) * dth)[None, :, None] * (2.0 * np.pi / L)   # dOmega of each (j, l)
-    nx = (np.sin(th)[:, None] * np.cos(ph)[None, :])[None]
-    ny = (np.sin(th)[:, None] * np.sin(ph)[None, :])[None]
-    nz = np.cos(th)[None, :, None]
-    I2 = np.abs(Nf) ** 2
+    eph = [np.exp(1j * m * (ph + shift))[None, :] for m in ms]   # e^{i m phi~} on the grid
+    dA = (np.sin(th) * dth)[:, None] * (2.0 * np.pi / L)          # dOmega of each (j, l)
+    nx = np.sin(th)[:, None] * np.cos(ph)[None, :]
+    ny = np.sin(th)[:, None] * np.sin(ph)[None, :]
+    nz = np.cos(th)[:, None] * np.ones(L)[None, :]
     rates = np.zeros((nrec, 5))
-    rates[:, 0] = (I2 * dA).sum(axis=(1, 2)) / (4.0 * np.pi)
-    rates[:, 1] = (nx * I2 * dA).sum(axis=(1, 2)) / (4.0 * np.pi)
-    rates[:, 2] = (ny * I2 * dA).sum(axis=(1, 2)) / (4.0 * np.pi)
-    rates[:, 3] = (nz * I2 * dA).sum(axis=(1, 2)) / (4.0 * np.pi)
-    rates[:, 4] = -(np.real(np.conj(Nf) * dHf) * dA).sum(axis=(1, 2)) / (4.0 * np.pi)
+    for k in range(nrec):
+        Nf = np.zeros((nth, L), np.complex128)      # N(theta_j, phi_l) at record k
+        dHf = np.zeros((nth, L), np.complex128)     # d_phi H
+        for i, m in enumerate(ms):
+            Nf += N[i][k][:, None] * eph[i]
+            dHf += 1j * m * H[i][k][:, None] * eph[i]
+        I2 = np.abs(Nf) ** 2
+        rates[k, 0] = (I2 * dA).sum() / (4.0 * np.pi)
+        rates[k, 1] = (nx * I2 * dA).sum() / (4.0 * np.pi)
+        rates[k, 2] = (ny * I2 * dA).sum() / (4.0 * np.pi)
+        rates[k, 3] = (nz * I2 * dA).sum() / (4.0 * np.pi)
+        rates[k, 4] = -(np.real(np.conj(Nf) * dHf) * dA).sum() / (4.0 * np.pi)
     out = np.zeros((nrec, 10))
     out[:, :5] = rates
     for k in range(1, nrec):

@@ -51,6 +51,7 @@ _PROTOS = {
     "teuk_set_source": (_I, [_P, _I, ctypes.POINTER(teuk_orbit), _P, _L]),
     "teuk_set_trajectory": (_I, [_P, _I, ctypes.POINTER(teuk_orbit), _P, _L]),
     "teuk_mode_sum": (_I, [_P, _P, _I, _L, _L, _P]),
+    "teuk_radiated_flux": (_I, [_P, _L, _L, _P]),
     "teuk_set_state": (_I, [_P, _I, _P, _L]),
     "teuk_get_state": (_I, [_P, _I, _P]),
     "teuk_step_n": (_I, [_P, _L]),

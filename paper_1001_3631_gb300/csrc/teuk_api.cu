@@ -1260,14 +1260,13 @@ namespace {
 double r_of_rstar_host(double M, double a, double target);
 }  // namespace
 
-extern "C" teuk_status teuk_mode_sum(teuk_ctx* c, const double* phi, int n_phi, int64_t first,
-                                     int64_t n_records, double* out) {
-    if (!c) return TEUK_EINVAL;
-    if (n_phi < 1 || !phi || n_records < 0 || (n_records > 0 && !out))
-        TK_FAIL(c, TEUK_EINVAL, "need n_phi >= 1, phi, n_records >= 0 and an output buffer");
+// The instances as modes of one problem (the same s, M, a, n_theta, time step and
+// extraction radius), each holding the records first .. first + n_records - 1.
+static teuk_status modes_of_problem(teuk_ctx* c, int64_t first, int64_t n_records,
+                                    std::vector<ModeRing>& modes) {
     const Instance& I0 = c->inst[0];
     const int nth = I0.p.n_theta;
-    std::vector<ModeRing> modes(c->inst.size());
+    modes.resize(c->inst.size());
     for (size_t i = 0; i < c->inst.size(); ++i) {
         const Instance& I = c->inst[i];
         if (I.p.s != I0.p.s || I.p.M != I0.p.M || I.p.a != I0.p.a || I.p.n_theta != nth ||
@@ -1283,6 +1282,19 @@ extern "C" teuk_status teuk_mode_sum(teuk_ctx* c, const double* phi, int n_phi, 
                     (long long)(first + n_records));
         modes[i] = ModeRing{I.wave, I.wave_cap, I.p.m, 0};
     }
+    return TEUK_OK;
+}
+
+extern "C" teuk_status teuk_mode_sum(teuk_ctx* c, const double* phi, int n_phi, int64_t first,
+                                     int64_t n_records, double* out) {
+    if (!c) return TEUK_EINVAL;
+    if (n_phi < 1 || !phi || n_records < 0 || (n_records > 0 && !out))
+        TK_FAIL(c, TEUK_EINVAL, "need n_phi >= 1, phi, n_records >= 0 and an output buffer");
+    const Instance& I0 = c->inst[0];
+    const int nth = I0.p.n_theta;
+    std::vector<ModeRing> modes;
+    const teuk_status ms = modes_of_problem(c, first, n_records, modes);
+    if (ms != TEUK_OK) return ms;
     if (n_records == 0) return TEUK_OK;
     // Eq. (3): phi~ = phi + a/(r_+ - r_-) ln((r - r_+)/(r - r_-)) at the extraction radius;
     // Eq. (4): Psi = e^{i m phi~} r^3 Phi
@@ -1307,6 +1319,77 @@ extern "C" teuk_status teuk_mode_sum(teuk_ctx* c, const double* phi, int n_phi, 
     dfree(c, buf, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) TK_FAIL(c, TEUK_ECUDA, "mode sum: %s", cudaGetErrorString(e));
+    return TEUK_OK;
+}
+
+extern "C" teuk_status teuk_radiated_flux(teuk_ctx* c, int64_t first, int64_t n_records, double* out) {
+    if (!c) return TEUK_EINVAL;
+    if (n_records < 0 || (n_records > 0 && !out))
+        TK_FAIL(c, TEUK_EINVAL, "need n_records >= 0 and an output buffer");
+    std::vector<ModeRing> modes;
+    const teuk_status ms = modes_of_problem(c, first, n_records, modes);
+    if (ms != TEUK_OK) return ms;
+    const int K = (int)modes.size();
+    std::vector<int> partner(K, -1);
+    for (int i = 0; i < K; ++i)
+        for (int k = 0; k < K; ++k) {
+            if (k != i && modes[k].m == modes[i].m)
+                TK_FAIL(c, TEUK_EINVAL, "instances %d and %d are the same mode m = %d", i, k, modes[i].m);
+            if (modes[k].m == modes[i].m + 1) partner[i] = k;
+        }
+    if (n_records == 0) return TEUK_OK;
+    const Instance& I0 = c->inst[0];
+    const int nth = I0.p.n_theta;
+    const int64_t E = (int64_t)K * nth;
+    const double r_ext = r_of_rstar_host(I0.p.M, I0.p.a, I0.p.rstar_ext);
+    const double shift = I0.p.a / (I0.rp - I0.rm) * std::log((r_ext - I0.rp) / (r_ext - I0.rm));
+    // rows in groups of RB: a block of K RB <= 256 threads, whole warps
+    if (K > 256) TK_FAIL(c, TEUK_EINVAL, "radiated flux: at most 256 modes (got %d)", K);
+    const int RB = std::max(1, std::min(256 / K, nth));
+    const int n_rg = (nth + RB - 1) / RB;
+    // chunks of the time scans: about 155 648 (152 SMs x 1024) integrating threads, their
+    // starts and totals in at most 128 MB, at most 65535 chunks (the grid's y extent)
+    int64_t n_chunks = (152 * 1024 + E - 1) / E;
+    if (n_chunks * E * 64 > ((int64_t)128 << 20)) n_chunks = std::max<int64_t>(1, ((int64_t)128 << 20) / (E * 64));
+    n_chunks = std::min<int64_t>(std::min<int64_t>(n_chunks, n_records), 65535);
+    const int64_t Lc = (n_records + n_chunks - 1) / n_chunks;
+    n_chunks = (n_records + Lc - 1) / Lc;
+    if (Lc > INT32_MAX)
+        TK_FAIL(c, TEUK_EINVAL, "radiated flux: %lld records are too many", (long long)n_records);
+    auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+    const size_t b_modes = al(sizeof(ModeRing) * K), b_part = al(sizeof(int) * K);
+    const size_t b_chunk = al(sizeof(double2) * (size_t)n_chunks * E);
+    const size_t b_g = al(sizeof(FluxWeights) * (size_t)E), b_gp = al(sizeof(double2) * (size_t)E);
+    const size_t b_sums = al(sizeof(double) * 5 * (size_t)n_rg * (size_t)n_records);
+    const size_t b_out = sizeof(double) * 10 * (size_t)n_records;
+    char* buf = nullptr;
+    TK_CUDA(c, dmalloc(c, (void**)&buf, b_modes + b_part + 4 * b_chunk + b_g + b_gp + b_sums + b_out,
+                       c->stream));
+    char* q = buf;
+    auto take = [&](size_t b) { char* r = q; q += b; return r; };
+    ModeRing* d_modes = (ModeRing*)take(b_modes);
+    int* d_part = (int*)take(b_part);
+    FluxScratch fs;
+    fs.totN = (double2*)take(b_chunk);
+    fs.totH = (double2*)take(b_chunk);
+    fs.stN = (double2*)take(b_chunk);
+    fs.stH = (double2*)take(b_chunk);
+    fs.g = (FluxWeights*)take(b_g);
+    fs.gp = (double2*)take(b_gp);
+    fs.partner = d_part;
+    fs.part = (double*)take(b_sums);
+    fs.out = (double*)take(b_out);
+    cudaMemcpyAsync(d_modes, modes.data(), sizeof(ModeRing) * K, cudaMemcpyHostToDevice, c->stream);
+    cudaMemcpyAsync(d_part, partner.data(), sizeof(int) * K, cudaMemcpyHostToDevice, c->stream);
+    const FluxDev f{d_modes, K, nth, first, n_records, (int)Lc, (int)n_chunks, RB, n_rg,
+                    I0.dt, r_ext, I0.p.a, shift};
+    c->launches += launch_radiated_flux(c->stream, f, fs);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out, fs.out, b_out, cudaMemcpyDeviceToHost, c->stream);
+    dfree(c, buf, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) TK_FAIL(c, TEUK_ECUDA, "radiated flux: %s", cudaGetErrorString(e));
     return TEUK_OK;
 }
 

@@ -196,6 +196,16 @@ class TeukSolver:
                                         ptr(out)), self.ctx)
         return out[..., 0] + 1j * out[..., 1]
 
+    def radiated_flux(self, first, n_records):
+        """Energy, linear momentum and Jz carried off by the field of the instances (distinct
+        modes of one problem), from the records first .. first + n_records - 1: array
+        [n_records][10] = dE/dt, dPx/dt, dPy/dt, dPz/dt, dJz/dt, E, Px, Py, Pz, Jz (totals
+        from `first`; the recoil velocity is -P / M_total)."""
+        out = np.empty((int(n_records), 10))
+        check(_lib.load().teuk_radiated_flux(self.ctx, int(first), int(n_records), ptr(out)),
+              self.ctx)
+        return out
+
     def adjoint(self, n, step0=0, grad_wave=None, ckpt_every=100, instance=0):
         """Returns (grad_amps [n], grad_r0, loss).  ckpt_every (built-in loss only): K > 0
         recomputes each K-step segment's records from a state checkpoint in the reverse
