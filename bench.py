@@ -535,8 +535,8 @@ def radiated_flux_leg(peaks=None, n_modes=8, n_steps=4000):
                          "frac": tflops / FP64_PEAK_TFLOPS, "flops_per_entry_record": FLUX_FLOPS_PER_ENTRY,
                          "peak_note": "FP64 nominal (152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz)",
                          "pipe_note": "about 39 FP64 instructions per entry and record, mostly "
-                                      "adds and multiplies: the scan and sum kernels issue at "
-                                      "~86 % of the FP64 pipe (ncu launch list)",
+                                      "adds and multiplies; ncu: the sums kernel keeps the FP64 "
+                                      "pipe 86 % busy",
                          "record_bytes_gbs": gbs, "hbm_frac": (gbs / hbm) if hbm else None,
                          "kernel": "the whole call (allocation, four kernels, copy back)"},
             "E_total": float(out[-1, 5]), "P_total": [float(x) for x in out[-1, 6:9]],
