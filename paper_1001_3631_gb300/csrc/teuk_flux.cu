@@ -16,15 +16,16 @@
 // The factor F_ij = (r / (r - i a cos theta_j))^4 e^{i m_i shift} is constant in time, so
 // the scans integrate the records themselves (N = F Nw, H = F Hw with Nw = int W dt,
 // Hw = int Nw dt) and F enters the sums once per entry: w_j |F|^2 for E, Pz and Jz,
-// w_j sin th_j F_i conj(F_i') for the x-y momentum (one pass before the scans).
+// w_j sin th_j F_i conj(F_i') for the x-y momentum (formed with the chunk starts).
 // The time integrals are scans along the records.  They run in chunks of Lc records:
 // one pass integrates every chunk from zero (its totals), a second carries the totals
 // from chunk to chunk (N and H at each chunk's start; H gains n dt N_start over a
 // chunk of n steps), a third integrates every chunk again from its start, a block per
-// (chunk, group of rows of every mode), and reduces each record's terms over the
-// block (fixed order: a shuffle tree, then the warps in order); the last adds the
-// groups' sums of each record in order and scans the rates into the totals, one block
-// per quantity.  All arithmetic is FP64.
+// (chunk, group of rows of every mode), and sums each record's terms over the block
+// in a fixed order (each term by one warp: per lane over the warps, then a shuffle
+// tree); the last adds the groups' sums of each record in order and scans the rates
+// into the totals, one block per quantity.  All arithmetic is FP64, and the results do
+// not depend on the scheduling.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
