@@ -396,13 +396,15 @@ cudaStream_t capture_stream(teuk_ctx* c) {
 // Steps per replayed graph (even, so that the state returns to the buffer it started in).
 constexpr int64_t kStepGraph = 64;
 
-// The graph of kStepGraph per-step launches for the instance's current buffer parity and
-// configuration, captured on first use and again whenever the configuration changed.
-// The graph is captured on the context's private stream and replayed on its stream (any
-// stream, the legacy default one included).  Returns nullptr while the caller is
-// capturing the context's stream, or if capture failed; the steps are then launched
-// directly.
-cudaGraphExec_t step_graph(teuk_ctx* c, Instance& I, int strip) {
+// The graph of kStepGraph per-step launches of the descriptor dv (the instance's own,
+// or one whose buffers or records are elsewhere) starting in buffer p, captured on first
+// use and again whenever the descriptor or configuration changed (one cached graph per
+// starting buffer).  The graph is captured on the context's private stream and replayed
+// on its stream (any stream, the legacy default one included).  Returns nullptr while
+// the caller is capturing the context's stream, or if capture failed; the steps are
+// then launched directly.
+cudaGraphExec_t step_graph_of(teuk_ctx* c, Instance& I, const InstDev& dv, int p, int strip,
+                              const int* part) {
     if (I.sg_failed) return nullptr;
     cudaStreamCaptureStatus ucs = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(c->stream, &ucs) != cudaSuccess || ucs != cudaStreamCaptureStatusNone) {
@@ -418,12 +420,10 @@ cudaGraphExec_t step_graph(teuk_ctx* c, Instance& I, int strip) {
     // only the members)
     StepGraphKey key;
     std::memset(&key, 0, sizeof key);
-    const InstDev cur_d = dev_of(c, I);
-    std::memcpy(&key.d, &cur_d, sizeof cur_d);
+    std::memcpy(&key.d, &dv, sizeof dv);
     key.d.step_base = I.d_step;
-    key.part = I.part_strip == strip ? I.d_part : nullptr;
+    key.part = part;
     key.strip = strip;
-    const int p = I.cur;
     if (I.sg_exec[p] && std::memcmp(&key, &I.sg_key[p], sizeof key) == 0) return I.sg_exec[p];
     if (I.sg_exec[p]) cudaGraphExecDestroy(I.sg_exec[p]);
     I.sg_exec[p] = nullptr;
@@ -449,6 +449,45 @@ cudaGraphExec_t step_graph(teuk_ctx* c, Instance& I, int strip) {
     I.sg_exec[p] = e;
     std::memcpy(&I.sg_key[p], &key, sizeof key);
     return e;
+}
+
+cudaGraphExec_t step_graph(teuk_ctx* c, Instance& I, int strip) {
+    return step_graph_of(c, I, dev_of(c, I), I.cur, strip, I.part_strip == strip ? I.d_part : nullptr);
+}
+
+// Run count steps of the descriptor dv from buffer cur at time level `level` on stream st:
+// whole graphs of kStepGraph steps (the device step base set to `level` first), then
+// the rest one launch at a time.  Returns the buffer holding the result.
+int run_steps(teuk_ctx* c, Instance& I, const InstDev& dv, cudaStream_t st, int cur, int64_t level,
+              int64_t count, int strip) {
+    const int* part = I.part_strip == strip ? I.d_part : nullptr;
+    int64_t k = 0;
+    cudaGraphExec_t e = (st == c->stream && count >= kStepGraph)
+                            ? step_graph_of(c, I, dv, cur, strip, part) : nullptr;
+    if (e && I.graph_base != level) {
+        I.h_step = level;
+        if (cudaMemcpyAsync(I.d_step, &I.h_step, sizeof(int64_t), cudaMemcpyHostToDevice, st) != cudaSuccess) {
+            cudaGetLastError();
+            e = nullptr;
+        } else {
+            I.graph_base = level;
+        }
+    }
+    if (e)
+        for (; k + kStepGraph <= count; k += kStepGraph) {
+            if (cudaGraphLaunch(e, st) != cudaSuccess) {
+                cudaGetLastError();
+                break;
+            }
+            c->launches += kStepGraph + 1;
+            I.graph_base += kStepGraph;   // advanced by the graph's last node
+        }
+    for (; k < count; ++k) {   // (kStepGraph is even: the graphs leave the buffer unchanged)
+        launch_step(st, dv, level + k, cur, strip, part);
+        c->launches++;
+        cur = 1 - cur;
+    }
+    return cur;
 }
 
 void free_instance(const teuk_ctx* c, Instance& I) {
@@ -1946,12 +1985,7 @@ extern "C" teuk_status teuk_adjoint_n(teuk_ctx* c, int instance, int64_t step0, 
     // run `count` steps on the buffers of dv (which start in buffer cur), recording
     // levels into the ring of dv; returns the buffer holding the result.
     auto forward = [&](InstDev dv, int cur, int64_t level, int64_t count, int strip) {
-        const int* part = I.part_strip == strip ? I.d_part : nullptr;
-        for (int64_t k = 0; k < count; ++k) {
-            launch_step(s, dv, level + k, cur, strip, part);
-            c->launches++;
-            cur = 1 - cur;
-        }
+        cur = run_steps(c, I, dv, s, cur, level, count, strip);
         launch_extract(s, dv, level + count, cur);
         c->launches++;
         return cur;

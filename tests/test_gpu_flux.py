@@ -1,8 +1,9 @@
 """Radiated energy, momentum and Jz fluxes (the recoil of Sec. 2.2) on the GPU against the
 oracle: the modes of one particle on a circular orbit run as instances of one context,
-their fluxes from the records (chunked time scans, a block per record) compared with the
-oracle's plain record-by-record integrals, end to end (oracle run + oracle fluxes) and
-on the same records; ragged chunks, several record batches, and the argument errors."""
+their fluxes from the records (chunked time scans, per-record sums over a block per chunk
+and group of rows) compared with the oracle's plain record-by-record integrals, end to
+end (oracle run + oracle fluxes) and on the same records; ragged chunks, many records
+and chunks, and the argument errors."""
 import numpy as np
 import pytest
 
@@ -70,9 +71,9 @@ def test_flux_on_fp32_kahan_records_same_records(orc):
     _close(g, orc.radiated_flux(ps, recs), 1e-11)
 
 
-def test_flux_many_records_several_batches(orc):
-    """8 modes x 128 rows and 12 001 records: ~300 chunks of 40 records, their N and H
-    written in two batches."""
+def test_flux_many_records_and_chunks(orc):
+    """8 modes x 128 rows and 12 001 records: 152 chunks of 79 records (the chain of
+    chunk starts longer than its eight-load batches), 4 row groups of 32."""
     ms = list(range(-2, 6))
     base = dict(s=-2, a=0.6, rstar_min=-10.0, rstar_max=30.0, n_rstar=48, n_theta=128,
                 rstar_ext=9.0, dt=0.001, wave_capacity=16384)
